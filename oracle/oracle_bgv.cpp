@@ -1,0 +1,828 @@
+// Plain CPU reference: number theory, transforms, slots, keys, encryption and
+// the BGV operations. TEST INFRASTRUCTURE ONLY (see oracle.hpp).
+#include "oracle.hpp"
+
+#include <algorithm>
+#include <cmath>
+
+namespace orc {
+
+// ================================================================ arithmetic
+u64 mulmod(u64 a, u64 b, u64 m) { return (u64)((u128)a * b % m); }
+u64 addmod(u64 a, u64 b, u64 m) { return (u64)(((u128)a + b) % m); }
+u64 submod(u64 a, u64 b, u64 m) { return (u64)(((u128)a + m - b) % m); }
+
+u64 powmod(u64 a, u64 e, u64 m) {
+  u64 r = 1 % m;
+  a %= m;
+  while (e) {
+    if (e & 1) r = mulmod(r, a, m);
+    a = mulmod(a, a, m);
+    e >>= 1;
+  }
+  return r;
+}
+
+u64 invmod(u64 a, u64 m) {
+  // extended Euclid over signed 128-bit integers
+  __int128 t = 0, nt = 1, r = m, nr = a % m;
+  while (nr != 0) {
+    __int128 q = r / nr;
+    __int128 tmp = t - q * nt; t = nt; nt = tmp;
+    tmp = r - q * nr; r = nr; nr = tmp;
+  }
+  if (r != 1) throw std::runtime_error("invmod: not invertible");
+  if (t < 0) t += m;
+  return (u64)t;
+}
+
+u64 lift(i64 c, u64 m) {
+  __int128 v = (__int128)c % (__int128)m;
+  if (v < 0) v += m;
+  return (u64)v;
+}
+
+i64 centre(u64 v, u64 m) {
+  v %= m;
+  return v > m / 2 ? (i64)v - (i64)m : (i64)v;
+}
+
+bool is_prime(u64 n) {
+  if (n < 2) return false;
+  static const u64 small[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+  for (u64 s : small) {
+    if (n % s == 0) return n == s;
+  }
+  u64 d = n - 1;
+  int s = 0;
+  while ((d & 1) == 0) { d >>= 1; ++s; }
+  for (u64 a : small) {
+    u64 x = powmod(a, d, n);
+    if (x == 1 || x == n - 1) continue;
+    bool comp = true;
+    for (int i = 1; i < s; ++i) {
+      x = mulmod(x, x, n);
+      if (x == n - 1) { comp = false; break; }
+    }
+    if (comp) return false;
+  }
+  return true;
+}
+
+int bitrev(int x, int logn) {
+  int r = 0;
+  for (int i = 0; i < logn; ++i) { r = (r << 1) | (x & 1); x >>= 1; }
+  return r;
+}
+
+// =============================================================== big integer
+Big Big::from(u64 x) { Big b; b.w.push_back(x); b.trim(); return b; }
+void Big::trim() { while (!w.empty() && w.back() == 0) w.pop_back(); }
+bool Big::is_zero() const { return w.empty(); }
+
+Big big_mul_u64(const Big& a, u64 b) {
+  Big r;
+  u128 carry = 0;
+  for (u64 x : a.w) {
+    u128 cur = (u128)x * b + carry;
+    r.w.push_back((u64)cur);
+    carry = cur >> 64;
+  }
+  if (carry) r.w.push_back((u64)carry);
+  r.trim();
+  return r;
+}
+
+Big big_add(const Big& a, const Big& b) {
+  Big r;
+  size_t n = std::max(a.w.size(), b.w.size());
+  u128 carry = 0;
+  for (size_t i = 0; i < n; ++i) {
+    u128 cur = carry;
+    if (i < a.w.size()) cur += a.w[i];
+    if (i < b.w.size()) cur += b.w[i];
+    r.w.push_back((u64)cur);
+    carry = cur >> 64;
+  }
+  if (carry) r.w.push_back((u64)carry);
+  r.trim();
+  return r;
+}
+
+int big_cmp(const Big& a, const Big& b) {
+  if (a.w.size() != b.w.size()) return a.w.size() < b.w.size() ? -1 : 1;
+  for (size_t i = a.w.size(); i-- > 0;) {
+    if (a.w[i] != b.w[i]) return a.w[i] < b.w[i] ? -1 : 1;
+  }
+  return 0;
+}
+
+Big big_sub(const Big& a, const Big& b) {
+  if (big_cmp(a, b) < 0) throw std::runtime_error("big_sub: negative");
+  Big r;
+  u64 borrow = 0;
+  for (size_t i = 0; i < a.w.size(); ++i) {
+    u64 bi = i < b.w.size() ? b.w[i] : 0;
+    u128 sub = (u128)bi + borrow;
+    u64 ai = a.w[i];
+    if ((u128)ai >= sub) { r.w.push_back((u64)(ai - sub)); borrow = 0; }
+    else { r.w.push_back((u64)(((u128)1 << 64) + ai - sub)); borrow = 1; }
+  }
+  r.trim();
+  return r;
+}
+
+u64 big_mod_u64(const Big& a, u64 m) {
+  u128 rem = 0;
+  for (size_t i = a.w.size(); i-- > 0;) rem = ((rem << 64) | a.w[i]) % m;
+  return (u64)rem;
+}
+
+Big big_shr1(const Big& a) {
+  Big r;
+  r.w.resize(a.w.size());
+  for (size_t i = 0; i < a.w.size(); ++i) {
+    u64 hi = (i + 1 < a.w.size()) ? a.w[i + 1] : 0;
+    r.w[i] = (a.w[i] >> 1) | (hi << 63);
+  }
+  r.trim();
+  return r;
+}
+
+double big_log2(const Big& a) {
+  if (a.is_zero()) return -1e300;
+  size_t n = a.w.size();
+  double top = (double)a.w[n - 1];
+  if (n >= 2) top += (double)a.w[n - 2] / 18446744073709551616.0;
+  return std::log2(top) + 64.0 * (double)(n - 1);
+}
+
+// ==================================================================== philox
+void philox4x32_10(const u32 ctr[4], const u32 key[2], u32 out[4]) {
+  const u32 M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const u32 W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  u32 c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  u32 k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    uint64_t p0 = (uint64_t)M0 * c0;
+    uint64_t p1 = (uint64_t)M1 * c2;
+    u32 hi0 = (u32)(p0 >> 32), lo0 = (u32)p0;
+    u32 hi1 = (u32)(p1 >> 32), lo1 = (u32)p1;
+    u32 n0 = hi1 ^ c1 ^ k0;
+    u32 n1 = lo1;
+    u32 n2 = hi0 ^ c3 ^ k1;
+    u32 n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += W0; k1 += W1;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static void draw(const Context& C, u32 a, u32 b, u32 c, u32 d, u32 out[4]) {
+  u32 ctr[4] = {a, b, c, d};
+  u32 key[2] = {(u32)(C.P.seed & 0xffffffffu), (u32)(C.P.seed >> 32)};
+  philox4x32_10(ctr, key, out);
+}
+
+// 128 bits of one Philox block, reduced modulo q.
+static u64 sample_uniform(const Context& C, u32 n, u32 limb, u32 id, u32 tag, u64 q) {
+  u32 x[4];
+  draw(C, n, limb, id, tag, x);
+  u64 lo = ((u64)x[1] << 32) | x[0];
+  u64 hi = ((u64)x[3] << 32) | x[2];
+  u128 v = ((u128)hi << 64) | lo;
+  return (u64)(v % q);
+}
+
+// Centred binomial with eta = 21: popcount of 21 bits minus popcount of 21 bits.
+static i64 sample_cbd(const Context& C, u32 n, u32 id, u32 tag) {
+  u32 x[4];
+  draw(C, n, 0, id, tag, x);
+  return (i64)__builtin_popcount(x[0] & 0x1FFFFFu) - (i64)__builtin_popcount(x[1] & 0x1FFFFFu);
+}
+
+// ============================================================ construction
+std::vector<u64> gen_primes(int bits, u64 M, int count) {
+  std::vector<u64> out;
+  u64 top = (bits >= 64) ? ~0ULL : ((1ULL << bits) - 2);
+  u64 k = top / M;
+  u64 low = 1ULL << (bits - 1);
+  while ((int)out.size() < count) {
+    if (k == 0) throw std::runtime_error("gen_primes: ran out of candidates");
+    u64 q = k * M + 1;
+    if (q <= low) throw std::runtime_error("gen_primes: not enough primes of this width");
+    if (is_prime(q)) out.push_back(q);
+    --k;
+  }
+  return out;
+}
+
+u64 find_psi(u64 q, int N) {
+  u64 c = 0;
+  for (u64 x = 2;; ++x) {
+    c = powmod(x, (q - 1) / (2 * (u64)N), q);
+    if (powmod(c, (u64)N, q) == q - 1) break;
+  }
+  // The primitive 2N-th roots are exactly the odd powers of c; take the smallest.
+  u64 best = c, w = c, c2 = mulmod(c, c, q);
+  for (int j = 1; j < N; ++j) {
+    w = mulmod(w, c2, q);
+    if (w < best) best = w;
+  }
+  return best;
+}
+
+static u64 ipow(u64 b, int e) { u64 r = 1; while (e-- > 0) r *= b; return r; }
+
+Context make_context(const Params& P0) {
+  Context C;
+  C.P = P0;
+  Params& P = C.P;
+  if (P.N != (1 << P.logN)) throw std::runtime_error("N must be 2^logN");
+  if (P.nmax == 0) P.nmax = P.N;
+  if (P.nmax < P.N) throw std::runtime_error("nmax < N");
+  C.t = ipow((u64)P.p, P.r);
+  // primes q = 1 mod lcm(2*nmax, p^r); p is odd, so the lcm is the product
+  u64 M = 2 * (u64)P.nmax * C.t;
+  C.primes = gen_primes(P.bits, M, P.L + P.alpha);
+  for (u64 q : C.primes) C.psi.push_back(find_psi(q, P.N));
+  // slots: X^N + 1 = prod_j (X^d - zeta_j) over Z_{p^r} when 2*slots | p - 1
+  int d = 1;
+  {
+    u64 x = (u64)P.p % (2 * (u64)P.N);
+    while (x != 1) { x = x * (u64)P.p % (2 * (u64)P.N); ++d; }
+  }
+  C.d = d;
+  C.slots = P.N / d;
+  if (((u64)P.p - 1) % (2 * (u64)C.slots) != 0)
+    throw std::runtime_error("plaintext prime does not split X^N+1 into linear slot factors");
+  // omega: smallest x mod p with x^slots = -1, Hensel-lifted to p^r
+  u64 w0 = 0;
+  for (u64 x = 2; x < (u64)P.p; ++x) {
+    if (powmod(x, (u64)C.slots, (u64)P.p) == (u64)P.p - 1) { w0 = x; break; }
+  }
+  if (!w0) throw std::runtime_error("no slot root");
+  u64 w = w0;
+  for (int it = 0; it < P.r + 1; ++it) {
+    u64 f = addmod(powmod(w, (u64)C.slots, C.t), 1, C.t);
+    u64 fp = mulmod((u64)C.slots % C.t, powmod(w, (u64)C.slots - 1, C.t), C.t);
+    w = submod(w, mulmod(f, invmod(fp, C.t), C.t), C.t);
+  }
+  if (powmod(w, (u64)C.slots, C.t) != C.t - 1) throw std::runtime_error("Hensel lift failed");
+  C.omega = w;
+  C.slot_exp.resize(C.slots);
+  int two_l = 2 * C.slots;
+  if (C.slots == 1) {
+    C.slot_exp[0] = 1;
+  } else {
+    int half = C.slots / 2;
+    int g = 1;
+    for (int j = 0; j < half; ++j) {
+      C.slot_exp[j] = g;
+      C.slot_exp[j + half] = (two_l - g) % two_l;
+      g = (g * 5) % two_l;
+    }
+  }
+  return C;
+}
+
+// ================================================================= transform
+// Negacyclic transform, written as the definition: twist by psi^i, then the
+// textbook iterative radix-2 cyclic transform with omega = psi^2 (CLRS
+// "iterative-FFT"), giving A[k] = a(psi^(2k+1)). The stored evaluation form is
+// that vector in bit-reversed order: slot j holds a(psi^(2*bitrev(j)+1)).
+static void cyclic_ntt(std::vector<u64>& A, u64 omega, u64 q, int logN) {
+  int N = 1 << logN;
+  std::vector<u64> B(N);
+  for (int i = 0; i < N; ++i) B[bitrev(i, logN)] = A[i];
+  for (int s = 1; s <= logN; ++s) {
+    int m = 1 << s;
+    u64 wm = powmod(omega, (u64)(N / m), q);
+    for (int k = 0; k < N; k += m) {
+      u64 w = 1;
+      for (int j = 0; j < m / 2; ++j) {
+        u64 t = mulmod(w, B[k + j + m / 2], q);
+        u64 u = B[k + j];
+        B[k + j] = addmod(u, t, q);
+        B[k + j + m / 2] = submod(u, t, q);
+        w = mulmod(w, wm, q);
+      }
+    }
+  }
+  A = B;
+}
+
+void ntt_fwd(const Context& C, int pi, Poly& a) {
+  int N = C.P.N, logN = C.P.logN;
+  u64 q = C.primes[pi], psi = C.psi[pi];
+  std::vector<u64> b(N);
+  u64 pw = 1;
+  for (int i = 0; i < N; ++i) { b[i] = mulmod(a[i], pw, q); pw = mulmod(pw, psi, q); }
+  cyclic_ntt(b, mulmod(psi, psi, q), q, logN);
+  for (int j = 0; j < N; ++j) a[j] = b[bitrev(j, logN)];
+}
+
+void ntt_inv(const Context& C, int pi, Poly& a) {
+  int N = C.P.N, logN = C.P.logN;
+  u64 q = C.primes[pi], psi = C.psi[pi];
+  std::vector<u64> A(N);
+  for (int k = 0; k < N; ++k) A[k] = a[bitrev(k, logN)];
+  u64 psi_inv = invmod(psi, q);
+  cyclic_ntt(A, mulmod(psi_inv, psi_inv, q), q, logN);
+  u64 n_inv = invmod((u64)N, q);
+  u64 pw = 1;
+  for (int i = 0; i < N; ++i) {
+    a[i] = mulmod(mulmod(A[i], n_inv, q), pw, q);
+    pw = mulmod(pw, psi_inv, q);
+  }
+}
+
+Poly automorph_coeff(const Poly& a, int g, u64 q) {
+  int N = (int)a.size();
+  Poly out(N, 0);
+  for (int i = 0; i < N; ++i) {
+    long e = ((long)g * i) % (2L * N);
+    if (e < N) out[e] = a[i];
+    else out[e - N] = (q - a[i]) % q;
+  }
+  return out;
+}
+
+// ===================================================================== slots
+std::vector<u64> encode(const Context& C, int t_exp, const std::vector<u64>& v) {
+  u64 t = ipow((u64)C.P.p, t_exp);
+  if ((int)v.size() != C.slots) throw std::runtime_error("encode: wrong slot count");
+  u64 w = C.omega % t;
+  u64 inv_l = invmod((u64)C.slots % t, t);
+  std::vector<u64> m(C.P.N, 0);
+  int two_l = 2 * C.slots;
+  for (int k = 0; k < C.slots; ++k) {
+    u64 acc = 0;
+    for (int j = 0; j < C.slots; ++j) {
+      // zeta_j^(-k) = omega^(-e_j k)
+      long e = ((long)(two_l - C.slot_exp[j]) * k) % two_l;
+      acc = addmod(acc, mulmod(v[j] % t, powmod(w, (u64)e, t), t), t);
+    }
+    m[(size_t)k * C.d] = mulmod(acc, inv_l, t);
+  }
+  return m;
+}
+
+std::vector<u64> decode(const Context& C, int t_exp, const std::vector<u64>& coeffs) {
+  u64 t = ipow((u64)C.P.p, t_exp);
+  u64 w = C.omega % t;
+  int two_l = 2 * C.slots;
+  std::vector<u64> v(C.slots, 0);
+  for (int j = 0; j < C.slots; ++j) {
+    u64 acc = 0;
+    for (int k = 0; k < C.slots; ++k) {
+      long e = ((long)C.slot_exp[j] * k) % two_l;
+      acc = addmod(acc, mulmod(coeffs[(size_t)k * C.d] % t, powmod(w, (u64)e, t), t), t);
+    }
+    v[j] = acc;
+  }
+  return v;
+}
+
+// ====================================================================== keys
+std::vector<i64> sample_secret(const Context& C) {
+  int N = C.P.N;
+  std::vector<int> idx(N);
+  for (int i = 0; i < N; ++i) idx[i] = i;
+  std::vector<i64> s(N, 0);
+  for (int i = 0; i < C.P.h; ++i) {
+    u32 x[4];
+    draw(C, (u32)i, 0, 0, TAG_SK, x);
+    u64 r64 = ((u64)x[1] << 32) | x[0];
+    int j = i + (int)(r64 % (u64)(N - i));
+    std::swap(idx[i], idx[j]);
+    s[idx[i]] = (x[2] & 1) ? -1 : 1;
+  }
+  return s;
+}
+
+static Poly to_limb(const Context& C, const std::vector<i64>& v, int pi) {
+  Poly a(C.P.N);
+  for (int i = 0; i < C.P.N; ++i) a[i] = lift(v[i], C.primes[pi]);
+  return a;
+}
+
+KSKey make_ksk(const Context& C, const std::vector<Poly>& sp_hat, u32 key_id) {
+  const Params& P = C.P;
+  int nl = P.L + P.alpha;
+  int dnum = (P.L + P.alpha - 1) / P.alpha;
+  // P = product of special primes, needed modulo each data prime
+  KSKey K;
+  K.b.resize(dnum);
+  K.a.resize(dnum);
+  for (int j = 0; j < dnum; ++j) {
+    u32 id = key_id * 256u + (u32)j;
+    std::vector<i64> e(P.N);
+    for (int n = 0; n < P.N; ++n) e[n] = sample_cbd(C, (u32)n, id, TAG_KSK_E);
+    K.b[j].resize(nl);
+    K.a[j].resize(nl);
+    for (int i = 0; i < nl; ++i) {
+      u64 q = C.primes[i];
+      Poly a(P.N);
+      for (int n = 0; n < P.N; ++n) a[n] = sample_uniform(C, (u32)n, (u32)i, id, TAG_KSK_A, q);
+      Poly eh = to_limb(C, e, i);
+      ntt_fwd(C, i, eh);
+      u64 Pmod = 1;
+      for (int k = 0; k < P.alpha; ++k) Pmod = mulmod(Pmod, C.primes[P.L + k] % q, q);
+      bool in_digit = (i < P.L) && (i / P.alpha == j);
+      Poly b(P.N);
+      for (int n = 0; n < P.N; ++n) {
+        u64 v = submod(mulmod(C.t % q, eh[n], q), mulmod(a[n], C.sk_hat[i][n], q), q);
+        if (in_digit) v = addmod(v, mulmod(Pmod, sp_hat[i][n], q), q);
+        b[n] = v;
+      }
+      K.b[j][i] = b;
+      K.a[j][i] = a;
+    }
+  }
+  return K;
+}
+
+void keygen(Context& C, const std::vector<int>& galois) {
+  const Params& P = C.P;
+  int nl = P.L + P.alpha;
+  C.sk = sample_secret(C);
+  C.sk_hat.resize(nl);
+  for (int i = 0; i < nl; ++i) {
+    C.sk_hat[i] = to_limb(C, C.sk, i);
+    ntt_fwd(C, i, C.sk_hat[i]);
+  }
+  // relinearisation key: s' = s^2
+  std::vector<Poly> s2(nl);
+  for (int i = 0; i < nl; ++i) {
+    s2[i].resize(P.N);
+    for (int n = 0; n < P.N; ++n) s2[i][n] = mulmod(C.sk_hat[i][n], C.sk_hat[i][n], C.primes[i]);
+  }
+  C.rlk = make_ksk(C, s2, 0);
+  C.gk.clear();
+  for (int g : galois) {
+    std::vector<Poly> sg(nl);
+    for (int i = 0; i < nl; ++i) {
+      sg[i] = automorph_coeff(to_limb(C, C.sk, i), g, C.primes[i]);
+      ntt_fwd(C, i, sg[i]);
+    }
+    C.gk[g] = make_ksk(C, sg, (u32)g);
+  }
+  C.have_keys = true;
+}
+
+// ======================================================== encrypt / decrypt
+Ct encrypt(const Context& C, const std::vector<u64>& m, u32 nonce, int t_exp) {
+  const Params& P = C.P;
+  if (!C.have_keys) throw std::runtime_error("encrypt: no keys");
+  u64 t = ipow((u64)P.p, t_exp);
+  Ct ct;
+  ct.ncomp = 2;
+  ct.level = P.L;
+  ct.t_exp = t_exp;
+  ct.c.assign(2, std::vector<Poly>(P.L));
+  std::vector<i64> e(P.N);
+  for (int n = 0; n < P.N; ++n) e[n] = sample_cbd(C, (u32)n, nonce, TAG_ENC_E);
+  for (int i = 0; i < P.L; ++i) {
+    u64 q = C.primes[i];
+    Poly a(P.N), me(P.N);
+    for (int n = 0; n < P.N; ++n) a[n] = sample_uniform(C, (u32)n, (u32)i, nonce, TAG_ENC_A, q);
+    for (int n = 0; n < P.N; ++n)
+      me[n] = addmod(m[n] % t % q, mulmod(t % q, lift(e[n], q), q), q);
+    ntt_fwd(C, i, me);
+    Poly c0(P.N);
+    for (int n = 0; n < P.N; ++n) c0[n] = submod(me[n], mulmod(a[n], C.sk_hat[i][n], q), q);
+    ct.c[0][i] = c0;
+    ct.c[1][i] = a;
+  }
+  return ct;
+}
+
+// v = c0 + c1 s (+ c2 s^2) as the centred integer representative modulo Q_level
+static std::vector<std::pair<bool, Big>> decrypt_raw(const Context& C, const Ct& ct) {
+  const Params& P = C.P;
+  int l = ct.level;
+  std::vector<Poly> v(l);
+  for (int i = 0; i < l; ++i) {
+    u64 q = C.primes[i];
+    Poly x(P.N);
+    for (int n = 0; n < P.N; ++n) {
+      u64 s = C.sk_hat[i][n];
+      u64 acc = ct.c[0][i][n];
+      acc = addmod(acc, mulmod(ct.c[1][i][n], s, q), q);
+      if (ct.ncomp == 3) acc = addmod(acc, mulmod(ct.c[2][i][n], mulmod(s, s, q), q), q);
+      x[n] = acc;
+    }
+    ntt_inv(C, i, x);
+    v[i] = x;
+  }
+  // CRT: V = sum_i [v_i * (Q/q_i)^{-1}]_{q_i} * (Q/q_i) mod Q
+  Big Q = Big::from(1);
+  for (int i = 0; i < l; ++i) Q = big_mul_u64(Q, C.primes[i]);
+  std::vector<Big> Qhat(l);
+  std::vector<u64> Qhat_inv(l);
+  for (int i = 0; i < l; ++i) {
+    Big h = Big::from(1);
+    for (int k = 0; k < l; ++k) if (k != i) h = big_mul_u64(h, C.primes[k]);
+    Qhat[i] = h;
+    Qhat_inv[i] = invmod(big_mod_u64(h, C.primes[i]), C.primes[i]);
+  }
+  Big half = big_shr1(Q);
+  std::vector<std::pair<bool, Big>> out(P.N);
+  for (int n = 0; n < P.N; ++n) {
+    Big V;
+    for (int i = 0; i < l; ++i) {
+      u64 y = mulmod(v[i][n], Qhat_inv[i], C.primes[i]);
+      V = big_add(V, big_mul_u64(Qhat[i], y));
+    }
+    while (big_cmp(V, Q) >= 0) V = big_sub(V, Q);
+    if (big_cmp(V, half) > 0) out[n] = {true, big_sub(Q, V)};  // negative: -(Q - V)
+    else out[n] = {false, V};
+  }
+  return out;
+}
+
+std::vector<u64> decrypt(const Context& C, const Ct& ct) {
+  u64 t = ipow((u64)C.P.p, ct.t_exp);
+  auto raw = decrypt_raw(C, ct);
+  std::vector<u64> m(C.P.N);
+  for (int n = 0; n < C.P.N; ++n) {
+    u64 r = big_mod_u64(raw[n].second, t);
+    m[n] = raw[n].first ? (t - r) % t : r;
+  }
+  return m;
+}
+
+double noise_budget(const Context& C, const Ct& ct) {
+  auto raw = decrypt_raw(C, ct);
+  double mx = 0;
+  for (auto& x : raw) mx = std::max(mx, big_log2(x.second));
+  double logQ = 0;
+  for (int i = 0; i < ct.level; ++i) logQ += std::log2((double)C.primes[i]);
+  return logQ - 1.0 - mx;
+}
+
+// ==================================================================== BGV ops
+static void need_same(const Ct& a, const Ct& b) {
+  if (a.level != b.level) throw std::runtime_error("level mismatch");
+  if (a.t_exp != b.t_exp) throw std::runtime_error("plaintext modulus mismatch");
+}
+
+static u64 cur_t(const Context& C, const Ct& a) { return ipow((u64)C.P.p, a.t_exp); }
+
+Ct add(const Context& C, const Ct& a, const Ct& b) {
+  need_same(a, b);
+  Ct r = a.ncomp >= b.ncomp ? a : b;
+  const Ct& o = a.ncomp >= b.ncomp ? b : a;
+  for (int c = 0; c < o.ncomp; ++c)
+    for (int i = 0; i < a.level; ++i)
+      for (int n = 0; n < C.P.N; ++n)
+        r.c[c][i][n] = addmod(r.c[c][i][n], o.c[c][i][n], C.primes[i]);
+  return r;
+}
+
+Ct sub(const Context& C, const Ct& a, const Ct& b) {
+  return add(C, a, mul_scalar(C, b, -1));
+}
+
+Ct mul_scalar(const Context& C, const Ct& a, i64 s) {
+  Ct r = a;
+  for (int c = 0; c < a.ncomp; ++c)
+    for (int i = 0; i < a.level; ++i) {
+      u64 q = C.primes[i], k = lift(s, q);
+      for (int n = 0; n < C.P.N; ++n) r.c[c][i][n] = mulmod(a.c[c][i][n], k, q);
+    }
+  return r;
+}
+
+Ct add_scalar(const Context& C, const Ct& a, i64 s) {
+  // the constant polynomial s evaluates to s at every point
+  Ct r = a;
+  for (int i = 0; i < a.level; ++i) {
+    u64 q = C.primes[i], k = lift(s, q);
+    for (int n = 0; n < C.P.N; ++n) r.c[0][i][n] = addmod(r.c[0][i][n], k, q);
+  }
+  return r;
+}
+
+Ct tensor(const Context& C, const Ct& a, const Ct& b) {
+  need_same(a, b);
+  if (a.ncomp != 2 || b.ncomp != 2) throw std::runtime_error("tensor: needs 2-component inputs");
+  Ct r;
+  r.ncomp = 3; r.level = a.level; r.t_exp = a.t_exp;
+  r.c.assign(3, std::vector<Poly>(a.level, Poly(C.P.N)));
+  for (int i = 0; i < a.level; ++i) {
+    u64 q = C.primes[i];
+    for (int n = 0; n < C.P.N; ++n) {
+      u64 a0 = a.c[0][i][n], a1 = a.c[1][i][n], b0 = b.c[0][i][n], b1 = b.c[1][i][n];
+      r.c[0][i][n] = mulmod(a0, b0, q);
+      r.c[1][i][n] = addmod(mulmod(a0, b1, q), mulmod(a1, b0, q), q);
+      r.c[2][i][n] = mulmod(a1, b1, q);
+    }
+  }
+  return r;
+}
+
+// Drop the primes with global indices src[] from x (given in coefficient form on
+// those primes): returns delta = t * conv(t^{-1} x mod Q_src) on each destination
+// prime dst[m], in coefficient form. conv is the fast base conversion
+//   conv(r) = sum_i [r_i * (Q_src/q_i)^{-1}]_{q_i} * (Q_src/q_i)   (mod q_dst).
+static std::vector<Poly> scaled_base_conv(const Context& C, const std::vector<Poly>& x,
+                                          const std::vector<int>& src, const std::vector<int>& dst,
+                                          u64 t) {
+  int N = C.P.N, k = (int)src.size();
+  std::vector<Poly> y(k, Poly(N));
+  for (int a = 0; a < k; ++a) {
+    u64 qa = C.primes[src[a]];
+    u64 hat = 1;  // Q_src / q_a mod q_a
+    for (int b = 0; b < k; ++b) if (b != a) hat = mulmod(hat, C.primes[src[b]] % qa, qa);
+    u64 hat_inv = invmod(hat, qa);
+    u64 t_inv = invmod(t % qa, qa);
+    for (int n = 0; n < N; ++n) y[a][n] = mulmod(mulmod(x[a][n], t_inv, qa), hat_inv, qa);
+  }
+  std::vector<Poly> out(dst.size(), Poly(N));
+  for (size_t m = 0; m < dst.size(); ++m) {
+    u64 qm = C.primes[dst[m]];
+    std::vector<u64> hat_m(k);
+    for (int a = 0; a < k; ++a) {
+      u64 h = 1;
+      for (int b = 0; b < k; ++b) if (b != a) h = mulmod(h, C.primes[src[b]] % qm, qm);
+      hat_m[a] = h;
+    }
+    for (int n = 0; n < N; ++n) {
+      u64 acc = 0;
+      for (int a = 0; a < k; ++a) acc = addmod(acc, mulmod(y[a][n] % qm, hat_m[a], qm), qm);
+      out[m][n] = mulmod(acc, t % qm, qm);
+    }
+  }
+  return out;
+}
+
+void keyswitch(const Context& C, const std::vector<Poly>& d, int l, const KSKey& K, int t_exp,
+               std::vector<Poly>& k0, std::vector<Poly>& k1) {
+  const Params& P = C.P;
+  int N = P.N, alpha = P.alpha;
+  u64 t = ipow((u64)P.p, t_exp);
+  std::vector<Poly> dc = d;
+  for (int i = 0; i < l; ++i) ntt_inv(C, i, dc[i]);
+  // target primes: the current data primes, then the special primes
+  std::vector<int> tgt;
+  for (int i = 0; i < l; ++i) tgt.push_back(i);
+  for (int k = 0; k < alpha; ++k) tgt.push_back(P.L + k);
+  std::vector<Poly> acc0(tgt.size(), Poly(N, 0)), acc1(tgt.size(), Poly(N, 0));
+  int dnum = (l + alpha - 1) / alpha;
+  for (int j = 0; j < dnum; ++j) {
+    int lo = j * alpha, hi = std::min((j + 1) * alpha, l);
+    for (size_t m = 0; m < tgt.size(); ++m) {
+      int gm = tgt[m];
+      u64 qm = C.primes[gm];
+      Poly ext(N);
+      if (gm >= lo && gm < hi) {
+        ext = d[gm];
+      } else {
+        // fast base conversion of the digit's residues to prime gm:
+        //   sum_i [d_i * (Q_j/q_i)^{-1}]_{q_i} * (Q_j/q_i)  (mod q_gm)
+        std::vector<u64> hat_inv(hi - lo), hat_m(hi - lo);
+        for (int i = lo; i < hi; ++i) {
+          u64 qi = C.primes[i];
+          u64 hat = 1, hm = 1;
+          for (int b = lo; b < hi; ++b) if (b != i) {
+            hat = mulmod(hat, C.primes[b] % qi, qi);
+            hm = mulmod(hm, C.primes[b] % qm, qm);
+          }
+          hat_inv[i - lo] = invmod(hat, qi);
+          hat_m[i - lo] = hm;
+        }
+        for (int n = 0; n < N; ++n) {
+          u64 acc = 0;
+          for (int i = lo; i < hi; ++i) {
+            u64 y = mulmod(dc[i][n], hat_inv[i - lo], C.primes[i]);
+            acc = addmod(acc, mulmod(y % qm, hat_m[i - lo], qm), qm);
+          }
+          ext[n] = acc;
+        }
+        ntt_fwd(C, gm, ext);
+      }
+      for (int n = 0; n < N; ++n) {
+        acc0[m][n] = addmod(acc0[m][n], mulmod(ext[n], K.b[j][gm][n], qm), qm);
+        acc1[m][n] = addmod(acc1[m][n], mulmod(ext[n], K.a[j][gm][n], qm), qm);
+      }
+    }
+  }
+  // ModDown: (acc - t*conv(t^{-1} acc mod P)) * P^{-1} on the data primes
+  std::vector<int> sp, dp;
+  for (int k = 0; k < alpha; ++k) sp.push_back(P.L + k);
+  for (int i = 0; i < l; ++i) dp.push_back(i);
+  auto moddown = [&](std::vector<Poly>& acc, std::vector<Poly>& out) {
+    std::vector<Poly> xs(alpha);
+    for (int k = 0; k < alpha; ++k) { xs[k] = acc[l + k]; ntt_inv(C, P.L + k, xs[k]); }
+    std::vector<Poly> delta = scaled_base_conv(C, xs, sp, dp, t);
+    out.assign(l, Poly(N));
+    for (int i = 0; i < l; ++i) {
+      u64 q = C.primes[i];
+      ntt_fwd(C, i, delta[i]);
+      u64 Pm = 1;
+      for (int k = 0; k < alpha; ++k) Pm = mulmod(Pm, C.primes[P.L + k] % q, q);
+      u64 Pinv = invmod(Pm, q);
+      for (int n = 0; n < N; ++n) out[i][n] = mulmod(submod(acc[i][n], delta[i][n], q), Pinv, q);
+    }
+  };
+  moddown(acc0, k0);
+  moddown(acc1, k1);
+}
+
+Ct relin(const Context& C, const Ct& a) {
+  if (a.ncomp != 3) throw std::runtime_error("relin: needs 3 components");
+  std::vector<Poly> k0, k1;
+  keyswitch(C, a.c[2], a.level, C.rlk, a.t_exp, k0, k1);
+  Ct r;
+  r.ncomp = 2; r.level = a.level; r.t_exp = a.t_exp;
+  r.c.assign(2, std::vector<Poly>(a.level, Poly(C.P.N)));
+  for (int i = 0; i < a.level; ++i) {
+    u64 q = C.primes[i];
+    for (int n = 0; n < C.P.N; ++n) {
+      r.c[0][i][n] = addmod(a.c[0][i][n], k0[i][n], q);
+      r.c[1][i][n] = addmod(a.c[1][i][n], k1[i][n], q);
+    }
+  }
+  return r;
+}
+
+Ct modswitch(const Context& C, const Ct& a, int drop) {
+  if (drop <= 0) return a;
+  int l = a.level, nl = l - drop;
+  if (nl < 1) throw std::runtime_error("modswitch: out of levels");
+  u64 t = cur_t(C, a);
+  std::vector<int> src, dst;
+  for (int i = nl; i < l; ++i) src.push_back(i);
+  for (int i = 0; i < nl; ++i) dst.push_back(i);
+  Ct r;
+  r.ncomp = a.ncomp; r.level = nl; r.t_exp = a.t_exp;
+  r.c.assign(a.ncomp, std::vector<Poly>(nl, Poly(C.P.N)));
+  for (int c = 0; c < a.ncomp; ++c) {
+    std::vector<Poly> xs(drop);
+    for (int k = 0; k < drop; ++k) { xs[k] = a.c[c][nl + k]; ntt_inv(C, nl + k, xs[k]); }
+    std::vector<Poly> delta = scaled_base_conv(C, xs, src, dst, t);
+    for (int i = 0; i < nl; ++i) {
+      u64 q = C.primes[i];
+      ntt_fwd(C, i, delta[i]);
+      u64 Qd = 1;
+      for (int k = nl; k < l; ++k) Qd = mulmod(Qd, C.primes[k] % q, q);
+      u64 inv = invmod(Qd, q);
+      for (int n = 0; n < C.P.N; ++n)
+        r.c[c][i][n] = mulmod(submod(a.c[c][i][n], delta[i][n], q), inv, q);
+    }
+  }
+  return r;
+}
+
+Ct modswitch_to(const Context& C, const Ct& a, int level) {
+  if (level > a.level) throw std::runtime_error("modswitch_to: cannot raise level");
+  return modswitch(C, a, a.level - level);
+}
+
+Ct rotate(const Context& C, const Ct& a, int g) {
+  if (a.ncomp != 2) throw std::runtime_error("rotate: needs 2 components");
+  auto it = C.gk.find(g);
+  if (it == C.gk.end()) throw std::runtime_error("rotate: no Galois key");
+  Ct s = a;
+  for (int c = 0; c < 2; ++c)
+    for (int i = 0; i < a.level; ++i) {
+      Poly x = a.c[c][i];
+      ntt_inv(C, i, x);
+      x = automorph_coeff(x, g, C.primes[i]);
+      ntt_fwd(C, i, x);
+      s.c[c][i] = x;
+    }
+  std::vector<Poly> k0, k1;
+  keyswitch(C, s.c[1], a.level, it->second, a.t_exp, k0, k1);
+  Ct r = s;
+  for (int i = 0; i < a.level; ++i) {
+    u64 q = C.primes[i];
+    for (int n = 0; n < C.P.N; ++n) {
+      r.c[0][i][n] = addmod(s.c[0][i][n], k0[i][n], q);
+      r.c[1][i][n] = k1[i][n];
+    }
+  }
+  return r;
+}
+
+Ct divide_by_p(const Context& C, const Ct& a) {
+  if (a.t_exp < 2) throw std::runtime_error("divide_by_p: plaintext modulus already p");
+  Ct r = a;
+  for (int c = 0; c < a.ncomp; ++c)
+    for (int i = 0; i < a.level; ++i) {
+      u64 q = C.primes[i], pinv = invmod((u64)C.P.p % q, q);
+      for (int n = 0; n < C.P.N; ++n) r.c[c][i][n] = mulmod(a.c[c][i][n], pinv, q);
+    }
+  r.t_exp = a.t_exp - 1;
+  return r;
+}
+
+Ct mul(const Context& C, const Ct& a, const Ct& b) {
+  int l = std::min(a.level, b.level);
+  Ct x = modswitch_to(C, a, l), y = modswitch_to(C, b, l);
+  return modswitch(C, relin(C, tensor(C, x, y)), 1);
+}
+
+}  // namespace orc
