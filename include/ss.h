@@ -1,0 +1,180 @@
+/*
+ * ss.h -- C ABI of the GB300 space-switching BGV library (libss.so).
+ *
+ * Method: "space switching" (arXiv 2604.19890): BGV arithmetic stays in the
+ * number space Z_{p^r}; before a comparison each value is reduced
+ * homomorphically to its r balanced base-p digits in Z_p (Algorithm 3), each
+ * digit is compared with interpolation polynomials evaluated by
+ * Paterson-Stockmeyer (Section 4.3, Algorithm 4), and the result is raised
+ * back to Z_{p^r} with G_{p,r} (Section 4.4).
+ *
+ * Conventions shared by every call
+ *  - Ring Z[X]/(X^N+1), N a power of two. RNS chain of L data primes
+ *    q_0 > ... > q_{L-1} and alpha special primes, all = 1 mod 2*nmax*p^r.
+ *  - A ciphertext batch (ss_ct) lives in caller-owned DEVICE memory laid out
+ *    uint64[count][ncomp][capacity][N]: limb i of component c of ciphertext b
+ *    starts at data + ((b*ncomp + c)*capacity + i)*N. Limbs are stored in
+ *    evaluation (NTT) form: word j of limb i is a(psi_i^(2*bitrev(j)+1)) mod
+ *    q_i with psi_i the smallest primitive 2N-th root of unity mod q_i.
+ *    Only limbs 0..level-1 are meaningful. The library never frees caller
+ *    memory; outputs must have capacity >= the level they receive.
+ *  - Every device call is enqueued on the given stream (NULL = legacy default
+ *    stream) and is asynchronous unless stated otherwise. The library keeps
+ *    its own scratch in a stream-ordered pool (cudaMallocAsync).
+ *  - Every call returns an ss_status; ss_last_error() gives a thread-local
+ *    message for the last failure. Errors never cross the ABI as exceptions.
+ *  - Keys and contexts are library-owned and released with *_destroy.
+ */
+#ifndef SS_H
+#define SS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SS_OK = 0,
+  SS_ERR_PARAM = 1,   /* invalid argument or parameter set */
+  SS_ERR_LEVEL = 2,   /* not enough levels for the operation */
+  SS_ERR_NOISE = 3,   /* the evaluation plan needs more depth than remains */
+  SS_ERR_TMOD = 4,    /* mismatched plaintext modulus (t_exp) */
+  SS_ERR_SHAPE = 5,   /* mismatched batch count, component count or capacity */
+  SS_ERR_OOM = 6,     /* device allocation failed */
+  SS_ERR_TIMEOUT = 7, /* a bounded wait gave up */
+  SS_ERR_CUDA = 8     /* a CUDA call failed */
+} ss_status;
+
+typedef struct ss_ctx ss_ctx;   /* opaque: parameters, tables, keys */
+typedef void* ss_stream;        /* a cudaStream_t */
+
+typedef struct {
+  int32_t logN;     /* ring dimension N = 2^logN (3..16) */
+  int32_t L;        /* data primes */
+  int32_t alpha;    /* special primes = key-switching digit width */
+  int32_t bits;     /* primes lie in (2^(bits-1), 2^bits); 20 <= bits <= 58 */
+  int32_t p;        /* plaintext prime, p = 1 mod 4 */
+  int32_t r;        /* plaintext modulus p^r */
+  int32_t h;        /* Hamming weight of the ternary secret (Section 5.1: 120) */
+  int32_t nmax;     /* largest N the prime chain must support (0 = N) */
+  uint64_t seed;    /* Philox4x32-10 key for every sampled value */
+} ss_params;
+
+typedef struct {
+  uint64_t* data;   /* device pointer, see layout above */
+  int32_t count;    /* ciphertexts in the batch */
+  int32_t ncomp;    /* 2, or 3 after ss_mul */
+  int32_t level;    /* data primes held */
+  int32_t t_exp;    /* plaintext modulus p^t_exp */
+  int32_t capacity; /* limbs allocated per component */
+  int32_t reserved;
+} ss_ct;
+
+const char* ss_last_error(void);
+
+/* Named parameter sets. id 0: N=2^13, 36-bit primes, p^r=17^2 (toy);
+ * 1: N=2^15, 55-bit, 257^2; 2: N=2^16, 55-bit, 257^3. The chain length L is
+ * the one the query needs (the depth of Algorithms 3/4, raise and SUM). */
+ss_status ss_params_preset(int id, ss_params* out);
+
+/* Builds the prime chain, transform tables, base-conversion constants and
+ * slot structure (Section 2.1: R_{p^r} splits into `slots` factors). */
+ss_status ss_context_create(const ss_params* prm, ss_ctx** out);
+void ss_context_destroy(ss_ctx* ctx);
+
+/* Sizes: N, L, alpha, slots, d = N/slots, p, r, primes[L+alpha] (may be NULL). */
+ss_status ss_context_info(const ss_ctx* ctx, int32_t* N, int32_t* L, int32_t* alpha, int32_t* slots,
+                          int32_t* d, uint64_t* primes);
+
+/* Secret key (ternary, Hamming weight h; Section 2.1 and 5.1), the
+ * relinearisation key for s^2 and one Galois key per element of `galois`
+ * (odd residues mod 2N). Keys are hybrid key-switching keys over the data and
+ * special primes, device-resident and owned by ctx. Synchronous. */
+ss_status ss_keygen(ss_ctx* ctx, const int32_t* galois, int32_t ngalois);
+
+/* Galois elements ss_rotate_sum uses (5^(2^i) mod 2N for i < log2(slots/2),
+ * then 2N-1); returns the count, writes up to cap elements. */
+int32_t ss_rotate_sum_elements(const ss_ctx* ctx, int32_t* out, int32_t cap);
+
+/* Slot encoding over Z_{p^t_exp} (host, synchronous): slots[slots] ->
+ * coefficients[N]; slot j is the constant value modulo X^d - zeta_j. */
+ss_status ss_encode(const ss_ctx* ctx, int32_t t_exp, const uint64_t* slots, uint64_t* coeffs);
+ss_status ss_decode(const ss_ctx* ctx, int32_t t_exp, const uint64_t* coeffs, uint64_t* slots);
+
+/* Algorithm 1 (secret-key BGV encryption) for a batch: coeffs is a DEVICE
+ * array uint64[count][N] of plaintext coefficients in [0, p^t_exp);
+ * ciphertext b uses Philox nonce (nonce0 + b). out gets level L. */
+ss_status ss_encrypt(ss_ctx* ctx, const uint64_t* coeffs, int32_t count, uint32_t nonce0, int32_t t_exp,
+                     ss_ct* out, ss_stream stream);
+
+/* Algorithm 2: m = c0 + c1 s (+ c2 s^2) mod Q, centred, reduced mod the
+ * ciphertext's current p^t_exp (Lemma 4). Writes DEVICE uint64[count][N].
+ * Only the coefficients at multiples of d are computed (the slot
+ * coefficients); the others are written as zero. */
+ss_status ss_decrypt(ss_ctx* ctx, const ss_ct* in, uint64_t* coeffs, ss_stream stream);
+
+/* ---- BGV operations (Section 2.1); operands must share level and t_exp ---- */
+ss_status ss_add(ss_ctx* ctx, const ss_ct* a, const ss_ct* b, ss_ct* out, ss_stream stream);
+ss_status ss_sub(ss_ctx* ctx, const ss_ct* a, const ss_ct* b, ss_ct* out, ss_stream stream);
+ss_status ss_mul_scalar(ss_ctx* ctx, const ss_ct* a, int64_t c, ss_ct* out, ss_stream stream);
+ss_status ss_add_scalar(ss_ctx* ctx, const ss_ct* a, int64_t c, ss_ct* out, ss_stream stream);
+/* tensor product: out gets 3 components */
+ss_status ss_mul(ss_ctx* ctx, const ss_ct* a, const ss_ct* b, ss_ct* out, ss_stream stream);
+/* hybrid key switch of c2 with the relinearisation key: 3 -> 2 components */
+ss_status ss_relin(ss_ctx* ctx, const ss_ct* a, ss_ct* out, ss_stream stream);
+/* drops the last `drop` primes at once: c' = (c - t*conv(t^-1 c mod Q_drop)) / Q_drop */
+ss_status ss_modswitch(ss_ctx* ctx, const ss_ct* a, int32_t drop, ss_ct* out, ss_stream stream);
+/* sigma_g (X -> X^g) then key switch back to s with the Galois key of g */
+ss_status ss_rotate(ss_ctx* ctx, const ss_ct* a, int32_t g, ss_ct* out, ss_stream stream);
+/* total over all slots into every slot (SUM, Section 5.2) */
+ss_status ss_rotate_sum(ss_ctx* ctx, const ss_ct* a, ss_ct* out, ss_stream stream);
+/* DivideByP (Section 4.2): times p^-1 mod Q, t_exp - 1 */
+ss_status ss_divide_by_p(ss_ctx* ctx, const ss_ct* a, ss_ct* out, ss_stream stream);
+
+/* ---- space switching ---- */
+/* G_{p,e}(x) (Lemma 3) evaluated as x*H(x^2) by Paterson-Stockmeyer (Theorem 2) */
+ss_status ss_eval_g(ss_ctx* ctx, const ss_ct* x, int32_t e, ss_ct* out, ss_stream stream);
+/* Algorithm 3: digits[i] (i < r) receive the balanced base-p digits at t = p */
+ss_status ss_reduce_to_digits(ss_ctx* ctx, const ss_ct* a, ss_ct* digits, ss_stream stream);
+/* Algorithm 4: out = [centred(a - b) < 0] at t = p; b may have count 1 (broadcast) */
+ss_status ss_compare_lt(ss_ctx* ctx, const ss_ct* a, const ss_ct* b, ss_ct* out, ss_stream stream);
+/* Section 4.4: t <- p^r, out = G_{p,r}(in) */
+ss_status ss_raise_modulus(ss_ctx* ctx, const ss_ct* in, ss_ct* out, ss_stream stream);
+/* compare-then-SUM query (Section 1, Fig. 1; Section 5.2): one ciphertext whose
+ * every slot holds sum over rows of A*B*[C1 < C2] mod p^r. A, B, C1 have the
+ * same count; C2 has that count or 1 (an encrypted threshold). */
+ss_status ss_query_sum_where_lt(ss_ctx* ctx, const ss_ct* A, const ss_ct* B, const ss_ct* C1, const ss_ct* C2,
+                                ss_ct* out, ss_stream stream);
+/* Same query with every input in HOST memory: copies the four columns to the
+ * device, runs the query and copies the result ciphertext back to host_out
+ * (uint64[2][out_level][N]); writes its level and t_exp. Synchronous. */
+ss_status ss_query_sum_where_lt_host(ss_ctx* ctx, const uint64_t* A, const uint64_t* B, const uint64_t* C1,
+                                     const uint64_t* C2, int32_t count, int32_t count2, int32_t level,
+                                     uint64_t* host_out, int32_t* out_level, int32_t* out_t_exp,
+                                     ss_stream stream);
+/* Number of levels a query consumes on inputs at `level` (the plan's depth);
+ * SS_ERR_NOISE if the chain is too short. */
+ss_status ss_query_depth(ss_ctx* ctx, int32_t level, int32_t* out_level);
+/* Ciphertexts the query evaluates together per pass (memory/throughput knob). */
+ss_status ss_set_batch(ss_ctx* ctx, int32_t batch);
+
+/* ---- raw transform (for kernel-level measurement) ---- */
+/* In-place negacyclic NTT of `npoly` consecutive limbs of N words; limb k uses
+ * data prime (first_prime + k % nprimes). */
+ss_status ss_ntt_forward(ss_ctx* ctx, uint64_t* data, int32_t npoly, int32_t first_prime, int32_t nprimes,
+                         ss_stream stream);
+ss_status ss_ntt_inverse(ss_ctx* ctx, uint64_t* data, int32_t npoly, int32_t first_prime, int32_t nprimes,
+                         ss_stream stream);
+
+/* ---- evaluation trace (schedule check) ---- */
+ss_status ss_trace(ss_ctx* ctx, int32_t on);
+int32_t ss_trace_get(ss_ctx* ctx, char* buf, int32_t len);
+
+/* Count of kernels this library has launched since context creation. */
+uint64_t ss_launch_count(const ss_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SS_H */

@@ -32,6 +32,7 @@ def lib():
             "orc_automorph_coeff": (i32, [vp, i32, i32, P(u64)]),
             "orc_keygen": (i32, [vp, P(i32), i32]),
             "orc_secret": (i32, [vp, P(i64)]),
+            "orc_secret_keygen": (i32, [vp]),
             "orc_ksk_export": (i32, [vp, i32, P(u64), P(u64)]),
             "orc_rotate_sum_elements": (i32, [vp, P(i32)]),
             "orc_encode": (i32, [vp, i32, P(u64), P(u64)]),
@@ -195,6 +196,10 @@ class Oracle:
             galois = self.rotate_sum_elements()
         g = np.ascontiguousarray(galois, dtype=np.int32)
         _chk(lib().orc_keygen(self.h, _ptr(g, C.c_int), len(g)))
+
+    def secret_keygen(self):
+        """Secret key only (no key-switching keys): enough to encrypt and decrypt."""
+        _chk(lib().orc_secret_keygen(self.h))
 
     def secret(self):
         out = np.zeros(self.N, dtype=np.int64)

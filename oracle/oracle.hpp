@@ -135,6 +135,7 @@ std::vector<u64> decode(const Context& C, int t_exp, const std::vector<u64>& coe
 // --------------------------------------------------------------------- keys
 std::vector<i64> sample_secret(const Context& C);
 void keygen(Context& C, const std::vector<int>& galois);
+void secret_keygen(Context& C);  // secret only: enough to encrypt and decrypt
 KSKey make_ksk(const Context& C, const std::vector<Poly>& s_prime_hat, u32 key_id);
 
 // ------------------------------------------------------------ encrypt/decrypt

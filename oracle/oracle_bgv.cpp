@@ -443,15 +443,21 @@ KSKey make_ksk(const Context& C, const std::vector<Poly>& sp_hat, u32 key_id) {
   return K;
 }
 
-void keygen(Context& C, const std::vector<int>& galois) {
-  const Params& P = C.P;
-  int nl = P.L + P.alpha;
+void secret_keygen(Context& C) {
+  int nl = C.P.L + C.P.alpha;
   C.sk = sample_secret(C);
   C.sk_hat.resize(nl);
   for (int i = 0; i < nl; ++i) {
     C.sk_hat[i] = to_limb(C, C.sk, i);
     ntt_fwd(C, i, C.sk_hat[i]);
   }
+  C.have_keys = true;
+}
+
+void keygen(Context& C, const std::vector<int>& galois) {
+  const Params& P = C.P;
+  int nl = P.L + P.alpha;
+  secret_keygen(C);
   // relinearisation key: s' = s^2
   std::vector<Poly> s2(nl);
   for (int i = 0; i < nl; ++i) {

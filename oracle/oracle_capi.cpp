@@ -89,6 +89,8 @@ int orc_keygen(void* h, const int* galois, int ng) {
   return guard([&] { keygen(ctx(h), std::vector<int>(galois, galois + ng)); });
 }
 
+int orc_secret_keygen(void* h) { return guard([&] { secret_keygen(ctx(h)); }); }
+
 int orc_secret(void* h, int64_t* out) {
   return guard([&] { for (int n = 0; n < ctx(h).P.N; ++n) out[n] = ctx(h).sk[n]; });
 }

@@ -1,0 +1,453 @@
+// Host-side number theory and context construction: prime chain, roots of
+// unity, transform twiddles, base-conversion constants, CRT constants, slot
+// structure and the interpolation coefficient tables.
+#include <algorithm>
+#include <cstring>
+
+#include "philox.h"
+#include "ss_internal.h"
+
+namespace ss {
+
+typedef unsigned __int128 u128;
+
+namespace nt {
+
+u64 mul(u64 a, u64 b, u64 m) { return (u64)(((u128)a * b) % m); }
+
+u64 pow(u64 a, u64 e, u64 m) {
+  u64 r = 1 % m, x = a % m;
+  for (; e; e >>= 1, x = mul(x, x, m))
+    if (e & 1) r = mul(r, x, m);
+  return r;
+}
+
+u64 inv(u64 a, u64 m) {
+  i64 r0 = (i64)m, r1 = (i64)(a % m);
+  __int128 s0 = 0, s1 = 1;
+  while (r1) {
+    i64 q = r0 / r1;
+    i64 r2 = r0 - q * r1; r0 = r1; r1 = r2;
+    __int128 s2 = s0 - (__int128)q * s1; s0 = s1; s1 = s2;
+  }
+  if (r0 != 1) throw Error(SS_ERR_PARAM, "modular inverse does not exist");
+  __int128 v = s0 % (__int128)m;
+  if (v < 0) v += m;
+  return (u64)v;
+}
+
+u64 lift(i64 c, u64 m) {
+  if (c >= 0) return (u64)c % m;
+  u64 k = (u64)(-(c + 1)) % m;  // -(c) - 1 without overflow
+  return m - 1 - k;
+}
+
+bool prime(u64 n) {
+  if (n < 4) return n >= 2;
+  if (n % 2 == 0) return false;
+  u64 d = n - 1;
+  int s = 0;
+  while (!(d & 1)) { d >>= 1; ++s; }
+  const u64 bases[12] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+  for (u64 a : bases) {
+    if (a % n == 0) continue;
+    u64 x = pow(a, d, n);
+    if (x == 1 || x == n - 1) continue;
+    int i = 1;
+    for (; i < s; ++i) {
+      x = mul(x, x, n);
+      if (x == n - 1) break;
+    }
+    if (i == s) return false;
+  }
+  return true;
+}
+
+u64 shoup(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+
+int brv(int x, int logn) {
+  unsigned v = (unsigned)x, r = 0;
+  for (int i = 0; i < logn; ++i, v >>= 1) r = (r << 1) | (v & 1u);
+  return (int)r;
+}
+
+// Largest primes below 2^bits that are 1 mod step, in descending order.
+std::vector<u64> chain(int bits, u64 step, int count) {
+  std::vector<u64> out;
+  u64 hi = (1ULL << bits) - 1;
+  u64 q = (hi - 1) / step * step + 1;
+  for (; (int)out.size() < count; q -= step) {
+    if (q < step || q <= (1ULL << (bits - 1))) throw Error(SS_ERR_PARAM, "prime chain exhausted at this width");
+    if (prime(q)) out.push_back(q);
+  }
+  return out;
+}
+
+// Smallest primitive 2N-th root of unity mod q.
+u64 root2n(u64 q, int N) {
+  u64 g = 0;
+  for (u64 x = 2; !g; ++x) {
+    u64 c = pow(x, (q - 1) / (2 * (u64)N), q);
+    if (pow(c, (u64)N, q) == q - 1) g = c;
+  }
+  u64 g2 = mul(g, g, q), best = g, cur = g;
+  for (int j = 1; j < N; ++j) {
+    cur = mul(cur, g2, q);
+    best = std::min(best, cur);
+  }
+  return best;
+}
+
+static u64 upow(u64 b, int e) {
+  u64 r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+static i64 centred(u64 v, u64 m) { return v > m / 2 ? (i64)v - (i64)m : (i64)v; }
+
+// G_{p,e}: the Newton interpolant of f(x) = balanced(x mod p) through
+// x = 0..D, D = (e-1)(p-1)+1, written in monomials mod p^e, odd part kept.
+std::vector<i64> g_coeffs(int p, int e) {
+  const int D = (e - 1) * (p - 1) + 1;
+  const u64 pe = upow((u64)p, e);
+  int extra = 0;
+  for (long q = p; q <= D; q *= p) extra += (int)(D / q);
+  const u64 M = pe * upow((u64)p, extra);
+  std::vector<u64> f(D + 1);
+  for (int x = 0; x <= D; ++x) {
+    int z = x % p;
+    f[x] = lift(z > p / 2 ? z - p : z, M);
+  }
+  // Delta^k f(0) = sum_j (-1)^(k-j) C(k, j) f(j), binomials from Pascal rows mod M
+  std::vector<u64> binom(1, 1 % M), dk(D + 1);
+  for (int k = 0; k <= D; ++k) {
+    if (k > 0) {
+      std::vector<u64> nb(k + 1);
+      nb[0] = nb[k] = 1 % M;
+      for (int j = 1; j < k; ++j) nb[j] = (binom[j - 1] + binom[j]) % M;
+      binom.swap(nb);
+    }
+    u64 s = 0;
+    for (int j = 0; j <= k; ++j) {
+      u64 term = mul(binom[j], f[j], M);
+      s = ((k - j) % 2 == 0) ? (s + term) % M : (s + M - term) % M;
+    }
+    dk[k] = s;
+  }
+  std::vector<u64> mono(D + 1, 0), ff(1, 1 % pe);
+  u64 unit = 1 % pe;
+  int vk = 0;
+  for (int k = 0; k <= D; ++k) {
+    if (k > 0) {
+      long x = k;
+      while (x % p == 0) { x /= p; ++vk; }
+      unit = mul(unit, (u64)x % pe, pe);
+      ff.push_back(0);
+      for (int j = k; j >= 1; --j) ff[j] = (ff[j - 1] + pe - mul(ff[j], (u64)(k - 1) % pe, pe)) % pe;
+      ff[0] = (pe - mul(ff[0], (u64)(k - 1) % pe, pe)) % pe;
+    }
+    u64 pv = upow((u64)p, vk);
+    if (dk[k] % pv) throw Error(SS_ERR_PARAM, "G table: non-integral difference");
+    u64 ck = mul((dk[k] / pv) % pe, inv(unit, pe), pe);
+    for (int j = 0; j <= k; ++j) mono[j] = (mono[j] + mul(ck, ff[j], pe)) % pe;
+  }
+  std::vector<i64> out(D + 1, 0);
+  for (int i = 1; i <= D; i += 2) out[i] = centred(mono[i], pe);
+  return out;
+}
+
+// F_LT over Z_p: coefficient of x^(p-1) is (p+1)/2; odd i <= p-2 carry
+// c_i = sum_{j=1}^{(p-1)/2} j^(p-1-i).
+std::vector<i64> flt_coeffs(int p) {
+  std::vector<i64> c(p, 0);
+  c[p - 1] = centred((u64)((p + 1) / 2) % p, (u64)p);
+  for (int i = 1; i < p - 1; i += 2) {
+    u64 s = 0;
+    for (int j = 1; 2 * j <= p - 1; ++j) s = (s + pow((u64)j, (u64)(p - 1 - i), (u64)p)) % (u64)p;
+    c[i] = centred(s, (u64)p);
+  }
+  return c;
+}
+
+}  // namespace nt
+
+// ------------------------------------------------------------------ context
+static void upload(void** dst, const void* src, size_t bytes) {
+  SS_CUDA(cudaMalloc(dst, bytes));
+  SS_CUDA(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+}
+
+Context::~Context() {
+  cudaFree(d_mod);
+  cudaFree(d_tw);
+  cudaFree(d_ninv);
+  cudaFree(d_pinv);
+  cudaFree(d_tmod);
+  cudaFree(d_tables);
+  cudaFree(d_crt);
+  cudaFree(d_sk);
+  cudaFree(d_sk2);
+  cudaFree(rlk.a);
+  cudaFree(rlk.b);
+  for (auto& kv : gk) { cudaFree(kv.second.a); cudaFree(kv.second.b); }
+}
+
+void build_context(Context& C, const ss_params& prm) {
+  C.prm = prm;
+  if (prm.logN < 3 || prm.logN > 16) throw Error(SS_ERR_PARAM, "logN must be in [3, 16]");
+  if (prm.L < 1 || prm.alpha < 1 || prm.L > 200 || prm.alpha > 16) throw Error(SS_ERR_PARAM, "bad L/alpha");
+  if (prm.bits < 20 || prm.bits > 58) throw Error(SS_ERR_PARAM, "bits must be in [20, 58]");
+  if (prm.p < 5 || prm.p % 4 != 1 || !nt::prime((u64)prm.p)) throw Error(SS_ERR_PARAM, "p must be a prime = 1 mod 4");
+  if (prm.r < 1 || prm.r > 8) throw Error(SS_ERR_PARAM, "bad r");
+  C.logN = prm.logN;
+  C.N = 1 << prm.logN;
+  if (prm.h < 1 || prm.h > C.N) throw Error(SS_ERR_PARAM, "bad Hamming weight");
+  int nmax = prm.nmax ? prm.nmax : C.N;
+  if (nmax < C.N || (nmax & (nmax - 1))) throw Error(SS_ERR_PARAM, "nmax must be a power of two >= N");
+  C.L = prm.L;
+  C.alpha = prm.alpha;
+  C.ntot = C.L + C.alpha;
+  C.dnum = (C.L + C.alpha - 1) / C.alpha;
+  C.p = prm.p;
+  C.r = prm.r;
+  C.tpow.assign(C.r + 1, 1);
+  for (int e = 1; e <= C.r; ++e) C.tpow[e] = C.tpow[e - 1] * (u64)C.p;
+  C.t = C.tpow[C.r];
+  if (C.t >= (1ULL << 40) || C.t >= (1ULL << (prm.bits - 2))) throw Error(SS_ERR_PARAM, "p^r too large for the primes");
+  // lazy 128-bit sums in the key-switch inner product need dnum * q^2 < 2^(63+k)
+  if ((double)C.dnum * 2.0 >= (double)(1ULL << (63 - prm.bits)))
+    throw Error(SS_ERR_PARAM, "too many digits for the lazy inner product at this prime width");
+
+  C.primes = nt::chain(prm.bits, 2 * (u64)nmax * C.t, C.ntot);
+  C.psi.resize(C.ntot);
+  for (int i = 0; i < C.ntot; ++i) C.psi[i] = nt::root2n(C.primes[i], C.N);
+
+  // slots: d = order of p mod 2N, slots = N/d, X^N+1 = prod (X^d - zeta_j)
+  {
+    u64 m2 = 2 * (u64)C.N, x = (u64)C.p % m2;
+    int d = 1;
+    while (x != 1) { x = x * (u64)C.p % m2; ++d; }
+    C.d = d;
+    C.slots = C.N / d;
+    if (((u64)C.p - 1) % (2 * (u64)C.slots)) throw Error(SS_ERR_PARAM, "slots do not split into linear factors");
+    u64 w = 0;
+    for (u64 c = 2; c < (u64)C.p && !w; ++c)
+      if (nt::pow(c, (u64)C.slots, (u64)C.p) == (u64)C.p - 1) w = c;
+    // Newton iteration for w^slots + 1 = 0 mod p^r
+    for (int it = 0; it <= C.r; ++it) {
+      u64 f = (nt::pow(w, (u64)C.slots, C.t) + 1) % C.t;
+      u64 df = nt::mul((u64)C.slots % C.t, nt::pow(w, (u64)C.slots - 1, C.t), C.t);
+      w = (w + C.t - nt::mul(f, nt::inv(df, C.t), C.t)) % C.t;
+    }
+    C.omega = w;
+    C.slot_exp.assign(C.slots, 1);
+    if (C.slots > 1) {
+      int h = C.slots / 2, m = 2 * C.slots;
+      long g = 1;
+      for (int j = 0; j < h; ++j, g = g * 5 % m) {
+        C.slot_exp[j] = (int)g;
+        C.slot_exp[j + h] = (int)((m - g) % m);
+      }
+    }
+  }
+
+  const int N = C.N, T = C.ntot;
+  // moduli
+  std::vector<ModDesc> md(T);
+  for (int i = 0; i < T; ++i) {
+    u64 q = C.primes[i];
+    int k = 64 - __builtin_clzll(q);
+    md[i].q = q;
+    md[i].kbits = k;
+    md[i].mu = (u64)(((u128)1 << (63 + k)) / q);
+    md[i].pad = 0;
+  }
+  upload((void**)&C.d_mod, md.data(), sizeof(ModDesc) * T);
+
+  // twiddles: psi^brv(i) and psi^-brv(i) with Shoup companions
+  {
+    std::vector<u64> tw((size_t)T * 4 * N);
+    std::vector<u64> ninv(2 * T), pinv(2 * T);
+    for (int i = 0; i < T; ++i) {
+      u64 q = C.primes[i], ps = C.psi[i], pi = nt::inv(ps, q);
+      std::vector<u64> fw(N), bw(N);
+      u64 a = 1, b = 1;
+      for (int k = 0; k < N; ++k) { fw[k] = a; bw[k] = b; a = nt::mul(a, ps, q); b = nt::mul(b, pi, q); }
+      u64* o = &tw[(size_t)i * 4 * N];
+      for (int k = 0; k < N; ++k) {
+        int rk = nt::brv(k, C.logN);
+        o[k] = fw[rk];
+        o[N + k] = nt::shoup(fw[rk], q);
+        o[2 * N + k] = bw[rk];
+        o[3 * N + k] = nt::shoup(bw[rk], q);
+      }
+      u64 ni = nt::inv((u64)N % q, q);
+      ninv[2 * i] = ni;
+      ninv[2 * i + 1] = nt::shoup(ni, q);
+      u64 pv = nt::inv((u64)C.p % q, q);
+      pinv[2 * i] = pv;
+      pinv[2 * i + 1] = nt::shoup(pv, q);
+    }
+    upload((void**)&C.d_tw, tw.data(), tw.size() * 8);
+    upload((void**)&C.d_ninv, ninv.data(), ninv.size() * 8);
+    upload((void**)&C.d_pinv, pinv.data(), pinv.size() * 8);
+    std::vector<u64> tm((size_t)(C.r + 1) * T * 2);
+    for (int e = 0; e <= C.r; ++e)
+      for (int i = 0; i < T; ++i) {
+        u64 v = C.tpow[e] % C.primes[i];
+        tm[((size_t)e * T + i) * 2] = v;
+        tm[((size_t)e * T + i) * 2 + 1] = nt::shoup(v, C.primes[i]);
+      }
+    upload((void**)&C.d_tmod, tm.data(), tm.size() * 8);
+  }
+
+  // base-conversion constants
+  std::vector<u64> tab;
+  auto put2 = [&](u64 v, u64 q) { tab.push_back(v); tab.push_back(nt::shoup(v, q)); };
+  // hat(src range [a, b), s) mod q_g = prod_{s' in [a,b), s' != s} q_s' mod q_g
+  auto hat = [&](int a, int b, int s, int g) {
+    u64 qg = C.primes[g], v = 1 % qg;
+    for (int x = a; x < b; ++x)
+      if (x != s) v = nt::mul(v, C.primes[x] % qg, qg);
+    return v;
+  };
+  // ModUp: digit j = [j*alpha, e)
+  for (int j = 0; j * C.alpha < C.L; ++j) {
+    int a = j * C.alpha;
+    for (int e = a + 1; e <= std::min(a + C.alpha, C.L); ++e) {
+      C.off_modup[{j, e}] = tab.size();
+      for (int s = a; s < e; ++s) put2(nt::inv(hat(a, e, s, s), C.primes[s]), C.primes[s]);
+      for (int s = a; s < e; ++s)
+        for (int g = 0; g < T; ++g) tab.push_back(g >= a && g < e ? 0 : hat(a, e, s, g));
+    }
+  }
+  // ModDown: src = special primes [L, L+alpha)
+  C.off_md_c1.assign(C.r + 1, 0);
+  for (int te = 1; te <= C.r; ++te) {
+    C.off_md_c1[te] = tab.size();
+    for (int k = C.L; k < T; ++k) {
+      u64 q = C.primes[k];
+      put2(nt::mul(nt::inv(C.tpow[te] % q, q), nt::inv(hat(C.L, T, k, k), q), q), q);
+    }
+  }
+  C.off_md_c2 = tab.size();
+  for (int k = C.L; k < T; ++k)
+    for (int g = 0; g < T; ++g) tab.push_back(g >= C.L ? 0 : hat(C.L, T, k, g));
+  C.off_md_pinv = tab.size();
+  for (int g = 0; g < T; ++g) {
+    u64 q = C.primes[g];
+    if (g >= C.L) { tab.push_back(0); tab.push_back(0); continue; }
+    u64 P = 1;
+    for (int k = C.L; k < T; ++k) P = nt::mul(P, C.primes[k] % q, q);
+    put2(nt::inv(P, q), q);
+  }
+  // modulus switching: level l drops [l-k, l)
+  for (int l = 2; l <= C.L; ++l)
+    for (int k = 1; k < l; ++k) {
+      int a = l - k;
+      C.off_ms[{l, k}] = tab.size();
+      // c2 rows over the kept primes (row length T, only [0, a) used)
+      std::vector<u64> QD(a);
+      for (int g = 0; g < a; ++g) {
+        u64 q = C.primes[g], v = 1;
+        for (int x = a; x < l; ++x) v = nt::mul(v, C.primes[x] % q, q);
+        QD[g] = v;
+      }
+      for (int s = a; s < l; ++s)
+        for (int g = 0; g < T; ++g)
+          tab.push_back(g < a ? nt::mul(QD[g], nt::inv(C.primes[s] % C.primes[g], C.primes[g]), C.primes[g]) : 0);
+      for (int g = 0; g < T; ++g) {
+        if (g < a) put2(nt::inv(QD[g], C.primes[g]), C.primes[g]);
+        else { tab.push_back(0); tab.push_back(0); }
+      }
+      for (int te = 1; te <= C.r; ++te) {
+        C.off_ms_c1[std::make_tuple(l, k, te)] = tab.size();
+        for (int s = a; s < l; ++s) {
+          u64 q = C.primes[s];
+          put2(nt::mul(nt::inv(C.tpow[te] % q, q), nt::inv(hat(a, l, s, s), q), q), q);
+        }
+      }
+    }
+  C.tables_words = tab.size();
+  upload((void**)&C.d_tables, tab.data(), tab.size() * 8);
+
+  // decryption CRT (Garner): inverse prefix products, half-Q digits per level,
+  // prefix products mod p^e.
+  {
+    std::vector<u64> crt;
+    C.off_crt_pinv = 0;
+    for (int i = 0; i < C.L; ++i) {
+      u64 q = C.primes[i], v = 1;
+      for (int j = 0; j < i; ++j) v = nt::mul(v, C.primes[j] % q, q);
+      crt.push_back(i == 0 ? 1 : nt::inv(v, q));
+    }
+    C.off_crt_half.assign(C.L + 1, 0);
+    for (int l = 1; l <= C.L; ++l) {
+      C.off_crt_half[l] = crt.size();
+      // mixed-radix digits of (Q_l - 1)/2, whose residues are (q_i - 1)/2
+      std::vector<u64> v(l);
+      for (int i = 0; i < l; ++i) {
+        u64 q = C.primes[i], x = (q - 1) / 2;
+        u64 acc = 0;
+        for (int j = i - 1; j >= 0; --j) acc = (nt::mul(acc, C.primes[j] % q, q) + v[j]) % q;
+        v[i] = nt::mul((x + q - acc) % q, crt[i], q);
+        crt.push_back(v[i]);
+      }
+    }
+    C.off_crt_qmodt = crt.size();
+    // [e][i]: (q_0 ... q_{i-1}) mod p^e, i = 0..L
+    for (int e = 0; e <= C.r; ++e) {
+      u64 te = C.tpow[e], v = 1 % te;
+      for (int i = 0; i <= C.L; ++i) {
+        crt.push_back(v);
+        if (i < C.L) v = nt::mul(v, C.primes[i] % te, te);
+      }
+    }
+    upload((void**)&C.d_crt, crt.data(), crt.size() * 8);
+  }
+}
+
+// ------------------------------------------------------------------ slots
+static u64 zeta(const Context& C, int j, int power, u64 te) {
+  u64 m = 2 * (u64)C.slots;
+  u64 e = ((u64)C.slot_exp[j] * (u64)power) % m;
+  return nt::pow(C.omega % te, e, te);
+}
+
+std::vector<u64> encode(const Context& C, int t_exp, const u64* v) {
+  if (t_exp < 1 || t_exp > C.r) throw Error(SS_ERR_PARAM, "bad t_exp");
+  u64 te = C.tpow[t_exp];
+  u64 il = nt::inv((u64)C.slots % te, te);
+  std::vector<u64> m(C.N, 0);
+  for (int k = 0; k < C.slots; ++k) {
+    u64 acc = 0;
+    for (int j = 0; j < C.slots; ++j)  // zeta_j^(-k) = zeta_j^(2*slots - k)
+      acc = (acc + nt::mul(v[j] % te, zeta(C, j, 2 * C.slots - k, te), te)) % te;
+    m[(size_t)k * C.d] = nt::mul(acc, il, te);
+  }
+  return m;
+}
+
+std::vector<u64> decode(const Context& C, int t_exp, const u64* m) {
+  if (t_exp < 1 || t_exp > C.r) throw Error(SS_ERR_PARAM, "bad t_exp");
+  u64 te = C.tpow[t_exp];
+  std::vector<u64> v(C.slots, 0);
+  for (int j = 0; j < C.slots; ++j) {
+    u64 acc = 0;
+    for (int k = 0; k < C.slots; ++k) acc = (acc + nt::mul(m[(size_t)k * C.d] % te, zeta(C, j, k, te), te)) % te;
+    v[j] = acc;
+  }
+  return v;
+}
+
+std::vector<int> rotate_sum_elements(const Context& C) {
+  std::vector<int> g;
+  if (C.slots < 2) return g;
+  long m = 2L * C.N, e = 5;
+  for (int s = 1; s < C.slots / 2; s *= 2, e = e * e % m) g.push_back((int)e);
+  g.push_back((int)(m - 1));
+  return g;
+}
+
+}  // namespace ss

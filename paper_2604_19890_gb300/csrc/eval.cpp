@@ -1,0 +1,342 @@
+// Evaluator for space switching on ciphertext batches. One schedule serves
+// every ciphertext of a batch, so each kernel launch covers the whole batch.
+//
+// Schedule (fixed, so that results are reproducible word for word):
+//  * multiplication: align both operands to the lower level by modulus
+//    switching the higher one (dropping all extra primes at once), tensor,
+//    relinearise, then drop exactly one prime;
+//  * powers of y: y^e = (y^(e/2))^2 when e is a power of two, otherwise
+//    y^(2^floor(log2 e)) * y^(e - 2^floor(log2 e));
+//  * Paterson-Stockmeyer (Theorem 2) for H(y) = sum_j h_j y^j:
+//    k = 2^ceil(floor(log2(n+1))/2) baby steps y^1..y^(k-1), giant steps
+//    y^(k 2^i), coefficient vector padded to k 2^m >= n+1 and split in halves
+//    recursively (H = H_lo + H_hi * y^half); empty halves are skipped and a
+//    half that is a bare constant multiplies the giant step as a scalar;
+//  * G_{p,e}(x) = x * H(x^2) with H the odd coefficients (Section 4.2);
+//  * per digit: F_LT(x) = x * H_LT(x^2) + c_(p-1) y^((p-1)/2) and
+//    F_EQ(x) = 1 - y^((p-1)/2), sharing y = x^2 (Section 4.3).
+#include <algorithm>
+#include <functional>
+#include <map>
+
+#include "ss_internal.h"
+
+namespace ss {
+
+static std::string L_(int l) { return "L" + std::to_string(l); }
+
+// ------------------------------------------------------------------ primitives
+BufP ev_modswitch_to(Context& C, const BufP& a, int level, cudaStream_t st) {
+  if (level == a->level) return a;
+  if (level > a->level) throw Error(SS_ERR_LEVEL, "cannot raise a level");
+  if (level < 1) throw Error(SS_ERR_NOISE, "the plan needs more levels than the chain has");
+  BufP out = alloc_buf(C, a->count, a->ncomp, level, a->t_exp, st);
+  if (!C.dry) op_modswitch(C, *a, a->level - level, *out, st);
+  return out;
+}
+
+static void same_t(const BufP& a, const BufP& b) {
+  if (a->t_exp != b->t_exp) throw Error(SS_ERR_TMOD, "plaintext moduli differ");
+}
+
+static int out_count(const BufP& a, const BufP& b) {
+  if (a->count == b->count) return a->count;
+  if (b->count == 1) return a->count;
+  if (a->count == 1) return b->count;
+  throw Error(SS_ERR_SHAPE, "batch sizes differ");
+}
+
+static BufP binary(Context& C, int op, const BufP& a0, const BufP& b0, cudaStream_t st) {
+  same_t(a0, b0);
+  if (a0->ncomp != b0->ncomp) throw Error(SS_ERR_SHAPE, "component counts differ");
+  int l = std::min(a0->level, b0->level);
+  BufP a = ev_modswitch_to(C, a0, l, st), b = ev_modswitch_to(C, b0, l, st);
+  if (a->count == 1 && b->count > 1) {
+    if (op == 1) throw Error(SS_ERR_SHAPE, "broadcast of the left operand of a subtraction");
+    std::swap(a, b);
+  }
+  BufP out = alloc_buf(C, out_count(a, b), a->ncomp, l, a->t_exp, st);
+  if (!C.dry) k_binary(C, op, *a, *b, *out, st);
+  return out;
+}
+
+BufP ev_add(Context& C, const BufP& a, const BufP& b, cudaStream_t st) { return binary(C, 0, a, b, st); }
+BufP ev_sub(Context& C, const BufP& a, const BufP& b, cudaStream_t st) { return binary(C, 1, a, b, st); }
+
+BufP ev_scalar(Context& C, int op, const BufP& a, i64 c, cudaStream_t st) {
+  BufP out = alloc_buf(C, a->count, a->ncomp, a->level, op == 2 ? a->t_exp - 1 : a->t_exp, st);
+  if (!C.dry) k_scalar(C, op, *a, c, *out, st);
+  return out;
+}
+
+BufP ev_mul(Context& C, const BufP& a0, const BufP& b0, cudaStream_t st) {
+  same_t(a0, b0);
+  if (a0->ncomp != 2 || b0->ncomp != 2) throw Error(SS_ERR_SHAPE, "multiplication needs 2-component inputs");
+  int l = std::min(a0->level, b0->level);
+  if (l < 2) throw Error(SS_ERR_NOISE, "the plan needs more levels than the chain has");
+  BufP a = ev_modswitch_to(C, a0, l, st), b = ev_modswitch_to(C, b0, l, st);
+  if (a->count != b->count) throw Error(SS_ERR_SHAPE, "batch sizes differ");
+  BufP t3 = alloc_buf(C, a->count, 3, l, a->t_exp, st);
+  BufP r = alloc_buf(C, a->count, 2, l, a->t_exp, st);
+  BufP out = alloc_buf(C, a->count, 2, l - 1, a->t_exp, st);
+  if (!C.dry) {
+    k_tensor(C, *a, *b, *t3, st);
+    op_relin(C, *t3, *r, st);
+    op_modswitch(C, *r, 1, *out, st);
+  }
+  return out;
+}
+
+// ------------------------------------------------------------------ powers and BSGS
+namespace {
+
+struct Powers {
+  Context& C;
+  cudaStream_t st;
+  std::map<int, BufP> pw;
+  std::map<std::pair<int, int>, BufP> aligned;
+  Powers(Context& c, const BufP& y, cudaStream_t s) : C(c), st(s) { pw[1] = y; }
+  BufP get(int e) {
+    auto it = pw.find(e);
+    if (it != pw.end()) return it->second;
+    int h = 1;
+    while (h * 2 <= e) h *= 2;
+    BufP r;
+    if (h == e) {
+      BufP z = get(e / 2);
+      r = ev_mul(C, z, z, st);
+      note(C, "pow " + std::to_string(e) + " = sq " + std::to_string(e / 2) + " -> " + L_(r->level));
+    } else {
+      BufP a = get(h);
+      BufP b = get(e - h);
+      r = ev_mul(C, a, b, st);
+      note(C, "pow " + std::to_string(e) + " = " + std::to_string(h) + "*" + std::to_string(e - h) + " -> " +
+                  L_(r->level));
+    }
+    pw[e] = r;
+    return r;
+  }
+  BufP at_level(int e, int level) {
+    BufP x = get(e);
+    if (x->level == level) return x;
+    auto key = std::make_pair(e, level);
+    auto it = aligned.find(key);
+    if (it != aligned.end()) return it->second;
+    BufP r = ev_modswitch_to(C, x, level, st);
+    aligned[key] = r;
+    return r;
+  }
+};
+
+struct Term {
+  BufP ct;  // null when the value is a bare constant
+  i64 cst = 0;
+};
+
+Term bsgs(Context& C, const std::vector<i64>& h, Powers& P, cudaStream_t st) {
+  int n1 = (int)h.size();
+  int lg = 0;
+  while ((2 << lg) <= n1) ++lg;
+  int k = 1 << ((lg + 1) / 2);
+  int len = k;
+  while (len < n1) len *= 2;
+  std::vector<i64> c(len, 0);
+  std::copy(h.begin(), h.end(), c.begin());
+  note(C, "bsgs n+1=" + std::to_string(n1) + " k=" + std::to_string(k) + " len=" + std::to_string(len));
+  std::function<Term(int, int)> rec = [&](int lo, int ln) -> Term {
+    Term out;
+    if (ln == k) {
+      out.cst = c[lo];
+      std::vector<int> idx;
+      for (int i = 1; i < k; ++i)
+        if (c[lo + i] != 0) idx.push_back(i);
+      if (idx.empty()) return out;
+      int lvl = 1 << 30;
+      for (int i : idx) lvl = std::min(lvl, P.get(i)->level);
+      for (int i : idx) {
+        BufP term = ev_scalar(C, 0, P.at_level(i, lvl), c[lo + i], st);
+        out.ct = out.ct ? ev_add(C, out.ct, term, st) : term;
+      }
+      note(C, "baby lo=" + std::to_string(lo) + " terms=" + std::to_string(idx.size()) + " " + L_(lvl));
+      return out;
+    }
+    int half = ln / 2;
+    Term A = rec(lo, half), B = rec(lo + half, half);
+    if (!B.ct && B.cst == 0) return A;
+    BufP G = P.get(half);
+    BufP prod;
+    if (B.ct) {
+      BufP b = B.cst != 0 ? ev_scalar(C, 1, B.ct, B.cst, st) : B.ct;
+      prod = ev_mul(C, b, G, st);
+    } else {
+      prod = ev_scalar(C, 0, G, B.cst, st);
+    }
+    out.cst = A.cst;
+    out.ct = A.ct ? ev_add(C, A.ct, prod, st) : prod;
+    note(C, "giant lo=" + std::to_string(lo) + " half=" + std::to_string(half) + " -> " + L_(out.ct->level));
+    return out;
+  };
+  return rec(0, len);
+}
+
+BufP mul_term(Context& C, const BufP& x, const Term& T, cudaStream_t st) {
+  if (!T.ct) return ev_scalar(C, 0, x, T.cst, st);
+  BufP b = T.cst != 0 ? ev_scalar(C, 1, T.ct, T.cst, st) : T.ct;
+  return ev_mul(C, x, b, st);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ space switching
+BufP ev_eval_g(Context& C, const BufP& x, int e, cudaStream_t st) {
+  std::vector<i64> g = nt::g_coeffs(C.p, e);
+  std::vector<i64> h;
+  for (size_t i = 1; i < g.size(); i += 2) h.push_back(g[i]);
+  while (h.size() > 1 && h.back() == 0) h.pop_back();
+  note(C, "G p=" + std::to_string(C.p) + " e=" + std::to_string(e) + " in " + L_(x->level));
+  BufP y = ev_mul(C, x, x, st);
+  Powers P(C, y, st);
+  Term H = bsgs(C, h, P, st);
+  BufP out = mul_term(C, x, H, st);
+  note(C, "G done -> " + L_(out->level));
+  return out;
+}
+
+// Algorithm 3
+std::vector<BufP> ev_reduce(Context& C, const BufP& a, cudaStream_t st) {
+  int r = C.r;
+  if (a->t_exp != r) throw Error(SS_ERR_TMOD, "reduction input must be at t = p^r");
+  std::vector<BufP> digits;
+  BufP b = a;
+  for (int i = 0; i + 1 < r; ++i) {
+    BufP ai = ev_eval_g(C, b, r - i, st);
+    BufP diff = ev_sub(C, ev_modswitch_to(C, b, ai->level, st), ai, st);
+    b = ev_scalar(C, 2, diff, 0, st);  // DivideByP
+    note(C, "digit " + std::to_string(i) + " " + L_(ai->level));
+    digits.push_back(ai);
+  }
+  digits.push_back(b);
+  std::vector<BufP> out;
+  for (auto& d : digits) {  // ChangeModToP: same words, t <- p
+    auto v = std::make_shared<Buf>(*d);
+    v->owned = false;
+    v->parent = d;
+    v->t_exp = 1;
+    out.push_back(v);
+  }
+  return out;
+}
+
+static void compare_digit(Context& C, const BufP& x, BufP& lt, BufP& eq, cudaStream_t st) {
+  int p = C.p;
+  std::vector<i64> f = nt::flt_coeffs(p);
+  std::vector<i64> h;
+  for (int i = 1; i <= p - 2; i += 2) h.push_back(f[i]);
+  while (h.size() > 1 && h.back() == 0) h.pop_back();
+  BufP y = ev_mul(C, x, x, st);
+  Powers P(C, y, st);
+  Term H = bsgs(C, h, P, st);
+  BufP T = P.get((p - 1) / 2);
+  BufP a = mul_term(C, x, H, st);
+  BufP b = ev_scalar(C, 0, T, f[p - 1], st);
+  lt = ev_add(C, a, b, st);
+  eq = ev_scalar(C, 1, ev_scalar(C, 0, T, -1, st), 1, st);
+  note(C, "cmp digit -> LT " + L_(lt->level) + " EQ " + L_(eq->level));
+}
+
+// Algorithm 4
+BufP ev_compare_lt(Context& C, const BufP& a, const BufP& b, cudaStream_t st) {
+  int r = C.r;
+  BufP d = ev_sub(C, a, b, st);
+  std::vector<BufP> dg = ev_reduce(C, d, st);
+  std::vector<BufP> LT(r), EQ(r);
+  for (int i = 0; i < r; ++i) compare_digit(C, dg[i], LT[i], EQ[i], st);
+  BufP lt = LT[r - 1], eq = EQ[r - 1];
+  for (int i = r - 2; i >= 0; --i) {
+    lt = ev_add(C, lt, ev_mul(C, eq, LT[i], st), st);
+    if (i > 0) eq = ev_mul(C, eq, EQ[i], st);
+  }
+  note(C, "LT -> " + L_(lt->level));
+  return lt;
+}
+
+// Section 4.4
+BufP ev_raise(Context& C, const BufP& a, cudaStream_t st) {
+  if (a->t_exp != 1) throw Error(SS_ERR_TMOD, "raise input must be at t = p");
+  auto k = std::make_shared<Buf>(*a);
+  k->owned = false;
+  k->parent = a;
+  k->t_exp = C.r;
+  BufP out = ev_eval_g(C, k, C.r, st);
+  note(C, "raise -> " + L_(out->level));
+  return out;
+}
+
+BufP ev_rotate_sum(Context& C, const BufP& a, cudaStream_t st) {
+  BufP s = a;
+  for (int g : rotate_sum_elements(C)) {
+    BufP r = alloc_buf(C, s->count, 2, s->level, s->t_exp, st);
+    if (!C.dry) op_rotate(C, *s, g, *r, st);
+    s = ev_add(C, s, r, st);
+    note(C, "rot " + std::to_string(g));
+  }
+  return s;
+}
+
+static BufP batch_total(Context& C, const BufP& R, cudaStream_t st) {
+  if (R->count == 1) return R;
+  BufP out = alloc_buf(C, 1, R->ncomp, R->level, R->t_exp, st);
+  if (!C.dry) k_batch_sum(C, *R, *out, st);
+  return out;
+}
+
+// SUM(A*B WHERE C1 < C2) per ciphertext: ind = Raise(LT(C1, C2)), R = ind*(A*B),
+// total = rotate_sum(sum R). Ciphertexts are processed C.batch at a time.
+BufP ev_query(Context& C, const BufP& A, const BufP& B, const BufP& C1, const BufP& C2, cudaStream_t st) {
+  int n = A->count;
+  if (B->count != n || C1->count != n || (C2->count != n && C2->count != 1))
+    throw Error(SS_ERR_SHAPE, "column batch sizes differ");
+  BufP total;
+  int step = std::max(1, C.batch);
+  for (int b0 = 0; b0 < n; b0 += step) {
+    int cnt = std::min(step, n - b0);
+    BufP a = slice_buf(A, b0, cnt, C.N), b = slice_buf(B, b0, cnt, C.N), c1 = slice_buf(C1, b0, cnt, C.N);
+    BufP c2 = C2->count == 1 ? C2 : slice_buf(C2, b0, cnt, C.N);
+    BufP ind = ev_raise(C, ev_compare_lt(C, c1, c2, st), st);
+    BufP prod = ev_mul(C, a, b, st);
+    BufP R = ev_mul(C, ind, prod, st);
+    BufP part = batch_total(C, R, st);
+    total = total ? ev_add(C, total, part, st) : part;
+  }
+  return ev_rotate_sum(C, total, st);
+}
+
+int plan_query_depth(Context& C, int level) {
+  bool dry = C.dry, tr = C.trace_on;
+  C.dry = true;
+  C.trace_on = false;
+  int out = -1;
+  try {
+    auto mk = [&](int cnt) {
+      auto b = std::make_shared<Buf>();
+      b->count = cnt;
+      b->ncomp = 2;
+      b->level = level;
+      b->t_exp = C.r;
+      b->cap = level;
+      return b;
+    };
+    BufP x = mk(1);
+    BufP r = ev_query(C, x, x, x, x, nullptr);
+    out = r->level;
+  } catch (...) {
+    C.dry = dry;
+    C.trace_on = tr;
+    throw;
+  }
+  C.dry = dry;
+  C.trace_on = tr;
+  return out;
+}
+
+}  // namespace ss

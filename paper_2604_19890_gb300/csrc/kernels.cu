@@ -1,0 +1,488 @@
+// Streaming kernels of the BGV hot path: elementwise RNS arithmetic, the
+// tensor product, fast base conversion (ModUp / ModDown / modulus switching),
+// the key-switching inner product, automorphisms in evaluation form, Philox
+// sampling and the CRT step of decryption.
+//
+// All of them are bound by HBM traffic on limb-major [.. ][limb][N] arrays:
+// threads walk the coefficient index n, so every warp touches 32 consecutive
+// 8-byte words of one limb (256 B, fully coalesced).
+#include <cstdio>
+
+#include "modarith.cuh"
+#include "philox.h"
+#include "ss_internal.h"
+
+namespace ss {
+
+namespace {
+
+constexpr int TPB = 256;
+
+__device__ __forceinline__ const Modulus& MOD(const ModDesc* m, int i) {
+  return reinterpret_cast<const Modulus*>(m)[i];
+}
+
+dim3 grid_for(int N, int polys) {
+  int bx = (N + TPB - 1) / TPB;
+  return dim3(bx, polys);
+}
+
+// ---------------------------------------------------------------- add / sub
+__global__ void k_binary_impl(int op, const u64* a, const u64* b, u64* out, int N, int ncomp, int level, int acap,
+                              int bcap, int ocap, int bcast, const ModDesc* mods) {
+  int poly = blockIdx.y;  // (bt, c, i)
+  int i = poly % level, c = (poly / level) % ncomp, bt = poly / (level * ncomp);
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  u64 q = MOD(mods, i).q;
+  int bb = bcast ? 0 : bt;
+  u64 x = a[((size_t)(bt * ncomp + c) * acap + i) * N + n];
+  u64 y = b[((size_t)(bb * ncomp + c) * bcap + i) * N + n];
+  out[((size_t)(bt * ncomp + c) * ocap + i) * N + n] = op == 0 ? add_mod(x, y, q) : sub_mod(x, y, q);
+}
+
+// ---------------------------------------------------------------- scalars
+__global__ void k_scalar_impl(int op, const u64* a, i64 c, u64* out, int N, int ncomp, int level, int acap,
+                              int ocap, const ModDesc* mods, const u64* pinv) {
+  __shared__ u64 sw[2];
+  int poly = blockIdx.y;
+  int i = poly % level, comp = (poly / level) % ncomp, bt = poly / (level * ncomp);
+  const Modulus& md = MOD(mods, i);
+  u64 q = md.q;
+  if (threadIdx.x == 0) {
+    u64 w;
+    if (op == 2) {
+      sw[0] = pinv[2 * i];
+      sw[1] = pinv[2 * i + 1];
+    } else {
+      if (c >= 0) w = (u64)c % q;
+      else { u64 k = (u64)(-(c + 1)) % q; w = q - 1 - k; }
+      sw[0] = w;
+      sw[1] = (u64)(((u128)w << 64) / q);
+    }
+  }
+  __syncthreads();
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  u64 x = a[((size_t)(bt * ncomp + comp) * acap + i) * N + n];
+  u64 y;
+  if (op == 1) y = comp == 0 ? add_mod(x, sw[0], q) : x;
+  else y = shoup(x, sw[0], sw[1], q);
+  out[((size_t)(bt * ncomp + comp) * ocap + i) * N + n] = y;
+}
+
+__global__ void k_copy_impl(const u64* a, u64* out, int N, int ncomp, int level, int acap, int ocap) {
+  int poly = blockIdx.y;
+  int i = poly % level, comp = (poly / level) % ncomp, bt = poly / (level * ncomp);
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  out[((size_t)(bt * ncomp + comp) * ocap + i) * N + n] = a[((size_t)(bt * ncomp + comp) * acap + i) * N + n];
+}
+
+// ---------------------------------------------------------------- tensor
+__global__ void k_tensor_impl(const u64* a, const u64* b, u64* out, int N, int level, int acap, int bcap, int ocap,
+                              const ModDesc* mods) {
+  int poly = blockIdx.y;  // (bt, i)
+  int i = poly % level, bt = poly / level;
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const Modulus& md = MOD(mods, i);
+  size_t la = (size_t)acap * N, lb = (size_t)bcap * N, lo = (size_t)ocap * N;
+  const u64* A = a + (size_t)bt * 2 * la + (size_t)i * N + n;
+  const u64* B = b + (size_t)bt * 2 * lb + (size_t)i * N + n;
+  u64* O = out + (size_t)bt * 3 * lo + (size_t)i * N + n;
+  u64 a0 = A[0], a1 = A[la], b0 = B[0], b1 = B[lb];
+  O[0] = mul_mod(a0, b0, md);
+  Acc128 x;
+  x.zero();
+  x.mac(a0, b1);
+  x.mac(a1, b0);
+  O[lo] = barrett_reduce128(x.hi, x.lo, md);
+  O[2 * lo] = mul_mod(a1, b1, md);
+}
+
+// ---------------------------------------------------------------- base conversion
+// dst limb m (global prime g(m) = m < nq ? m : L + m - nq), m outside
+// [skip_lo, skip_hi):  sum_s [src_s * c1_s]_{q_s} * c2[s][g(m)]  (mod q_g), then
+// times post[g] when post != null.
+template <int MAXS>
+__global__ void k_bconv_impl(const u64* src, long src_os, int ns, int sp0, const u64* c1, const u64* c2, int T,
+                             u64* dst, long dst_os, int nd, int nq, int L, int skip_lo, int skip_hi, const u64* post,
+                             int N, const ModDesc* mods) {
+  int o = blockIdx.y;
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  u64 y[MAXS];
+#pragma unroll
+  for (int s = 0; s < MAXS; ++s) {
+    if (s < ns) {
+      u64 q = MOD(mods, sp0 + s).q;
+      u64 x = src[(long)o * src_os + (long)s * N + n];
+      y[s] = shoup(x, c1[2 * s], c1[2 * s + 1], q);
+    }
+  }
+  for (int m = 0; m < nd; ++m) {
+    if (m >= skip_lo && m < skip_hi) continue;
+    int g = m < nq ? m : L + (m - nq);
+    const Modulus& md = MOD(mods, g);
+    Acc128 acc;
+    acc.zero();
+#pragma unroll
+    for (int s = 0; s < MAXS; ++s)
+      if (s < ns) acc.mac(y[s], __ldg(c2 + (long)s * T + g));
+    u64 v = barrett_reduce128(acc.hi, acc.lo, md);
+    if (post) v = shoup(v, __ldg(post + 2 * g), __ldg(post + 2 * g + 1), md.q);
+    dst[(long)o * dst_os + (long)m * N + n] = v;
+  }
+}
+
+// out[m] = (a[m] - d[m]) * scale[m] (+ add[m]); limb m is data prime m.
+__global__ void k_sub_scale_impl(const u64* a, long a_os, const u64* dl, long d_os, const u64* scale, const u64* add,
+                                 long add_os, u64* out, long out_os, int nl, int N, const ModDesc* mods) {
+  int poly = blockIdx.y;
+  int m = poly % nl, o = poly / nl;
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  u64 q = MOD(mods, m).q;
+  u64 x = sub_mod(a[(long)o * a_os + (long)m * N + n], dl[(long)o * d_os + (long)m * N + n], q);
+  x = shoup(x, __ldg(scale + 2 * m), __ldg(scale + 2 * m + 1), q);
+  if (add) x = add_mod(x, add[(long)o * add_os + (long)m * N + n], q);
+  out[(long)o * out_os + (long)m * N + n] = x;
+}
+
+// ---------------------------------------------------------------- key-switch inner product
+// acc[comp][m] = sum_j ext_j[m] * key_j[comp][g(m)], with ext_j[m] = d[m] on the
+// digit's own primes. 128-bit lazy sum over the digits, one reduction.
+__global__ void k_ks_ip_impl(const u64* d, long d_os, const u64* ext, long ext_os, const u64* kb, const u64* ka,
+                             int level, int alpha, int L, int T, u64* acc, long acc_os, int n_outer, int N,
+                             const ModDesc* mods) {
+  int m = blockIdx.y;  // local limb over level + alpha
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  int g = m < level ? m : L + (m - level);
+  const Modulus& md = MOD(mods, g);
+  int dn = (level + alpha - 1) / alpha;
+  int nlx = level + alpha;
+  for (int o = 0; o < n_outer; ++o) {
+    Acc128 s0, s1;
+    s0.zero();
+    s1.zero();
+    for (int j = 0; j < dn; ++j) {
+      bool own = m < level && m / alpha == j;
+      u64 x = own ? d[(long)o * d_os + (long)m * N + n] : ext[(long)o * ext_os + ((long)j * nlx + m) * N + n];
+      size_t ko = ((size_t)j * T + g) * N + n;
+      s0.mac(x, __ldg(kb + ko));
+      s1.mac(x, __ldg(ka + ko));
+    }
+    acc[(long)o * acc_os + (long)m * N + n] = barrett_reduce128(s0.hi, s0.lo, md);
+    acc[(long)o * acc_os + ((long)nlx + m) * N + n] = barrett_reduce128(s1.hi, s1.lo, md);
+  }
+}
+
+// ---------------------------------------------------------------- automorphism
+// evaluation form: word j holds a(psi^(2 brv(j)+1)); sigma_g(a) at that point is
+// a(psi^(g (2 brv(j)+1))), i.e. the word at brv((g (2 brv(j)+1) mod 2N - 1)/2).
+__global__ void k_automorph_impl(const u64* a, u64* out, int g, int N, int logN, int nrows, int acap, int ocap,
+                                 int level) {
+  int poly = blockIdx.y;  // (bt*ncomp + c, i)
+  int i = poly % level, row = poly / level;
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  unsigned rj = __brev((unsigned)j) >> (32 - logN);
+  unsigned k = (unsigned)(((unsigned long long)g * (2 * rj + 1)) % (2u * (unsigned)N));
+  unsigned src = __brev((k - 1) / 2) >> (32 - logN);
+  out[((size_t)row * ocap + i) * N + j] = a[((size_t)row * acap + i) * N + src];
+}
+
+// ---------------------------------------------------------------- sampling
+__global__ void k_uniform_impl(u64* out, long out_os, int nl, int q0, int nq, int L, u32 id0, u32 tag, u32 k0,
+                               u32 k1, int N, const ModDesc* mods) {
+  int poly = blockIdx.y;
+  int i = poly % nl, o = poly / nl;
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  int g = i < nq ? q0 + i : L + (i - nq);
+  const Modulus& md = MOD(mods, g);
+  Philox4 r = philox((u32)n, (u32)g, id0 + (u32)o, tag, k0, k1);
+  u64 lo = ((u64)r.x[1] << 32) | r.x[0];
+  u64 hi = ((u64)r.x[3] << 32) | r.x[2];
+  // (hi 2^64 + lo) mod q = (hi mod q)(2^64 mod q) + lo mod q
+  u64 R = barrett_reduce128(1, 0, md);
+  u64 h = barrett_reduce128(0, hi, md);
+  u64 v = add_mod(mul_mod(h, R, md), barrett_reduce128(0, lo, md), md.q);
+  out[(long)o * out_os + (long)i * N + n] = v;
+}
+
+__global__ void k_cbd_impl(i64* out, u32 id0, u32 tag, u32 k0, u32 k1, int N) {
+  int o = blockIdx.y;
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  Philox4 r = philox((u32)n, 0u, id0 + (u32)o, tag, k0, k1);
+  out[(long)o * N + n] = (i64)__popc(r.x[0] & 0x1FFFFFu) - (i64)__popc(r.x[1] & 0x1FFFFFu);
+}
+
+// out[o][i] = (m[o] + tmul * e[o]) mod q_g  (coefficient form)
+__global__ void k_lift_small_impl(const i64* e, const u64* m, u64 tmul, u64* out, long out_os, int nl, int q0,
+                                  int nq, int L, int N, const ModDesc* mods) {
+  int poly = blockIdx.y;
+  int i = poly % nl, o = poly / nl;
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  int g = i < nq ? q0 + i : L + (i - nq);
+  const Modulus& md = MOD(mods, g);
+  u64 q = md.q;
+  i64 ev = e ? e[(long)o * N + n] : 0;
+  u64 el = ev >= 0 ? (u64)ev : q - (u64)(-ev);
+  u64 v = mul_mod(el, tmul, md);  // tmul, m < p^r < q (checked at context creation)
+  if (m) v = add_mod(v, m[(long)o * N + n], q);
+  out[(long)o * out_os + (long)i * N + n] = v;
+}
+
+// out = x - a * s  (evaluation form); s indexed by global prime
+__global__ void k_mul_sub_impl(const u64* x, long x_os, const u64* a, long a_os, const u64* s, u64* out, long out_os,
+                               int nl, int q0, int nq, int L, int N, const ModDesc* mods) {
+  int poly = blockIdx.y;
+  int i = poly % nl, o = poly / nl;
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  int g = i < nq ? q0 + i : L + (i - nq);
+  const Modulus& md = MOD(mods, g);
+  u64 p = mul_mod(a[(long)o * a_os + (long)i * N + n], s[(long)g * N + n], md);
+  out[(long)o * out_os + (long)i * N + n] = sub_mod(x[(long)o * x_os + (long)i * N + n], p, md.q);
+}
+
+struct GadgetArgs {
+  u64 pmod[16];
+};
+
+// b_j[i] += (P mod q_i) * s'[i] for the data primes i of digit j
+__global__ void k_gadget_impl(u64* b, const u64* sp, int j, int alpha, int L, int T, int N, GadgetArgs G,
+                              const ModDesc* mods) {
+  int k = blockIdx.y;
+  int i = j * alpha + k;
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N || i >= L) return;
+  const Modulus& md = MOD(mods, i);
+  size_t o = ((size_t)j * T + i) * N + n;
+  b[o] = add_mod(b[o], mul_mod(G.pmod[k], sp[(size_t)i * N + n], md), md.q);
+}
+
+// v = c0 + c1 s (+ c2 s^2)
+__global__ void k_dec_dot_impl(const u64* a, int ncomp, int level, int cap, const u64* s, const u64* s2, u64* v,
+                               int N, const ModDesc* mods) {
+  int poly = blockIdx.y;  // (bt, i)
+  int i = poly % level, bt = poly / level;
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const Modulus& md = MOD(mods, i);
+  size_t lc = (size_t)cap * N;
+  const u64* A = a + (size_t)bt * ncomp * lc + (size_t)i * N + n;
+  Acc128 acc;
+  acc.zero();
+  acc.add(A[0]);
+  acc.mac(A[lc], s[(size_t)i * N + n]);
+  if (ncomp == 3) acc.mac(A[2 * lc], s2[(size_t)i * N + n]);
+  v[((size_t)bt * level + i) * N + n] = barrett_reduce128(acc.hi, acc.lo, md);
+}
+
+// Garner mixed-radix CRT of one coefficient, centred against (Q-1)/2, mod p^e.
+__global__ void k_crt_impl(const u64* v, int level, int N, int d, int slots, const u64* pinv, const u64* half,
+                           const u64* qmodt, u64 te, u64* out, const ModDesc* mods) {
+  int bt = blockIdx.y;
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= slots) return;
+  int n = k * d;
+  u64 dig[200];
+  for (int i = 0; i < level; ++i) {
+    const Modulus& md = MOD(mods, i);
+    u64 q = md.q;
+    u64 x = v[((size_t)bt * level + i) * N + n];
+    u64 acc = 0;
+    for (int j = i - 1; j >= 0; --j) {
+      u64 qj = MOD(mods, j).q;
+      u64 qjm = qj >= q ? qj - q : qj;
+      acc = add_mod(mul_mod(acc, qjm, md), dig[j], q);
+    }
+    dig[i] = i == 0 ? x : mul_mod(sub_mod(x, acc, q), pinv[i], md);
+  }
+  int neg = 0;
+  for (int i = level - 1; i >= 0; --i) {
+    if (dig[i] != half[i]) { neg = dig[i] > half[i]; break; }
+  }
+  u64 m = 0;
+  for (int i = 0; i < level; ++i) m = (m + (u64)(((u128)(dig[i] % te) * qmodt[i]) % te)) % te;
+  if (neg) m = (m + te - qmodt[level]) % te;
+  out[(size_t)bt * N + n] = m;
+}
+
+// out[g] = a[g]^2 for every prime g (evaluation form)
+__global__ void k_square_impl(const u64* a, u64* out, int N, const ModDesc* mods) {
+  int g = blockIdx.y;
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  u64 x = a[(size_t)g * N + n];
+  out[(size_t)g * N + n] = mul_mod(x, x, MOD(mods, g));
+}
+
+// out[c][i] = sum_b a[b][c][i]
+__global__ void k_batch_sum_impl(const u64* a, u64* out, int count, int ncomp, int level, int acap, int ocap, int N,
+                                 const ModDesc* mods) {
+  int poly = blockIdx.y;  // (c, i)
+  int i = poly % level, c = poly / level;
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  u64 q = MOD(mods, i).q;
+  u64 s = 0;
+  for (int b = 0; b < count; ++b) s = add_mod(s, a[((size_t)(b * ncomp + c) * acap + i) * N + n], q);
+  out[((size_t)c * ocap + i) * N + n] = s;
+}
+
+}  // namespace
+
+// ======================================================================= launchers
+void k_square(Context& C, const u64* a, u64* out, int nprimes, cudaStream_t st) {
+  k_square_impl<<<grid_for(C.N, nprimes), TPB, 0, st>>>(a, out, C.N, C.d_mod);
+  ++C.launches;
+  SS_CUDA(cudaGetLastError());
+}
+
+void k_batch_sum(Context& C, const Buf& a, Buf& out, cudaStream_t st) {
+  k_batch_sum_impl<<<grid_for(C.N, a.ncomp * a.level), TPB, 0, st>>>(a.data, out.data, a.count, a.ncomp, a.level,
+                                                                      a.cap, out.cap, C.N, C.d_mod);
+  ++C.launches;
+  SS_CUDA(cudaGetLastError());
+}
+
+#define LAUNCHED() do { ++C.launches; SS_CUDA(cudaGetLastError()); } while (0)
+
+void k_binary(Context& C, int op, const Buf& a, const Buf& b, Buf& out, cudaStream_t st) {
+  int polys = a.count * a.ncomp * a.level;
+  k_binary_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(op, a.data, b.data, out.data, C.N, a.ncomp, a.level, a.cap,
+                                                       b.cap, out.cap, b.count == 1 && a.count > 1, C.d_mod);
+  LAUNCHED();
+}
+
+void k_scalar(Context& C, int op, const Buf& a, i64 c, Buf& out, cudaStream_t st) {
+  int polys = a.count * a.ncomp * a.level;
+  k_scalar_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(op, a.data, c, out.data, C.N, a.ncomp, a.level, a.cap,
+                                                       out.cap, C.d_mod, C.d_pinv);
+  LAUNCHED();
+}
+
+void k_copy_limbs(Context& C, const Buf& a, Buf& out, int level, cudaStream_t st) {
+  int polys = a.count * a.ncomp * level;
+  k_copy_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(a.data, out.data, C.N, a.ncomp, level, a.cap, out.cap);
+  LAUNCHED();
+}
+
+void k_tensor(Context& C, const Buf& a, const Buf& b, Buf& out, cudaStream_t st) {
+  int polys = a.count * a.level;
+  k_tensor_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(a.data, b.data, out.data, C.N, a.level, a.cap, b.cap, out.cap,
+                                                       C.d_mod);
+  LAUNCHED();
+}
+
+void k_bconv(Context& C, const u64* src, long src_os, int ns, int sp0, const u64* c1, const u64* c2, u64* dst,
+             long dst_os, int nd, int nq, int skip_lo, int skip_hi, const u64* post, int n_outer, cudaStream_t st) {
+  dim3 g = grid_for(C.N, n_outer);
+  if (ns <= 4)
+    k_bconv_impl<4><<<g, TPB, 0, st>>>(src, src_os, ns, sp0, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo,
+                                        skip_hi, post, C.N, C.d_mod);
+  else if (ns <= 16)
+    k_bconv_impl<16><<<g, TPB, 0, st>>>(src, src_os, ns, sp0, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo,
+                                         skip_hi, post, C.N, C.d_mod);
+  else if (ns <= 64)
+    k_bconv_impl<64><<<g, TPB, 0, st>>>(src, src_os, ns, sp0, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo,
+                                         skip_hi, post, C.N, C.d_mod);
+  else
+    throw Error(SS_ERR_PARAM, "base conversion from more than 64 primes");
+  LAUNCHED();
+}
+
+void k_sub_scale(Context& C, const u64* a, long a_os, const u64* dl, long d_os, const u64* scale, const u64* add,
+                 long add_os, u64* out, long out_os, int nl, int n_outer, cudaStream_t st) {
+  k_sub_scale_impl<<<grid_for(C.N, nl * n_outer), TPB, 0, st>>>(a, a_os, dl, d_os, scale, add, add_os, out, out_os,
+                                                                 nl, C.N, C.d_mod);
+  LAUNCHED();
+}
+
+void k_ks_ip(Context& C, const u64* d, long d_os, const u64* ext, long ext_os, const KeyDev& K, int level, u64* acc,
+             long acc_os, int n_outer, cudaStream_t st) {
+  k_ks_ip_impl<<<grid_for(C.N, level + C.alpha), TPB, 0, st>>>(d, d_os, ext, ext_os, K.b, K.a, level, C.alpha, C.L,
+                                                                C.ntot, acc, acc_os, n_outer, C.N, C.d_mod);
+  LAUNCHED();
+}
+
+void k_automorph(Context& C, const Buf& a, int g, Buf& out, cudaStream_t st) {
+  int rows = a.count * a.ncomp;
+  k_automorph_impl<<<grid_for(C.N, rows * a.level), TPB, 0, st>>>(a.data, out.data, g, C.N, C.logN, rows, a.cap,
+                                                                   out.cap, a.level);
+  LAUNCHED();
+}
+
+static void seed_words(const Context& C, u32& k0, u32& k1) {
+  k0 = (u32)(C.prm.seed & 0xffffffffu);
+  k1 = (u32)(C.prm.seed >> 32);
+}
+
+void k_uniform(Context& C, u64* out, long out_os, int n_outer, int nl, int q0, int nq, u32 id0, u32 tag,
+               cudaStream_t st) {
+  u32 k0, k1;
+  seed_words(C, k0, k1);
+  k_uniform_impl<<<grid_for(C.N, n_outer * nl), TPB, 0, st>>>(out, out_os, nl, q0, nq, C.L, id0, tag, k0, k1, C.N,
+                                                               C.d_mod);
+  LAUNCHED();
+}
+
+void k_cbd(Context& C, i64* out, int n_outer, u32 id0, u32 tag, cudaStream_t st) {
+  u32 k0, k1;
+  seed_words(C, k0, k1);
+  k_cbd_impl<<<grid_for(C.N, n_outer), TPB, 0, st>>>(out, id0, tag, k0, k1, C.N);
+  LAUNCHED();
+}
+
+void k_lift_small(Context& C, const i64* e, const u64* m, u64 tmul, u64* out, long out_os, int n_outer, int nl,
+                  int q0, int nq, cudaStream_t st) {
+  k_lift_small_impl<<<grid_for(C.N, n_outer * nl), TPB, 0, st>>>(e, m, tmul, out, out_os, nl, q0, nq, C.L, C.N,
+                                                                  C.d_mod);
+  LAUNCHED();
+}
+
+void k_mul_sub(Context& C, const u64* x, long x_os, const u64* a, long a_os, const u64* s, u64* out, long out_os,
+               int n_outer, int nl, int q0, int nq, int, cudaStream_t st) {
+  k_mul_sub_impl<<<grid_for(C.N, n_outer * nl), TPB, 0, st>>>(x, x_os, a, a_os, s, out, out_os, nl, q0, nq, C.L, C.N,
+                                                               C.d_mod);
+  LAUNCHED();
+}
+
+void k_ksk_gadget(Context& C, u64* b, const u64* sprime, int j, cudaStream_t st) {
+  GadgetArgs G;
+  int lo = j * C.alpha, hi = std::min(lo + C.alpha, C.L);
+  if (hi - lo > 16) throw Error(SS_ERR_PARAM, "alpha > 16");
+  for (int i = lo; i < hi; ++i) {
+    u64 q = C.primes[i], P = 1;
+    for (int k = C.L; k < C.ntot; ++k) P = nt::mul(P, C.primes[k] % q, q);
+    G.pmod[i - lo] = P;
+  }
+  if (hi <= lo) return;
+  k_gadget_impl<<<grid_for(C.N, hi - lo), TPB, 0, st>>>(b, sprime, j, C.alpha, C.L, C.ntot, C.N, G, C.d_mod);
+  LAUNCHED();
+}
+
+void k_dec_dot(Context& C, const Buf& a, u64* v, cudaStream_t st) {
+  k_dec_dot_impl<<<grid_for(C.N, a.count * a.level), TPB, 0, st>>>(a.data, a.ncomp, a.level, a.cap, C.d_sk, C.d_sk2,
+                                                                     v, C.N, C.d_mod);
+  LAUNCHED();
+}
+
+void k_crt(Context& C, const u64* v, int count, int level, int t_exp, u64* out, cudaStream_t st) {
+  if (level > 200) throw Error(SS_ERR_PARAM, "level too large for CRT");
+  const u64* pinv = C.d_crt + C.off_crt_pinv;
+  const u64* half = C.d_crt + C.off_crt_half[level];
+  const u64* qmodt = C.d_crt + C.off_crt_qmodt + (size_t)t_exp * (C.L + 1);
+  dim3 g((C.slots + 127) / 128, count);
+  k_crt_impl<<<g, 128, 0, st>>>(v, level, C.N, C.d, C.slots, pinv, half, qmodt, C.tpow[t_exp], out, C.d_mod);
+  LAUNCHED();
+}
+
+}  // namespace ss

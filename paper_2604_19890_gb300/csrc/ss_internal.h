@@ -1,0 +1,201 @@
+// Internal declarations of the GB300 space-switching library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/ss.h"
+
+namespace ss {
+
+typedef uint64_t u64;
+typedef int64_t i64;
+typedef uint32_t u32;
+
+struct Error : std::runtime_error {
+  ss_status code;
+  Error(ss_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define SS_CUDA(x)                                                                          \
+  do {                                                                                      \
+    cudaError_t e_ = (x);                                                                   \
+    if (e_ != cudaSuccess)                                                                  \
+      throw ::ss::Error(e_ == cudaErrorMemoryAllocation ? SS_ERR_OOM : SS_ERR_CUDA,         \
+                        std::string(#x) + ": " + cudaGetErrorString(e_));                   \
+  } while (0)
+
+// ------------------------------------------------------------ host number theory
+namespace nt {
+u64 mul(u64 a, u64 b, u64 m);
+u64 pow(u64 a, u64 e, u64 m);
+u64 inv(u64 a, u64 m);
+u64 lift(i64 c, u64 m);
+bool prime(u64 n);
+u64 shoup(u64 w, u64 q);  // floor(w * 2^64 / q)
+int brv(int x, int logn);
+std::vector<u64> chain(int bits, u64 step, int count);
+u64 root2n(u64 q, int N);
+std::vector<i64> g_coeffs(int p, int e);  // centred mod p^e, odd, degree (e-1)(p-1)+1
+std::vector<i64> flt_coeffs(int p);       // centred mod p
+}  // namespace nt
+
+// Modulus descriptor shared with device code (layout matches Modulus in modarith.cuh)
+struct ModDesc {
+  u64 q, mu;
+  int kbits, pad;
+};
+
+// A batch of ciphertexts with one shape; either a view of caller memory or a
+// pool allocation released on the owning stream.
+struct Buf {
+  u64* data = nullptr;
+  int count = 0, ncomp = 0, level = 0, t_exp = 0, cap = 0;
+  size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+  bool owned = false;
+  std::shared_ptr<Buf> parent;  // keeps the allocation of a slice alive
+  ~Buf();
+  u64* limb(int b, int c, int i, int N) const { return data + ((size_t)(b * ncomp + c) * cap + i) * N; }
+};
+typedef std::shared_ptr<Buf> BufP;
+
+struct KeyDev {
+  u64* b = nullptr;  // [dnum][L+alpha][N]
+  u64* a = nullptr;
+};
+
+struct Context {
+  ss_params prm;
+  int N = 0, logN = 0, L = 0, alpha = 0, ntot = 0, dnum = 0;
+  int p = 0, r = 0;
+  u64 t = 0;  // p^r
+  std::vector<u64> tpow;  // p^e, e = 0..r
+  std::vector<u64> primes, psi;
+  int slots = 0, d = 0;
+  u64 omega = 0;
+  std::vector<int> slot_exp;
+
+  // device tables
+  ModDesc* d_mod = nullptr;           // [ntot]
+  u64* d_tw = nullptr;                // per prime 4N words: psi_brv, shoup, psiinv_brv, shoup
+  u64* d_ninv = nullptr;              // [ntot][2] N^{-1}, shoup
+  u64* d_pinv = nullptr;              // [ntot][2] p^{-1}, shoup
+  u64* d_tmod = nullptr;              // [r+1][ntot][2]: p^e mod q, shoup
+  u64* d_tables = nullptr;            // base-conversion constants (offsets below)
+  size_t tables_words = 0;
+  // ModUp: key (j, e) -> offset of c1[k], c1s[k], c2[k][ntot]
+  std::map<std::pair<int, int>, size_t> off_modup;
+  // ModDown: t_exp -> offset of c1[alpha], c1s[alpha]; c2 [alpha][ntot]; Pinv[ntot][2]
+  std::vector<size_t> off_md_c1;
+  size_t off_md_c2 = 0, off_md_pinv = 0;
+  // modswitch: (level, k) -> offset of c2[k][ntot], Qinv[ntot][2]; (level,k,t_exp) -> c1
+  std::map<std::pair<int, int>, size_t> off_ms;
+  std::map<std::tuple<int, int, int>, size_t> off_ms_c1;
+  // decryption CRT: inv of prefix products, per-level half-Q digits, prefix mod t
+  u64* d_crt = nullptr;
+  std::vector<size_t> off_crt_half;  // per level
+  size_t off_crt_pinv = 0, off_crt_qmodt = 0;
+
+  // keys
+  bool have_keys = false;
+  std::vector<i64> sk;
+  u64* d_sk = nullptr;  // NTT(s) per prime [ntot][N]
+  u64* d_sk2 = nullptr; // NTT(s^2) per prime [ntot][N]
+  KeyDev rlk;
+  std::map<int, KeyDev> gk;
+
+  // evaluator
+  int batch = 8;
+  bool dry = false;  // plan only: track levels, launch nothing
+  bool trace_on = false;
+  std::vector<std::string> trace;
+  unsigned long long launches = 0;
+
+  ~Context();
+};
+
+// ------------------------------------------------------------------ memory
+BufP alloc_buf(Context& C, int count, int ncomp, int level, int t_exp, cudaStream_t s);
+BufP view_buf(const ss_ct& c);
+BufP slice_buf(const BufP& a, int b0, int count, int N);
+void* pool_alloc(size_t bytes, cudaStream_t s);
+void pool_free(void* p, cudaStream_t s);
+
+// ------------------------------------------------------------------ launchers
+// Polys (o, i) at base + o*outer_stride + i*N, i < nl; global prime of limb i:
+// i < nq ? q0 + i : L + (i - nq). Limbs inside [skip_lo, skip_hi) of digit
+// (o % skip_mod) * skip_w .. are skipped when skip_w > 0 (ModUp outputs).
+struct PolySet {
+  u64* base;
+  long outer_stride;
+  int n_outer, nl, q0, nq;
+  int skip_w = 0, skip_mod = 1, skip_level = 0;
+};
+void ntt_forward(Context& C, const PolySet& s, cudaStream_t st);
+void ntt_inverse(Context& C, const PolySet& s, cudaStream_t st);
+
+void k_binary(Context& C, int op, const Buf& a, const Buf& b, Buf& out, cudaStream_t st);  // 0 add, 1 sub
+void k_scalar(Context& C, int op, const Buf& a, i64 c, Buf& out, cudaStream_t st);       // 0 mul, 1 add(c0), 2 mul p^-1
+void k_copy_limbs(Context& C, const Buf& a, Buf& out, int level, cudaStream_t st);
+void k_tensor(Context& C, const Buf& a, const Buf& b, Buf& out, cudaStream_t st);
+void k_bconv(Context& C, const u64* src, long src_os, int ns, int sp0, const u64* c1, const u64* c2, u64* dst,
+             long dst_os, int nd, int nq, int skip_lo, int skip_hi, const u64* post, int n_outer, cudaStream_t st);
+void k_sub_scale(Context& C, const u64* a, long a_os, const u64* dl, long d_os, const u64* scale, const u64* add,
+                 long add_os, u64* out, long out_os, int nl, int n_outer, cudaStream_t st);
+void k_ks_ip(Context& C, const u64* d, long d_os, const u64* ext, long ext_os, const KeyDev& K, int level,
+             u64* acc, long acc_os, int n_outer, cudaStream_t st);
+void k_automorph(Context& C, const Buf& a, int g, Buf& out, cudaStream_t st);
+void k_uniform(Context& C, u64* out, long out_os, int n_outer, int nl, int q0, int nq, u32 id0, u32 tag,
+               cudaStream_t st);
+void k_cbd(Context& C, i64* out, int n_outer, u32 id0, u32 tag, cudaStream_t st);
+void k_lift_small(Context& C, const i64* e, const u64* m, u64 tmul, u64* out, long out_os, int n_outer, int nl,
+                  int q0, int nq, cudaStream_t st);
+void k_mul_sub(Context& C, const u64* x, long x_os, const u64* a, long a_os, const u64* s, u64* out, long out_os,
+               int n_outer, int nl, int q0, int nq, int s_stride_primes, cudaStream_t st);
+void k_dec_dot(Context& C, const Buf& a, u64* out, cudaStream_t st);
+void k_crt(Context& C, const u64* v, int count, int level, int t_exp, u64* out, cudaStream_t st);
+void k_ksk_gadget(Context& C, u64* b, const u64* sprime, int j, cudaStream_t st);
+void k_square(Context& C, const u64* a, u64* out, int nprimes, cudaStream_t st);
+void k_batch_sum(Context& C, const Buf& a, Buf& out, cudaStream_t st);
+
+// ------------------------------------------------------------------ operations
+void op_encrypt(Context& C, const u64* d_coeffs, int count, u32 nonce0, int t_exp, Buf& out, cudaStream_t st);
+void op_decrypt(Context& C, const Buf& a, u64* d_out, cudaStream_t st);
+void op_keygen(Context& C, const std::vector<int>& galois);
+void op_keyswitch(Context& C, const Buf& in, int comp, const KeyDev& K, const Buf* addend, Buf& out,
+                  cudaStream_t st);  // out = addend + KS(in.comp)
+void op_relin(Context& C, const Buf& a, Buf& out, cudaStream_t st);
+void op_modswitch(Context& C, const Buf& a, int drop, Buf& out, cudaStream_t st);
+void op_rotate(Context& C, const Buf& a, int g, Buf& out, cudaStream_t st);
+
+// evaluator (batched, one plan for every ciphertext of a batch)
+BufP ev_modswitch_to(Context& C, const BufP& a, int level, cudaStream_t st);
+BufP ev_mul(Context& C, const BufP& a, const BufP& b, cudaStream_t st);
+BufP ev_add(Context& C, const BufP& a, const BufP& b, cudaStream_t st);
+BufP ev_sub(Context& C, const BufP& a, const BufP& b, cudaStream_t st);
+BufP ev_scalar(Context& C, int op, const BufP& a, i64 c, cudaStream_t st);
+BufP ev_eval_g(Context& C, const BufP& x, int e, cudaStream_t st);
+std::vector<BufP> ev_reduce(Context& C, const BufP& a, cudaStream_t st);
+BufP ev_compare_lt(Context& C, const BufP& a, const BufP& b, cudaStream_t st);
+BufP ev_raise(Context& C, const BufP& a, cudaStream_t st);
+BufP ev_rotate_sum(Context& C, const BufP& a, cudaStream_t st);
+BufP ev_query(Context& C, const BufP& A, const BufP& B, const BufP& C1, const BufP& C2, cudaStream_t st);
+int plan_query_depth(Context& C, int level);
+std::vector<int> rotate_sum_elements(const Context& C);
+
+// host-side setup
+void build_context(Context& C, const ss_params& prm);
+std::vector<u64> encode(const Context& C, int t_exp, const u64* slots);
+std::vector<u64> decode(const Context& C, int t_exp, const u64* coeffs);
+
+inline void note(Context& C, const std::string& s) {
+  if (C.trace_on) C.trace.push_back(s);
+}
+
+}  // namespace ss

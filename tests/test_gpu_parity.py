@@ -1,0 +1,226 @@
+"""GPU path vs the CPU reference, word for word (all arithmetic is exact modular
+integer arithmetic, so the tolerance is zero), through the C-ABI.
+
+Small rings (N = 64) cover every operation and the space-switching
+procedures; larger rings cover the transform and the batched kernels with
+several tiles and ragged batch sizes.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import plain
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_ctx(**kw):
+    import paper_2604_19890_gb300 as ssg
+    return ssg.Context(**kw)
+
+
+def make_pair(logN=6, L=26, alpha=2, bits=36, p=17, r=2, h=16, seed=7, galois=None, keys=True):
+    g = gpu_ctx(logN=logN, L=L, alpha=alpha, bits=bits, p=p, r=r, h=h, nmax=0, seed=seed)
+    o = O.Oracle(logN=logN, L=L, alpha=alpha, bits=bits, p=p, r=r, h=h, seed=seed)
+    if keys:
+        gal = g.rotate_sum_elements() if galois is None else galois
+        g.keygen(gal)
+        o.keygen(gal)
+    return g, o
+
+
+def same(gct, oct_list):
+    """GPU batch words == oracle words for every ciphertext of the batch."""
+    w = gct.words()
+    assert w.shape[0] == len(oct_list)
+    for b, oc in enumerate(oct_list):
+        assert (gct.ncomp, gct.level, gct.t_exp) == (oc.ncomp, oc.level, oc.t_exp)
+        ow = oc.words()
+        assert w[b].shape == ow.shape
+        diff = np.argwhere(w[b] != ow)
+        assert diff.size == 0, "first differing word %s of %d" % (diff[0], len(diff))
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return make_pair()
+
+
+def encrypt_both(g, o, vals, nonce0):
+    vals = np.atleast_2d(np.asarray(vals, dtype=np.uint64))
+    gc = g.encrypt(np.stack([g.encode(v) for v in vals]), nonce0)
+    oc = [o.encrypt(o.encode(v), nonce0 + i) for i, v in enumerate(vals)]
+    return gc, oc
+
+
+def test_context_tables_match(tiny):
+    g, o = tiny
+    assert (g.primes == o.primes()).all()
+    assert g.slots == o.slots and g.d == o.d
+
+
+@pytest.mark.parametrize("logN", [3, 6, 12, 13, 14, 15, 16])
+def test_ntt_parity(logN):
+    import torch
+    L = 3
+    g = gpu_ctx(logN=logN, L=L, alpha=1, bits=55, p=257, r=2, h=4, nmax=0, seed=1)
+    o = O.Oracle(logN=logN, L=L, alpha=1, bits=55, p=257, r=2, h=4, seed=1)
+    rng = np.random.default_rng(logN)
+    npoly = 2 * L + 1 if logN <= 13 else L  # ragged batch: more polys than primes
+    npoly -= npoly % L
+    data = np.stack([rng.integers(0, int(g.primes[i % L]), g.N, dtype=np.uint64) for i in range(npoly)])
+    t = torch.from_numpy(data.view(np.int64).copy()).cuda()
+    g.ntt_forward(t, 0, L)
+    fw = t.cpu().numpy().view(np.uint64).copy()
+    for i in range(npoly):
+        assert (fw[i] == o.ntt_fwd(i % L, data[i])).all(), i
+    g.ntt_inverse(t, 0, L)
+    assert (t.cpu().numpy().view(np.uint64) == data).all()
+
+
+def test_encrypt_batch_parity(tiny):
+    g, o = tiny
+    rng = np.random.default_rng(1)
+    vals = rng.integers(0, g.t, (3, g.slots))
+    gc, oc = encrypt_both(g, o, vals, 40)
+    same(gc, oc)
+    assert (g.decrypt_slots(gc) == vals).all()
+
+
+def test_ops_parity(tiny):
+    g, o = tiny
+    rng = np.random.default_rng(2)
+    A = rng.integers(0, g.t, (2, g.slots))
+    B = rng.integers(0, g.t, (2, g.slots))
+    ga, oa = encrypt_both(g, o, A, 100)
+    gb, ob = encrypt_both(g, o, B, 200)
+    same(g.add(ga, gb), [o.add(x, y) for x, y in zip(oa, ob)])
+    same(g.sub(ga, gb), [o.sub(x, y) for x, y in zip(oa, ob)])
+    same(g.mul_scalar(ga, -12345), [o.mul_scalar(x, -12345) for x in oa])
+    same(g.add_scalar(ga, 77), [o.add_scalar(x, 77) for x in oa])
+    gt = g.mul(ga, gb)
+    ot = [o.tensor(x, y) for x, y in zip(oa, ob)]
+    same(gt, ot)
+    gr = g.relin(gt)
+    orl = [o.relin(x) for x in ot]
+    same(gr, orl)
+    for drop in (1, 2, 5):
+        same(g.modswitch(gr, drop), [o.modswitch(x, drop) for x in orl])
+    for gel in g.rotate_sum_elements():
+        same(g.rotate(ga, gel), [o.rotate(x, gel) for x in oa])
+    same(g.rotate_sum(ga), [o.rotate_sum(x) for x in oa])
+    # DivideByP on multiples of p
+    gm, om = encrypt_both(g, o, (A * g.p) % g.t, 300)
+    same(g.divide_by_p(gm), [o.divide_by_p(x) for x in om])
+    # decrypted semantics of the GPU results
+    assert (g.decrypt_slots(gr) == (A * B) % g.t).all()
+
+
+def test_eval_g_reduce_compare_raise_parity(tiny):
+    g, o = tiny
+    rng = np.random.default_rng(3)
+    A = rng.integers(0, g.t, (2, g.slots))
+    B = rng.integers(0, g.t, (2, g.slots))
+    ga, oa = encrypt_both(g, o, A, 400)
+    gb, ob = encrypt_both(g, o, B, 500)
+    same(g.eval_g(ga, 2), [o.eval_g(x, 2) for x in oa])
+    gd = g.reduce(ga)
+    od = [o.reduce(x) for x in oa]
+    for i in range(g.r):
+        same(gd[i], [d[i] for d in od])
+    lt = g.compare_lt(ga, gb)
+    olt = [o.compare_lt(x, y) for x, y in zip(oa, ob)]
+    same(lt, olt)
+    exp = np.array([[plain.lt(x, y, g.t) for x, y in zip(ra, rb)] for ra, rb in zip(A, B)])
+    assert (g.decrypt_slots(lt) == exp).all()
+    up = g.raise_modulus(lt)
+    same(up, [o.raise_modulus(x) for x in olt])
+    assert (g.decrypt_slots(up) == exp).all()
+
+
+def test_compare_with_broadcast_threshold(tiny):
+    g, o = tiny
+    rng = np.random.default_rng(4)
+    A = rng.integers(0, g.t, (3, g.slots))
+    T = np.full((1, g.slots), 150)
+    ga, oa = encrypt_both(g, o, A, 600)
+    gt, ot = encrypt_both(g, o, T, 700)
+    lt = g.compare_lt(ga, gt)
+    same(lt, [o.compare_lt(x, ot[0]) for x in oa])
+
+
+@pytest.mark.parametrize("n_ct,batch", [(1, 8), (3, 2), (5, 8)])
+def test_query_parity(tiny, n_ct, batch):
+    g, o = tiny
+    rng = np.random.default_rng(10 + n_ct)
+    cols = {k: rng.integers(0, g.t, (n_ct, g.slots)) for k in ("a", "b", "c1")}
+    thr = np.full((1, g.slots), 150)
+    gA, oA = encrypt_both(g, o, cols["a"], 1000)
+    gB, oB = encrypt_both(g, o, cols["b"], 2000)
+    gC, oC = encrypt_both(g, o, cols["c1"], 3000)
+    gT, oT = encrypt_both(g, o, thr, 4000)
+    g.set_batch(batch)
+    res = g.query(gA, gB, gC, gT)
+    ores = o.query(oA, oB, oC, oT)
+    same(res, [ores])
+    exp = plain.query(cols["a"], cols["b"], cols["c1"], thr, g.t)
+    assert (g.decrypt_slots(res) == exp).all()
+    assert o.noise_budget(ores) > 0
+    g.set_batch(8)
+
+
+def test_schedule_trace_matches_reference(tiny):
+    g, o = tiny
+    rng = np.random.default_rng(5)
+    ga, oa = encrypt_both(g, o, rng.integers(0, g.t, (1, g.slots)), 800)
+    gb, ob = encrypt_both(g, o, rng.integers(0, g.t, (1, g.slots)), 900)
+    g.trace(True)
+    o.trace(True)
+    g.compare_lt(ga, gb)
+    o.compare_lt(oa[0], ob[0])
+    gt, ot = g.trace_text(), o.trace_text()
+    g.trace(False)
+    o.trace(False)
+    assert gt == ot and len(gt.splitlines()) > 20
+
+
+def test_query_depth_matches_reference(tiny):
+    g, o = tiny
+    d = g.query_depth()
+    rng = np.random.default_rng(6)
+    ga, oa = encrypt_both(g, o, rng.integers(0, g.t, (1, g.slots)), 950)
+    res = o.query(oa, oa, oa, oa)
+    assert d == res.level
+
+
+def test_errors_are_reported(tiny):
+    import paper_2604_19890_gb300 as ssg
+    g, o = tiny
+    ga, _ = encrypt_both(g, o, np.zeros((1, g.slots)), 960)
+    low = g.modswitch(ga, 3)
+    with pytest.raises(ssg.SSError) as e:
+        g.add(ga, low)
+    assert e.value.code == ssg.SS_ERR_LEVEL
+    with pytest.raises(ssg.SSError) as e:
+        g.modswitch(ga, ga.level)
+    assert e.value.code == ssg.SS_ERR_LEVEL
+    d = g.divide_by_p(g.encrypt_slots(np.zeros((1, g.slots)), 970))
+    with pytest.raises(ssg.SSError) as e:
+        g.add(ga, d)
+    assert e.value.code == ssg.SS_ERR_TMOD
+    with pytest.raises(ssg.SSError) as e:
+        g.rotate(ga, 3)
+    assert e.value.code == ssg.SS_ERR_PARAM
+
+
+def test_p257_r3_small_ring():
+    g, o = make_pair(logN=5, L=44, alpha=3, bits=55, p=257, r=3, h=8, seed=21)
+    rng = np.random.default_rng(7)
+    A = rng.integers(0, g.t, (2, g.slots))
+    B = rng.integers(0, g.t, (2, g.slots))
+    ga, oa = encrypt_both(g, o, A, 10)
+    gb, ob = encrypt_both(g, o, B, 20)
+    lt = g.compare_lt(ga, gb)
+    same(lt, [o.compare_lt(x, y) for x, y in zip(oa, ob)])
+    exp = np.array([[plain.lt(x, y, g.t) for x, y in zip(ra, rb)] for ra, rb in zip(A, B)])
+    assert (g.decrypt_slots(lt) == exp).all()
