@@ -1,0 +1,329 @@
+"""Benchmark: encrypted compare-then-SUM query throughput on one GB300.
+
+Workload: N = 2^16, 41 data primes of 55 bits + 3 special primes,
+p^r = 257^3, 128 slots per ciphertext; four encrypted columns a, b, c1, c2
+of 32 ciphertexts each (4096 rows, uniform in [0, 257^3)); one step is the
+query SUM(a*b) WHERE c1 < c2 (3-digit comparison, Algorithm 4) over the
+whole table with every input resident in HBM. The inputs (5.5 GB) exceed L2.
+
+Prints one JSON line. `--impl reference` times the plain CPU reference on a
+bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encrypted compare+SUM rows/s at N=2^16; NTT/keyswitch HBM GB/s; p99 latency"
+PRESET = 2
+N_CT = 32
+SEED = 0x5EED0002
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks during the timed region."""
+
+    def __init__(self):
+        self.samples, self.proc, self.thr = [], None, None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", os.environ.get("LOCAL_RANK", "0"),
+                                          "--query-gpu=" + q, "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+
+        def read():
+            for line in self.proc.stdout:
+                self.samples.append([x.strip() for x in line.split(",")])
+        self.thr = threading.Thread(target=read, daemon=True)
+        self.thr.start()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.thr.join(timeout=2)
+        sm = sorted(float(s[0]) for s in self.samples if len(s) >= 7 and s[0].replace(".", "").isdigit())
+        mx = [float(s[1]) for s in self.samples if len(s) >= 7 and s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples if len(s) >= 7 for i in range(4)
+                          if s[3 + i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("SS_BENCH_BACKEND") != "gloo" else "gloo")
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def plain_query(A, B, C1, C2, t):
+    """Plaintext meaning of the query: sum of a*b over rows whose centred
+    difference c1 - c2 (mod t) is negative (Algorithm 4), mod t."""
+    d = (C1.astype(object) - C2.astype(object)) % t
+    keep = d > t // 2
+    return int((A.astype(object) * B.astype(object))[keep].sum()) % t
+
+
+# ------------------------------------------------------------------ CPU reference sample
+def cpu_sample(rows, query_ntts_per_ct, n_ct, level=20):
+    """Times the plain CPU reference on one ciphertext multiply (tensor,
+    relinearisation, modulus switch) at `level` of the N = 2^16, 257^3 chain and
+    scales it to a full query by the query's count of limb transforms (the
+    reference's own count, taken on a small ring where it is the same)."""
+    import numpy as np
+    import oracle as O
+    p = {"logN": 16, "L": level, "alpha": 3, "bits": 55, "p": 257, "r": 3, "h": 120, "seed": SEED}
+    o = O.Oracle(**p)
+    o.keygen([])
+    rng = np.random.default_rng(1)
+    a = o.encrypt_slots(rng.integers(0, o.t, o.slots, dtype=np.uint64), 1)
+    b = o.encrypt_slots(rng.integers(0, o.t, o.slots, dtype=np.uint64), 2)
+    O.ntt_count(True)
+    t0 = time.perf_counter()
+    o.mul(a, b)
+    dt = time.perf_counter() - t0
+    ntts = O.ntt_count()
+    per_ntt = dt / ntts
+    t_query = per_ntt * query_ntts_per_ct * n_ct
+    return rows / t_query, dt, ntts
+
+
+def query_ntt_count(n_ct_small=(1, 2)):
+    """Limb transforms the reference runs for the query, per ciphertext of a
+    column (slope) plus the fixed rotate-and-sum part, on a 256-point ring with
+    the same chain and slot count (the count does not depend on N)."""
+    import numpy as np
+    import oracle as O
+    o = O.Oracle(logN=8, L=41, alpha=3, bits=55, p=257, r=3, h=120, seed=SEED)
+    o.keygen()
+    counts = []
+    for n in n_ct_small:
+        cs = [o.encrypt_slots(np.arange(o.slots, dtype=np.uint64), 100 + i) for i in range(n)]
+        O.ntt_count(True)
+        o.query(cs, cs, cs, cs)
+        counts.append(O.ntt_count())
+    slope = counts[1] - counts[0]
+    return slope, counts[0] - slope
+
+
+def run_reference(args):
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return 0
+    rows = N_CT * 128
+    slope, fixed = query_ntt_count()
+    per_ct = slope + fixed / N_CT
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, dt, ntts = cpu_sample(rows, per_ct, N_CT)
+        if i >= args.warmup:
+            vals.append(v)
+    v = sum(vals) / len(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "rows/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rows / v * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "N=2^16, L=41 x 55-bit + 3 special, p^r=257^3, 32 ct/column (4096 rows)"},
+            "cpu_baseline": {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                             "sample": "per step: one tensor+relin+modswitch at level 20 of the N=2^16 chain "
+                                       "(%d limb transforms), scaled by the query's %.0f transforms per "
+                                       "ciphertext x 32" % (ntts, per_ct)},
+            "e2e": {"value": v, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2604_19890_gb300 as ssg
+    from paper_2604_19890_gb300 import build as ssbuild
+    from paper_2604_19890_gb300 import synth
+
+    rank, world = dist_init()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    ssbuild.build()
+    prm = ssg.preset(PRESET)
+    prm.seed = SEED + 1000 * rank
+    g = ssg.Context(params=prm)
+    g.keygen()
+    g.set_batch(args.batch)
+    t = g.t
+    cols = synth.table(SEED + rank, N_CT, g.slots, t, columns=("a", "b", "c1", "c2"))
+    enc = {}
+    for i, (k, v) in enumerate(cols.items()):
+        enc[k] = g.encrypt(np.stack([g.encode(x) for x in v]), 1000 * (i + 1))
+    rows = N_CT * g.slots
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return g.query(enc["a"], enc["b"], enc["c1"], enc["c2"])
+
+    # correctness of the benchmarked configuration (not timed)
+    res = step()
+    exp = plain_query(cols["a"], cols["b"], cols["c1"], cols["c2"], t)
+    got = g.decrypt_slots(res)
+    verified = bool((got == exp).all())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = Clocks()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat = []
+    l0 = g.launches()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        lat.append((e0, e1))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = (g.launches() - l0) // max(1, args.steps)
+    clk = clocks.stop()
+    barrier(world)
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), world)
+    lat_ms = sorted(a.elapsed_time(b) for a, b in lat)
+    ms_step = ms_total / args.steps
+    value = rows * world * args.steps / (ms_total / 1e3)
+
+    # kernel classes over one instrumented step (events on the launching stream)
+    g.kernel_timing(True)
+    step()
+    torch.cuda.synchronize()
+    ks = g.kernel_stats()
+    g.kernel_timing(False)
+    total_k = sum(v[1] for v in ks.values())
+    dom = max(ks, key=lambda k: ks[k][1])
+    peak, peak_kind = hbm_peak()
+
+    def gbs(k):
+        n, ms, b = ks[k]
+        return b / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+
+    roof = {"kernel": dom, "bound": "hbm", "achieved": gbs(dom), "peak": peak, "unit": "GB/s",
+            "frac": gbs(dom) / peak, "traffic": None, "peak_source": peak_kind,
+            "avg_launch_ms": ks[dom][1] / max(1, ks[dom][0]),
+            "algorithmic_bytes_per_launch": ks[dom][2] / max(1, ks[dom][0]),
+            "share_of_kernel_time": ks[dom][1] / total_k if total_k else None}
+    classes = {k: {"launches": v[0], "ms": round(v[1], 3), "GB/s": round(gbs(k), 1),
+                   "frac_of_hbm": round(gbs(k) / peak, 3)} for k, v in ks.items() if v[0]}
+
+    # end to end through the host-memory entry point: H2D of the four columns,
+    # the query, D2H of the result ciphertext, every step
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.empty(tuple(v.buf.shape), dtype=torch.int64, pin_memory=True) for k, v in enc.items()}
+        for k, v in enc.items():
+            host[k].copy_(v.buf)
+        arrs = {k: host[k].numpy().view(np.uint64) for k in host}
+        L = enc["a"].level
+        h2d = sum(a.nbytes for a in arrs.values())
+        ol = None
+        torch.cuda.synchronize()
+        e_steps = max(1, min(args.steps, args.e2e_steps))
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            out, ol, ot = g.query_host(arrs["a"], arrs["b"], arrs["c1"], arrs["c2"], L)
+        dt = (time.perf_counter() - t0) / e_steps
+        e2e = {"value": rows / dt, "unit": "rows/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(2 * ol * g.N * 8), "ms_per_step": dt * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        slope, fixed = query_ntt_count()
+        per_ct = slope + fixed / N_CT
+        v, dt, ntts = cpu_sample(rows, per_ct, N_CT)
+        cpu = {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
+               "sample": "one tensor+relin+modswitch at level 20 of the N=2^16 chain (%d limb transforms, "
+                         "%.1f s), scaled by the query's %.0f transforms per ciphertext x 32" % (ntts, dt, per_ct)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": "compare-then-SUM query, N=2^16, L=41 x 55-bit + 3 special primes, "
+                                       "p^r=257^3, 128 slots, 32 ciphertexts per column (4096 rows) per GPU",
+                           "batch": args.batch, "l2": "inputs (5.5 GB) larger than L2"},
+                "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
+                                                                                   int(0.99 * len(lat_ms)))]},
+                "verified_against_plaintext": verified,
+                "roofline": roof, "kernel_classes": classes,
+                "ntt_gbs": gbs("ntt"), "keyswitch_ip_gbs": gbs("keyswitch_inner_product"),
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0 if verified else 1
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

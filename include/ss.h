@@ -171,6 +171,20 @@ ss_status ss_ntt_inverse(ss_ctx* ctx, uint64_t* data, int32_t npoly, int32_t fir
 ss_status ss_trace(ss_ctx* ctx, int32_t on);
 int32_t ss_trace_get(ss_ctx* ctx, char* buf, int32_t len);
 
+/* ---- kernel timing (measurement) ----
+ * When on, every library kernel launch is bracketed by CUDA events recorded on
+ * the stream it is launched on, and attributed to a class with the bytes the
+ * operation must move (its algorithmic traffic, not the measured traffic):
+ *   0 NTT (both phases of one transform; 16 N bytes per limb)
+ *   1 base conversion   2 key-switch inner product   3 tensor product
+ *   4 subtract-and-scale (ModDown / modulus-switch epilogue)
+ *   5 automorphism   6 other elementwise   7 sampling.
+ * ss_kernel_stats synchronises on the recorded events and returns, for one
+ * class, the launches, total milliseconds and total algorithmic bytes since
+ * timing was switched on. Switching it on resets the counters. */
+ss_status ss_kernel_timing(ss_ctx* ctx, int32_t on);
+ss_status ss_kernel_stats(ss_ctx* ctx, int32_t cls, uint64_t* launches, double* ms, double* bytes);
+
 /* Count of kernels this library has launched since context creation. */
 uint64_t ss_launch_count(const ss_ctx* ctx);
 

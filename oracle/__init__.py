@@ -64,6 +64,7 @@ def lib():
             "orc_rotate_sum": (vp, [vp, vp]),
             "orc_query": (vp, [vp, P(vp), P(vp), P(vp), P(vp), i32, i32]),
             "orc_trace": (i32, [vp, i32]),
+            "orc_ntt_count": (C.c_ulonglong, [i32]),
             "orc_trace_get": (i32, [vp, C.c_char_p, i32]),
         }
         for name, (res, args) in sig.items():
@@ -89,6 +90,11 @@ def _ptr(a, ty=C.c_uint64):
 def _chk(rc):
     if rc != 0:
         raise _err()
+
+
+def ntt_count(reset=False):
+    """Limb transforms (forward + inverse) the reference has run in this process."""
+    return int(lib().orc_ntt_count(1 if reset else 0))
 
 
 def g_table(p, e):

@@ -127,6 +127,7 @@ Context make_context(const Params& P);
 void ntt_fwd(const Context& C, int prime_idx, Poly& a);  // coefficients -> evaluation form
 void ntt_inv(const Context& C, int prime_idx, Poly& a);  // evaluation form -> coefficients
 Poly automorph_coeff(const Poly& a, int g, u64 q);        // a(X) -> a(X^g) mod X^N+1
+extern unsigned long long g_ntt_count;                    // limb transforms run so far
 
 // -------------------------------------------------------------------- slots
 std::vector<u64> encode(const Context& C, int t_exp, const std::vector<u64>& slots);

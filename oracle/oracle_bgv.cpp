@@ -312,7 +312,10 @@ static void cyclic_ntt(std::vector<u64>& A, u64 omega, u64 q, int logN) {
   A = B;
 }
 
+unsigned long long g_ntt_count = 0;
+
 void ntt_fwd(const Context& C, int pi, Poly& a) {
+  ++g_ntt_count;
   int N = C.P.N, logN = C.P.logN;
   u64 q = C.primes[pi], psi = C.psi[pi];
   std::vector<u64> b(N);
@@ -323,6 +326,7 @@ void ntt_fwd(const Context& C, int pi, Poly& a) {
 }
 
 void ntt_inv(const Context& C, int pi, Poly& a) {
+  ++g_ntt_count;
   int N = C.P.N, logN = C.P.logN;
   u64 q = C.primes[pi], psi = C.psi[pi];
   std::vector<u64> A(N);

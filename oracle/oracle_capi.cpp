@@ -254,6 +254,12 @@ void* orc_query(void* h, void** A, void** B, void** C1, void** C2, int n, int n2
   });
 }
 
+unsigned long long orc_ntt_count(int reset) {
+  unsigned long long v = g_ntt_count;
+  if (reset) g_ntt_count = 0;
+  return v;
+}
+
 int orc_trace(void* h, int on) {
   Trace* t = trace(h);
   t->on = on != 0;

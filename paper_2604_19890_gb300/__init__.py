@@ -75,7 +75,13 @@ _SIGS = {
     "ss_trace": (C.c_int, [C.c_void_p, C.c_int32]),
     "ss_trace_get": (C.c_int32, [C.c_void_p, C.c_char_p, C.c_int32]),
     "ss_launch_count": (C.c_uint64, [C.c_void_p]),
+    "ss_kernel_timing": (C.c_int, [C.c_void_p, C.c_int32]),
+    "ss_kernel_stats": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double)]),
 }
+
+KERNEL_CLASSES = ["ntt", "base_conversion", "keyswitch_inner_product", "tensor", "sub_scale", "automorphism",
+                  "elementwise", "sampling"]
 
 
 def declared_symbols():
@@ -364,3 +370,15 @@ class Context:
 
     def launches(self):
         return int(lib().ss_launch_count(self.h))
+
+    def kernel_timing(self, on=True):
+        _chk(lib().ss_kernel_timing(self.h, 1 if on else 0))
+
+    def kernel_stats(self):
+        """{class: (launches, total ms, algorithmic bytes)} since timing was switched on."""
+        out = {}
+        for i, name in enumerate(KERNEL_CLASSES):
+            n, ms, b = C.c_uint64(), C.c_double(), C.c_double()
+            _chk(lib().ss_kernel_stats(self.h, i, C.byref(n), C.byref(ms), C.byref(b)))
+            out[name] = (n.value, ms.value, b.value)
+        return out

@@ -428,6 +428,29 @@ int32_t ss_trace_get(ss_ctx* ctx, char* buf, int32_t len) {
   return (int32_t)s.size();
 }
 
+ss_status ss_kernel_timing(ss_ctx* ctx, int32_t on) {
+  return guard([&] {
+    need(ctx != nullptr, SS_ERR_PARAM, "null context");
+    ss::Context& C = ctx->C;
+    ss::kt_collect(C);
+    if (on) {
+      for (int k = 0; k < ss::KC_N; ++k) { C.kt.launches[k] = 0; C.kt.ms[k] = 0; C.kt.bytes[k] = 0; }
+    }
+    C.kt.on = on != 0;
+  });
+}
+
+ss_status ss_kernel_stats(ss_ctx* ctx, int32_t cls, uint64_t* launches, double* ms, double* bytes) {
+  return guard([&] {
+    need(ctx != nullptr && cls >= 0 && cls < ss::KC_N, SS_ERR_PARAM, "bad argument");
+    ss::Context& C = ctx->C;
+    ss::kt_collect(C);
+    if (launches) *launches = C.kt.launches[cls];
+    if (ms) *ms = C.kt.ms[cls];
+    if (bytes) *bytes = C.kt.bytes[cls];
+  });
+}
+
 uint64_t ss_launch_count(const ss_ctx* ctx) { return ctx ? ctx->C.launches : 0; }
 
 }  // extern "C"

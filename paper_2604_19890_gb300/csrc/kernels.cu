@@ -354,37 +354,49 @@ void k_batch_sum(Context& C, const Buf& a, Buf& out, cudaStream_t st) {
 }
 
 #define LAUNCHED() do { ++C.launches; SS_CUDA(cudaGetLastError()); } while (0)
+// launch bracketed by timing events (when kernel timing is on) with its algorithmic bytes
+#define TIMED(cls, bytes, ...)                      \
+  do {                                              \
+    int kr_ = kt_begin(C, st);                      \
+    __VA_ARGS__;                                    \
+    kt_end(C, kr_, (cls), (double)(bytes), st);     \
+  } while (0)
 
 void k_binary(Context& C, int op, const Buf& a, const Buf& b, Buf& out, cudaStream_t st) {
   int polys = a.count * a.ncomp * a.level;
+  TIMED(KC_ELEM, 3.0 * polys * (double)C.N * 8.0,
   k_binary_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(op, a.data, b.data, out.data, C.N, a.ncomp, a.level, a.cap,
-                                                       b.cap, out.cap, b.count == 1 && a.count > 1, C.d_mod);
+                                                       b.cap, out.cap, b.count == 1 && a.count > 1, C.d_mod));
   LAUNCHED();
 }
 
 void k_scalar(Context& C, int op, const Buf& a, i64 c, Buf& out, cudaStream_t st) {
   int polys = a.count * a.ncomp * a.level;
+  TIMED(KC_ELEM, 2.0 * polys * (double)C.N * 8.0,
   k_scalar_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(op, a.data, c, out.data, C.N, a.ncomp, a.level, a.cap,
-                                                       out.cap, C.d_mod, C.d_pinv);
+                                                       out.cap, C.d_mod, C.d_pinv));
   LAUNCHED();
 }
 
 void k_copy_limbs(Context& C, const Buf& a, Buf& out, int level, cudaStream_t st) {
   int polys = a.count * a.ncomp * level;
-  k_copy_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(a.data, out.data, C.N, a.ncomp, level, a.cap, out.cap);
+  TIMED(KC_ELEM, 2.0 * polys * (double)C.N * 8.0,
+  k_copy_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(a.data, out.data, C.N, a.ncomp, level, a.cap, out.cap));
   LAUNCHED();
 }
 
 void k_tensor(Context& C, const Buf& a, const Buf& b, Buf& out, cudaStream_t st) {
   int polys = a.count * a.level;
+  TIMED(KC_TENSOR, 7.0 * polys * (double)C.N * 8.0,
   k_tensor_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(a.data, b.data, out.data, C.N, a.level, a.cap, b.cap, out.cap,
-                                                       C.d_mod);
+                                                       C.d_mod));
   LAUNCHED();
 }
 
 void k_bconv(Context& C, const u64* src, long src_os, int ns, int sp0, const u64* c1, const u64* c2, u64* dst,
              long dst_os, int nd, int nq, int skip_lo, int skip_hi, const u64* post, int n_outer, cudaStream_t st) {
   dim3 g = grid_for(C.N, n_outer);
+  int kr_ = kt_begin(C, st);
   if (ns <= 4)
     k_bconv_impl<4><<<g, TPB, 0, st>>>(src, src_os, ns, sp0, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo,
                                         skip_hi, post, C.N, C.d_mod);
@@ -396,27 +408,31 @@ void k_bconv(Context& C, const u64* src, long src_os, int ns, int sp0, const u64
                                          skip_hi, post, C.N, C.d_mod);
   else
     throw Error(SS_ERR_PARAM, "base conversion from more than 64 primes");
+  kt_end(C, kr_, KC_BCONV, (double)(ns + nd - (skip_hi - skip_lo)) * n_outer * C.N * 8.0, st);
   LAUNCHED();
 }
 
 void k_sub_scale(Context& C, const u64* a, long a_os, const u64* dl, long d_os, const u64* scale, const u64* add,
                  long add_os, u64* out, long out_os, int nl, int n_outer, cudaStream_t st) {
+  TIMED(KC_SUBSCALE, (add ? 4.0 : 3.0) * nl * n_outer * (double)C.N * 8.0,
   k_sub_scale_impl<<<grid_for(C.N, nl * n_outer), TPB, 0, st>>>(a, a_os, dl, d_os, scale, add, add_os, out, out_os,
-                                                                 nl, C.N, C.d_mod);
+                                                                 nl, C.N, C.d_mod));
   LAUNCHED();
 }
 
 void k_ks_ip(Context& C, const u64* d, long d_os, const u64* ext, long ext_os, const KeyDev& K, int level, u64* acc,
              long acc_os, int n_outer, cudaStream_t st) {
+  TIMED(KC_KSIP, ((double)((level + C.alpha - 1) / C.alpha) * (level + C.alpha) * (n_outer + 2.0) + 2.0 * (level + C.alpha) * n_outer) * (double)C.N * 8.0,
   k_ks_ip_impl<<<grid_for(C.N, level + C.alpha), TPB, 0, st>>>(d, d_os, ext, ext_os, K.b, K.a, level, C.alpha, C.L,
-                                                                C.ntot, acc, acc_os, n_outer, C.N, C.d_mod);
+                                                                C.ntot, acc, acc_os, n_outer, C.N, C.d_mod));
   LAUNCHED();
 }
 
 void k_automorph(Context& C, const Buf& a, int g, Buf& out, cudaStream_t st) {
   int rows = a.count * a.ncomp;
+  TIMED(KC_AUTOMORPH, 2.0 * rows * a.level * (double)C.N * 8.0,
   k_automorph_impl<<<grid_for(C.N, rows * a.level), TPB, 0, st>>>(a.data, out.data, g, C.N, C.logN, rows, a.cap,
-                                                                   out.cap, a.level);
+                                                                   out.cap, a.level));
   LAUNCHED();
 }
 

@@ -185,6 +185,17 @@ NttArgs make_args(Context& C, const PolySet& s) {
   return A;
 }
 
+// polynomials a transform actually touches (ModUp outputs skip the digit's own limbs)
+double active_polys(const PolySet& s) {
+  double n = (double)s.n_outer * s.nl;
+  if (s.skip_w > 0)
+    for (int o = 0; o < s.n_outer; ++o) {
+      int lo = (o % s.skip_mod) * s.skip_w, hi = std::min(lo + s.skip_w, s.skip_level);
+      if (hi > lo) n -= hi - lo;
+    }
+  return n;
+}
+
 int ilog2(int x) {
   int l = 0;
   while ((1 << l) < x) ++l;
@@ -200,6 +211,7 @@ void ntt_forward(Context& C, const PolySet& s, cudaStream_t st) {
   NttArgs A = make_args(C, s);
   int N = C.N, logN = C.logN;
   size_t smem = TILE * 8;
+  int kr = kt_begin(C, st);
   if (N <= TILE) {
     int thr = std::min(THREADS, N / 2);
     k_ntt_fwd<false, true><<<dim3(1, npoly), thr, N * 8, st>>>(A, N, logN, 1, 1);
@@ -212,6 +224,7 @@ void ntt_forward(Context& C, const PolySet& s, cudaStream_t st) {
     k_ntt_fwd<false, true><<<dim3(N1 / cpb2, npoly), THREADS, smem, st>>>(A, N2, 8, cpb2, N1);
     C.launches += 2;
   }
+  kt_end(C, kr, KC_NTT, 16.0 * N * active_polys(s), st);
   SS_CUDA(cudaGetLastError());
 }
 
@@ -222,6 +235,7 @@ void ntt_inverse(Context& C, const PolySet& s, cudaStream_t st) {
   NttArgs A = make_args(C, s);
   int N = C.N, logN = C.logN;
   size_t smem = TILE * 8;
+  int kr = kt_begin(C, st);
   if (N <= TILE) {
     int thr = std::min(THREADS, N / 2);
     k_ntt_inv<false, true><<<dim3(1, npoly), thr, N * 8, st>>>(A, N, logN, 1, 1);
@@ -234,6 +248,7 @@ void ntt_inverse(Context& C, const PolySet& s, cudaStream_t st) {
     k_ntt_inv<true, true><<<dim3(N2 / cpb1, npoly), THREADS, smem, st>>>(A, N1, log1, cpb1, 1);
     C.launches += 2;
   }
+  kt_end(C, kr, KC_NTT, 16.0 * N * active_polys(s), st);
   SS_CUDA(cudaGetLastError());
 }
 

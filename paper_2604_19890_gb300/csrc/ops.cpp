@@ -289,3 +289,55 @@ void op_keygen(Context& C, const std::vector<int>& galois) {
 }
 
 }  // namespace ss
+
+namespace ss {
+
+// ------------------------------------------------------------------ kernel timing
+static cudaEvent_t kt_event(Context& C) {
+  if (!C.kt.pool.empty()) {
+    cudaEvent_t e = C.kt.pool.back();
+    C.kt.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  SS_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+int kt_begin(Context& C, cudaStream_t st) {
+  if (!C.kt.on) return -1;
+  KTimer::Rec r;
+  r.a = kt_event(C);
+  r.b = kt_event(C);
+  r.cls = 0;
+  r.bytes = 0;
+  SS_CUDA(cudaEventRecord(r.a, st));
+  C.kt.recs.push_back(r);
+  return (int)C.kt.recs.size() - 1;
+}
+
+void kt_end(Context& C, int rec, int cls, double bytes, cudaStream_t st) {
+  if (rec < 0) return;
+  KTimer::Rec& r = C.kt.recs[rec];
+  r.cls = cls;
+  r.bytes = bytes;
+  SS_CUDA(cudaEventRecord(r.b, st));
+  if (C.kt.recs.size() > 4096) kt_collect(C);
+}
+
+void kt_collect(Context& C) {
+  if (C.kt.recs.empty()) return;
+  SS_CUDA(cudaEventSynchronize(C.kt.recs.back().b));
+  for (auto& r : C.kt.recs) {
+    float ms = 0;
+    SS_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    C.kt.launches[r.cls] += 1;
+    C.kt.ms[r.cls] += ms;
+    C.kt.bytes[r.cls] += r.bytes;
+    C.kt.pool.push_back(r.a);
+    C.kt.pool.push_back(r.b);
+  }
+  C.kt.recs.clear();
+}
+
+}  // namespace ss

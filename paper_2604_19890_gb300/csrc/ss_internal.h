@@ -70,6 +70,23 @@ struct KeyDev {
   u64* a = nullptr;
 };
 
+// Kernel classes for the optional per-launch timing (CUDA events on the
+// launching stream) and their algorithmic byte counts.
+enum KClass { KC_NTT = 0, KC_BCONV, KC_KSIP, KC_TENSOR, KC_SUBSCALE, KC_AUTOMORPH, KC_ELEM, KC_SAMPLE, KC_N };
+
+struct KTimer {
+  bool on = false;
+  struct Rec {
+    cudaEvent_t a, b;
+    int cls;
+    double bytes;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  unsigned long long launches[KC_N] = {};
+  double ms[KC_N] = {}, bytes[KC_N] = {};
+};
+
 struct Context {
   ss_params prm;
   int N = 0, logN = 0, L = 0, alpha = 0, ntot = 0, dnum = 0;
@@ -116,6 +133,7 @@ struct Context {
   bool trace_on = false;
   std::vector<std::string> trace;
   unsigned long long launches = 0;
+  KTimer kt;
 
   ~Context();
 };
@@ -193,6 +211,10 @@ std::vector<int> rotate_sum_elements(const Context& C);
 void build_context(Context& C, const ss_params& prm);
 std::vector<u64> encode(const Context& C, int t_exp, const u64* slots);
 std::vector<u64> decode(const Context& C, int t_exp, const u64* coeffs);
+
+int kt_begin(Context& C, cudaStream_t st);
+void kt_end(Context& C, int rec, int cls, double bytes, cudaStream_t st);
+void kt_collect(Context& C);
 
 inline void note(Context& C, const std::string& s) {
   if (C.trace_on) C.trace.push_back(s);
