@@ -175,6 +175,64 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ kernel micro mode
+def run_kernel(args):
+    """Times one kernel family alone on the benchmark's parameter set (for
+    profiling): `ntt` runs forward then inverse transforms over `--limbs` limbs
+    of the N = 2^16 chain; `relin` runs tensor + relinearisation + modulus
+    switch on a batch of `--n-ct` ciphertexts at the top level."""
+    import numpy as np
+    import torch
+
+    import paper_2604_19890_gb300 as ssg
+    from paper_2604_19890_gb300 import build as ssbuild
+
+    ssbuild.build()
+    prm = ssg.preset(PRESET)
+    g = ssg.Context(params=prm)
+    peak, kind = hbm_peak()
+    out = {"kernel": args.kernel}
+    if args.kernel == "ntt":
+        L = g.L
+        n = args.limbs - args.limbs % L
+        rng = np.random.default_rng(0)
+        data = torch.from_numpy(np.stack([rng.integers(0, int(g.primes[i % L]), g.N, dtype=np.uint64)
+                                          for i in range(L)]).view(np.int64)).cuda().repeat(n // L, 1)
+        for _ in range(args.warmup):
+            g.ntt_forward(data, 0, L)
+            g.ntt_inverse(data, 0, L)
+        g.kernel_timing(True)
+        for _ in range(args.steps):
+            g.ntt_forward(data, 0, L)
+            g.ntt_inverse(data, 0, L)
+        st = g.kernel_stats()["ntt"]
+        g.kernel_timing(False)
+        out.update({"limbs": n, "launches": st[0], "avg_launch_ms": st[1] / st[0],
+                    "GB/s": st[2] / (st[1] / 1e3) / 1e9, "us_per_limb": st[1] * 1e3 / (st[0] * n)})
+    else:
+        g.keygen([])
+        rng = np.random.default_rng(0)
+        a = g.encrypt(np.stack([g.encode(rng.integers(0, g.t, g.slots)) for _ in range(args.n_ct)]), 1)
+        b = g.encrypt(np.stack([g.encode(rng.integers(0, g.t, g.slots)) for _ in range(args.n_ct)]), 100)
+        for _ in range(args.warmup):
+            g.modswitch(g.relin(g.mul(a, b)), 1)
+        g.kernel_timing(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            g.modswitch(g.relin(g.mul(a, b)), 1)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        ks = g.kernel_stats()
+        g.kernel_timing(False)
+        out.update({"n_ct": args.n_ct, "level": g.L, "ms_per_mul": dt * 1e3,
+                    "classes": {k: {"launches": v[0], "ms": v[1], "GB/s": v[2] / (v[1] / 1e3) / 1e9 if v[1] else 0}
+                                for k, v in ks.items() if v[0]}})
+    out["peak_hbm_gbs"] = peak
+    print(json.dumps(out))
+    return 0
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     import numpy as np
@@ -194,11 +252,12 @@ def run_ours(args):
     g.keygen()
     g.set_batch(args.batch)
     t = g.t
-    cols = synth.table(SEED + rank, N_CT, g.slots, t, columns=("a", "b", "c1", "c2"))
+    n_ct = args.n_ct
+    cols = synth.table(SEED + rank, n_ct, g.slots, t, columns=("a", "b", "c1", "c2"))
     enc = {}
     for i, (k, v) in enumerate(cols.items()):
         enc[k] = g.encrypt(np.stack([g.encode(x) for x in v]), 1000 * (i + 1))
-    rows = N_CT * g.slots
+    rows = n_ct * g.slots
     stream = torch.cuda.current_stream()
 
     def step():
@@ -283,8 +342,8 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         slope, fixed = query_ntt_count()
-        per_ct = slope + fixed / N_CT
-        v, dt, ntts = cpu_sample(rows, per_ct, N_CT)
+        per_ct = slope + fixed / n_ct
+        v, dt, ntts = cpu_sample(rows, per_ct, n_ct)
         cpu = {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
                "sample": "one tensor+relin+modswitch at level 20 of the N=2^16 chain (%d limb transforms, "
                          "%.1f s), scaled by the query's %.0f transforms per ciphertext x 32" % (ntts, dt, per_ct)}
@@ -319,7 +378,13 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--kernel", choices=["ntt", "relin"], default=None,
+                    help="time one kernel family alone (profiling mode)")
+    ap.add_argument("--limbs", type=int, default=512)
+    ap.add_argument("--n-ct", type=int, default=N_CT, help="ciphertexts per column")
     args = ap.parse_args()
+    if args.kernel:
+        return run_kernel(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
