@@ -69,6 +69,33 @@ BufP ev_scalar(Context& C, int op, const BufP& a, i64 c, cudaStream_t st) {
   return out;
 }
 
+// sum_t c_t * y_t + cst (cst on component 0), all terms aligned to the lowest
+// level; equal word for word to the chain of scalar products and additions.
+BufP ev_lincomb(Context& C, const std::vector<std::pair<BufP, i64>>& terms, i64 cst, cudaStream_t st) {
+  if (terms.empty()) throw Error(SS_ERR_PARAM, "empty linear combination");
+  int l = terms[0].first->level, cnt = terms[0].first->count;
+  for (auto& t : terms) {
+    same_t(terms[0].first, t.first);
+    if (t.first->ncomp != 2) throw Error(SS_ERR_SHAPE, "linear combination of 2-component ciphertexts");
+    if (t.first->count != cnt) throw Error(SS_ERR_SHAPE, "batch sizes differ");
+    l = std::min(l, t.first->level);
+  }
+  std::vector<BufP> al;
+  for (auto& t : terms) al.push_back(ev_modswitch_to(C, t.first, l, st));
+  BufP acc;
+  size_t i = 0;
+  while (i < al.size()) {
+    std::vector<const Buf*> ys;
+    std::vector<i64> cs;
+    if (acc) { ys.push_back(acc.get()); cs.push_back(1); }
+    while (i < al.size() && ys.size() < 16) { ys.push_back(al[i].get()); cs.push_back(terms[i].second); ++i; }
+    BufP out = alloc_buf(C, cnt, 2, l, terms[0].first->t_exp, st);
+    if (!C.dry) k_lincomb(C, ys, cs, i == al.size() ? cst : 0, *out, st);
+    acc = out;
+  }
+  return acc;
+}
+
 BufP ev_mul(Context& C, const BufP& a0, const BufP& b0, cudaStream_t st) {
   same_t(a0, b0);
   if (a0->ncomp != 2 || b0->ncomp != 2) throw Error(SS_ERR_SHAPE, "multiplication needs 2-component inputs");
@@ -153,10 +180,9 @@ Term bsgs(Context& C, const std::vector<i64>& h, Powers& P, cudaStream_t st) {
       if (idx.empty()) return out;
       int lvl = 1 << 30;
       for (int i : idx) lvl = std::min(lvl, P.get(i)->level);
-      for (int i : idx) {
-        BufP term = ev_scalar(C, 0, P.at_level(i, lvl), c[lo + i], st);
-        out.ct = out.ct ? ev_add(C, out.ct, term, st) : term;
-      }
+      std::vector<std::pair<BufP, i64>> terms;
+      for (int i : idx) terms.push_back({P.at_level(i, lvl), c[lo + i]});
+      out.ct = ev_lincomb(C, terms, 0, st);
       note(C, "baby lo=" + std::to_string(lo) + " terms=" + std::to_string(idx.size()) + " " + L_(lvl));
       return out;
     }
@@ -164,15 +190,16 @@ Term bsgs(Context& C, const std::vector<i64>& h, Powers& P, cudaStream_t st) {
     Term A = rec(lo, half), B = rec(lo + half, half);
     if (!B.ct && B.cst == 0) return A;
     BufP G = P.get(half);
-    BufP prod;
+    out.cst = A.cst;
     if (B.ct) {
       BufP b = B.cst != 0 ? ev_scalar(C, 1, B.ct, B.cst, st) : B.ct;
-      prod = ev_mul(C, b, G, st);
+      BufP prod = ev_mul(C, b, G, st);
+      out.ct = A.ct ? ev_add(C, A.ct, prod, st) : prod;
+    } else if (A.ct) {
+      out.ct = ev_lincomb(C, {{A.ct, 1}, {G, B.cst}}, 0, st);
     } else {
-      prod = ev_scalar(C, 0, G, B.cst, st);
+      out.ct = ev_lincomb(C, {{G, B.cst}}, 0, st);
     }
-    out.cst = A.cst;
-    out.ct = A.ct ? ev_add(C, A.ct, prod, st) : prod;
     note(C, "giant lo=" + std::to_string(lo) + " half=" + std::to_string(half) + " -> " + L_(out.ct->level));
     return out;
   };
@@ -237,10 +264,8 @@ static void compare_digit(Context& C, const BufP& x, BufP& lt, BufP& eq, cudaStr
   Powers P(C, y, st);
   Term H = bsgs(C, h, P, st);
   BufP T = P.get((p - 1) / 2);
-  BufP a = mul_term(C, x, H, st);
-  BufP b = ev_scalar(C, 0, T, f[p - 1], st);
-  lt = ev_add(C, a, b, st);
-  eq = ev_scalar(C, 1, ev_scalar(C, 0, T, -1, st), 1, st);
+  lt = ev_lincomb(C, {{mul_term(C, x, H, st), 1}, {T, f[p - 1]}}, 0, st);
+  eq = ev_lincomb(C, {{T, -1}}, 1, st);
   note(C, "cmp digit -> LT " + L_(lt->level) + " EQ " + L_(eq->level));
 }
 

@@ -14,6 +14,15 @@
 
 namespace ss {
 
+#define LAUNCHED() do { ++C.launches; SS_CUDA(cudaGetLastError()); } while (0)
+// launch bracketed by timing events (when kernel timing is on) with its algorithmic bytes
+#define TIMED(cls, bytes, ...)                      \
+  do {                                              \
+    int kr_ = kt_begin(C, st);                      \
+    __VA_ARGS__;                                    \
+    kt_end(C, kr_, (cls), (double)(bytes), st);     \
+  } while (0)
+
 namespace {
 
 constexpr int TPB = 256;
@@ -315,6 +324,33 @@ __global__ void k_crt_impl(const u64* v, int level, int N, int d, int slots, con
   out[(size_t)bt * N + n] = m;
 }
 
+// out = sum_t c_t * y_t (+ cst on component 0), one 128-bit lazy sum per word.
+// Scalars are centred integers with |c| < q, so the lift is one add.
+struct LinArgs {
+  const u64* ptr[16];
+  int cap[16];
+  i64 c[16];
+};
+
+__global__ void k_lincomb_impl(LinArgs A, int nterms, i64 cst, u64* out, int ocap, int N, int ncomp, int level,
+                               const ModDesc* mods) {
+  int poly = blockIdx.y;  // (bt, comp, i)
+  int i = poly % level, comp = (poly / level) % ncomp, bt = poly / (level * ncomp);
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const Modulus& md = MOD(mods, i);
+  const u64 q = md.q;
+  Acc128 acc;
+  acc.zero();
+  for (int t = 0; t < nterms; ++t) {
+    u64 y = A.ptr[t][((size_t)(bt * ncomp + comp) * A.cap[t] + i) * N + n];
+    i64 c = A.c[t];
+    acc.mac(y, c >= 0 ? (u64)c : q - (u64)(-c));
+  }
+  if (comp == 0 && cst != 0) acc.add(cst >= 0 ? (u64)cst : q - (u64)(-cst));
+  out[((size_t)(bt * ncomp + comp) * ocap + i) * N + n] = barrett_reduce128(acc.hi, acc.lo, md);
+}
+
 // out[g] = a[g]^2 for every prime g (evaluation form)
 __global__ void k_square_impl(const u64* a, u64* out, int N, const ModDesc* mods) {
   int g = blockIdx.y;
@@ -346,6 +382,23 @@ void k_square(Context& C, const u64* a, u64* out, int nprimes, cudaStream_t st) 
   SS_CUDA(cudaGetLastError());
 }
 
+void k_lincomb(Context& C, const std::vector<const Buf*>& ys, const std::vector<i64>& cs, i64 cst, Buf& out,
+               cudaStream_t st) {
+  int nt = (int)ys.size();
+  if (nt < 1 || nt > 16) throw Error(SS_ERR_PARAM, "linear combination of 1..16 terms");
+  LinArgs A;
+  for (int t = 0; t < nt; ++t) {
+    A.ptr[t] = ys[t]->data;
+    A.cap[t] = ys[t]->cap;
+    A.c[t] = cs[t];
+  }
+  int polys = out.count * out.ncomp * out.level;
+  TIMED(KC_ELEM, (nt + 1.0) * polys * C.N * 8.0,
+        k_lincomb_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(A, nt, cst, out.data, out.cap, C.N, out.ncomp,
+                                                              out.level, C.d_mod));
+  LAUNCHED();
+}
+
 void k_batch_sum(Context& C, const Buf& a, Buf& out, cudaStream_t st) {
   k_batch_sum_impl<<<grid_for(C.N, a.ncomp * a.level), TPB, 0, st>>>(a.data, out.data, a.count, a.ncomp, a.level,
                                                                       a.cap, out.cap, C.N, C.d_mod);
@@ -353,14 +406,7 @@ void k_batch_sum(Context& C, const Buf& a, Buf& out, cudaStream_t st) {
   SS_CUDA(cudaGetLastError());
 }
 
-#define LAUNCHED() do { ++C.launches; SS_CUDA(cudaGetLastError()); } while (0)
-// launch bracketed by timing events (when kernel timing is on) with its algorithmic bytes
-#define TIMED(cls, bytes, ...)                      \
-  do {                                              \
-    int kr_ = kt_begin(C, st);                      \
-    __VA_ARGS__;                                    \
-    kt_end(C, kr_, (cls), (double)(bytes), st);     \
-  } while (0)
+
 
 void k_binary(Context& C, int op, const Buf& a, const Buf& b, Buf& out, cudaStream_t st) {
   int polys = a.count * a.ncomp * a.level;

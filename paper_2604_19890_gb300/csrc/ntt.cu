@@ -18,7 +18,6 @@ namespace ss {
 namespace {
 
 constexpr int TILE = 4096;  // words per CTA tile (32 KiB of shared memory)
-constexpr int THREADS = 256;
 
 struct NttArgs {
   u64* base;
@@ -42,128 +41,138 @@ __device__ __forceinline__ bool poly_of(const NttArgs& A, int poly, u64*& ptr, i
   return true;
 }
 
-// COLS: the tile is CPB columns (stride N/S between rows); else CPB chunks of S.
-// Forward stages sigma = 0..s-1 with global twiddle index (m0 + g0) 2^sigma + group.
-template <bool COLS, bool LAST>
-__global__ void __launch_bounds__(THREADS) k_ntt_fwd(NttArgs A, int S, int logS, int CPB, int m0) {
-  extern __shared__ u64 sm[];
-  // map polys so that consecutive blocks share a prime (twiddles stay in L2)
-  int poly = blockIdx.y;
-  u64* ptr;
-  int pidx;
-  if (!poly_of(A, poly, ptr, pidx)) return;
-  const Modulus md = A.mods[pidx];
-  const u64 q = md.q, q2 = 2 * q;
-  const u64* tw = A.tw + (size_t)pidx * 4 * A.N;
-  const u64* tws = tw + A.N;
-  const int tile = blockIdx.x;
-  const int words = CPB * S;
-  const int stride = A.N / S;  // column stride (COLS)
-  // load
-  for (int e = threadIdx.x; e < words; e += blockDim.x) {
-    if (COLS) {
-      int c = e % CPB, r = e / CPB;
-      sm[e] = ptr[(long)r * stride + tile * CPB + c];
-    } else {
-      sm[e] = ptr[(long)tile * words + e];
-    }
-  }
-  __syncthreads();
-  const int half = words / 2;
-  for (int sg = 0; sg < logS; ++sg) {
-    int t = S >> (sg + 1);
-    for (int b = threadIdx.x; b < half; b += blockDim.x) {
-      int c, bb;
-      if (COLS) { c = b % CPB; bb = b / CPB; }
-      else { c = b / (S / 2); bb = b % (S / 2); }
-      int grp = bb / t, pos = bb % t;
-      int r = grp * 2 * t + pos;
-      int g0 = COLS ? 0 : tile * CPB + c;
-      int widx = ((m0 + g0) << sg) + grp;
-      u64 w = __ldg(tw + widx), wp = __ldg(tws + widx);
-      int i0, i1;
-      if (COLS) { i0 = r * CPB + c; i1 = (r + t) * CPB + c; }
-      else { i0 = c * S + r; i1 = i0 + t; }
-      u64 U = sm[i0], V = sm[i1];
-      if (U >= q2) U -= q2;
-      V = shoup_lazy(V, w, wp, q);
-      sm[i0] = U + V;
-      sm[i1] = U - V + q2;
-    }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < words; e += blockDim.x) {
-    u64 x = sm[e];
-    if (LAST) {
-      if (x >= q2) x -= q2;
-      if (x >= q) x -= q;
-    }
-    if (COLS) {
-      int c = e % CPB, r = e / CPB;
-      ptr[(long)r * stride + tile * CPB + c] = x;
-    } else {
-      ptr[(long)tile * words + e] = x;
+// Shared-memory word for linear tile index `lin`: one pad word per 8, which
+// spreads the strided round accesses over all banks.
+__device__ __forceinline__ int swz(int lin) { return lin + (lin >> 3); }
+
+// One round of up to three radix-2 stages held in registers. The thread owns
+// the eight words r_k = rbase + k*u (rbase = B*8u + o, o < u); the round's
+// stages have half-distances t = u*2^j for j in [JLO, JHI] and pair the
+// registers (k, k + 2^j). Butterflies of one 2t-block share one twiddle,
+// index (mg << sg) + r/(2t), sg = logS - 1 - log2(t).
+template <bool FWD, int JLO, int JHI>
+__device__ __forceinline__ void ntt_round(u64 (&x)[8], int rbase, int logu, int logS, int mg, const u64* __restrict__ tw,
+                                          const u64* __restrict__ tws, u64 q) {
+  const u64 q2 = 2 * q;
+#pragma unroll
+  for (int jj = JLO; jj <= JHI; ++jj) {
+    const int j = FWD ? JHI + JLO - jj : jj;
+    const int d = 1 << j;
+    const int logt = logu + j;
+    const int sg = logS - 1 - logt;
+#pragma unroll
+    for (int blk = 0; blk < 4 / d; ++blk) {
+      const int k0 = blk * 2 * d;
+      const int widx = (mg << sg) + ((rbase + (k0 << logu)) >> (logt + 1));
+      const u64 w = __ldg(tw + widx), wp = __ldg(tws + widx);
+#pragma unroll
+      for (int p = 0; p < d; ++p) {
+        const int k = k0 + p;
+        u64 U = x[k], V = x[k + d];
+        if (FWD) {
+          if (U >= q2) U -= q2;
+          V = shoup_lazy(V, w, wp, q);
+          x[k] = U + V;
+          x[k + d] = U - V + q2;
+        } else {
+          u64 s = U + V;
+          if (s >= q2) s -= q2;
+          x[k] = s;
+          x[k + d] = shoup_lazy(U - V + q2, w, wp, q);
+        }
+      }
     }
   }
 }
 
-template <bool COLS, bool LAST>
-__global__ void __launch_bounds__(THREADS) k_ntt_inv(NttArgs A, int S, int logS, int CPB, int m0) {
+template <bool FWD>
+__device__ __forceinline__ void ntt_round_dispatch(int jlo, int jhi, u64 (&x)[8], int rbase, int logu, int logS, int mg,
+                                                   const u64* tw, const u64* tws, u64 q) {
+  switch (jlo * 3 + jhi) {
+    case 0: ntt_round<FWD, 0, 0>(x, rbase, logu, logS, mg, tw, tws, q); break;
+    case 1: ntt_round<FWD, 0, 1>(x, rbase, logu, logS, mg, tw, tws, q); break;
+    case 2: ntt_round<FWD, 0, 2>(x, rbase, logu, logS, mg, tw, tws, q); break;
+    case 4: ntt_round<FWD, 1, 1>(x, rbase, logu, logS, mg, tw, tws, q); break;
+    case 5: ntt_round<FWD, 1, 2>(x, rbase, logu, logS, mg, tw, tws, q); break;
+    default: ntt_round<FWD, 2, 2>(x, rbase, logu, logS, mg, tw, tws, q); break;
+  }
+}
+
+// One phase: the tile is CPB sub-transforms of S = 2^logS words (columns of
+// stride N/S when COLS, else contiguous chunks), staged in shared memory.
+// blockDim = CPB*S/8. Residues stay lazy ([0,4q) forward, [0,2q) inverse)
+// except in the LAST phase, which writes canonical values (times N^-1 for
+// the inverse).
+template <bool FWD, bool COLS, bool LAST>
+__global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, int m0) {
   extern __shared__ u64 sm[];
-  int poly = blockIdx.y;
   u64* ptr;
   int pidx;
-  if (!poly_of(A, poly, ptr, pidx)) return;
-  const Modulus md = A.mods[pidx];
-  const u64 q = md.q, q2 = 2 * q;
-  const u64* tw = A.tw + (size_t)pidx * 4 * A.N + 2 * A.N;
+  if (!poly_of(A, blockIdx.y, ptr, pidx)) return;
+  const u64 q = A.mods[pidx].q;
+  const u64* tw = A.tw + (size_t)pidx * 4 * A.N + (FWD ? 0 : 2 * A.N);
   const u64* tws = tw + A.N;
+  const int S = 1 << logS, CPB = 1 << logCPB, W = S << logCPB;
+  const int tid = threadIdx.x, T = blockDim.x;
   const int tile = blockIdx.x;
-  const int words = CPB * S;
-  const int stride = A.N / S;
-  for (int e = threadIdx.x; e < words; e += blockDim.x) {
-    if (COLS) {
-      int c = e % CPB, r = e / CPB;
-      sm[e] = ptr[(long)r * stride + tile * CPB + c];
-    } else {
-      sm[e] = ptr[(long)tile * words + e];
-    }
+  const long colbase = (long)tile * CPB;
+  const int stride = A.N >> logS;
+  // global -> shared, coalesced: consecutive lin are consecutive addresses
+  for (int lin = tid; lin < W; lin += T) {
+    long g = COLS ? (long)(lin >> logCPB) * stride + colbase + (lin & (CPB - 1)) : (long)tile * W + lin;
+    sm[swz(lin)] = ptr[g];
   }
   __syncthreads();
-  const int half = words / 2;
-  for (int sg = logS - 1; sg >= 0; --sg) {
-    int t = S >> (sg + 1);
-    for (int b = threadIdx.x; b < half; b += blockDim.x) {
-      int c, bb;
-      if (COLS) { c = b % CPB; bb = b / CPB; }
-      else { c = b / (S / 2); bb = b % (S / 2); }
-      int grp = bb / t, pos = bb % t;
-      int r = grp * 2 * t + pos;
-      int g0 = COLS ? 0 : tile * CPB + c;
-      int widx = ((m0 + g0) << sg) + grp;
-      u64 w = __ldg(tw + widx), wp = __ldg(tws + widx);
-      int i0, i1;
-      if (COLS) { i0 = r * CPB + c; i1 = (r + t) * CPB + c; }
-      else { i0 = c * S + r; i1 = i0 + t; }
-      u64 U = sm[i0], V = sm[i1];
-      u64 s = U + V;
-      if (s >= q2) s -= q2;
-      sm[i0] = s;
-      sm[i1] = shoup_lazy(U - V + q2, w, wp, q);
+  const int rounds = (logS + 2) / 3;
+  for (int rho = 0; rho < rounds; ++rho) {
+    // log2 of the smallest (a) and largest (b) half-distance of this round
+    const int ns = min(3, logS - 3 * rho);
+    const int b = FWD ? logS - 1 - 3 * rho : 3 * rho + ns - 1;
+    const int a = b - ns + 1;
+    const int logu = max(0, b - 2);
+    int c, o, B;
+    if (COLS) {
+      c = tid & (CPB - 1);
+      int rest = tid >> logCPB;
+      o = rest & ((1 << logu) - 1);
+      B = rest >> logu;
+    } else {
+      o = tid & ((1 << logu) - 1);
+      int rest = tid >> logu;
+      int logB = logS - 3 - logu;
+      B = rest & ((1 << logB) - 1);
+      c = rest >> logB;
+    }
+    const int rbase = (B << (logu + 3)) + o;
+    const int mg = m0 + (COLS ? 0 : tile * CPB + c);
+    u64 x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      int r = rbase + (k << logu);
+      x[k] = sm[swz(COLS ? (r << logCPB) + c : (c << logS) + r)];
+    }
+    ntt_round_dispatch<FWD>(a - logu, b - logu, x, rbase, logu, logS, mg, tw, tws, q);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      int r = rbase + (k << logu);
+      sm[swz(COLS ? (r << logCPB) + c : (c << logS) + r)] = x[k];
     }
     __syncthreads();
   }
   u64 ni = 0, nip = 0;
-  if (LAST) { ni = A.ninv[2 * pidx]; nip = A.ninv[2 * pidx + 1]; }
-  for (int e = threadIdx.x; e < words; e += blockDim.x) {
-    u64 x = sm[e];
-    if (LAST) x = shoup(x, ni, nip, q);
-    if (COLS) {
-      int c = e % CPB, r = e / CPB;
-      ptr[(long)r * stride + tile * CPB + c] = x;
-    } else {
-      ptr[(long)tile * words + e] = x;
+  if (LAST && !FWD) { ni = A.ninv[2 * pidx]; nip = A.ninv[2 * pidx + 1]; }
+  for (int lin = tid; lin < W; lin += T) {
+    u64 v = sm[swz(lin)];
+    if (LAST) {
+      if (FWD) {
+        if (v >= 2 * q) v -= 2 * q;
+        if (v >= q) v -= q;
+      } else {
+        v = shoup(v, ni, nip, q);
+      }
     }
+    long g = COLS ? (long)(lin >> logCPB) * stride + colbase + (lin & (CPB - 1)) : (long)tile * W + lin;
+    ptr[g] = v;
   }
 }
 
@@ -204,52 +213,40 @@ int ilog2(int x) {
 
 }  // namespace
 
-void ntt_forward(Context& C, const PolySet& s, cudaStream_t st) {
+static void launch(Context& C, const PolySet& s, bool fwd, cudaStream_t st) {
   int npoly = s.n_outer * s.nl;
   if (npoly == 0) return;
   if (npoly > 65535) throw Error(SS_ERR_SHAPE, "too many polynomials in one transform");
   NttArgs A = make_args(C, s);
-  int N = C.N, logN = C.logN;
-  size_t smem = TILE * 8;
+  const int N = C.N, logN = C.logN;
   int kr = kt_begin(C, st);
+  auto smem = [](int words) { return (size_t)(words + words / 8) * 8; };
   if (N <= TILE) {
-    int thr = std::min(THREADS, N / 2);
-    k_ntt_fwd<false, true><<<dim3(1, npoly), thr, N * 8, st>>>(A, N, logN, 1, 1);
+    dim3 g(1, npoly);
+    int thr = N / 8;
+    if (fwd) k_ntt<true, false, true><<<g, thr, smem(N), st>>>(A, logN, 0, 1);
+    else k_ntt<false, false, true><<<g, thr, smem(N), st>>>(A, logN, 0, 1);
     ++C.launches;
   } else {
-    int N2 = 256, N1 = N / N2;
-    int log1 = ilog2(N1);
-    int cpb1 = TILE / N1, cpb2 = TILE / N2;
-    k_ntt_fwd<true, false><<<dim3(N2 / cpb1, npoly), THREADS, smem, st>>>(A, N1, log1, cpb1, 1);
-    k_ntt_fwd<false, true><<<dim3(N1 / cpb2, npoly), THREADS, smem, st>>>(A, N2, 8, cpb2, N1);
+    const int log2n = 8, log1 = logN - log2n;  // N = N1 * N2, N2 = 256
+    const int logc1 = ilog2(TILE) - log1, logc2 = ilog2(TILE) - log2n;
+    dim3 g1(1 << (log2n - logc1), npoly), g2(1 << (log1 - logc2), npoly);
+    const int thr = TILE / 8;
+    if (fwd) {
+      k_ntt<true, true, false><<<g1, thr, smem(TILE), st>>>(A, log1, logc1, 1);
+      k_ntt<true, false, true><<<g2, thr, smem(TILE), st>>>(A, log2n, logc2, 1 << log1);
+    } else {
+      k_ntt<false, false, false><<<g2, thr, smem(TILE), st>>>(A, log2n, logc2, 1 << log1);
+      k_ntt<false, true, true><<<g1, thr, smem(TILE), st>>>(A, log1, logc1, 1);
+    }
     C.launches += 2;
   }
   kt_end(C, kr, KC_NTT, 16.0 * N * active_polys(s), st);
   SS_CUDA(cudaGetLastError());
 }
 
-void ntt_inverse(Context& C, const PolySet& s, cudaStream_t st) {
-  int npoly = s.n_outer * s.nl;
-  if (npoly == 0) return;
-  if (npoly > 65535) throw Error(SS_ERR_SHAPE, "too many polynomials in one transform");
-  NttArgs A = make_args(C, s);
-  int N = C.N, logN = C.logN;
-  size_t smem = TILE * 8;
-  int kr = kt_begin(C, st);
-  if (N <= TILE) {
-    int thr = std::min(THREADS, N / 2);
-    k_ntt_inv<false, true><<<dim3(1, npoly), thr, N * 8, st>>>(A, N, logN, 1, 1);
-    ++C.launches;
-  } else {
-    int N2 = 256, N1 = N / N2;
-    int log1 = ilog2(N1);
-    int cpb1 = TILE / N1, cpb2 = TILE / N2;
-    k_ntt_inv<false, false><<<dim3(N1 / cpb2, npoly), THREADS, smem, st>>>(A, N2, 8, cpb2, N1);
-    k_ntt_inv<true, true><<<dim3(N2 / cpb1, npoly), THREADS, smem, st>>>(A, N1, log1, cpb1, 1);
-    C.launches += 2;
-  }
-  kt_end(C, kr, KC_NTT, 16.0 * N * active_polys(s), st);
-  SS_CUDA(cudaGetLastError());
-}
+void ntt_forward(Context& C, const PolySet& s, cudaStream_t st) { launch(C, s, true, st); }
+
+void ntt_inverse(Context& C, const PolySet& s, cudaStream_t st) { launch(C, s, false, st); }
 
 }  // namespace ss

@@ -181,6 +181,8 @@ void k_crt(Context& C, const u64* v, int count, int level, int t_exp, u64* out, 
 void k_ksk_gadget(Context& C, u64* b, const u64* sprime, int j, cudaStream_t st);
 void k_square(Context& C, const u64* a, u64* out, int nprimes, cudaStream_t st);
 void k_batch_sum(Context& C, const Buf& a, Buf& out, cudaStream_t st);
+void k_lincomb(Context& C, const std::vector<const Buf*>& ys, const std::vector<i64>& cs, i64 cst, Buf& out,
+               cudaStream_t st);
 
 // ------------------------------------------------------------------ operations
 void op_encrypt(Context& C, const u64* d_coeffs, int count, u32 nonce0, int t_exp, Buf& out, cudaStream_t st);
@@ -198,6 +200,7 @@ BufP ev_mul(Context& C, const BufP& a, const BufP& b, cudaStream_t st);
 BufP ev_add(Context& C, const BufP& a, const BufP& b, cudaStream_t st);
 BufP ev_sub(Context& C, const BufP& a, const BufP& b, cudaStream_t st);
 BufP ev_scalar(Context& C, int op, const BufP& a, i64 c, cudaStream_t st);
+BufP ev_lincomb(Context& C, const std::vector<std::pair<BufP, i64>>& terms, i64 cst, cudaStream_t st);
 BufP ev_eval_g(Context& C, const BufP& x, int e, cudaStream_t st);
 std::vector<BufP> ev_reduce(Context& C, const BufP& a, cudaStream_t st);
 BufP ev_compare_lt(Context& C, const BufP& a, const BufP& b, cudaStream_t st);
