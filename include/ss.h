@@ -129,6 +129,11 @@ ss_status ss_modswitch(ss_ctx* ctx, const ss_ct* a, int32_t drop, ss_ct* out, ss
 ss_status ss_rotate(ss_ctx* ctx, const ss_ct* a, int32_t g, ss_ct* out, ss_stream stream);
 /* total over all slots into every slot (SUM, Section 5.2) */
 ss_status ss_rotate_sum(ss_ctx* ctx, const ss_ct* a, ss_ct* out, ss_stream stream);
+/* out = sum_i coeffs[i] * terms[i] + cst (cst added to component 0): the
+ * Paterson-Stockmeyer inner step (Theorem 2) in one pass. Every term must
+ * share count, level and t_exp; |coeffs[i]|, |cst| < the smallest prime. */
+ss_status ss_linear_combination(ss_ctx* ctx, const ss_ct* terms, const int64_t* coeffs, int32_t nterms, int64_t cst,
+                                ss_ct* out, ss_stream stream);
 /* DivideByP (Section 4.2): times p^-1 mod Q, t_exp - 1 */
 ss_status ss_divide_by_p(ss_ctx* ctx, const ss_ct* a, ss_ct* out, ss_stream stream);
 

@@ -60,6 +60,8 @@ _SIGS = {
     "ss_modswitch": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.c_int32, C.POINTER(ss_ct), C.c_void_p]),
     "ss_rotate": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.c_int32, C.POINTER(ss_ct), C.c_void_p]),
     "ss_rotate_sum": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.POINTER(ss_ct), C.c_void_p]),
+    "ss_linear_combination": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.POINTER(C.c_int64), C.c_int32, C.c_int64,
+                                        C.POINTER(ss_ct), C.c_void_p]),
     "ss_divide_by_p": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.POINTER(ss_ct), C.c_void_p]),
     "ss_eval_g": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.c_int32, C.POINTER(ss_ct), C.c_void_p]),
     "ss_reduce_to_digits": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.POINTER(ss_ct), C.c_void_p]),
@@ -305,6 +307,14 @@ class Context:
 
     def rotate_sum(self, a):
         return self._call1(lib().ss_rotate_sum, a, self._out(a))
+
+    def linear_combination(self, terms, coeffs, cst=0):
+        arr = (ss_ct * len(terms))(*[x.desc() for x in terms])
+        cf = (C.c_int64 * len(terms))(*[int(c) for c in coeffs])
+        out = self._out(terms[0])
+        do = out.desc()
+        _chk(lib().ss_linear_combination(self.h, arr, cf, len(terms), int(cst), C.byref(do), _stream(self.torch)))
+        return out.update(do)
 
     def divide_by_p(self, a):
         return self._call1(lib().ss_divide_by_p, a, self._out(a))

@@ -236,6 +236,22 @@ ss_status ss_mul_scalar(ss_ctx* ctx, const ss_ct* a, int64_t c, ss_ct* out, ss_s
 ss_status ss_add_scalar(ss_ctx* ctx, const ss_ct* a, int64_t c, ss_ct* out, ss_stream s) { return scalar_op(ctx, 1, a, c, out, s); }
 ss_status ss_divide_by_p(ss_ctx* ctx, const ss_ct* a, ss_ct* out, ss_stream s) { return scalar_op(ctx, 2, a, 0, out, s); }
 
+ss_status ss_linear_combination(ss_ctx* ctx, const ss_ct* terms, const int64_t* coeffs, int32_t nterms, int64_t cst,
+                                ss_ct* out, ss_stream stream) {
+  return guard([&] {
+    need(ctx != nullptr && terms != nullptr && coeffs != nullptr && nterms >= 1, SS_ERR_PARAM, "bad argument");
+    std::vector<std::pair<ss::BufP, int64_t>> t;
+    for (int i = 0; i < nterms; ++i) {
+      check_ct(ctx->C, &terms[i], "null term");
+      need(terms[i].level == terms[0].level, SS_ERR_LEVEL, "terms at different levels");
+      need(terms[i].count == terms[0].count, SS_ERR_SHAPE, "batch sizes differ");
+      t.push_back({ss::view_buf(terms[i]), coeffs[i]});
+    }
+    auto r = ss::ev_lincomb(ctx->C, t, cst, S(stream));
+    deliver(ctx->C, r, out, S(stream));
+  });
+}
+
 ss_status ss_mul(ss_ctx* ctx, const ss_ct* a, const ss_ct* b, ss_ct* out, ss_stream stream) {
   return guard([&] {
     need(ctx != nullptr, SS_ERR_PARAM, "null context");

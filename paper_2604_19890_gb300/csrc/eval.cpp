@@ -5,6 +5,9 @@
 //  * multiplication: align both operands to the lower level by modulus
 //    switching the higher one (dropping all extra primes at once), tensor,
 //    relinearise, then drop exactly one prime;
+//  * linear combinations: a term above the combination's level is scaled at
+//    its own level, then switched down; terms already at that level are
+//    scaled and summed in one pass;
 //  * powers of y: y^e = (y^(e/2))^2 when e is a power of two, otherwise
 //    y^(2^floor(log2 e)) * y^(e - 2^floor(log2 e));
 //  * Paterson-Stockmeyer (Theorem 2) for H(y) = sum_j h_j y^j:
@@ -80,15 +83,27 @@ BufP ev_lincomb(Context& C, const std::vector<std::pair<BufP, i64>>& terms, i64 
     if (t.first->count != cnt) throw Error(SS_ERR_SHAPE, "batch sizes differ");
     l = std::min(l, t.first->level);
   }
+  // A term above the common level is scaled at its own level and then switched
+  // down (modulus switching does not commute word for word with scaling, and
+  // scaling first keeps the rounding noise unscaled).
   std::vector<BufP> al;
-  for (auto& t : terms) al.push_back(ev_modswitch_to(C, t.first, l, st));
+  std::vector<i64> cf;
+  for (auto& t : terms) {
+    if (t.first->level > l && t.second != 1) {
+      al.push_back(ev_modswitch_to(C, ev_scalar(C, 0, t.first, t.second, st), l, st));
+      cf.push_back(1);
+    } else {
+      al.push_back(ev_modswitch_to(C, t.first, l, st));
+      cf.push_back(t.second);
+    }
+  }
   BufP acc;
   size_t i = 0;
   while (i < al.size()) {
     std::vector<const Buf*> ys;
     std::vector<i64> cs;
     if (acc) { ys.push_back(acc.get()); cs.push_back(1); }
-    while (i < al.size() && ys.size() < 16) { ys.push_back(al[i].get()); cs.push_back(terms[i].second); ++i; }
+    while (i < al.size() && ys.size() < 16) { ys.push_back(al[i].get()); cs.push_back(cf[i]); ++i; }
     BufP out = alloc_buf(C, cnt, 2, l, terms[0].first->t_exp, st);
     if (!C.dry) k_lincomb(C, ys, cs, i == al.size() ? cst : 0, *out, st);
     acc = out;

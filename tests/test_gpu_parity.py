@@ -116,6 +116,24 @@ def test_ops_parity(tiny):
     assert (g.decrypt_slots(gr) == (A * B) % g.t).all()
 
 
+@pytest.mark.parametrize("nterms", [1, 3, 15, 20])
+def test_linear_combination_parity(tiny, nterms):
+    g, o = tiny
+    rng = np.random.default_rng(30 + nterms)
+    cts = [encrypt_both(g, o, rng.integers(0, g.t, (2, g.slots)), 2000 + 10 * i) for i in range(nterms)]
+    coeffs = [int(c) for c in rng.integers(-g.t // 2, g.t // 2, nterms)]
+    cst = int(rng.integers(-100, 100))
+    got = g.linear_combination([c[0] for c in cts], coeffs, cst)
+    ref = []
+    for b in range(2):
+        acc = None
+        for (gc, oc), cf in zip(cts, coeffs):
+            term = o.mul_scalar(oc[b], cf)
+            acc = term if acc is None else o.add(acc, term)
+        ref.append(o.add_scalar(acc, cst))
+    same(got, ref)
+
+
 def test_eval_g_reduce_compare_raise_parity(tiny):
     g, o = tiny
     rng = np.random.default_rng(3)
