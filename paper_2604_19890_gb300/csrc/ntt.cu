@@ -176,6 +176,167 @@ __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, in
   }
 }
 
+// ---------------------------------------------------------------- radix-16 phases
+// Same scheme with sixteen words per thread (four stages per register round,
+// two rounds per 256-point phase) for the two-phase transforms (N >= 8192).
+// Round 0 reads global memory straight into registers and the last round
+// writes straight back whenever that access is coalesced (always for column
+// tiles; for chunk tiles when the round's spacing u >= 16), otherwise the
+// tile passes through shared memory once more.
+// blockDim = CPB*S/16, S = 2^LOGS with 5 <= LOGS <= 8. Every round's stage
+// range is a compile-time constant, so the sixteen words stay in registers.
+template <bool FWD, bool COLS, bool LAST, int LOGS>
+__global__ void __launch_bounds__(256, 2) k_ntt16(NttArgs A, int logCPB, int m0) {
+  extern __shared__ u64 sm[];
+  u64* ptr;
+  int pidx;
+  if (!poly_of(A, blockIdx.y, ptr, pidx)) return;
+  const u64 q = A.mods[pidx].q;
+  const u64* tw = A.tw + (size_t)pidx * 4 * A.N + (FWD ? 0 : 2 * A.N);
+  const u64* tws = tw + A.N;
+  constexpr int S = 1 << LOGS;
+  const int CPB = 1 << logCPB, W = S << logCPB;
+  const int tid = threadIdx.x, T = blockDim.x;
+  const int tile = blockIdx.x;
+  const int stride = A.N >> LOGS;
+  u64* gbase = COLS ? ptr + (long)tile * CPB : ptr + (long)tile * W;
+  constexpr int NR = (LOGS + 3) / 4;
+  constexpr int B0 = FWD ? LOGS - 1 : (LOGS < 4 ? LOGS : 4) - 1;
+  constexpr int NSL = LOGS - 4 * (NR - 1);
+  constexpr int BL = FWD ? LOGS - 1 - 4 * (NR - 1) : 4 * (NR - 1) + NSL - 1;
+  constexpr bool DIN = COLS || (B0 - 3 >= 4);
+  constexpr bool DOUT = COLS || (BL - 3 >= 4);
+  if (!DIN) {
+    for (int lin = tid; lin < W; lin += T) sm[swz(lin)] = gbase[lin];
+    __syncthreads();
+  }
+  u64 ni = 0, nip = 0;
+  if (LAST && !FWD) { ni = A.ninv[2 * pidx]; nip = A.ninv[2 * pidx + 1]; }
+#pragma unroll
+  for (int rho = 0; rho < NR; ++rho) {
+    const int ns = (LOGS - 4 * rho) < 4 ? (LOGS - 4 * rho) : 4;
+    const int b = FWD ? LOGS - 1 - 4 * rho : 4 * rho + ns - 1;
+    const int a = b - ns + 1;
+    const int logu = b - 3 > 0 ? b - 3 : 0;
+    int c, o, B;
+    if (COLS) {
+      c = tid & (CPB - 1);
+      int rest = tid >> logCPB;
+      o = rest & ((1 << logu) - 1);
+      B = rest >> logu;
+    } else {
+      o = tid & ((1 << logu) - 1);
+      int rest = tid >> logu;
+      const int logB = LOGS - 4 - logu;
+      B = rest & ((1 << logB) - 1);
+      c = rest >> logB;
+    }
+    const int rbase = (B << (logu + 4)) + o;
+    const int mg = m0 + (COLS ? 0 : tile * CPB + c);
+    u64 x[16];
+    if (rho == 0 && DIN) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        int r = rbase + (k << logu);
+        x[k] = COLS ? gbase[(long)r * stride + c] : gbase[(c << LOGS) + r];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        int r = rbase + (k << logu);
+        x[k] = sm[swz(COLS ? (r << logCPB) + c : (c << LOGS) + r)];
+      }
+    }
+    // stages j in [a - logu, b - logu]: d = 2^j registers apart
+    const u64 q2 = 2 * q;
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int jlo = a - logu, jhi = b - logu;
+      const int j = FWD ? jhi - jj : jlo + jj;
+      if (jj < ns) {
+        const int d = 1 << j;
+        const int logt = logu + j;
+        const int sg = LOGS - 1 - logt;
+#pragma unroll
+        for (int blk = 0; blk < 8; ++blk) {
+          if (blk < 8 / d) {
+            const int k0 = blk * 2 * d;
+            const int widx = (mg << sg) + ((rbase + (k0 << logu)) >> (logt + 1));
+            const u64 w = __ldg(tw + widx), wp = __ldg(tws + widx);
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+              if (p < d) {
+                const int k = k0 + p;
+                u64 U = x[k], V = x[k + d];
+                if (FWD) {
+                  if (U >= q2) U -= q2;
+                  V = shoup_lazy(V, w, wp, q);
+                  x[k] = U + V;
+                  x[k + d] = U - V + q2;
+                } else {
+                  u64 s2 = U + V;
+                  if (s2 >= q2) s2 -= q2;
+                  x[k] = s2;
+                  x[k + d] = shoup_lazy(U - V + q2, w, wp, q);
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+    if (rho == NR - 1 && DOUT) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        int r = rbase + (k << logu);
+        u64 v = x[k];
+        if (LAST) {
+          if (FWD) {
+            if (v >= 2 * q) v -= 2 * q;
+            if (v >= q) v -= q;
+          } else {
+            v = shoup(v, ni, nip, q);
+          }
+        }
+        if (COLS) gbase[(long)r * stride + c] = v;
+        else gbase[(c << LOGS) + r] = v;
+      }
+    } else {
+      if (rho > 0 || !DIN) __syncthreads();  // every read of the previous layout is done
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        int r = rbase + (k << logu);
+        sm[swz(COLS ? (r << logCPB) + c : (c << LOGS) + r)] = x[k];
+      }
+      __syncthreads();
+    }
+  }
+  if (!DOUT) {
+    for (int lin = tid; lin < W; lin += T) {
+      u64 v = sm[swz(lin)];
+      if (LAST) {
+        if (FWD) {
+          if (v >= 2 * q) v -= 2 * q;
+          if (v >= q) v -= q;
+        } else {
+          v = shoup(v, ni, nip, q);
+        }
+      }
+      gbase[lin] = v;
+    }
+  }
+}
+
+template <bool FWD, bool COLS, bool LAST>
+void launch16(int logS, dim3 g, int thr, size_t smem, cudaStream_t st, const NttArgs& A, int logc, int m0) {
+  switch (logS) {
+    case 5: k_ntt16<FWD, COLS, LAST, 5><<<g, thr, smem, st>>>(A, logc, m0); break;
+    case 6: k_ntt16<FWD, COLS, LAST, 6><<<g, thr, smem, st>>>(A, logc, m0); break;
+    case 7: k_ntt16<FWD, COLS, LAST, 7><<<g, thr, smem, st>>>(A, logc, m0); break;
+    default: k_ntt16<FWD, COLS, LAST, 8><<<g, thr, smem, st>>>(A, logc, m0); break;
+  }
+}
+
 NttArgs make_args(Context& C, const PolySet& s) {
   NttArgs A;
   A.base = s.base;
@@ -231,13 +392,13 @@ static void launch(Context& C, const PolySet& s, bool fwd, cudaStream_t st) {
     const int log2n = 8, log1 = logN - log2n;  // N = N1 * N2, N2 = 256
     const int logc1 = ilog2(TILE) - log1, logc2 = ilog2(TILE) - log2n;
     dim3 g1(1 << (log2n - logc1), npoly), g2(1 << (log1 - logc2), npoly);
-    const int thr = TILE / 8;
+    const int thr = TILE / 16;
     if (fwd) {
-      k_ntt<true, true, false><<<g1, thr, smem(TILE), st>>>(A, log1, logc1, 1);
-      k_ntt<true, false, true><<<g2, thr, smem(TILE), st>>>(A, log2n, logc2, 1 << log1);
+      launch16<true, true, false>(log1, g1, thr, smem(TILE), st, A, logc1, 1);
+      launch16<true, false, true>(log2n, g2, thr, smem(TILE), st, A, logc2, 1 << log1);
     } else {
-      k_ntt<false, false, false><<<g2, thr, smem(TILE), st>>>(A, log2n, logc2, 1 << log1);
-      k_ntt<false, true, true><<<g1, thr, smem(TILE), st>>>(A, log1, logc1, 1);
+      launch16<false, false, false>(log2n, g2, thr, smem(TILE), st, A, logc2, 1 << log1);
+      launch16<false, true, true>(log1, g1, thr, smem(TILE), st, A, logc1, 1);
     }
     C.launches += 2;
   }
