@@ -123,6 +123,18 @@ ss_status ss_add_scalar(ss_ctx* ctx, const ss_ct* a, int64_t c, ss_ct* out, ss_s
 ss_status ss_mul(ss_ctx* ctx, const ss_ct* a, const ss_ct* b, ss_ct* out, ss_stream stream);
 /* hybrid key switch of c2 with the relinearisation key: 3 -> 2 components */
 ss_status ss_relin(ss_ctx* ctx, const ss_ct* a, ss_ct* out, ss_stream stream);
+/* Same result as ss_relin, for callers that cannot allocate device memory
+ * while they run (a host framework that owns all device memory through its
+ * own allocator, or a service that must not risk an allocation stalling or
+ * failing mid-request). The paper has no counterpart: this is a deployment
+ * variant. Scratch comes from one file-scope device array of 64 MiB that
+ * every GPU loading the library holds until the process exits; the call
+ * allocates nothing. A call needs count*(l + dnum*(l+alpha) + 2*(l+alpha) +
+ * 2*l)*N words at level l (dnum = ceil(l/alpha)); larger calls fail with
+ * SS_ERR_PARAM. All calls share the array, so calls that overlap on the GPU
+ * race. The first call on a device looks up the array's address (with that
+ * device current); make it before any stream capture. */
+ss_status ss_relin_noalloc(ss_ctx* ctx, const ss_ct* a, ss_ct* out, ss_stream stream);
 /* drops the last `drop` primes at once: c' = (c - t*conv(t^-1 c mod Q_drop)) / Q_drop */
 ss_status ss_modswitch(ss_ctx* ctx, const ss_ct* a, int32_t drop, ss_ct* out, ss_stream stream);
 /* sigma_g (X -> X^g) then key switch back to s with the Galois key of g */

@@ -57,6 +57,7 @@ _SIGS = {
     "ss_add_scalar": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.c_int64, C.POINTER(ss_ct), C.c_void_p]),
     "ss_mul": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.POINTER(ss_ct), C.POINTER(ss_ct), C.c_void_p]),
     "ss_relin": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.POINTER(ss_ct), C.c_void_p]),
+    "ss_relin_noalloc": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.POINTER(ss_ct), C.c_void_p]),
     "ss_modswitch": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.c_int32, C.POINTER(ss_ct), C.c_void_p]),
     "ss_rotate": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.c_int32, C.POINTER(ss_ct), C.c_void_p]),
     "ss_rotate_sum": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.POINTER(ss_ct), C.c_void_p]),
@@ -298,6 +299,10 @@ class Context:
 
     def relin(self, a):
         return self._call1(lib().ss_relin, a, self._out(a, ncomp=2))
+
+    def relin_noalloc(self, a):
+        """ss_relin without any device allocation (scratch in a static device array)."""
+        return self._call1(lib().ss_relin_noalloc, a, self._out(a, ncomp=2))
 
     def modswitch(self, a, drop=1):
         return self._call1(lib().ss_modswitch, a, self._out(a, level=a.level - drop), C.c_int32(drop))

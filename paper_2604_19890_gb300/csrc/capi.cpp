@@ -283,6 +283,18 @@ ss_status ss_relin(ss_ctx* ctx, const ss_ct* a, ss_ct* out, ss_stream stream) {
   });
 }
 
+ss_status ss_relin_noalloc(ss_ctx* ctx, const ss_ct* a, ss_ct* out, ss_stream stream) {
+  return guard([&] {
+    need(ctx != nullptr, SS_ERR_PARAM, "null context");
+    check_ct(ctx->C, a, "null a");
+    check_out(out, a->count, 2, a->level);
+    need(out->data != a->data, SS_ERR_PARAM, "relinearisation output must not alias its input");
+    ss::Buf o = as_out(out);
+    ss::op_relin_noalloc(ctx->C, *ss::view_buf(*a), o, S(stream));
+    write_back(o, out);
+  });
+}
+
 ss_status ss_modswitch(ss_ctx* ctx, const ss_ct* a, int32_t drop, ss_ct* out, ss_stream stream) {
   return guard([&] {
     need(ctx != nullptr, SS_ERR_PARAM, "null context");

@@ -193,6 +193,10 @@ void op_keyswitch(Context& C, const Buf& in, int comp, const KeyDev& K, const Bu
 void op_relin(Context& C, const Buf& a, Buf& out, cudaStream_t st);
 void op_modswitch(Context& C, const Buf& a, int drop, Buf& out, cudaStream_t st);
 void op_rotate(Context& C, const Buf& a, int g, Buf& out, cudaStream_t st);
+// relinearisation with its scratch in a static device array (allocates nothing)
+void op_relin_noalloc(Context& C, const Buf& a, Buf& out, cudaStream_t st);
+size_t relin_noalloc_words(const Context& C, int level, int count);
+size_t relin_noalloc_capacity();
 
 // evaluator (batched, one plan for every ciphertext of a batch)
 BufP ev_modswitch_to(Context& C, const BufP& a, int level, cudaStream_t st);
