@@ -233,6 +233,79 @@ def run_kernel(args):
     return 0
 
 
+# ------------------------------------------------------------------ served form
+def run_serve(args):
+    """Poisson-arriving compare-then-SUM queries against device-resident tables
+    (N = 2^16, 257^3, `--serve-ct` ciphertexts per column each, keys resident).
+    Compares the plain form (one worker, one query per pass) with the served
+    form (two workers, up to 8 compatible queries merged per pass) at arrival
+    rates relative to the measured single-query capacity and at 10 q/s."""
+    import numpy as np
+    import torch
+
+    import paper_2604_19890_gb300 as ssg
+    from paper_2604_19890_gb300 import build as ssbuild
+    from paper_2604_19890_gb300 import synth
+
+    ssbuild.build()
+    prm = ssg.preset(PRESET)
+    g = ssg.Context(params=prm)
+    g.keygen()
+    g.set_batch(args.batch)
+    n_tables = 8
+    tables = []
+    for i in range(n_tables):
+        cols = synth.table(SEED + 100 + i, args.serve_ct, g.slots, g.t)
+        enc = [g.encrypt(np.stack([g.encode(x) for x in cols[k]]), 10000 * (i + 1) + 100 * j)
+               for j, k in enumerate(("a", "b", "c1", "c2"))]
+        tables.append((enc, plain_query(cols["a"], cols["b"], cols["c1"], cols["c2"], g.t)))
+    # single-query service time
+    for _ in range(2):
+        g.query(*tables[0][0])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(3):
+        g.query(*tables[i % n_tables][0])
+    torch.cuda.synchronize()
+    t1 = (time.perf_counter() - t0) / 3
+    cap = 1.0 / t1
+    rng = np.random.default_rng(7)
+    out = {"metric": "served compare-then-SUM queries/s and latency", "unit": "queries/s",
+           "config": {"workload": "N=2^16, L=41, p^r=257^3, %d ciphertexts (%d rows) per column per query, "
+                                  "%d device-resident tables" % (args.serve_ct, args.serve_ct * g.slots, n_tables)},
+           "single_query_ms": t1 * 1e3, "capacity_qps": cap, "runs": []}
+    ok = True
+    for rate in [0.5 * cap, 1.0 * cap, 2.0 * cap, 10.0]:
+        gaps = rng.exponential(1.0 / rate, args.serve_queries)
+        arrivals = np.cumsum(gaps) - gaps[0]
+        for form, workers, merge in [("plain", 1, 1), ("served", 2, 8)]:
+            srv = ssg.Server(g, workers=workers, max_merge=merge)
+            tickets = []
+            start = time.perf_counter()
+            for i, at in enumerate(arrivals):
+                now = time.perf_counter() - start
+                if at > now:
+                    time.sleep(at - now)
+                tickets.append((srv.submit(*tables[i % n_tables][0]), time.perf_counter(), i))
+            lat, last = [], 0.0
+            for tk, t_sub, i in tickets:
+                res, q_ms, r_ms = srv.wait(tk, timeout_ms=600000)
+                lat.append(q_ms + r_ms)
+                last = max(last, t_sub - start + (q_ms + r_ms) / 1e3)
+                if i < 2:
+                    ok &= bool((g.decrypt_slots(res) == tables[i % n_tables][1]).all())
+            st = srv.stats()
+            srv.close()
+            lat.sort()
+            out["runs"].append({"form": form, "arrival_qps": round(rate, 3), "queries": len(lat),
+                                "qps": len(lat) / last, "p50_ms": lat[len(lat) // 2],
+                                "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                                "passes": st["batches"]})
+    out["verified_against_plaintext"] = ok
+    print(json.dumps(out))
+    return 0 if ok else 1
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     import numpy as np
@@ -374,7 +447,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -382,7 +455,12 @@ def main():
                     help="time one kernel family alone (profiling mode)")
     ap.add_argument("--limbs", type=int, default=512)
     ap.add_argument("--n-ct", type=int, default=N_CT, help="ciphertexts per column")
+    ap.add_argument("--serve", action="store_true", help="served form: Poisson arrivals, p50/p99")
+    ap.add_argument("--serve-ct", type=int, default=2)
+    ap.add_argument("--serve-queries", type=int, default=16)
     args = ap.parse_args()
+    if args.serve:
+        return run_serve(args)
     if args.kernel:
         return run_kernel(args)
     if args.impl == "reference":

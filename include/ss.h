@@ -170,6 +170,31 @@ ss_status ss_query_sum_where_lt_host(ss_ctx* ctx, const uint64_t* A, const uint6
                                      const uint64_t* C2, int32_t count, int32_t count2, int32_t level,
                                      uint64_t* host_out, int32_t* out_level, int32_t* out_t_exp,
                                      ss_stream stream);
+/* ---- served form: request loop with continuous batching ----
+ * A server owns `workers` host threads, each with its own CUDA stream. A free
+ * worker takes the oldest pending query plus every other pending query of the
+ * same level and plaintext modulus that fits the HBM budget (at most
+ * max_merge in all), runs them as one batch and splits the results, so
+ * queries that arrive while others run are admitted as soon as a worker and
+ * memory free up and their work overlaps on the device. Every result equals
+ * the same query run alone (ss_query_sum_where_lt). hbm_budget = 0 takes 80 %
+ * of the free device memory. Kernel timing and tracing must be off while a
+ * server runs. */
+typedef struct ss_server ss_server;
+ss_status ss_server_create(ss_ctx* ctx, int32_t workers, int32_t max_merge, uint64_t hbm_budget, ss_server** out);
+/* Queues one query on device-resident columns (as ss_query_sum_where_lt);
+ * `out` (count 1, capacity >= the columns' level) receives the result. The
+ * caller keeps the columns and *out alive until ss_server_wait returns. */
+ss_status ss_server_submit(ss_server* s, const ss_ct* A, const ss_ct* B, const ss_ct* C1, const ss_ct* C2,
+                           ss_ct* out, uint64_t* ticket);
+/* Waits at most timeout_ms (negative: no bound) for a ticket: SS_ERR_TIMEOUT if
+ * it is still running; otherwise releases it and returns its status with the
+ * time it waited for admission and the time its batch ran (host clock). */
+ss_status ss_server_wait(ss_server* s, uint64_t ticket, int32_t timeout_ms, double* queued_ms, double* run_ms);
+ss_status ss_server_stats(ss_server* s, uint64_t* completed, uint64_t* batches, uint64_t* peak_inflight_bytes);
+/* Finishes every queued query, then stops the workers. */
+void ss_server_destroy(ss_server* s);
+
 /* Number of levels a query consumes on inputs at `level` (the plan's depth);
  * SS_ERR_NOISE if the chain is too short. */
 ss_status ss_query_depth(ss_ctx* ctx, int32_t level, int32_t* out_level);

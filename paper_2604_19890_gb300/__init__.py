@@ -78,6 +78,11 @@ _SIGS = {
     "ss_trace": (C.c_int, [C.c_void_p, C.c_int32]),
     "ss_trace_get": (C.c_int32, [C.c_void_p, C.c_char_p, C.c_int32]),
     "ss_launch_count": (C.c_uint64, [C.c_void_p]),
+    "ss_server_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(C.c_void_p)]),
+    "ss_server_submit": (C.c_int, [C.c_void_p] + [C.POINTER(ss_ct)] * 5 + [C.POINTER(C.c_uint64)]),
+    "ss_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "ss_server_stats": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_uint64)] * 3),
+    "ss_server_destroy": (None, [C.c_void_p]),
     "ss_kernel_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "ss_kernel_stats": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_double),
                                   C.POINTER(C.c_double)]),
@@ -157,6 +162,52 @@ class CtBatch:
 
     def slice(self, b0, n):
         return CtBatch(self.buf[b0:b0 + n], n, self.ncomp, self.level, self.t_exp)
+
+
+class Server:
+    """Request loop with continuous batching over one context (ss_server_*)."""
+
+    def __init__(self, ctx, workers=2, max_merge=8, hbm_budget=0):
+        self.ctx = ctx
+        h = C.c_void_p()
+        _chk(lib().ss_server_create(ctx.h, workers, max_merge, hbm_budget, C.byref(h)))
+        self.h = h
+        self._live = {}
+
+    def submit(self, A, B, C1, C2):
+        """Queues a query; returns a ticket. Keeps the descriptors alive until wait()."""
+        out = self.ctx.empty(1, level=A.level)
+        descs = [x.desc() for x in (A, B, C1, C2)] + [out.desc()]
+        t = C.c_uint64()
+        _chk(lib().ss_server_submit(self.h, *[C.byref(d) for d in descs], C.byref(t)))
+        self._live[t.value] = (descs, out, (A, B, C1, C2))
+        return t.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        """Returns (result CtBatch, queued_ms, run_ms)."""
+        q, r = C.c_double(), C.c_double()
+        rc = lib().ss_server_wait(self.h, ticket, timeout_ms, C.byref(q), C.byref(r))
+        if rc == SS_ERR_TIMEOUT:
+            raise SSError(rc, lib().ss_last_error().decode())
+        descs, out, _ = self._live.pop(ticket)
+        _chk(rc)
+        return out.update(descs[4]), q.value, r.value
+
+    def stats(self):
+        c, b, p = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        _chk(lib().ss_server_stats(self.h, C.byref(c), C.byref(b), C.byref(p)))
+        return {"completed": c.value, "batches": b.value, "peak_inflight_bytes": p.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ss_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Context:

@@ -81,6 +81,11 @@ void write_back(const ss::Buf& b, ss_ct* o) {
 
 }  // namespace
 
+namespace ss {
+Context& context_of(ss_ctx* c) { return c->C; }
+void set_error(const std::string& m) { g_err = m; }
+}  // namespace ss
+
 extern "C" {
 
 const char* ss_last_error(void) { return g_err.c_str(); }
@@ -479,6 +484,6 @@ ss_status ss_kernel_stats(ss_ctx* ctx, int32_t cls, uint64_t* launches, double* 
   });
 }
 
-uint64_t ss_launch_count(const ss_ctx* ctx) { return ctx ? ctx->C.launches : 0; }
+uint64_t ss_launch_count(const ss_ctx* ctx) { return ctx ? ctx->C.launches.load() : 0; }
 
 }  // extern "C"

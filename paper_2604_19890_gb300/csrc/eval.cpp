@@ -380,3 +380,87 @@ int plan_query_depth(Context& C, int level) {
 }
 
 }  // namespace ss
+
+namespace ss {
+
+// Batches with one shape, joined along the batch axis (a broadcast part of
+// count 1 is repeated `rep` times).
+static BufP concat(Context& C, const std::vector<std::pair<BufP, int>>& parts, cudaStream_t st) {
+  int total = 0;
+  for (auto& p : parts) total += p.second;
+  const Buf& f = *parts[0].first;
+  BufP out = alloc_buf(C, total, f.ncomp, f.level, f.t_exp, st);
+  if (C.dry) return out;
+  const size_t row = (size_t)f.level * C.N * 8, ct = (size_t)f.ncomp * f.level * C.N;
+  size_t off = 0;
+  for (auto& p : parts) {
+    const Buf& b = *p.first;
+    if (b.level != f.level || b.ncomp != f.ncomp || b.t_exp != f.t_exp) throw Error(SS_ERR_SHAPE, "parts differ");
+    if (b.count == p.second) {
+      SS_CUDA(cudaMemcpy2DAsync(out->data + off * ct, row, b.data, (size_t)b.cap * C.N * 8, row,
+                                (size_t)b.count * b.ncomp, cudaMemcpyDeviceToDevice, st));
+    } else {
+      for (int r = 0; r < p.second; ++r)
+        SS_CUDA(cudaMemcpy2DAsync(out->data + (off + r) * ct, row, b.data, (size_t)b.cap * C.N * 8, row, b.ncomp,
+                                  cudaMemcpyDeviceToDevice, st));
+    }
+    off += p.second;
+  }
+  return out;
+}
+
+// Several queries of one shape in one pass: their columns are joined into one
+// batch, every ciphertext goes through the same schedule as ev_query, and the
+// per-query sums are rotated and summed as one batch. Each result equals
+// ev_query on that query alone word for word.
+std::vector<BufP> ev_query_multi(Context& C, const std::vector<QueryCols>& qs, cudaStream_t st) {
+  if (qs.empty()) return {};
+  std::vector<std::pair<BufP, int>> a, b, c1, c2;
+  std::vector<int> n;
+  for (auto& q : qs) {
+    int k = q.A->count;
+    if (q.B->count != k || q.C1->count != k || (q.C2->count != k && q.C2->count != 1))
+      throw Error(SS_ERR_SHAPE, "column batch sizes differ");
+    n.push_back(k);
+    a.push_back({q.A, k});
+    b.push_back({q.B, k});
+    c1.push_back({q.C1, k});
+    c2.push_back({q.C2, k});
+  }
+  BufP A = concat(C, a, st), B = concat(C, b, st), C1 = concat(C, c1, st), C2 = concat(C, c2, st);
+  const int total = A->count, step = std::max(1, C.batch);
+  std::vector<std::pair<BufP, int>> Rs;
+  for (int b0 = 0; b0 < total; b0 += step) {
+    int cnt = std::min(step, total - b0);
+    BufP ind = ev_raise(C, ev_compare_lt(C, slice_buf(C1, b0, cnt, C.N), slice_buf(C2, b0, cnt, C.N), st), st);
+    BufP R = ev_mul(C, ind, ev_mul(C, slice_buf(A, b0, cnt, C.N), slice_buf(B, b0, cnt, C.N), st), st);
+    Rs.push_back({R, cnt});
+  }
+  BufP R = Rs.size() == 1 ? Rs[0].first : concat(C, Rs, st);
+  std::vector<std::pair<BufP, int>> parts;
+  int off = 0;
+  for (int k : n) {
+    BufP s = slice_buf(R, off, k, C.N);
+    BufP part = alloc_buf(C, 1, R->ncomp, R->level, R->t_exp, st);
+    if (!C.dry) k_batch_sum(C, *s, *part, st);
+    parts.push_back({part, 1});
+    off += k;
+  }
+  BufP S = ev_rotate_sum(C, parts.size() == 1 ? parts[0].first : concat(C, parts, st), st);
+  std::vector<BufP> out;
+  for (size_t i = 0; i < qs.size(); ++i) out.push_back(slice_buf(S, (int)i, 1, C.N));
+  return out;
+}
+
+// Device bytes a query of n_ct ciphertexts per column at `level` may hold at
+// its peak (inputs joined, the live powers of one Paterson-Stockmeyer
+// evaluation, key-switch scratch), for admission control.
+size_t query_bytes_estimate(const Context& C, int n_ct, int level) {
+  const size_t ct = (size_t)2 * level * C.N * 8;
+  const int b = std::min(n_ct, std::max(1, C.batch));
+  const int dn = (level + C.alpha - 1) / C.alpha, nx = level + C.alpha;
+  const size_t ks = (size_t)b * ((size_t)dn * nx + 4 * (size_t)nx + 2 * (size_t)level) * C.N * 8;
+  return 4 * (size_t)n_ct * ct + (size_t)b * ct * 48 + ks;
+}
+
+}  // namespace ss

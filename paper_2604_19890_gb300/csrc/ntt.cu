@@ -22,15 +22,17 @@ constexpr int TILE = 4096;  // words per CTA tile (32 KiB of shared memory)
 struct NttArgs {
   u64* base;
   long outer_stride;
-  int nl, q0, nq, L, N;
+  int n_outer, nl, q0, nq, L, N;
   int skip_w, skip_mod, skip_level;
   const Modulus* mods;
   const u64* tw;     // per prime 4N words
   const u64* ninv;   // per prime (N^-1, shoup)
 };
 
+// Blocks walk the polynomials limb-major (all outer copies of limb 0, then of
+// limb 1, ...) so consecutive blocks share a prime and its twiddles stay in L2.
 __device__ __forceinline__ bool poly_of(const NttArgs& A, int poly, u64*& ptr, int& pidx) {
-  int o = poly / A.nl, i = poly % A.nl;
+  int i = poly / A.n_outer, o = poly % A.n_outer;
   if (A.skip_w > 0) {
     int j = o % A.skip_mod;
     int lo = j * A.skip_w, hi = min(lo + A.skip_w, A.skip_level);
@@ -341,6 +343,7 @@ NttArgs make_args(Context& C, const PolySet& s) {
   NttArgs A;
   A.base = s.base;
   A.outer_stride = s.outer_stride;
+  A.n_outer = s.n_outer;
   A.nl = s.nl;
   A.q0 = s.q0;
   A.nq = s.nq;

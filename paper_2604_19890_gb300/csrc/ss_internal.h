@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <memory>
@@ -132,7 +133,7 @@ struct Context {
   bool dry = false;  // plan only: track levels, launch nothing
   bool trace_on = false;
   std::vector<std::string> trace;
-  unsigned long long launches = 0;
+  std::atomic<unsigned long long> launches{0};  // shared by server worker threads
   KTimer kt;
 
   ~Context();
@@ -211,6 +212,11 @@ BufP ev_compare_lt(Context& C, const BufP& a, const BufP& b, cudaStream_t st);
 BufP ev_raise(Context& C, const BufP& a, cudaStream_t st);
 BufP ev_rotate_sum(Context& C, const BufP& a, cudaStream_t st);
 BufP ev_query(Context& C, const BufP& A, const BufP& B, const BufP& C1, const BufP& C2, cudaStream_t st);
+struct QueryCols {
+  BufP A, B, C1, C2;
+};
+std::vector<BufP> ev_query_multi(Context& C, const std::vector<QueryCols>& qs, cudaStream_t st);
+size_t query_bytes_estimate(const Context& C, int n_ct, int level);
 int plan_query_depth(Context& C, int level);
 std::vector<int> rotate_sum_elements(const Context& C);
 
