@@ -170,6 +170,41 @@ ss_status ss_query_sum_where_lt_host(ss_ctx* ctx, const uint64_t* A, const uint6
                                      const uint64_t* C2, int32_t count, int32_t count2, int32_t level,
                                      uint64_t* host_out, int32_t* out_level, int32_t* out_t_exp,
                                      ss_stream stream);
+/* ---- batched form ----
+ * Many ciphertext pairs of mixed ring dimension (one context per parameter
+ * set) and level: each pair is multiplied (tensor, relinearisation, one prime
+ * dropped; the BGV multiplication of Section 2.1) into *prod and, when
+ * `reduce` is set and the remaining levels allow it, reduced to its r digits
+ * (Algorithm 3) into digits[0..r-1]. Items are grouped by (context, level);
+ * each group is joined into one batch, split into chunks over several streams,
+ * and the whole run can be captured once as a CUDA graph and replayed. The
+ * results do not depend on the chunking, stream count or NTT tile. */
+typedef struct {
+  int32_t ctx;      /* index into the context array */
+  int32_t reduce;   /* 1: also run Algorithm 3 on the product */
+  ss_ct a, b;       /* count 1 each, same level, t = p^r */
+  ss_ct* prod;      /* receives the product (count 1, capacity >= level - 1) */
+  ss_ct* digits;    /* r outputs when reduce is set, else NULL */
+} ss_batch_item;
+typedef struct ss_batch ss_batch;
+/* Groups the items (copies of the descriptors are kept; the caller keeps the
+ * data and the output descriptors alive). Items whose reduction does not fit
+ * in their remaining levels have it skipped and counted. */
+ss_status ss_batch_create(ss_ctx* const* ctxs, int32_t nctx, const ss_batch_item* items, int32_t n, ss_batch** out);
+/* chunk: ciphertexts per pass; nstreams: 1..8; ntt_tile_log: 11 or 12 (words per transform tile). */
+ss_status ss_batch_config(ss_batch* b, int32_t chunk, int32_t nstreams, int32_t ntt_tile_log);
+ss_status ss_batch_get_config(const ss_batch* b, int32_t* chunk, int32_t* nstreams, int32_t* ntt_tile_log,
+                              int32_t* groups, int32_t* skipped);
+/* Autotuner: times the run for chunk in {8, 32, 64} x streams in {1, 3} x tile in {2^11, 2^12} words
+ * on this work list and keeps the fastest setting. Synchronous. */
+ss_status ss_batch_tune(ss_batch* b, ss_stream stream, int32_t* best_chunk, int32_t* best_streams,
+                        int32_t* best_tile_log);
+/* Captures the whole run (current setting) as one CUDA graph on `stream` (not the legacy stream). */
+ss_status ss_batch_capture(ss_batch* b, ss_stream stream);
+/* Runs the batch: replays the captured graph if there is one, else launches eagerly. */
+ss_status ss_batch_run(ss_batch* b, ss_stream stream);
+void ss_batch_destroy(ss_batch* b);
+
 /* ---- served form: request loop with continuous batching ----
  * A server owns `workers` host threads, each with its own CUDA stream. A free
  * worker takes the oldest pending query plus every other pending query of the

@@ -36,6 +36,11 @@ class ss_ct(C.Structure):
                 ("t_exp", C.c_int32), ("capacity", C.c_int32), ("reserved", C.c_int32)]
 
 
+class ss_batch_item(C.Structure):
+    _fields_ = [("ctx", C.c_int32), ("reduce", C.c_int32), ("a", ss_ct), ("b", ss_ct),
+                ("prod", C.POINTER(ss_ct)), ("digits", C.POINTER(ss_ct))]
+
+
 _lib = None
 
 _SIGS = {
@@ -78,6 +83,14 @@ _SIGS = {
     "ss_trace": (C.c_int, [C.c_void_p, C.c_int32]),
     "ss_trace_get": (C.c_int32, [C.c_void_p, C.c_char_p, C.c_int32]),
     "ss_launch_count": (C.c_uint64, [C.c_void_p]),
+    "ss_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(ss_batch_item), C.c_int32,
+                                  C.POINTER(C.c_void_p)]),
+    "ss_batch_config": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
+    "ss_batch_get_config": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int32)] * 5),
+    "ss_batch_tune": (C.c_int, [C.c_void_p, C.c_void_p] + [C.POINTER(C.c_int32)] * 3),
+    "ss_batch_capture": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ss_batch_run": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ss_batch_destroy": (None, [C.c_void_p]),
     "ss_server_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(C.c_void_p)]),
     "ss_server_submit": (C.c_int, [C.c_void_p] + [C.POINTER(ss_ct)] * 5 + [C.POINTER(C.c_uint64)]),
     "ss_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -162,6 +175,72 @@ class CtBatch:
 
     def slice(self, b0, n):
         return CtBatch(self.buf[b0:b0 + n], n, self.ncomp, self.level, self.t_exp)
+
+
+class Batch:
+    """Batched form (ss_batch_*): pairs (ctx_index, a, b, reduce) of single
+    ciphertexts over several contexts; outputs are allocated here."""
+
+    def __init__(self, ctxs, pairs):
+        self.ctxs = ctxs
+        self.torch = ctxs[0].torch
+        items = (ss_batch_item * len(pairs))()
+        self._keep = []
+        self.outputs = []
+        for i, (ci, a, b, red) in enumerate(pairs):
+            g = ctxs[ci]
+            prod = g.empty(1, level=a.level - 1)
+            pd = prod.desc()
+            digs = [g.empty(1, level=a.level - 1) for _ in range(g.r)] if red else []
+            dd = (ss_ct * max(1, len(digs)))(*[d.desc() for d in digs]) if red else None
+            items[i] = ss_batch_item(ci, 1 if red else 0, a.desc(), b.desc(), C.pointer(pd),
+                                     C.cast(dd, C.POINTER(ss_ct)) if red else None)
+            self._keep.append((pd, dd, a, b))
+            self.outputs.append((prod, pd, digs, dd))
+        arr = (C.c_void_p * len(ctxs))(*[g.h.value for g in ctxs])
+        h = C.c_void_p()
+        _chk(lib().ss_batch_create(arr, len(ctxs), items, len(pairs), C.byref(h)))
+        self.h = h
+        self._items = items
+
+    def results(self):
+        """[(product CtBatch, [digit CtBatch...] or [])] with metadata from the last run."""
+        out = []
+        for prod, pd, digs, dd in self.outputs:
+            prod.update(pd)
+            ds = [d.update(dd[k]) for k, d in enumerate(digs)] if digs else []
+            out.append((prod, ds))
+        return out
+
+    def config(self, chunk, nstreams, tile_log=12):
+        _chk(lib().ss_batch_config(self.h, chunk, nstreams, tile_log))
+
+    def get_config(self):
+        v = [C.c_int32() for _ in range(5)]
+        _chk(lib().ss_batch_get_config(self.h, *[C.byref(x) for x in v]))
+        return dict(zip(["chunk", "nstreams", "tile_log", "groups", "skipped"], [x.value for x in v]))
+
+    def tune(self, stream):
+        v = [C.c_int32() for _ in range(3)]
+        _chk(lib().ss_batch_tune(self.h, C.c_void_p(stream.cuda_stream), *[C.byref(x) for x in v]))
+        return [x.value for x in v]
+
+    def capture(self, stream):
+        _chk(lib().ss_batch_capture(self.h, C.c_void_p(stream.cuda_stream)))
+
+    def run(self, stream):
+        _chk(lib().ss_batch_run(self.h, C.c_void_p(stream.cuda_stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ss_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

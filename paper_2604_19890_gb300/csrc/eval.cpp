@@ -385,7 +385,7 @@ namespace ss {
 
 // Batches with one shape, joined along the batch axis (a broadcast part of
 // count 1 is repeated `rep` times).
-static BufP concat(Context& C, const std::vector<std::pair<BufP, int>>& parts, cudaStream_t st) {
+BufP ev_concat(Context& C, const std::vector<std::pair<BufP, int>>& parts, cudaStream_t st) {
   int total = 0;
   for (auto& p : parts) total += p.second;
   const Buf& f = *parts[0].first;
@@ -427,7 +427,7 @@ std::vector<BufP> ev_query_multi(Context& C, const std::vector<QueryCols>& qs, c
     c1.push_back({q.C1, k});
     c2.push_back({q.C2, k});
   }
-  BufP A = concat(C, a, st), B = concat(C, b, st), C1 = concat(C, c1, st), C2 = concat(C, c2, st);
+  BufP A = ev_concat(C, a, st), B = ev_concat(C, b, st), C1 = ev_concat(C, c1, st), C2 = ev_concat(C, c2, st);
   const int total = A->count, step = std::max(1, C.batch);
   std::vector<std::pair<BufP, int>> Rs;
   for (int b0 = 0; b0 < total; b0 += step) {
@@ -436,7 +436,7 @@ std::vector<BufP> ev_query_multi(Context& C, const std::vector<QueryCols>& qs, c
     BufP R = ev_mul(C, ind, ev_mul(C, slice_buf(A, b0, cnt, C.N), slice_buf(B, b0, cnt, C.N), st), st);
     Rs.push_back({R, cnt});
   }
-  BufP R = Rs.size() == 1 ? Rs[0].first : concat(C, Rs, st);
+  BufP R = Rs.size() == 1 ? Rs[0].first : ev_concat(C, Rs, st);
   std::vector<std::pair<BufP, int>> parts;
   int off = 0;
   for (int k : n) {
@@ -446,7 +446,7 @@ std::vector<BufP> ev_query_multi(Context& C, const std::vector<QueryCols>& qs, c
     parts.push_back({part, 1});
     off += k;
   }
-  BufP S = ev_rotate_sum(C, parts.size() == 1 ? parts[0].first : concat(C, parts, st), st);
+  BufP S = ev_rotate_sum(C, parts.size() == 1 ? parts[0].first : ev_concat(C, parts, st), st);
   std::vector<BufP> out;
   for (size_t i = 0; i < qs.size(); ++i) out.push_back(slice_buf(S, (int)i, 1, C.N));
   return out;

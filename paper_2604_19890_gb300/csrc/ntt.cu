@@ -393,15 +393,16 @@ static void launch(Context& C, const PolySet& s, bool fwd, cudaStream_t st) {
     ++C.launches;
   } else {
     const int log2n = 8, log1 = logN - log2n;  // N = N1 * N2, N2 = 256
-    const int logc1 = ilog2(TILE) - log1, logc2 = ilog2(TILE) - log2n;
+    const int tl = C.ntt_tile_log == 11 ? 11 : 12, tile = 1 << tl;
+    const int logc1 = tl - log1, logc2 = tl - log2n;
     dim3 g1(1 << (log2n - logc1), npoly), g2(1 << (log1 - logc2), npoly);
-    const int thr = TILE / 16;
+    const int thr = tile / 16;
     if (fwd) {
-      launch16<true, true, false>(log1, g1, thr, smem(TILE), st, A, logc1, 1);
-      launch16<true, false, true>(log2n, g2, thr, smem(TILE), st, A, logc2, 1 << log1);
+      launch16<true, true, false>(log1, g1, thr, smem(tile), st, A, logc1, 1);
+      launch16<true, false, true>(log2n, g2, thr, smem(tile), st, A, logc2, 1 << log1);
     } else {
-      launch16<false, false, false>(log2n, g2, thr, smem(TILE), st, A, logc2, 1 << log1);
-      launch16<false, true, true>(log1, g1, thr, smem(TILE), st, A, logc1, 1);
+      launch16<false, false, false>(log2n, g2, thr, smem(tile), st, A, logc2, 1 << log1);
+      launch16<false, true, true>(log1, g1, thr, smem(tile), st, A, logc1, 1);
     }
     C.launches += 2;
   }

@@ -130,6 +130,7 @@ struct Context {
 
   // evaluator
   int batch = 8;
+  int ntt_tile_log = 12;  // words per CTA tile of the two-phase transform: 2^11 or 2^12
   bool dry = false;  // plan only: track levels, launch nothing
   bool trace_on = false;
   std::vector<std::string> trace;
@@ -217,6 +218,8 @@ struct QueryCols {
 };
 std::vector<BufP> ev_query_multi(Context& C, const std::vector<QueryCols>& qs, cudaStream_t st);
 size_t query_bytes_estimate(const Context& C, int n_ct, int level);
+// batches of one shape joined along the batch axis (a part of count 1 is repeated)
+BufP ev_concat(Context& C, const std::vector<std::pair<BufP, int>>& parts, cudaStream_t st);
 int plan_query_depth(Context& C, int level);
 std::vector<int> rotate_sum_elements(const Context& C);
 

