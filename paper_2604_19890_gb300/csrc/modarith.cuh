@@ -68,19 +68,6 @@ __device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 wp, u64 q) {
   return a * w - qh * q;
 }
 
-// a * w mod q in [0, 4q), any a < 2^64, q < 2^61. The Shoup quotient
-// hi64(a * w') is estimated from three 32-bit partial products
-//   a_hi w'_hi + hi32(a_hi w'_lo) + hi32(a_lo w'_hi),
-// dropping a_lo w'_lo and the carries of the middle products: the estimate is
-// at most 2 below the exact quotient, so the remainder is below 2q + 2q.
-// One wide and two high 32-bit products replace four wide ones.
-__device__ __forceinline__ u64 shoup_lazy4(u64 a, u64 w, u64 wp, u64 q) {
-  const uint32_t ah = (uint32_t)(a >> 32), al = (uint32_t)a;
-  const uint32_t wh = (uint32_t)(wp >> 32), wl = (uint32_t)wp;
-  const u64 qh = (u64)ah * wh + __umulhi(ah, wl) + __umulhi(al, wh);
-  return a * w - qh * q;
-}
-
 __device__ __forceinline__ u64 shoup(u64 a, u64 w, u64 wp, u64 q) {
   u64 r = shoup_lazy(a, w, wp, q);
   return r >= q ? r - q : r;

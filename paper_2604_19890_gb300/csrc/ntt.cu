@@ -180,7 +180,6 @@ __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, in
 
 // ---------------------------------------------------------------- radix-16 phases
 // Same scheme with sixteen words per thread (four stages per register round,
-// residues below 6q forward and 2q inverse with the cheaper quotient estimate,
 // two rounds per 256-point phase) for the two-phase transforms (N >= 8192).
 // Round 0 reads global memory straight into registers and the last round
 // writes straight back whenever that access is coalesced (always for column
@@ -251,7 +250,7 @@ __global__ void __launch_bounds__(256, 2) k_ntt16(NttArgs A, int logCPB, int m0)
       }
     }
     // stages j in [a - logu, b - logu]: d = 2^j registers apart
-    const u64 q2 = 2 * q, q4 = 4 * q;
+    const u64 q2 = 2 * q;
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
       const int jlo = a - logu, jhi = b - logu;
@@ -271,19 +270,16 @@ __global__ void __launch_bounds__(256, 2) k_ntt16(NttArgs A, int logCPB, int m0)
               if (p < d) {
                 const int k = k0 + p;
                 u64 U = x[k], V = x[k + d];
-                if (FWD) {  // residues stay below 6q
-                  if (U >= q4) U -= q4;
+                if (FWD) {
                   if (U >= q2) U -= q2;
-                  V = shoup_lazy4(V, w, wp, q);
+                  V = shoup_lazy(V, w, wp, q);
                   x[k] = U + V;
-                  x[k + d] = U - V + q4;
-                } else {  // residues stay below 2q
+                  x[k + d] = U - V + q2;
+                } else {
                   u64 s2 = U + V;
                   if (s2 >= q2) s2 -= q2;
-                  u64 t2 = shoup_lazy4(U - V + q2, w, wp, q);
-                  if (t2 >= q2) t2 -= q2;
                   x[k] = s2;
-                  x[k + d] = t2;
+                  x[k + d] = shoup_lazy(U - V + q2, w, wp, q);
                 }
               }
             }
@@ -298,7 +294,6 @@ __global__ void __launch_bounds__(256, 2) k_ntt16(NttArgs A, int logCPB, int m0)
         u64 v = x[k];
         if (LAST) {
           if (FWD) {
-            if (v >= 4 * q) v -= 4 * q;
             if (v >= 2 * q) v -= 2 * q;
             if (v >= q) v -= q;
           } else {
@@ -323,7 +318,6 @@ __global__ void __launch_bounds__(256, 2) k_ntt16(NttArgs A, int logCPB, int m0)
       u64 v = sm[swz(lin)];
       if (LAST) {
         if (FWD) {
-          if (v >= 4 * q) v -= 4 * q;
           if (v >= 2 * q) v -= 2 * q;
           if (v >= q) v -= q;
         } else {
