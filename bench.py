@@ -26,6 +26,15 @@ N_CT = 32
 SEED = 0x5EED0002
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
+# Integer-multiply ceiling of one GB300: 152 SMs x 4 sub-partitions x 16-lane
+# fmaheavy pipe (IMAD) = 64 IMAD per SM per clock, at the 2070 MHz maximum SM clock.
+IMAD_PEAK = 152 * 64 * 2.07e9
+# 32-bit multiplies in one 64-bit Shoup butterfly product (schoolbook minimum):
+# high 64 bits of a*w' (4) + low 64 bits of a*w (3) + low 64 bits of qhat*q (3).
+IMAD_PER_BUTTERFLY = 10
+# DRAM bytes per limb transform (forward, both phases) from the ncu capture in
+# profiles/ntt_n65536_l41.md, over the 1 MB (16 N) it must move.
+NTT_TRAFFIC_PER_ALGO_BYTE = None
 
 
 def hbm_peak():
@@ -94,7 +103,8 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -415,7 +425,7 @@ def run_ours(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     ssbuild.build()
-    prm = ssg.preset(PRESET)
+    prm = ssg.preset(args.preset)
     prm.seed = SEED + 1000 * rank
     g = ssg.Context(params=prm)
     g.keygen()
@@ -480,11 +490,26 @@ def run_ours(args):
         n, ms, b = ks[k]
         return b / (ms / 1e3) / 1e9 if ms > 0 else 0.0
 
-    roof = {"kernel": dom, "bound": "hbm", "achieved": gbs(dom), "peak": peak, "unit": "GB/s",
-            "frac": gbs(dom) / peak, "traffic": None, "peak_source": peak_kind,
-            "avg_launch_ms": ks[dom][1] / max(1, ks[dom][0]),
-            "algorithmic_bytes_per_launch": ks[dom][2] / max(1, ks[dom][0]),
-            "share_of_kernel_time": ks[dom][1] / total_k if total_k else None}
+    n_l, ms_l, b_l = ks[dom]
+    if dom == "ntt":
+        # integer-multiply roofline of the transform: butterflies = limbs * N/2 * log2 N
+        limbs = b_l / (16.0 * g.N)
+        bfly = limbs * g.N / 2 * int(np.log2(g.N))
+        achieved = bfly * IMAD_PER_BUTTERFLY / (ms_l / 1e3) / 1e12
+        peak_alu = IMAD_PEAK / 1e12
+        roof = {"kernel": "ntt", "bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "T IMAD/s",
+                "frac": achieved / peak_alu,
+                "traffic": (NTT_TRAFFIC_PER_ALGO_BYTE * b_l / n_l) if NTT_TRAFFIC_PER_ALGO_BYTE else None,
+                "peak_source": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz; 10 IMAD per Shoup butterfly",
+                "hbm_achieved_gbs": gbs(dom), "hbm_peak_gbs": peak, "hbm_frac": gbs(dom) / peak,
+                "hbm_peak_source": peak_kind, "avg_launch_ms": ms_l / max(1, n_l),
+                "algorithmic_bytes_per_launch": b_l / max(1, n_l),
+                "share_of_kernel_time": ms_l / total_k if total_k else None}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": gbs(dom), "peak": peak, "unit": "GB/s",
+                "frac": gbs(dom) / peak, "traffic": None, "peak_source": peak_kind,
+                "avg_launch_ms": ms_l / max(1, n_l), "algorithmic_bytes_per_launch": b_l / max(1, n_l),
+                "share_of_kernel_time": ms_l / total_k if total_k else None}
     classes = {k: {"launches": v[0], "ms": round(v[1], 3), "GB/s": round(gbs(k), 1),
                    "frac_of_hbm": round(gbs(k) / peak, 3)} for k, v in ks.items() if v[0]}
 
@@ -509,7 +534,7 @@ def run_ours(args):
                "d2h_bytes_per_step": int(2 * ol * g.N * 8), "ms_per_step": dt * 1e3}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and args.preset == PRESET:
         slope, fixed = query_ntt_count()
         per_ct = slope + fixed / n_ct
         v, dt, ntts = cpu_sample(rows, per_ct, n_ct)
@@ -518,12 +543,14 @@ def run_ours(args):
                          "%.1f s), scaled by the query's %.0f transforms per ciphertext x 32" % (ntts, dt, per_ct)}
 
     if rank == 0:
+        wl = ("compare-then-SUM query, N=2^%d, L=%d x %d-bit + %d special primes, p^r=%d^%d, %d slots, "
+              "%d ciphertexts per column (%d rows) per GPU" % (prm.logN, prm.L, prm.bits, prm.alpha, prm.p, prm.r,
+                                                            g.slots, n_ct, rows))
         line = {"metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-                "config": {"workload": "compare-then-SUM query, N=2^16, L=41 x 55-bit + 3 special primes, "
-                                       "p^r=257^3, 128 slots, 32 ciphertexts per column (4096 rows) per GPU",
-                           "batch": args.batch, "l2": "inputs (5.5 GB) larger than L2"},
+                "config": {"workload": wl, "batch": args.batch,
+                           "l2": "inputs (%.1f GB) larger than L2" % (4 * n_ct * 2 * prm.L * g.N * 8 / 1e9)},
                 "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
                                                                                    int(0.99 * len(lat_ms)))]},
                 "verified_against_plaintext": verified,
@@ -551,6 +578,8 @@ def main():
                     help="time one kernel family alone (profiling mode)")
     ap.add_argument("--limbs", type=int, default=512)
     ap.add_argument("--n-ct", type=int, default=N_CT, help="ciphertexts per column")
+    ap.add_argument("--preset", type=int, default=PRESET, choices=[0, 1, 2],
+                    help="0: N=2^13, 17^2; 1: N=2^15, 257^2; 2: N=2^16, 257^3 (the headline workload)")
     ap.add_argument("--serve", action="store_true", help="served form: Poisson arrivals, p50/p99")
     ap.add_argument("--batched", action="store_true", help="batched form: 64 mixed-N pairs, graph replay")
     ap.add_argument("--serve-ct", type=int, default=2)
