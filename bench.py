@@ -433,6 +433,11 @@ def run_ours(args):
     t = g.t
     n_ct = args.n_ct
     cols = synth.table(SEED + rank, n_ct, g.slots, t, columns=("a", "b", "c1", "c2"))
+    if args.preset == 0:  # SUM(a*a) WHERE c < 150, threshold encrypted
+        cols["b"] = cols["a"]
+        cols["c2"] = synth.threshold(SEED, g.slots, t, value=150)
+    elif args.preset == 1:  # SUM(a*b) WHERE c < t, t uniform and encrypted
+        cols["c2"] = synth.threshold(SEED, g.slots, t)
     enc = {}
     for i, (k, v) in enumerate(cols.items()):
         enc[k] = g.encrypt(np.stack([g.encode(x) for x in v]), 1000 * (i + 1))
