@@ -34,7 +34,7 @@ IMAD_PEAK = 152 * 64 * 2.07e9
 IMAD_PER_BUTTERFLY = 10
 # DRAM bytes per limb transform (forward, both phases) from the ncu capture in
 # profiles/ntt_n65536_l41.md, over the 1 MB (16 N) it must move.
-NTT_TRAFFIC_PER_ALGO_BYTE = None
+NTT_TRAFFIC_PER_ALGO_BYTE = 1.849
 
 
 def hbm_peak():
