@@ -56,6 +56,7 @@ def lib():
             "orc_rotate": (vp, [vp, vp, i32]),
             "orc_divide_by_p": (vp, [vp, vp]),
             "orc_mul": (vp, [vp, vp, vp]),
+            "orc_relin_drop": (vp, [vp, vp]),
             "orc_set_t_exp": (vp, [vp, vp, i32]),
             "orc_eval_g": (vp, [vp, vp, i32]),
             "orc_reduce": (i32, [vp, vp, P(vp)]),
@@ -295,6 +296,9 @@ class Oracle:
 
     def mul(self, a, b):
         return Ct(self, lib().orc_mul(self.h, a.h, b.h))
+
+    def relin_drop(self, a):
+        return Ct(self, lib().orc_relin_drop(self.h, a.h))
 
     def with_t_exp(self, a, t_exp):
         return Ct(self, lib().orc_set_t_exp(self.h, a.h, t_exp))

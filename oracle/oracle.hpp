@@ -157,7 +157,8 @@ Ct modswitch(const Context& C, const Ct& a, int drop);
 Ct modswitch_to(const Context& C, const Ct& a, int level);
 Ct rotate(const Context& C, const Ct& a, int g);
 Ct divide_by_p(const Context& C, const Ct& a);
-Ct mul(const Context& C, const Ct& a, const Ct& b);  // align, tensor, relin, drop one prime
+Ct relin_drop(const Context& C, const Ct& a);        // relinearise and drop the last prime in one ModDown
+Ct mul(const Context& C, const Ct& a, const Ct& b);  // align, tensor, relin_drop
 
 // ------------------------------------------------------------ coefficients
 std::vector<i64> g_table(int p, int e);    // G_{p,e} monomial coefficients, centred mod p^e

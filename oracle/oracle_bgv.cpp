@@ -668,18 +668,20 @@ static std::vector<Poly> scaled_base_conv(const Context& C, const std::vector<Po
   return out;
 }
 
-void keyswitch(const Context& C, const std::vector<Poly>& d, int l, const KSKey& K, int t_exp,
-               std::vector<Poly>& k0, std::vector<Poly>& k1) {
+// ModUp of every digit of d and the inner product with the key: acc0, acc1 over
+// the current data primes then the special primes (evaluation form).
+static void keyswitch_acc(const Context& C, const std::vector<Poly>& d, int l, const KSKey& K,
+                          std::vector<Poly>& acc0, std::vector<Poly>& acc1) {
   const Params& P = C.P;
   int N = P.N, alpha = P.alpha;
-  u64 t = ipow((u64)P.p, t_exp);
   std::vector<Poly> dc = d;
   for (int i = 0; i < l; ++i) ntt_inv(C, i, dc[i]);
   // target primes: the current data primes, then the special primes
   std::vector<int> tgt;
   for (int i = 0; i < l; ++i) tgt.push_back(i);
   for (int k = 0; k < alpha; ++k) tgt.push_back(P.L + k);
-  std::vector<Poly> acc0(tgt.size(), Poly(N, 0)), acc1(tgt.size(), Poly(N, 0));
+  acc0.assign(tgt.size(), Poly(N, 0));
+  acc1.assign(tgt.size(), Poly(N, 0));
   int dnum = (l + alpha - 1) / alpha;
   for (int j = 0; j < dnum; ++j) {
     int lo = j * alpha, hi = std::min((j + 1) * alpha, l);
@@ -719,6 +721,15 @@ void keyswitch(const Context& C, const std::vector<Poly>& d, int l, const KSKey&
       }
     }
   }
+}
+
+void keyswitch(const Context& C, const std::vector<Poly>& d, int l, const KSKey& K, int t_exp,
+               std::vector<Poly>& k0, std::vector<Poly>& k1) {
+  const Params& P = C.P;
+  int N = P.N, alpha = P.alpha;
+  u64 t = ipow((u64)P.p, t_exp);
+  std::vector<Poly> acc0, acc1;
+  keyswitch_acc(C, d, l, K, acc0, acc1);
   // ModDown: (acc - t*conv(t^{-1} acc mod P)) * P^{-1} on the data primes
   std::vector<int> sp, dp;
   for (int k = 0; k < alpha; ++k) sp.push_back(P.L + k);
@@ -829,10 +840,56 @@ Ct divide_by_p(const Context& C, const Ct& a) {
   return r;
 }
 
+// Relinearise a 3-component ciphertext and drop its last prime in one ModDown:
+// over Q_l and P, c_j = P*d_j + acc_j (P*d_j vanishes on the special primes);
+// with D = {q_{l-1}} and the special primes,
+//   c'_j = (c_j - t*conv([t^{-1} c_j]_D)) * (q_{l-1} P)^{-1}   over Q_{l-1}.
+Ct relin_drop(const Context& C, const Ct& a) {
+  if (a.ncomp != 3) throw std::runtime_error("relin_drop: needs 3 components");
+  const Params& P = C.P;
+  int N = P.N, l = a.level, alpha = P.alpha;
+  if (l < 2) throw std::runtime_error("relin_drop: out of levels");
+  u64 t = ipow((u64)P.p, a.t_exp);
+  std::vector<Poly> acc[2];
+  keyswitch_acc(C, a.c[2], l, C.rlk, acc[0], acc[1]);
+  std::vector<int> src, dst;
+  src.push_back(l - 1);
+  for (int k = 0; k < alpha; ++k) src.push_back(P.L + k);
+  for (int i = 0; i < l - 1; ++i) dst.push_back(i);
+  Ct r;
+  r.ncomp = 2; r.level = l - 1; r.t_exp = a.t_exp;
+  r.c.assign(2, std::vector<Poly>(l - 1, Poly(N)));
+  for (int c = 0; c < 2; ++c) {
+    // c_j on every data prime (index = prime) and special prime (index l + k)
+    std::vector<Poly> ext(l + alpha);
+    for (int i = 0; i < l; ++i) {
+      u64 q = C.primes[i], Pm = 1;
+      for (int k = 0; k < alpha; ++k) Pm = mulmod(Pm, C.primes[P.L + k] % q, q);
+      ext[i].resize(N);
+      for (int n = 0; n < N; ++n) ext[i][n] = addmod(mulmod(Pm, a.c[c][i][n], q), acc[c][i][n], q);
+    }
+    for (int k = 0; k < alpha; ++k) ext[l + k] = acc[c][l + k];
+    std::vector<Poly> xs;
+    xs.push_back(ext[l - 1]);
+    ntt_inv(C, l - 1, xs.back());
+    for (int k = 0; k < alpha; ++k) { xs.push_back(ext[l + k]); ntt_inv(C, P.L + k, xs.back()); }
+    std::vector<Poly> delta = scaled_base_conv(C, xs, src, dst, t);
+    for (int i = 0; i < l - 1; ++i) {
+      u64 q = C.primes[i];
+      ntt_fwd(C, i, delta[i]);
+      u64 Dm = C.primes[l - 1] % q;
+      for (int k = 0; k < alpha; ++k) Dm = mulmod(Dm, C.primes[P.L + k] % q, q);
+      u64 inv = invmod(Dm, q);
+      for (int n = 0; n < N; ++n) r.c[c][i][n] = mulmod(submod(ext[i][n], delta[i][n], q), inv, q);
+    }
+  }
+  return r;
+}
+
 Ct mul(const Context& C, const Ct& a, const Ct& b) {
   int l = std::min(a.level, b.level);
   Ct x = modswitch_to(C, a, l), y = modswitch_to(C, b, l);
-  return modswitch(C, relin(C, tensor(C, x, y)), 1);
+  return relin_drop(C, tensor(C, x, y));
 }
 
 }  // namespace orc

@@ -220,6 +220,7 @@ void* orc_modswitch(void* h, void* a, int drop) {
 }
 void* orc_rotate(void* h, void* a, int g) { return guard_ptr([&] { return box(rotate(ctx(h), ct(a), g)); }); }
 void* orc_divide_by_p(void* h, void* a) { return guard_ptr([&] { return box(divide_by_p(ctx(h), ct(a))); }); }
+void* orc_relin_drop(void* h, void* a) { return guard_ptr([&] { return box(relin_drop(ctx(h), ct(a))); }); }
 void* orc_mul(void* h, void* a, void* b) { return guard_ptr([&] { return box(mul(ctx(h), ct(a), ct(b))); }); }
 void* orc_set_t_exp(void* h, void* a, int t_exp) {
   return guard_ptr([&] { Ct x = ct(a); x.t_exp = t_exp; (void)h; return box(std::move(x)); });

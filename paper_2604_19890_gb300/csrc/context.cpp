@@ -342,6 +342,41 @@ void build_context(Context& C, const ss_params& prm) {
     for (int k = C.L; k < T; ++k) P = nt::mul(P, C.primes[k] % q, q);
     put2(nt::inv(P, q), q);
   }
+  // relinearise-and-drop: D = {q_{l-1}} and the special primes
+  C.off_pmod = tab.size();
+  for (int g = 0; g < T; ++g) {
+    if (g >= C.L) { tab.push_back(0); tab.push_back(0); continue; }
+    u64 q = C.primes[g], P = 1;
+    for (int k = C.L; k < T; ++k) P = nt::mul(P, C.primes[k] % q, q);
+    put2(P, q);
+  }
+  auto hatv = [&](const std::vector<int>& D, int s, int g) {
+    u64 qg = C.primes[g], v = 1 % qg;
+    for (int x : D)
+      if (x != s) v = nt::mul(v, C.primes[x] % qg, qg);
+    return v;
+  };
+  C.off_rd.assign(C.L + 1, 0);
+  for (int l = 2; l <= C.L; ++l) {
+    std::vector<int> D{l - 1};
+    for (int k = C.L; k < T; ++k) D.push_back(k);
+    C.off_rd[l] = tab.size();
+    for (int s : D)
+      for (int g = 0; g < T; ++g) tab.push_back(g < l - 1 ? hatv(D, s, g) : 0);
+    for (int g = 0; g < T; ++g) {
+      if (g >= l - 1) { tab.push_back(0); tab.push_back(0); continue; }
+      u64 q = C.primes[g], v = 1;
+      for (int x : D) v = nt::mul(v, C.primes[x] % q, q);
+      put2(nt::inv(v, q), q);
+    }
+    for (int te = 1; te <= C.r; ++te) {
+      C.off_rd_c1[{l, te}] = tab.size();
+      for (int s : D) {
+        u64 q = C.primes[s];
+        put2(nt::mul(nt::inv(C.tpow[te] % q, q), nt::inv(hatv(D, s, s), q), q), q);
+      }
+    }
+  }
   // modulus switching: level l drops [l-k, l)
   for (int l = 2; l <= C.L; ++l)
     for (int k = 1; k < l; ++k) {

@@ -4,7 +4,7 @@
 // Schedule (fixed, so that results are reproducible word for word):
 //  * multiplication: align both operands to the lower level by modulus
 //    switching the higher one (dropping all extra primes at once), tensor,
-//    relinearise, then drop exactly one prime;
+//    then relinearise and drop exactly one prime in one ModDown by q_{l-1} P;
 //  * linear combinations: a term above the combination's level is scaled at
 //    its own level, then switched down; terms already at that level are
 //    scaled and summed in one pass;
@@ -119,12 +119,10 @@ BufP ev_mul(Context& C, const BufP& a0, const BufP& b0, cudaStream_t st) {
   BufP a = ev_modswitch_to(C, a0, l, st), b = ev_modswitch_to(C, b0, l, st);
   if (a->count != b->count) throw Error(SS_ERR_SHAPE, "batch sizes differ");
   BufP t3 = alloc_buf(C, a->count, 3, l, a->t_exp, st);
-  BufP r = alloc_buf(C, a->count, 2, l, a->t_exp, st);
   BufP out = alloc_buf(C, a->count, 2, l - 1, a->t_exp, st);
   if (!C.dry) {
     k_tensor(C, *a, *b, *t3, st);
-    op_relin(C, *t3, *r, st);
-    op_modswitch(C, *r, 1, *out, st);
+    op_relin_drop(C, *t3, *out, st);
   }
   return out;
 }

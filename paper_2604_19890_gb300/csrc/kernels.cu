@@ -115,9 +115,9 @@ __global__ void k_tensor_impl(const u64* a, const u64* b, u64* out, int N, int l
 // [skip_lo, skip_hi):  sum_s [src_s * c1_s]_{q_s} * c2[s][g(m)]  (mod q_g), then
 // times post[g] when post != null.
 template <int MAXS>
-__global__ void k_bconv_impl(const u64* src, long src_os, int ns, int sp0, const u64* c1, const u64* c2, int T,
-                             u64* dst, long dst_os, int nd, int nq, int L, int skip_lo, int skip_hi, const u64* post,
-                             int N, const ModDesc* mods) {
+__global__ void k_bconv_impl(const u64* src, long src_os, int ns, int sp0, int nsq, const u64* c1, const u64* c2,
+                             int T, u64* dst, long dst_os, int nd, int nq, int L, int skip_lo, int skip_hi,
+                             const u64* post, int N, const ModDesc* mods) {
   int o = blockIdx.y;
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
@@ -125,7 +125,7 @@ __global__ void k_bconv_impl(const u64* src, long src_os, int ns, int sp0, const
 #pragma unroll
   for (int s = 0; s < MAXS; ++s) {
     if (s < ns) {
-      u64 q = MOD(mods, sp0 + s).q;
+      u64 q = MOD(mods, s < nsq ? sp0 + s : L + (s - nsq)).q;
       u64 x = src[(long)o * src_os + (long)s * N + n];
       y[s] = shoup(x, c1[2 * s], c1[2 * s + 1], q);
     }
@@ -351,6 +351,36 @@ __global__ void k_lincomb_impl(LinArgs A, int nterms, i64 cst, u64* out, int oca
   out[((size_t)(bt * ncomp + comp) * ocap + i) * N + n] = barrett_reduce128(acc.hi, acc.lo, md);
 }
 
+// acc_c[l-1] += P * d_c[l-1] (mod q_{l-1}) for c = 0, 1: the last data limb of
+// the extended ciphertext P*d + acc before it joins the dropped primes.
+__global__ void k_fixup_last_impl(u64* acc, long acc_os, int nx, const u64* d, long d_os, int dcap, int l,
+                                  const u64* pmod, int N, const ModDesc* mods) {
+  int o = blockIdx.y;  // (bt, c)
+  int bt = o >> 1, c = o & 1;
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int i = l - 1;
+  u64 q = MOD(mods, i).q;
+  u64* a = acc + (long)bt * acc_os + ((long)c * nx + i) * N + n;
+  u64 x = d[(long)bt * d_os + ((long)c * dcap + i) * N + n];
+  *a = add_mod(*a, shoup(x, pmod[2 * i], pmod[2 * i + 1], q), q);
+}
+
+// out_c[i] = ((P d_c[i] + acc_c[i]) - delta_c[i]) * (q_{l-1} P)^{-1}, i < l-1.
+__global__ void k_drop_combine_impl(const u64* acc, long acc_os, int nx, const u64* d, long d_os, int dcap,
+                                    const u64* delta, int nl, const u64* pmod, const u64* inv, u64* out, long out_os,
+                                    int ocap, int N, const ModDesc* mods) {
+  int poly = blockIdx.y;  // (bt, c, i)
+  int i = poly % nl, c = (poly / nl) & 1, bt = poly / (2 * nl);
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  u64 q = MOD(mods, i).q;
+  u64 x = d[(long)bt * d_os + ((long)c * dcap + i) * N + n];
+  u64 v = add_mod(shoup(x, pmod[2 * i], pmod[2 * i + 1], q), acc[(long)bt * acc_os + ((long)c * nx + i) * N + n], q);
+  v = sub_mod(v, delta[((long)(bt * 2 + c) * nl + i) * N + n], q);
+  out[(long)bt * out_os + ((long)c * ocap + i) * N + n] = shoup(v, inv[2 * i], inv[2 * i + 1], q);
+}
+
 // out[g] = a[g]^2 for every prime g (evaluation form)
 __global__ void k_square_impl(const u64* a, u64* out, int N, const ModDesc* mods) {
   int g = blockIdx.y;
@@ -376,6 +406,25 @@ __global__ void k_batch_sum_impl(const u64* a, u64* out, int count, int ncomp, i
 }  // namespace
 
 // ======================================================================= launchers
+void k_fixup_last(Context& C, u64* acc, long acc_os, int nx, const Buf& d, int l, const u64* pmod, int B,
+                  cudaStream_t st) {
+  TIMED(KC_ELEM, 3.0 * 2 * B * C.N * 8.0,
+        k_fixup_last_impl<<<grid_for(C.N, 2 * B), TPB, 0, st>>>(acc, acc_os, nx, d.data, (long)d.ncomp * d.cap * C.N,
+                                                                 d.cap, l, pmod, C.N, C.d_mod));
+  LAUNCHED();
+}
+
+void k_drop_combine(Context& C, const u64* acc, long acc_os, int nx, const Buf& d, const u64* delta, int nl,
+                    const u64* pmod, const u64* inv, Buf& out, int B, cudaStream_t st) {
+  TIMED(KC_SUBSCALE, 4.0 * 2 * B * nl * C.N * 8.0,
+        k_drop_combine_impl<<<grid_for(C.N, 2 * B * nl), TPB, 0, st>>>(acc, acc_os, nx, d.data,
+                                                                        (long)d.ncomp * d.cap * C.N, d.cap, delta, nl,
+                                                                        pmod, inv, out.data,
+                                                                        (long)out.ncomp * out.cap * C.N, out.cap, C.N,
+                                                                        C.d_mod));
+  LAUNCHED();
+}
+
 void k_square(Context& C, const u64* a, u64* out, int nprimes, cudaStream_t st) {
   k_square_impl<<<grid_for(C.N, nprimes), TPB, 0, st>>>(a, out, C.N, C.d_mod);
   ++C.launches;
@@ -440,17 +489,19 @@ void k_tensor(Context& C, const Buf& a, const Buf& b, Buf& out, cudaStream_t st)
 }
 
 void k_bconv(Context& C, const u64* src, long src_os, int ns, int sp0, const u64* c1, const u64* c2, u64* dst,
-             long dst_os, int nd, int nq, int skip_lo, int skip_hi, const u64* post, int n_outer, cudaStream_t st) {
+             long dst_os, int nd, int nq, int skip_lo, int skip_hi, const u64* post, int n_outer, cudaStream_t st,
+             int nsq) {
+  if (nsq < 0) nsq = ns;  // every source is the data or special prime sp0 + s
   dim3 g = grid_for(C.N, n_outer);
   int kr_ = kt_begin(C, st);
   if (ns <= 4)
-    k_bconv_impl<4><<<g, TPB, 0, st>>>(src, src_os, ns, sp0, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo,
+    k_bconv_impl<4><<<g, TPB, 0, st>>>(src, src_os, ns, sp0, nsq, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo,
                                         skip_hi, post, C.N, C.d_mod);
   else if (ns <= 16)
-    k_bconv_impl<16><<<g, TPB, 0, st>>>(src, src_os, ns, sp0, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo,
+    k_bconv_impl<16><<<g, TPB, 0, st>>>(src, src_os, ns, sp0, nsq, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo,
                                          skip_hi, post, C.N, C.d_mod);
   else if (ns <= 64)
-    k_bconv_impl<64><<<g, TPB, 0, st>>>(src, src_os, ns, sp0, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo,
+    k_bconv_impl<64><<<g, TPB, 0, st>>>(src, src_os, ns, sp0, nsq, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo,
                                          skip_hi, post, C.N, C.d_mod);
   else
     throw Error(SS_ERR_PARAM, "base conversion from more than 64 primes");

@@ -141,6 +141,63 @@ void op_relin(Context& C, const Buf& a, Buf& out, cudaStream_t st) {
   keyswitch_impl(C, a, 2, C.rlk, &a, true, out, st);
 }
 
+// Relinearise and drop the last prime in one ModDown: after the key-switch
+// inner product acc (over Q_l and P), the extended ciphertext is P*d_c + acc_c;
+// with D = {q_{l-1}} and the special primes (contiguous in acc: limbs l-1 ..
+// l+alpha-1), out_c = ((P d_c + acc_c) - t conv([t^{-1}(P d_c + acc_c)]_D)) /
+// (q_{l-1} P) on the first l-1 primes.
+void op_relin_drop(Context& C, const Buf& in, Buf& out, cudaStream_t st) {
+  if (in.ncomp != 3) throw Error(SS_ERR_SHAPE, "relinearisation needs a 3-component ciphertext");
+  if (!C.have_keys) throw Error(SS_ERR_PARAM, "no keys");
+  const int N = C.N, l = in.level, B = in.count, a = C.alpha;
+  if (l < 2) throw Error(SS_ERR_LEVEL, "no prime left to drop");
+  const int dn = (l + a - 1) / a, nx = l + a, nl = l - 1;
+  out.ncomp = 2;
+  out.level = nl;
+  out.t_exp = in.t_exp;
+  const long in_os = (long)in.ncomp * in.cap * N;
+  const u64* d = in.data + (size_t)2 * in.cap * N;
+  // 1-3: ModUp and inner product, as in keyswitch_impl
+  u64* dc = static_cast<u64*>(pool_alloc((size_t)B * l * N * 8, st));
+  SS_CUDA(cudaMemcpy2DAsync(dc, (size_t)l * N * 8, d, (size_t)in_os * 8, (size_t)l * N * 8, B,
+                            cudaMemcpyDeviceToDevice, st));
+  ntt_inverse(C, PolySet{dc, (long)l * N, B, l, 0, l}, st);
+  const long ext_os = (long)dn * nx * N;
+  u64* ext = static_cast<u64*>(pool_alloc((size_t)B * ext_os * 8, st));
+  for (int j = 0; j < dn; ++j) {
+    int lo = j * a, hi = std::min(lo + a, l);
+    const u64* c1 = C.d_tables + C.off_modup.at({j, hi});
+    const u64* c2 = c1 + 2 * (hi - lo);
+    k_bconv(C, dc + (size_t)lo * N, (long)l * N, hi - lo, lo, c1, c2, ext + (size_t)j * nx * N, ext_os, nx, l, lo,
+            hi, nullptr, B, st);
+  }
+  PolySet ps{ext, (long)nx * N, B * dn, nx, 0, l};
+  ps.skip_w = a;
+  ps.skip_mod = dn;
+  ps.skip_level = l;
+  ntt_forward(C, ps, st);
+  pool_free(dc, st);
+  const long acc_os = 2L * nx * N;
+  u64* acc = static_cast<u64*>(pool_alloc((size_t)B * acc_os * 8, st));
+  k_ks_ip(C, d, in_os, ext, ext_os, C.rlk, l, acc, acc_os, B, st);
+  pool_free(ext, st);
+  // 4. fused ModDown by q_{l-1} P
+  const u64* pmod = C.d_tables + C.off_pmod;
+  k_fixup_last(C, acc, acc_os, nx, in, l, pmod, B, st);
+  ntt_inverse(C, PolySet{acc + (size_t)(l - 1) * N, (long)nx * N, 2 * B, a + 1, l - 1, 1}, st);
+  u64* delta = static_cast<u64*>(pool_alloc((size_t)2 * B * nl * N * 8, st));
+  const u64* c2 = C.d_tables + C.off_rd[l];
+  const u64* inv = c2 + (size_t)(a + 1) * C.ntot;
+  const u64* c1 = C.d_tables + C.off_rd_c1.at({l, in.t_exp});
+  const u64* post = C.d_tmod + (size_t)in.t_exp * C.ntot * 2;
+  k_bconv(C, acc + (size_t)(l - 1) * N, (long)nx * N, a + 1, l - 1, c1, c2, delta, (long)nl * N, nl, nl, 0, 0, post,
+          2 * B, st, 1);
+  ntt_forward(C, PolySet{delta, (long)nl * N, 2 * B, nl, 0, nl}, st);
+  k_drop_combine(C, acc, acc_os, nx, in, delta, nl, pmod, inv, out, B, st);
+  pool_free(acc, st);
+  pool_free(delta, st);
+}
+
 void op_modswitch(Context& C, const Buf& a, int k, Buf& out, cudaStream_t st) {
   const int N = C.N, l = a.level, nl = l - k, B = a.count, nc = a.ncomp;
   if (k <= 0) throw Error(SS_ERR_PARAM, "modswitch drop must be positive");

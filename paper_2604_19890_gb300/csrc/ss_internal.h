@@ -112,6 +112,11 @@ struct Context {
   // ModDown: t_exp -> offset of c1[alpha], c1s[alpha]; c2 [alpha][ntot]; Pinv[ntot][2]
   std::vector<size_t> off_md_c1;
   size_t off_md_c2 = 0, off_md_pinv = 0;
+  // relinearise-and-drop: level -> offset of c2[alpha+1][ntot], inv[ntot][2]; (level, t_exp) -> c1;
+  // P mod q per data prime [ntot][2]
+  std::vector<size_t> off_rd;
+  std::map<std::pair<int, int>, size_t> off_rd_c1;
+  size_t off_pmod = 0;
   // modswitch: (level, k) -> offset of c2[k][ntot], Qinv[ntot][2]; (level,k,t_exp) -> c1
   std::map<std::pair<int, int>, size_t> off_ms;
   std::map<std::tuple<int, int, int>, size_t> off_ms_c1;
@@ -164,8 +169,14 @@ void k_binary(Context& C, int op, const Buf& a, const Buf& b, Buf& out, cudaStre
 void k_scalar(Context& C, int op, const Buf& a, i64 c, Buf& out, cudaStream_t st);       // 0 mul, 1 add(c0), 2 mul p^-1
 void k_copy_limbs(Context& C, const Buf& a, Buf& out, int level, cudaStream_t st);
 void k_tensor(Context& C, const Buf& a, const Buf& b, Buf& out, cudaStream_t st);
+// sources s < nsq are data primes sp0 + s, the rest special primes L + (s - nsq) (nsq < 0: all sp0 + s)
 void k_bconv(Context& C, const u64* src, long src_os, int ns, int sp0, const u64* c1, const u64* c2, u64* dst,
-             long dst_os, int nd, int nq, int skip_lo, int skip_hi, const u64* post, int n_outer, cudaStream_t st);
+             long dst_os, int nd, int nq, int skip_lo, int skip_hi, const u64* post, int n_outer, cudaStream_t st,
+             int nsq = -1);
+void k_fixup_last(Context& C, u64* acc, long acc_os, int nx, const Buf& d, int l, const u64* pmod, int B,
+                  cudaStream_t st);
+void k_drop_combine(Context& C, const u64* acc, long acc_os, int nx, const Buf& d, const u64* delta, int nl,
+                    const u64* pmod, const u64* inv, Buf& out, int B, cudaStream_t st);
 void k_sub_scale(Context& C, const u64* a, long a_os, const u64* dl, long d_os, const u64* scale, const u64* add,
                  long add_os, u64* out, long out_os, int nl, int n_outer, cudaStream_t st);
 void k_ks_ip(Context& C, const u64* d, long d_os, const u64* ext, long ext_os, const KeyDev& K, int level,
@@ -193,6 +204,8 @@ void op_keygen(Context& C, const std::vector<int>& galois);
 void op_keyswitch(Context& C, const Buf& in, int comp, const KeyDev& K, const Buf* addend, Buf& out,
                   cudaStream_t st);  // out = addend + KS(in.comp)
 void op_relin(Context& C, const Buf& a, Buf& out, cudaStream_t st);
+// relinearise a 3-component batch and drop its last prime in one ModDown by q_{l-1} P
+void op_relin_drop(Context& C, const Buf& a, Buf& out, cudaStream_t st);
 void op_modswitch(Context& C, const Buf& a, int drop, Buf& out, cudaStream_t st);
 void op_rotate(Context& C, const Buf& a, int g, Buf& out, cudaStream_t st);
 // relinearisation with its scratch in a static device array (allocates nothing)

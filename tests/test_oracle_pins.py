@@ -297,6 +297,9 @@ def test_homomorphic_ops(small17):
         assert ms.level == rl.level - drop and chk(ms, A * B)
     m = o.mul(ca, cb)
     assert m.level == o.L - 1 and chk(m, A * B)
+    rd = o.relin_drop(tc)  # relinearise and drop one prime in one ModDown
+    assert rd.ncomp == 2 and rd.level == tc.level - 1 and chk(rd, A * B)
+    assert o.noise_budget(rd) > o.noise_budget(o.modswitch(rl, 1)) - 2
     half = o.slots // 2
     r5 = o.rotate(ca, 5)
     assert chk(r5, [A[(j + 1) % half + (j // half) * half] for j in range(o.slots)])
