@@ -332,23 +332,45 @@ struct LinArgs {
   i64 c[16];
 };
 
-__global__ void k_lincomb_impl(LinArgs A, int nterms, i64 cst, u64* out, int ocap, int N, int ncomp, int level,
-                               const ModDesc* mods) {
+__global__ void k_lincomb_impl(LinArgs A, int nterms, i64 cst, int small, u64* out, int ocap, int N, int ncomp,
+                               int level, const ModDesc* mods) {
   int poly = blockIdx.y;  // (bt, comp, i)
   int i = poly % level, comp = (poly / level) % ncomp, bt = poly / (level * ncomp);
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const Modulus& md = MOD(mods, i);
   const u64 q = md.q;
-  Acc128 acc;
-  acc.zero();
-  for (int t = 0; t < nterms; ++t) {
-    u64 y = A.ptr[t][((size_t)(bt * ncomp + comp) * A.cap[t] + i) * N + n];
-    i64 c = A.c[t];
-    acc.mac(y, c >= 0 ? (u64)c : q - (u64)(-c));
+  u64 r;
+  if (small) {
+    // |c| < 2^32: y * |c| is two 32x32 products; positive and negative terms
+    // are summed apart (each sum < 2^92) and reduced once each.
+    Acc128 pos, neg;
+    pos.zero();
+    neg.zero();
+    for (int t = 0; t < nterms; ++t) {
+      u64 y = A.ptr[t][((size_t)(bt * ncomp + comp) * A.cap[t] + i) * N + n];
+      i64 c = A.c[t];
+      uint32_t m = (uint32_t)(c >= 0 ? c : -c);
+      u64 p0 = (u64)(uint32_t)y * m, p1 = (u64)(uint32_t)(y >> 32) * m;
+      Acc128& a = c >= 0 ? pos : neg;
+      a.add(p0);
+      a.add(p1 << 32);
+      a.hi += p1 >> 32;
+    }
+    if (comp == 0 && cst != 0) (cst >= 0 ? pos : neg).add((u64)(cst >= 0 ? cst : -cst));
+    r = sub_mod(barrett_reduce128(pos.hi, pos.lo, md), barrett_reduce128(neg.hi, neg.lo, md), q);
+  } else {
+    Acc128 acc;
+    acc.zero();
+    for (int t = 0; t < nterms; ++t) {
+      u64 y = A.ptr[t][((size_t)(bt * ncomp + comp) * A.cap[t] + i) * N + n];
+      i64 c = A.c[t];
+      acc.mac(y, c >= 0 ? (u64)c : q - (u64)(-c));
+    }
+    if (comp == 0 && cst != 0) acc.add(cst >= 0 ? (u64)cst : q - (u64)(-cst));
+    r = barrett_reduce128(acc.hi, acc.lo, md);
   }
-  if (comp == 0 && cst != 0) acc.add(cst >= 0 ? (u64)cst : q - (u64)(-cst));
-  out[((size_t)(bt * ncomp + comp) * ocap + i) * N + n] = barrett_reduce128(acc.hi, acc.lo, md);
+  out[((size_t)(bt * ncomp + comp) * ocap + i) * N + n] = r;
 }
 
 // acc_c[l-1] += P * d_c[l-1] (mod q_{l-1}) for c = 0, 1: the last data limb of
@@ -436,15 +458,17 @@ void k_lincomb(Context& C, const std::vector<const Buf*>& ys, const std::vector<
   int nt = (int)ys.size();
   if (nt < 1 || nt > 16) throw Error(SS_ERR_PARAM, "linear combination of 1..16 terms");
   LinArgs A;
+  bool small = cst > -(1LL << 32) && cst < (1LL << 32);
   for (int t = 0; t < nt; ++t) {
     A.ptr[t] = ys[t]->data;
     A.cap[t] = ys[t]->cap;
     A.c[t] = cs[t];
+    small = small && cs[t] > -(1LL << 32) && cs[t] < (1LL << 32);
   }
   int polys = out.count * out.ncomp * out.level;
   TIMED(KC_ELEM, (nt + 1.0) * polys * C.N * 8.0,
-        k_lincomb_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(A, nt, cst, out.data, out.cap, C.N, out.ncomp,
-                                                              out.level, C.d_mod));
+        k_lincomb_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(A, nt, cst, small ? 1 : 0, out.data, out.cap, C.N,
+                                                              out.ncomp, out.level, C.d_mod));
   LAUNCHED();
 }
 

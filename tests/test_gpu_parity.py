@@ -116,12 +116,13 @@ def test_ops_parity(tiny):
     assert (g.decrypt_slots(gr) == (A * B) % g.t).all()
 
 
-@pytest.mark.parametrize("nterms", [1, 3, 15, 20])
-def test_linear_combination_parity(tiny, nterms):
+@pytest.mark.parametrize("nterms,big", [(1, False), (3, False), (15, False), (20, False), (4, True)])
+def test_linear_combination_parity(tiny, nterms, big):
     g, o = tiny
     rng = np.random.default_rng(30 + nterms)
     cts = [encrypt_both(g, o, rng.integers(0, g.t, (2, g.slots)), 2000 + 10 * i) for i in range(nterms)]
-    coeffs = [int(c) for c in rng.integers(-g.t // 2, g.t // 2, nterms)]
+    lim = (1 << 34) if big else g.t // 2  # |c| >= 2^32 takes the general 64-bit product path
+    coeffs = [int(c) for c in rng.integers(-lim, lim, nterms)]
     cst = int(rng.integers(-100, 100))
     got = g.linear_combination([c[0] for c in cts], coeffs, cst)
     ref = []
