@@ -113,35 +113,62 @@ __global__ void k_tensor_impl(const u64* a, const u64* b, u64* out, int N, int l
 // ---------------------------------------------------------------- base conversion
 // dst limb m (global prime g(m) = m < nq ? m : L + m - nq), m outside
 // [skip_lo, skip_hi):  sum_s [src_s * c1_s]_{q_s} * c2[s][g(m)]  (mod q_g), then
-// times post[g] when post != null.
-template <int MAXS>
-__global__ void k_bconv_impl(const u64* src, long src_os, int ns, int sp0, int nsq, const u64* c1, const u64* c2,
-                             int T, u64* dst, long dst_os, int nd, int nq, int L, int skip_lo, int skip_hi,
-                             const u64* post, int N, const ModDesc* mods) {
-  int o = blockIdx.y;
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
+// times post[g] when post != null. Source s lives on prime sp0 + s (s < nsq)
+// or L + s - nsq. Per block, the target moduli, Barrett constants, post
+// scalars and conversion constants are staged once in shared memory
+// (row m: q, mu, k, post, post', c2[0..ns)); threads walk the coefficients.
+template <int NS>
+__global__ void __launch_bounds__(256) k_bconv_impl(const u64* __restrict__ src, long src_os, int ns, int sp0, int nsq,
+                                                    const u64* __restrict__ c1, const u64* __restrict__ c2, int T,
+                                                    u64* __restrict__ dst, long dst_os, int nd, int nq, int L,
+                                                    int skip_lo, int skip_hi, const u64* __restrict__ post, int N,
+                                                    const ModDesc* mods) {
+  extern __shared__ u64 sh[];
+  const int ns_ = NS > 0 ? NS : ns;
+  const int W = 5 + ns_;
+  for (int m = threadIdx.x; m < nd; m += blockDim.x) {
+    int g = m < nq ? m : L + (m - nq);
+    const Modulus& md = MOD(mods, g);
+    u64* e = sh + m * W;
+    e[0] = md.q;
+    e[1] = md.mu;
+    e[2] = (u64)md.kbits;
+    e[3] = post ? post[2 * g] : 0;
+    e[4] = post ? post[2 * g + 1] : 0;
+    for (int s = 0; s < ns_; ++s) e[5 + s] = c2[(long)s * T + g];
+  }
+  __syncthreads();
+  const int o = blockIdx.y;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
+  constexpr int MAXS = NS > 0 ? NS : 64;
   u64 y[MAXS];
 #pragma unroll
   for (int s = 0; s < MAXS; ++s) {
-    if (s < ns) {
-      u64 q = MOD(mods, s < nsq ? sp0 + s : L + (s - nsq)).q;
-      u64 x = src[(long)o * src_os + (long)s * N + n];
-      y[s] = shoup(x, c1[2 * s], c1[2 * s + 1], q);
+    if (s < ns_) {
+      const int gs = s < nsq ? sp0 + s : L + (s - nsq);
+      const u64 qs = MOD(mods, gs).q;
+      y[s] = shoup(src[o * src_os + (long)s * N + n], c1[2 * s], c1[2 * s + 1], qs);
     }
   }
-  for (int m = 0; m < nd; ++m) {
-    if (m >= skip_lo && m < skip_hi) continue;
-    int g = m < nq ? m : L + (m - nq);
-    const Modulus& md = MOD(mods, g);
-    Acc128 acc;
-    acc.zero();
+  u64* out = dst + o * dst_os + n;
+  for (int part = 0; part < 2; ++part) {
+    const int m0 = part == 0 ? 0 : skip_hi, m1 = part == 0 ? min(skip_lo, nd) : nd;
+    for (int m = m0; m < m1; ++m) {
+      const u64* e = sh + m * W;
+      Acc128 acc;
+      acc.zero();
 #pragma unroll
-    for (int s = 0; s < MAXS; ++s)
-      if (s < ns) acc.mac(y[s], __ldg(c2 + (long)s * T + g));
-    u64 v = barrett_reduce128(acc.hi, acc.lo, md);
-    if (post) v = shoup(v, __ldg(post + 2 * g), __ldg(post + 2 * g + 1), md.q);
-    dst[(long)o * dst_os + (long)m * N + n] = v;
+      for (int s = 0; s < MAXS; ++s)
+        if (s < ns_) acc.mac(y[s], e[5 + s]);
+      Modulus md;
+      md.q = e[0];
+      md.mu = e[1];
+      md.kbits = (int)e[2];
+      u64 v = barrett_reduce128(acc.hi, acc.lo, md);
+      if (post) v = shoup(v, e[3], e[4], md.q);
+      out[(long)m * N] = v;
+    }
   }
 }
 
@@ -344,20 +371,28 @@ __global__ void k_lincomb_impl(LinArgs A, int nterms, i64 cst, int small, u64* o
   if (small) {
     // |c| < 2^32: y * |c| is two 32x32 products; positive and negative terms
     // are summed apart (each sum < 2^92) and reduced once each.
+    // terms arrive sorted: the first `small` - 1 have c >= 0, the rest c < 0
     Acc128 pos, neg;
     pos.zero();
     neg.zero();
+    const int npos = small - 1;
     for (int t = 0; t < nterms; ++t) {
       u64 y = A.ptr[t][((size_t)(bt * ncomp + comp) * A.cap[t] + i) * N + n];
-      i64 c = A.c[t];
-      uint32_t m = (uint32_t)(c >= 0 ? c : -c);
-      u64 p0 = (u64)(uint32_t)y * m, p1 = (u64)(uint32_t)(y >> 32) * m;
-      Acc128& a = c >= 0 ? pos : neg;
-      a.add(p0);
-      a.add(p1 << 32);
-      a.hi += p1 >> 32;
+      const i64 c = A.c[t];
+      const uint32_t m = (uint32_t)(t < npos ? c : -c);
+      const u64 p0 = (u64)(uint32_t)y * m, p1 = (u64)(uint32_t)(y >> 32) * m;
+      if (t < npos) {
+        pos.add(p0);
+        pos.add(p1 << 32);
+        pos.hi += p1 >> 32;
+      } else {
+        neg.add(p0);
+        neg.add(p1 << 32);
+        neg.hi += p1 >> 32;
+      }
     }
-    if (comp == 0 && cst != 0) (cst >= 0 ? pos : neg).add((u64)(cst >= 0 ? cst : -cst));
+    if (comp == 0 && cst > 0) pos.add((u64)cst);
+    if (comp == 0 && cst < 0) neg.add((u64)(-cst));
     r = sub_mod(barrett_reduce128(pos.hi, pos.lo, md), barrett_reduce128(neg.hi, neg.lo, md), q);
   } else {
     Acc128 acc;
@@ -459,15 +494,19 @@ void k_lincomb(Context& C, const std::vector<const Buf*>& ys, const std::vector<
   if (nt < 1 || nt > 16) throw Error(SS_ERR_PARAM, "linear combination of 1..16 terms");
   LinArgs A;
   bool small = cst > -(1LL << 32) && cst < (1LL << 32);
-  for (int t = 0; t < nt; ++t) {
-    A.ptr[t] = ys[t]->data;
-    A.cap[t] = ys[t]->cap;
-    A.c[t] = cs[t];
-    small = small && cs[t] > -(1LL << 32) && cs[t] < (1LL << 32);
+  for (int t = 0; t < nt; ++t) small = small && cs[t] > -(1LL << 32) && cs[t] < (1LL << 32);
+  int npos = 0, k2 = 0;
+  if (small) {  // non-negative scalars first (the sum does not depend on the order)
+    for (int t = 0; t < nt; ++t)
+      if (cs[t] >= 0) { A.ptr[k2] = ys[t]->data; A.cap[k2] = ys[t]->cap; A.c[k2] = cs[t]; ++k2; ++npos; }
+    for (int t = 0; t < nt; ++t)
+      if (cs[t] < 0) { A.ptr[k2] = ys[t]->data; A.cap[k2] = ys[t]->cap; A.c[k2] = cs[t]; ++k2; }
+  } else {
+    for (int t = 0; t < nt; ++t) { A.ptr[t] = ys[t]->data; A.cap[t] = ys[t]->cap; A.c[t] = cs[t]; }
   }
   int polys = out.count * out.ncomp * out.level;
   TIMED(KC_ELEM, (nt + 1.0) * polys * C.N * 8.0,
-        k_lincomb_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(A, nt, cst, small ? 1 : 0, out.data, out.cap, C.N,
+        k_lincomb_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(A, nt, cst, small ? npos + 1 : 0, out.data, out.cap, C.N,
                                                               out.ncomp, out.level, C.d_mod));
   LAUNCHED();
 }
@@ -517,18 +556,22 @@ void k_bconv(Context& C, const u64* src, long src_os, int ns, int sp0, const u64
              int nsq) {
   if (nsq < 0) nsq = ns;  // every source is the data or special prime sp0 + s
   dim3 g = grid_for(C.N, n_outer);
+  if (ns < 1 || ns > 64) throw Error(SS_ERR_PARAM, "base conversion from 1..64 primes");
+  if (skip_hi <= skip_lo) skip_lo = skip_hi = nd;
+  size_t smem = (size_t)nd * (5 + ns) * 8;
+  if (smem > 48 * 1024) throw Error(SS_ERR_PARAM, "base conversion tables exceed 48 KiB of shared memory");
   int kr_ = kt_begin(C, st);
-  if (ns <= 4)
-    k_bconv_impl<4><<<g, TPB, 0, st>>>(src, src_os, ns, sp0, nsq, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo,
-                                        skip_hi, post, C.N, C.d_mod);
-  else if (ns <= 16)
-    k_bconv_impl<16><<<g, TPB, 0, st>>>(src, src_os, ns, sp0, nsq, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo,
-                                         skip_hi, post, C.N, C.d_mod);
-  else if (ns <= 64)
-    k_bconv_impl<64><<<g, TPB, 0, st>>>(src, src_os, ns, sp0, nsq, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo,
-                                         skip_hi, post, C.N, C.d_mod);
-  else
-    throw Error(SS_ERR_PARAM, "base conversion from more than 64 primes");
+#define SS_BCONV(NSV)                                                                                     \
+  k_bconv_impl<NSV><<<g, TPB, smem, st>>>(src, src_os, ns, sp0, nsq, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, \
+                                          skip_lo, skip_hi, post, C.N, C.d_mod)
+  switch (ns) {
+    case 1: SS_BCONV(1); break;
+    case 2: SS_BCONV(2); break;
+    case 3: SS_BCONV(3); break;
+    case 4: SS_BCONV(4); break;
+    default: SS_BCONV(0); break;
+  }
+#undef SS_BCONV
   kt_end(C, kr_, KC_BCONV, (double)(ns + nd - (skip_hi - skip_lo)) * n_outer * C.N * 8.0, st);
   LAUNCHED();
 }
