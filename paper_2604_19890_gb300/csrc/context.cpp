@@ -277,10 +277,10 @@ void build_context(Context& C, const ss_params& prm) {
       u64* o = &tw[(size_t)i * 4 * N];
       for (int k = 0; k < N; ++k) {
         int rk = nt::brv(k, C.logN);
-        o[k] = fw[rk];
-        o[N + k] = nt::shoup(fw[rk], q);
-        o[2 * N + k] = bw[rk];
-        o[3 * N + k] = nt::shoup(bw[rk], q);
+        o[2 * k] = fw[rk];
+        o[2 * k + 1] = nt::shoup(fw[rk], q);
+        o[2 * N + 2 * k] = bw[rk];
+        o[2 * N + 2 * k + 1] = nt::shoup(bw[rk], q);
       }
       u64 ni = nt::inv((u64)N % q, q);
       ninv[2 * i] = ni;

@@ -19,13 +19,21 @@ namespace {
 
 constexpr int TILE = 4096;  // words per CTA tile (32 KiB of shared memory)
 
+// resident CTAs per SM the radix-16 phases are compiled for (forward, inverse)
+#ifndef SS_NTT_MINB_F
+#define SS_NTT_MINB_F 3
+#endif
+#ifndef SS_NTT_MINB_I
+#define SS_NTT_MINB_I 3
+#endif
+
 struct NttArgs {
   u64* base;
   long outer_stride;
   int n_outer, nl, q0, nq, L, N;
   int skip_w, skip_mod, skip_level;
   const Modulus* mods;
-  const u64* tw;     // per prime 4N words
+  const u64* tw;     // per prime 4N words: (w, w') pairs forward, then inverse
   const u64* ninv;   // per prime (N^-1, shoup)
 };
 
@@ -53,8 +61,8 @@ __device__ __forceinline__ int swz(int lin) { return lin + (lin >> 3); }
 // registers (k, k + 2^j). Butterflies of one 2t-block share one twiddle,
 // index (mg << sg) + r/(2t), sg = logS - 1 - log2(t).
 template <bool FWD, int JLO, int JHI>
-__device__ __forceinline__ void ntt_round(u64 (&x)[8], int rbase, int logu, int logS, int mg, const u64* __restrict__ tw,
-                                          const u64* __restrict__ tws, u64 q) {
+__device__ __forceinline__ void ntt_round(u64 (&x)[8], int rbase, int logu, int logS, int mg,
+                                          const ulonglong2* __restrict__ tw, u64 q) {
   const u64 q2 = 2 * q;
 #pragma unroll
   for (int jj = JLO; jj <= JHI; ++jj) {
@@ -66,7 +74,8 @@ __device__ __forceinline__ void ntt_round(u64 (&x)[8], int rbase, int logu, int 
     for (int blk = 0; blk < 4 / d; ++blk) {
       const int k0 = blk * 2 * d;
       const int widx = (mg << sg) + ((rbase + (k0 << logu)) >> (logt + 1));
-      const u64 w = __ldg(tw + widx), wp = __ldg(tws + widx);
+      const ulonglong2 wv = __ldg(tw + widx);
+      const u64 w = wv.x, wp = wv.y;
 #pragma unroll
       for (int p = 0; p < d; ++p) {
         const int k = k0 + p;
@@ -89,14 +98,14 @@ __device__ __forceinline__ void ntt_round(u64 (&x)[8], int rbase, int logu, int 
 
 template <bool FWD>
 __device__ __forceinline__ void ntt_round_dispatch(int jlo, int jhi, u64 (&x)[8], int rbase, int logu, int logS, int mg,
-                                                   const u64* tw, const u64* tws, u64 q) {
+                                                   const ulonglong2* tw, u64 q) {
   switch (jlo * 3 + jhi) {
-    case 0: ntt_round<FWD, 0, 0>(x, rbase, logu, logS, mg, tw, tws, q); break;
-    case 1: ntt_round<FWD, 0, 1>(x, rbase, logu, logS, mg, tw, tws, q); break;
-    case 2: ntt_round<FWD, 0, 2>(x, rbase, logu, logS, mg, tw, tws, q); break;
-    case 4: ntt_round<FWD, 1, 1>(x, rbase, logu, logS, mg, tw, tws, q); break;
-    case 5: ntt_round<FWD, 1, 2>(x, rbase, logu, logS, mg, tw, tws, q); break;
-    default: ntt_round<FWD, 2, 2>(x, rbase, logu, logS, mg, tw, tws, q); break;
+    case 0: ntt_round<FWD, 0, 0>(x, rbase, logu, logS, mg, tw, q); break;
+    case 1: ntt_round<FWD, 0, 1>(x, rbase, logu, logS, mg, tw, q); break;
+    case 2: ntt_round<FWD, 0, 2>(x, rbase, logu, logS, mg, tw, q); break;
+    case 4: ntt_round<FWD, 1, 1>(x, rbase, logu, logS, mg, tw, q); break;
+    case 5: ntt_round<FWD, 1, 2>(x, rbase, logu, logS, mg, tw, q); break;
+    default: ntt_round<FWD, 2, 2>(x, rbase, logu, logS, mg, tw, q); break;
   }
 }
 
@@ -112,8 +121,7 @@ __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, in
   int pidx;
   if (!poly_of(A, blockIdx.y, ptr, pidx)) return;
   const u64 q = A.mods[pidx].q;
-  const u64* tw = A.tw + (size_t)pidx * 4 * A.N + (FWD ? 0 : 2 * A.N);
-  const u64* tws = tw + A.N;
+  const ulonglong2* tw = reinterpret_cast<const ulonglong2*>(A.tw + (size_t)pidx * 4 * A.N + (FWD ? 0 : 2 * A.N));
   const int S = 1 << logS, CPB = 1 << logCPB, W = S << logCPB;
   const int tid = threadIdx.x, T = blockDim.x;
   const int tile = blockIdx.x;
@@ -153,7 +161,7 @@ __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, in
       int r = rbase + (k << logu);
       x[k] = sm[swz(COLS ? (r << logCPB) + c : (c << logS) + r)];
     }
-    ntt_round_dispatch<FWD>(a - logu, b - logu, x, rbase, logu, logS, mg, tw, tws, q);
+    ntt_round_dispatch<FWD>(a - logu, b - logu, x, rbase, logu, logS, mg, tw, q);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       int r = rbase + (k << logu);
@@ -188,14 +196,13 @@ __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, in
 // blockDim = CPB*S/16, S = 2^LOGS with 5 <= LOGS <= 8. Every round's stage
 // range is a compile-time constant, so the sixteen words stay in registers.
 template <bool FWD, bool COLS, bool LAST, int LOGS>
-__global__ void __launch_bounds__(256, 2) k_ntt16(NttArgs A, int logCPB, int m0) {
+__global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_ntt16(NttArgs A, int logCPB, int m0) {
   extern __shared__ u64 sm[];
   u64* ptr;
   int pidx;
   if (!poly_of(A, blockIdx.y, ptr, pidx)) return;
   const u64 q = A.mods[pidx].q;
-  const u64* tw = A.tw + (size_t)pidx * 4 * A.N + (FWD ? 0 : 2 * A.N);
-  const u64* tws = tw + A.N;
+  const ulonglong2* tw = reinterpret_cast<const ulonglong2*>(A.tw + (size_t)pidx * 4 * A.N + (FWD ? 0 : 2 * A.N));
   constexpr int S = 1 << LOGS;
   const int CPB = 1 << logCPB, W = S << logCPB;
   const int tid = threadIdx.x, T = blockDim.x;
@@ -264,7 +271,8 @@ __global__ void __launch_bounds__(256, 2) k_ntt16(NttArgs A, int logCPB, int m0)
           if (blk < 8 / d) {
             const int k0 = blk * 2 * d;
             const int widx = (mg << sg) + ((rbase + (k0 << logu)) >> (logt + 1));
-            const u64 w = __ldg(tw + widx), wp = __ldg(tws + widx);
+            const ulonglong2 wv = __ldg(tw + widx);
+            const u64 w = wv.x, wp = wv.y;
 #pragma unroll
             for (int p = 0; p < 8; ++p) {
               if (p < d) {
