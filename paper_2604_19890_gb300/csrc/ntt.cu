@@ -55,6 +55,16 @@ __device__ __forceinline__ bool poly_of(const NttArgs& A, int poly, u64*& ptr, i
 // spreads the strided round accesses over all banks.
 __device__ __forceinline__ int swz(int lin) { return lin + (lin >> 3); }
 
+// v < 64q  ->  v mod q. The quotient estimate k = floor(t * mq / 2^24) from
+// t = floor(v / 2^(kb-8)) and mq = floor(2^(kb+16) / q) satisfies
+// v/q - 2 < k <= v/q, so v - k q lies in [0, 2q) and one subtraction ends it.
+__device__ __forceinline__ u64 reduce_lazy(u64 v, u64 q, int kb, uint32_t mq) {
+  const uint32_t t = (uint32_t)(v >> (kb - 8));
+  const uint32_t k = (t * mq) >> 24;
+  const u64 r = v - (u64)k * q;
+  return r >= q ? r - q : r;
+}
+
 // One round of up to three radix-2 stages held in registers. The thread owns
 // the eight words r_k = rbase + k*u (rbase = B*8u + o, o < u); the round's
 // stages have half-distances t = u*2^j for j in [JLO, JHI] and pair the
@@ -195,6 +205,10 @@ __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, in
 // tile passes through shared memory once more.
 // blockDim = CPB*S/16, S = 2^LOGS with 5 <= LOGS <= 8. Every round's stage
 // range is a compile-time constant, so the sixteen words stay in registers.
+// The forward butterfly here never reduces its upper input: each stage adds
+// less than 2q to the bound, so inputs below 4q leave a log2 N <= 16 stage
+// transform below 36q < 2^64 (primes below 2^58), and the last phase brings
+// every word back to [0, q) once (reduce_lazy).
 template <bool FWD, bool COLS, bool LAST, int LOGS>
 __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_ntt16(NttArgs A, int logCPB, int m0) {
   extern __shared__ u64 sm[];
@@ -221,6 +235,8 @@ __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_nt
   }
   u64 ni = 0, nip = 0;
   if (LAST && !FWD) { ni = A.ninv[2 * pidx]; nip = A.ninv[2 * pidx + 1]; }
+  const int kb = A.mods[pidx].kbits;
+  const uint32_t mq = (uint32_t)(A.mods[pidx].mu >> 47);
 #pragma unroll
   for (int rho = 0; rho < NR; ++rho) {
     const int ns = (LOGS - 4 * rho) < 4 ? (LOGS - 4 * rho) : 4;
@@ -279,7 +295,6 @@ __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_nt
                 const int k = k0 + p;
                 u64 U = x[k], V = x[k + d];
                 if (FWD) {
-                  if (U >= q2) U -= q2;
                   V = shoup_lazy(V, w, wp, q);
                   x[k] = U + V;
                   x[k + d] = U - V + q2;
@@ -300,14 +315,7 @@ __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_nt
       for (int k = 0; k < 16; ++k) {
         int r = rbase + (k << logu);
         u64 v = x[k];
-        if (LAST) {
-          if (FWD) {
-            if (v >= 2 * q) v -= 2 * q;
-            if (v >= q) v -= q;
-          } else {
-            v = shoup(v, ni, nip, q);
-          }
-        }
+        if (LAST) v = FWD ? reduce_lazy(v, q, kb, mq) : shoup(v, ni, nip, q);
         if (COLS) gbase[(long)r * stride + c] = v;
         else gbase[(c << LOGS) + r] = v;
       }
@@ -324,14 +332,7 @@ __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_nt
   if (!DOUT) {
     for (int lin = tid; lin < W; lin += T) {
       u64 v = sm[swz(lin)];
-      if (LAST) {
-        if (FWD) {
-          if (v >= 2 * q) v -= 2 * q;
-          if (v >= q) v -= q;
-        } else {
-          v = shoup(v, ni, nip, q);
-        }
-      }
+      if (LAST) v = FWD ? reduce_lazy(v, q, kb, mq) : shoup(v, ni, nip, q);
       gbase[lin] = v;
     }
   }

@@ -78,6 +78,34 @@ def test_ntt_parity(logN):
     assert (t.cpu().numpy().view(np.uint64) == data).all()
 
 
+@pytest.mark.parametrize("logN,bits", [(13, 58), (16, 58), (16, 30)])
+def test_ntt_extreme_inputs(logN, bits):
+    """Largest residues (every word q - 1, alternating 0 / q - 1, a single
+    q - 1) at the widest and narrowest allowed primes: the forward transform
+    lets lazy residues grow through all stages before one final reduction."""
+    import torch
+    L = 2
+    g = gpu_ctx(logN=logN, L=L, alpha=1, bits=bits, p=17, r=1, h=4, nmax=0, seed=3)
+    o = O.Oracle(logN=logN, L=L, alpha=1, bits=bits, p=17, r=1, h=4, seed=3)
+    rows = []
+    for i in range(L):
+        q = int(g.primes[i])
+        full = np.full(g.N, q - 1, dtype=np.uint64)
+        alt = full.copy()
+        alt[::2] = 0
+        one = np.zeros(g.N, dtype=np.uint64)
+        one[g.N // 3] = q - 1
+        rows.append((i, [full, alt, one]))
+    data = np.stack([rows[i % L][1][k] for k in range(3) for i in range(L)])
+    t = torch.from_numpy(data.view(np.int64).copy()).cuda()
+    g.ntt_forward(t, 0, L)
+    fw = t.cpu().numpy().view(np.uint64).copy()
+    for j in range(data.shape[0]):
+        assert (fw[j] == o.ntt_fwd(j % L, data[j])).all(), j
+    g.ntt_inverse(t, 0, L)
+    assert (t.cpu().numpy().view(np.uint64) == data).all()
+
+
 def test_encrypt_batch_parity(tiny):
     g, o = tiny
     rng = np.random.default_rng(1)
