@@ -262,6 +262,27 @@ int32_t ss_trace_get(ss_ctx* ctx, char* buf, int32_t len);
 ss_status ss_kernel_timing(ss_ctx* ctx, int32_t on);
 ss_status ss_kernel_stats(ss_ctx* ctx, int32_t cls, uint64_t* launches, double* ms, double* bytes);
 
+/* Per-stage breakdown of the query while kernel timing is on, mirroring the
+ * runtime breakdown of LT in Section 5 (reduction, comparison, aggregation,
+ * modulus raising) plus the rest of the query:
+ *   0 reduction (d = a - b and Algorithm 3)   1 comparison (F_LT, F_EQ per digit)
+ *   2 aggregation (the fold of Algorithm 4)   3 modulus raising (Section 4.4)
+ *   4 masked product ind * (a * b)            5 SUM (batch total and rotate-and-sum)
+ * Returns how many times the stage ran and its total milliseconds (CUDA events
+ * on the query's stream) since timing was switched on. The paper has no
+ * counterpart of this call; it is measurement. */
+ss_status ss_stage_stats(ss_ctx* ctx, int32_t stage, uint64_t* count, double* ms);
+
+/* Integer-pipe ceilings on the current device, for the roofline of the
+ * ALU-bound kernels (measurement; the paper has no counterpart). kind 0:
+ * 32-bit multiply-adds per second; kind 1: forward butterflies per second
+ * (Harvey's form: one conditional subtraction, one 64-bit Shoup product, the
+ * lazy add and subtract; residues held in registers, no memory traffic).
+ * iters in [1, 2^20] sets the loop length (every thread of one full wave of
+ * CTAs runs 8 operations per iteration). Allocates and frees a small buffer;
+ * synchronises its own stream. */
+ss_status ss_alu_probe(int32_t kind, int32_t iters, double* per_second);
+
 /* Count of kernels this library has launched since context creation. */
 uint64_t ss_launch_count(const ss_ctx* ctx);
 

@@ -83,6 +83,8 @@ _SIGS = {
     "ss_trace": (C.c_int, [C.c_void_p, C.c_int32]),
     "ss_trace_get": (C.c_int32, [C.c_void_p, C.c_char_p, C.c_int32]),
     "ss_launch_count": (C.c_uint64, [C.c_void_p]),
+    "ss_stage_stats": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_double)]),
+    "ss_alu_probe": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
     "ss_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(ss_batch_item), C.c_int32,
                                   C.POINTER(C.c_void_p)]),
     "ss_batch_config": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
@@ -103,6 +105,15 @@ _SIGS = {
 
 KERNEL_CLASSES = ["ntt", "base_conversion", "keyswitch_inner_product", "tensor", "sub_scale", "automorphism",
                   "elementwise", "sampling"]
+QUERY_STAGES = ["reduction", "comparison", "aggregation", "modulus_raising", "masked_product", "sum"]
+
+
+def alu_probe(kind, iters=4096):
+    """Integer-pipe ceiling on the current device: kind 0 = 32-bit IMAD/s,
+    kind 1 = 64-bit Shoup forward butterflies/s (registers only)."""
+    out = C.c_double()
+    _chk(lib().ss_alu_probe(int(kind), int(iters), C.byref(out)))
+    return out.value
 
 
 def declared_symbols():
@@ -526,4 +537,13 @@ class Context:
             n, ms, b = C.c_uint64(), C.c_double(), C.c_double()
             _chk(lib().ss_kernel_stats(self.h, i, C.byref(n), C.byref(ms), C.byref(b)))
             out[name] = (n.value, ms.value, b.value)
+        return out
+
+    def stage_stats(self):
+        """{stage: (runs, total ms)} of the query since timing was switched on."""
+        out = {}
+        for i, name in enumerate(QUERY_STAGES):
+            n, ms = C.c_uint64(), C.c_double()
+            _chk(lib().ss_stage_stats(self.h, i, C.byref(n), C.byref(ms)))
+            out[name] = (n.value, ms.value)
         return out

@@ -468,6 +468,7 @@ ss_status ss_kernel_timing(ss_ctx* ctx, int32_t on) {
     ss::kt_collect(C);
     if (on) {
       for (int k = 0; k < ss::KC_N; ++k) { C.kt.launches[k] = 0; C.kt.ms[k] = 0; C.kt.bytes[k] = 0; }
+      for (int k = 0; k < ss::ST_N; ++k) { C.kt.st_count[k] = 0; C.kt.st_ms[k] = 0; }
     }
     C.kt.on = on != 0;
   });
@@ -481,6 +482,23 @@ ss_status ss_kernel_stats(ss_ctx* ctx, int32_t cls, uint64_t* launches, double* 
     if (launches) *launches = C.kt.launches[cls];
     if (ms) *ms = C.kt.ms[cls];
     if (bytes) *bytes = C.kt.bytes[cls];
+  });
+}
+
+ss_status ss_stage_stats(ss_ctx* ctx, int32_t stage, uint64_t* count, double* ms) {
+  return guard([&] {
+    need(ctx != nullptr && stage >= 0 && stage < ss::ST_N, SS_ERR_PARAM, "bad argument");
+    ss::Context& C = ctx->C;
+    ss::kt_collect(C);
+    if (count) *count = C.kt.st_count[stage];
+    if (ms) *ms = C.kt.st_ms[stage];
+  });
+}
+
+ss_status ss_alu_probe(int32_t kind, int32_t iters, double* per_second) {
+  return guard([&] {
+    need((kind == 0 || kind == 1) && iters >= 1 && iters <= (1 << 20) && per_second, SS_ERR_PARAM, "bad argument");
+    *per_second = ss::alu_probe(kind, iters);
   });
 }
 

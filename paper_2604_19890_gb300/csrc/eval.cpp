@@ -285,10 +285,17 @@ static void compare_digit(Context& C, const BufP& x, BufP& lt, BufP& eq, cudaStr
 // Algorithm 4
 BufP ev_compare_lt(Context& C, const BufP& a, const BufP& b, cudaStream_t st) {
   int r = C.r;
-  BufP d = ev_sub(C, a, b, st);
-  std::vector<BufP> dg = ev_reduce(C, d, st);
+  std::vector<BufP> dg;
+  {
+    StageScope sc(C, ST_REDUCE, st);
+    dg = ev_reduce(C, ev_sub(C, a, b, st), st);
+  }
   std::vector<BufP> LT(r), EQ(r);
-  for (int i = 0; i < r; ++i) compare_digit(C, dg[i], LT[i], EQ[i], st);
+  {
+    StageScope sc(C, ST_COMPARE, st);
+    for (int i = 0; i < r; ++i) compare_digit(C, dg[i], LT[i], EQ[i], st);
+  }
+  StageScope sc(C, ST_AGGREGATE, st);
   BufP lt = LT[r - 1], eq = EQ[r - 1];
   for (int i = r - 2; i >= 0; --i) {
     lt = ev_add(C, lt, ev_mul(C, eq, LT[i], st), st);
@@ -301,6 +308,7 @@ BufP ev_compare_lt(Context& C, const BufP& a, const BufP& b, cudaStream_t st) {
 // Section 4.4
 BufP ev_raise(Context& C, const BufP& a, cudaStream_t st) {
   if (a->t_exp != 1) throw Error(SS_ERR_TMOD, "raise input must be at t = p");
+  StageScope sc(C, ST_RAISE, st);
   auto k = std::make_shared<Buf>(*a);
   k->owned = false;
   k->parent = a;
@@ -311,6 +319,7 @@ BufP ev_raise(Context& C, const BufP& a, cudaStream_t st) {
 }
 
 BufP ev_rotate_sum(Context& C, const BufP& a, cudaStream_t st) {
+  StageScope sc(C, ST_SUM, st);
   BufP s = a;
   for (int g : rotate_sum_elements(C)) {
     BufP r = alloc_buf(C, s->count, 2, s->level, s->t_exp, st);
@@ -323,6 +332,7 @@ BufP ev_rotate_sum(Context& C, const BufP& a, cudaStream_t st) {
 
 static BufP batch_total(Context& C, const BufP& R, cudaStream_t st) {
   if (R->count == 1) return R;
+  StageScope sc(C, ST_SUM, st);
   BufP out = alloc_buf(C, 1, R->ncomp, R->level, R->t_exp, st);
   if (!C.dry) k_batch_sum(C, *R, *out, st);
   return out;
@@ -341,9 +351,13 @@ BufP ev_query(Context& C, const BufP& A, const BufP& B, const BufP& C1, const Bu
     BufP a = slice_buf(A, b0, cnt, C.N), b = slice_buf(B, b0, cnt, C.N), c1 = slice_buf(C1, b0, cnt, C.N);
     BufP c2 = C2->count == 1 ? C2 : slice_buf(C2, b0, cnt, C.N);
     BufP ind = ev_raise(C, ev_compare_lt(C, c1, c2, st), st);
-    BufP prod = ev_mul(C, a, b, st);
-    BufP R = ev_mul(C, ind, prod, st);
+    BufP R;
+    {
+      StageScope sc(C, ST_PRODUCT, st);
+      R = ev_mul(C, ind, ev_mul(C, a, b, st), st);
+    }
     BufP part = batch_total(C, R, st);
+    StageScope sc(C, ST_SUM, st);
     total = total ? ev_add(C, total, part, st) : part;
   }
   return ev_rotate_sum(C, total, st);
@@ -431,18 +445,22 @@ std::vector<BufP> ev_query_multi(Context& C, const std::vector<QueryCols>& qs, c
   for (int b0 = 0; b0 < total; b0 += step) {
     int cnt = std::min(step, total - b0);
     BufP ind = ev_raise(C, ev_compare_lt(C, slice_buf(C1, b0, cnt, C.N), slice_buf(C2, b0, cnt, C.N), st), st);
+    StageScope sc(C, ST_PRODUCT, st);
     BufP R = ev_mul(C, ind, ev_mul(C, slice_buf(A, b0, cnt, C.N), slice_buf(B, b0, cnt, C.N), st), st);
     Rs.push_back({R, cnt});
   }
   BufP R = Rs.size() == 1 ? Rs[0].first : ev_concat(C, Rs, st);
   std::vector<std::pair<BufP, int>> parts;
-  int off = 0;
-  for (int k : n) {
-    BufP s = slice_buf(R, off, k, C.N);
-    BufP part = alloc_buf(C, 1, R->ncomp, R->level, R->t_exp, st);
-    if (!C.dry) k_batch_sum(C, *s, *part, st);
-    parts.push_back({part, 1});
-    off += k;
+  {
+    StageScope sc(C, ST_SUM, st);
+    int off = 0;
+    for (int k : n) {
+      BufP s = slice_buf(R, off, k, C.N);
+      BufP part = alloc_buf(C, 1, R->ncomp, R->level, R->t_exp, st);
+      if (!C.dry) k_batch_sum(C, *s, *part, st);
+      parts.push_back({part, 1});
+      off += k;
+    }
   }
   BufP S = ev_rotate_sum(C, parts.size() == 1 ? parts[0].first : ev_concat(C, parts, st), st);
   std::vector<BufP> out;

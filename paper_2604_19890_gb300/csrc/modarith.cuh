@@ -23,33 +23,7 @@ struct Modulus {
   int pad;
 };
 
-// High 64 bits of a 64x64 product. SS_MULHI_PTX selects an explicit chain of
-// 32-bit multiply-adds with carries (partial products a_i*b_j by word).
-#ifndef SS_MULHI_PTX
-#define SS_MULHI_PTX 0
-#endif
-__device__ __forceinline__ u64 mulhi64(u64 a, u64 b) {
-#if SS_MULHI_PTX
-  u64 r;
-  asm("{\n\t.reg .u32 a0, a1, b0, b1, t0, t1, t2;\n\t"
-      "mov.b64 {a0, a1}, %1;\n\t"
-      "mov.b64 {b0, b1}, %2;\n\t"
-      "mul.hi.u32 t0, a0, b0;\n\t"
-      "mad.lo.cc.u32 t0, a0, b1, t0;\n\t"
-      "madc.hi.u32 t1, a0, b1, 0;\n\t"
-      "mad.lo.cc.u32 t0, a1, b0, t0;\n\t"
-      "madc.hi.cc.u32 t1, a1, b0, t1;\n\t"
-      "madc.hi.u32 t2, a1, b1, 0;\n\t"
-      "mad.lo.cc.u32 t1, a1, b1, t1;\n\t"
-      "addc.u32 t2, t2, 0;\n\t"
-      "mov.b64 %0, {t1, t2};\n\t}"
-      : "=l"(r)
-      : "l"(a), "l"(b));
-  return r;
-#else
-  return __umul64hi(a, b);
-#endif
-}
+__device__ __forceinline__ u64 mulhi64(u64 a, u64 b) { return __umul64hi(a, b); }
 
 // x = (hi, lo) < 2^(63+k)  ->  x mod q in [0, q)
 __device__ __forceinline__ u64 barrett_reduce128(u64 hi, u64 lo, const Modulus& m) {

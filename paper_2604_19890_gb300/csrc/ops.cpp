@@ -382,7 +382,42 @@ void kt_end(Context& C, int rec, int cls, double bytes, cudaStream_t st) {
   if (C.kt.recs.size() > 4096) kt_collect(C);
 }
 
+int stage_begin(Context& C, int stage, cudaStream_t st) {
+  if (!C.kt.on || C.dry) return -1;
+  KTimer::SRec r;
+  r.a = kt_event(C);
+  r.b = kt_event(C);
+  r.stage = stage;
+  r.closed = false;
+  SS_CUDA(cudaEventRecord(r.a, st));
+  C.kt.srecs.push_back(r);
+  return (int)C.kt.srecs.size() - 1;
+}
+
+void stage_end(Context& C, int rec, cudaStream_t st) noexcept {
+  if (rec < 0 || rec >= (int)C.kt.srecs.size()) return;
+  if (cudaEventRecord(C.kt.srecs[rec].b, st) == cudaSuccess) C.kt.srecs[rec].closed = true;
+}
+
+// Stage records are folded in only when none is still open (a stage scope
+// keeps its index until it closes).
+static void stage_collect(Context& C) {
+  for (auto& r : C.kt.srecs)
+    if (!r.closed) return;
+  for (auto& r : C.kt.srecs) {
+    SS_CUDA(cudaEventSynchronize(r.b));
+    float ms = 0;
+    SS_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    C.kt.st_count[r.stage] += 1;
+    C.kt.st_ms[r.stage] += ms;
+    C.kt.pool.push_back(r.a);
+    C.kt.pool.push_back(r.b);
+  }
+  C.kt.srecs.clear();
+}
+
 void kt_collect(Context& C) {
+  stage_collect(C);
   if (C.kt.recs.empty()) return;
   SS_CUDA(cudaEventSynchronize(C.kt.recs.back().b));
   for (auto& r : C.kt.recs) {

@@ -75,6 +75,11 @@ struct KeyDev {
 // launching stream) and their algorithmic byte counts.
 enum KClass { KC_NTT = 0, KC_BCONV, KC_KSIP, KC_TENSOR, KC_SUBSCALE, KC_AUTOMORPH, KC_ELEM, KC_SAMPLE, KC_N };
 
+// Stages of the query for the per-stage breakdown (Section 5's runtime
+// breakdown of LT: reduction, comparison, aggregation, modulus raising; plus
+// the masked product and the SUM).
+enum Stage { ST_REDUCE = 0, ST_COMPARE, ST_AGGREGATE, ST_RAISE, ST_PRODUCT, ST_SUM, ST_N };
+
 struct KTimer {
   bool on = false;
   struct Rec {
@@ -86,6 +91,14 @@ struct KTimer {
   std::vector<cudaEvent_t> pool;
   unsigned long long launches[KC_N] = {};
   double ms[KC_N] = {}, bytes[KC_N] = {};
+  struct SRec {
+    cudaEvent_t a, b;
+    int stage;
+    bool closed;
+  };
+  std::vector<SRec> srecs;
+  unsigned long long st_count[ST_N] = {};
+  double st_ms[ST_N] = {};
 };
 
 struct Context {
@@ -244,6 +257,17 @@ std::vector<u64> decode(const Context& C, int t_exp, const u64* coeffs);
 int kt_begin(Context& C, cudaStream_t st);
 void kt_end(Context& C, int rec, int cls, double bytes, cudaStream_t st);
 void kt_collect(Context& C);
+double alu_probe(int kind, int iters);
+int stage_begin(Context& C, int stage, cudaStream_t st);
+void stage_end(Context& C, int rec, cudaStream_t st) noexcept;
+// Times the enclosing scope as one query stage when kernel timing is on.
+struct StageScope {
+  Context& C;
+  int rec;
+  cudaStream_t st;
+  StageScope(Context& c, int stage, cudaStream_t s) : C(c), rec(stage_begin(c, stage, s)), st(s) {}
+  ~StageScope() { stage_end(C, rec, st); }
+};
 
 inline void note(Context& C, const std::string& s) {
   if (C.trace_on) C.trace.push_back(s);
