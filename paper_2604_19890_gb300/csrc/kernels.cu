@@ -188,31 +188,41 @@ __global__ void k_sub_scale_impl(const u64* a, long a_os, const u64* dl, long d_
 
 // ---------------------------------------------------------------- key-switch inner product
 // acc[comp][m] = sum_j ext_j[m] * key_j[comp][g(m)], with ext_j[m] = d[m] on the
-// digit's own primes. 128-bit lazy sum over the digits, one reduction.
-__global__ void k_ks_ip_impl(const u64* d, long d_os, const u64* ext, long ext_os, const u64* kb, const u64* ka,
-                             int level, int alpha, int L, int T, u64* acc, long acc_os, int n_outer, int N,
-                             const ModDesc* mods) {
-  int m = blockIdx.y;  // local limb over level + alpha
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
+// digit's own primes. 128-bit lazy sum over the digits, one reduction. One
+// thread per (ciphertext o, limb m, coefficient n); the ciphertext index runs
+// fastest over the blocks, so the blocks that read one stretch of the key run
+// back to back and all but the first find it in L2.
+__global__ void __launch_bounds__(256) k_ks_ip_impl(const u64* __restrict__ d, long d_os, const u64* __restrict__ ext,
+                                                    long ext_os, const u64* __restrict__ kb,
+                                                    const u64* __restrict__ ka, int level, int alpha, int L, int T,
+                                                    u64* __restrict__ acc, long acc_os, int n_outer, int N,
+                                                    const ModDesc* mods) {
+  const int o = blockIdx.x % n_outer;
+  const int n = (blockIdx.x / n_outer) * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;  // local limb over level + alpha
   if (n >= N) return;
-  int g = m < level ? m : L + (m - level);
-  const Modulus& md = MOD(mods, g);
-  int dn = (level + alpha - 1) / alpha;
-  int nlx = level + alpha;
-  for (int o = 0; o < n_outer; ++o) {
-    Acc128 s0, s1;
-    s0.zero();
-    s1.zero();
-    for (int j = 0; j < dn; ++j) {
-      bool own = m < level && m / alpha == j;
-      u64 x = own ? d[(long)o * d_os + (long)m * N + n] : ext[(long)o * ext_os + ((long)j * nlx + m) * N + n];
-      size_t ko = ((size_t)j * T + g) * N + n;
-      s0.mac(x, __ldg(kb + ko));
-      s1.mac(x, __ldg(ka + ko));
-    }
-    acc[(long)o * acc_os + (long)m * N + n] = barrett_reduce128(s0.hi, s0.lo, md);
-    acc[(long)o * acc_os + ((long)nlx + m) * N + n] = barrett_reduce128(s1.hi, s1.lo, md);
+  const int g = m < level ? m : L + (m - level);
+  const Modulus md = MOD(mods, g);
+  const int dn = (level + alpha - 1) / alpha;
+  const int nlx = level + alpha;
+  const int jown = m < level ? m / alpha : -1;
+  const u64* kbp = kb + (size_t)g * N + n;
+  const u64* kap = ka + (size_t)g * N + n;
+  const size_t kstride = (size_t)T * N;
+  const u64* ep = ext + o * ext_os + (long)m * N + n;
+  const long jstride = (long)nlx * N;
+  Acc128 s0, s1;
+  s0.zero();
+  s1.zero();
+#pragma unroll 4
+  for (int j = 0; j < dn; ++j) {
+    const u64 x = j == jown ? d[o * d_os + (long)m * N + n] : ep[j * jstride];
+    s0.mac(x, __ldg(kbp + j * kstride));
+    s1.mac(x, __ldg(kap + j * kstride));
   }
+  u64* out = acc + o * acc_os + (long)m * N + n;
+  out[0] = barrett_reduce128(s0.hi, s0.lo, md);
+  out[(long)nlx * N] = barrett_reduce128(s1.hi, s1.lo, md);
 }
 
 // ---------------------------------------------------------------- automorphism
@@ -586,9 +596,11 @@ void k_sub_scale(Context& C, const u64* a, long a_os, const u64* dl, long d_os, 
 
 void k_ks_ip(Context& C, const u64* d, long d_os, const u64* ext, long ext_os, const KeyDev& K, int level, u64* acc,
              long acc_os, int n_outer, cudaStream_t st) {
-  TIMED(KC_KSIP, ((double)((level + C.alpha - 1) / C.alpha) * (level + C.alpha) * (n_outer + 2.0) + 2.0 * (level + C.alpha) * n_outer) * (double)C.N * 8.0,
-  k_ks_ip_impl<<<grid_for(C.N, level + C.alpha), TPB, 0, st>>>(d, d_os, ext, ext_os, K.b, K.a, level, C.alpha, C.L,
-                                                                C.ntot, acc, acc_os, n_outer, C.N, C.d_mod));
+  const int dn = (level + C.alpha - 1) / C.alpha;
+  const dim3 grid((unsigned)(n_outer * ((C.N + TPB - 1) / TPB)), (unsigned)(level + C.alpha));
+  TIMED(KC_KSIP, ((double)dn * (level + C.alpha) * (n_outer + 2.0) + 2.0 * (level + C.alpha) * n_outer) * (double)C.N * 8.0,
+        k_ks_ip_impl<<<grid, TPB, 0, st>>>(d, d_os, ext, ext_os, K.b, K.a, level, C.alpha, C.L, C.ntot, acc, acc_os,
+                                           n_outer, C.N, C.d_mod));
   LAUNCHED();
 }
 
