@@ -114,9 +114,12 @@ __global__ void k_tensor_impl(const u64* a, const u64* b, u64* out, int N, int l
 // dst limb m (global prime g(m) = m < nq ? m : L + m - nq), m outside
 // [skip_lo, skip_hi):  sum_s [src_s * c1_s]_{q_s} * c2[s][g(m)]  (mod q_g), then
 // times post[g] when post != null. Source s lives on prime sp0 + s (s < nsq)
-// or L + s - nsq. Per block, the target moduli, Barrett constants, post
-// scalars and conversion constants are staged once in shared memory
-// (row m: q, mu, k, post, post', c2[0..ns)); threads walk the coefficients.
+// or L + s - nsq. Per block, each target's modulus, its Montgomery inverse and
+// the constants c2[s][g] * post[g] * 2^64 mod q_g are staged once in shared
+// memory (row m: q, -q^-1 mod 2^64, c2'[0..ns)); every output is then a
+// 128-bit sum of ns products and one Montgomery reduction, which removes the
+// 2^64 and leaves the post factor applied. The sum stays below ns q_s q_g <
+// q_g 2^64 (primes below 2^58, ns <= 64), as the reduction needs.
 template <int NS>
 __global__ void __launch_bounds__(256) k_bconv_impl(const u64* __restrict__ src, long src_os, int ns, int sp0, int nsq,
                                                     const u64* __restrict__ c1, const u64* __restrict__ c2, int T,
@@ -125,17 +128,19 @@ __global__ void __launch_bounds__(256) k_bconv_impl(const u64* __restrict__ src,
                                                     const ModDesc* mods) {
   extern __shared__ u64 sh[];
   const int ns_ = NS > 0 ? NS : ns;
-  const int W = 5 + ns_;
+  const int W = 2 + ns_;
   for (int m = threadIdx.x; m < nd; m += blockDim.x) {
-    int g = m < nq ? m : L + (m - nq);
+    const int g = m < nq ? m : L + (m - nq);
     const Modulus& md = MOD(mods, g);
     u64* e = sh + m * W;
     e[0] = md.q;
-    e[1] = md.mu;
-    e[2] = (u64)md.kbits;
-    e[3] = post ? post[2 * g] : 0;
-    e[4] = post ? post[2 * g + 1] : 0;
-    for (int s = 0; s < ns_; ++s) e[5 + s] = c2[(long)s * T + g];
+    e[1] = neg_inv64(md.q);
+    const u64 R = barrett_reduce128(1, 0, md);  // 2^64 mod q
+    for (int s = 0; s < ns_; ++s) {
+      u64 v = c2[(long)s * T + g];
+      if (post) v = shoup(v, post[2 * g], post[2 * g + 1], md.q);
+      e[2 + s] = mul_mod(v, R, md);
+    }
   }
   __syncthreads();
   const int o = blockIdx.y;
@@ -160,14 +165,8 @@ __global__ void __launch_bounds__(256) k_bconv_impl(const u64* __restrict__ src,
       acc.zero();
 #pragma unroll
       for (int s = 0; s < MAXS; ++s)
-        if (s < ns_) acc.mac(y[s], e[5 + s]);
-      Modulus md;
-      md.q = e[0];
-      md.mu = e[1];
-      md.kbits = (int)e[2];
-      u64 v = barrett_reduce128(acc.hi, acc.lo, md);
-      if (post) v = shoup(v, e[3], e[4], md.q);
-      out[(long)m * N] = v;
+        if (s < ns_) acc.mac_wide(y[s], e[2 + s]);
+      out[(long)m * N] = redc128(acc.hi, acc.lo, e[0], e[1]);
     }
   }
 }
@@ -568,7 +567,7 @@ void k_bconv(Context& C, const u64* src, long src_os, int ns, int sp0, const u64
   dim3 g = grid_for(C.N, n_outer);
   if (ns < 1 || ns > 64) throw Error(SS_ERR_PARAM, "base conversion from 1..64 primes");
   if (skip_hi <= skip_lo) skip_lo = skip_hi = nd;
-  size_t smem = (size_t)nd * (5 + ns) * 8;
+  size_t smem = (size_t)nd * (2 + ns) * 8;
   if (smem > 48 * 1024) throw Error(SS_ERR_PARAM, "base conversion tables exceed 48 KiB of shared memory");
   int kr_ = kt_begin(C, st);
 #define SS_BCONV(NSV)                                                                                     \

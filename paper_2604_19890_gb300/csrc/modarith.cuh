@@ -40,6 +40,24 @@ __device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const Modulus& m) {
   return barrett_reduce128(mulhi64(a, b), a * b, m);
 }
 
+// -q^{-1} mod 2^64 for odd q: Newton's iteration x <- x (2 - q x) doubles the
+// number of correct low bits; q itself is correct to 3 bits.
+__device__ __forceinline__ u64 neg_inv64(u64 q) {
+  u64 x = q;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) x *= 2 - q * x;
+  return 0 - x;
+}
+
+// Montgomery reduction: x = (hi, lo) < q 2^64 -> x 2^-64 mod q in [0, q).
+// With m = lo * qinv mod 2^64, x + m q is divisible by 2^64; the low words
+// cancel with a carry exactly when lo != 0, and (x + m q) / 2^64 < 2q.
+__device__ __forceinline__ u64 redc128(u64 hi, u64 lo, u64 q, u64 qinv) {
+  const u64 m = lo * qinv;
+  const u64 t = hi + mulhi64(m, q) + (lo != 0 ? 1 : 0);
+  return t >= q ? t - q : t;
+}
+
 // 128-bit accumulator of products; reduce once at the end.
 struct Acc128 {
   u64 lo, hi;
@@ -48,6 +66,12 @@ struct Acc128 {
     u64 l = a * b, h = mulhi64(a, b);
     lo += l;
     hi += h + (lo < l ? 1 : 0);
+  }
+  // the same product-accumulate through the compiler's 128-bit arithmetic
+  __device__ __forceinline__ void mac_wide(u64 a, u64 b) {
+    const u128 s = (((u128)hi << 64) | lo) + (u128)a * b;
+    lo = (u64)s;
+    hi = (u64)(s >> 64);
   }
   __device__ __forceinline__ void add(u64 a) {
     lo += a;
