@@ -262,6 +262,9 @@ void build_context(Context& C, const ss_params& prm) {
     md[i].kbits = k;
     md[i].mu = (u64)(((u128)1 << (63 + k)) / q);
     md[i].pad = 0;
+    u64 x = q;  // Newton's iteration for q^-1 mod 2^64: 3, 6, 12, 24, 48, 96 correct bits
+    for (int it = 0; it < 5; ++it) x *= 2 - q * x;
+    md[i].qinv = 0 - x;
   }
   upload((void**)&C.d_mod, md.data(), sizeof(ModDesc) * T);
 

@@ -27,6 +27,7 @@ namespace {
 
 constexpr int TPB = 256;
 
+static_assert(sizeof(Modulus) == sizeof(ModDesc), "device modulus descriptors share one layout");
 __device__ __forceinline__ const Modulus& MOD(const ModDesc* m, int i) {
   return reinterpret_cast<const Modulus*>(m)[i];
 }
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(256) k_bconv_impl(const u64* __restrict__ src,
     const Modulus& md = MOD(mods, g);
     u64* e = sh + m * W;
     e[0] = md.q;
-    e[1] = neg_inv64(md.q);
+    e[1] = md.qinv;
     const u64 R = barrett_reduce128(1, 0, md);  // 2^64 mod q
     for (int s = 0; s < ns_; ++s) {
       u64 v = c2[(long)s * T + g];
@@ -187,7 +188,8 @@ __global__ void k_sub_scale_impl(const u64* a, long a_os, const u64* dl, long d_
 
 // ---------------------------------------------------------------- key-switch inner product
 // acc[comp][m] = sum_j ext_j[m] * key_j[comp][g(m)], with ext_j[m] = d[m] on the
-// digit's own primes. 128-bit lazy sum over the digits, one reduction. One
+// digit's own primes. 128-bit lazy sum over the digits, one Montgomery
+// reduction (the keys are stored times 2^64 mod q). One
 // thread per (ciphertext o, limb m, coefficient n); the ciphertext index runs
 // fastest over the blocks, so the blocks that read one stretch of the key run
 // back to back and all but the first find it in L2.
@@ -216,12 +218,13 @@ __global__ void __launch_bounds__(256) k_ks_ip_impl(const u64* __restrict__ d, l
 #pragma unroll 4
   for (int j = 0; j < dn; ++j) {
     const u64 x = j == jown ? d[o * d_os + (long)m * N + n] : ep[j * jstride];
-    s0.mac(x, __ldg(kbp + j * kstride));
-    s1.mac(x, __ldg(kap + j * kstride));
+    s0.mac_wide(x, __ldg(kbp + j * kstride));
+    s1.mac_wide(x, __ldg(kap + j * kstride));
   }
+  // keys carry 2^64 (Montgomery form); the sum is below dn q^2 < q 2^64
   u64* out = acc + o * acc_os + (long)m * N + n;
-  out[0] = barrett_reduce128(s0.hi, s0.lo, md);
-  out[(long)nlx * N] = barrett_reduce128(s1.hi, s1.lo, md);
+  out[0] = redc128(s0.hi, s0.lo, md.q, md.qinv);
+  out[(long)nlx * N] = redc128(s1.hi, s1.lo, md.q, md.qinv);
 }
 
 // ---------------------------------------------------------------- automorphism
@@ -294,6 +297,17 @@ __global__ void k_mul_sub_impl(const u64* x, long x_os, const u64* a, long a_os,
   const Modulus& md = MOD(mods, g);
   u64 p = mul_mod(a[(long)o * a_os + (long)i * N + n], s[(long)g * N + n], md);
   out[(long)o * out_os + (long)i * N + n] = sub_mod(x[(long)o * x_os + (long)i * N + n], p, md.q);
+}
+
+// every word of limb (poly mod T) times 2^64 mod its prime
+__global__ void k_to_mont_impl(u64* a, int T, int N, const ModDesc* mods) {
+  const int poly = blockIdx.y;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const Modulus& md = MOD(mods, poly % T);
+  const u64 R = barrett_reduce128(1, 0, md);
+  u64* w = a + (size_t)poly * N + n;
+  *w = mul_mod(*w, R, md);
 }
 
 struct GadgetArgs {
@@ -590,6 +604,11 @@ void k_sub_scale(Context& C, const u64* a, long a_os, const u64* dl, long d_os, 
   TIMED(KC_SUBSCALE, (add ? 4.0 : 3.0) * nl * n_outer * (double)C.N * 8.0,
   k_sub_scale_impl<<<grid_for(C.N, nl * n_outer), TPB, 0, st>>>(a, a_os, dl, d_os, scale, add, add_os, out, out_os,
                                                                  nl, C.N, C.d_mod));
+  LAUNCHED();
+}
+
+void k_to_montgomery(Context& C, u64* data, int npoly, cudaStream_t st) {
+  k_to_mont_impl<<<grid_for(C.N, npoly), TPB, 0, st>>>(data, C.ntot, C.N, C.d_mod);
   LAUNCHED();
 }
 

@@ -21,6 +21,7 @@ struct Modulus {
   u64 mu;     // floor(2^(63+k) / q)
   int kbits;  // bit length of q
   int pad;
+  u64 qinv;   // -q^-1 mod 2^64 (Montgomery reduction)
 };
 
 __device__ __forceinline__ u64 mulhi64(u64 a, u64 b) { return __umul64hi(a, b); }
@@ -38,15 +39,6 @@ __device__ __forceinline__ u64 barrett_reduce128(u64 hi, u64 lo, const Modulus& 
 
 __device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const Modulus& m) {
   return barrett_reduce128(mulhi64(a, b), a * b, m);
-}
-
-// -q^{-1} mod 2^64 for odd q: Newton's iteration x <- x (2 - q x) doubles the
-// number of correct low bits; q itself is correct to 3 bits.
-__device__ __forceinline__ u64 neg_inv64(u64 q) {
-  u64 x = q;
-#pragma unroll
-  for (int i = 0; i < 5; ++i) x *= 2 - q * x;
-  return 0 - x;
 }
 
 // Montgomery reduction: x = (hi, lo) < q 2^64 -> x 2^-64 mod q in [0, q).

@@ -301,6 +301,8 @@ static void make_ksk(Context& C, const u64* sprime, u32 key_id, KeyDev& K, cudaS
     k_mul_sub(C, b, 0, a, 0, C.d_sk, b, 0, 1, T, 0, T, 0, st);
     k_ksk_gadget(C, K.b, sprime, j, st);
   }
+  k_to_montgomery(C, K.a, dn * T, st);
+  k_to_montgomery(C, K.b, dn * T, st);
   pool_free(e, st);
 }
 

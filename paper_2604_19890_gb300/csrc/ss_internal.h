@@ -50,6 +50,7 @@ std::vector<i64> flt_coeffs(int p);       // centred mod p
 struct ModDesc {
   u64 q, mu;
   int kbits, pad;
+  u64 qinv;  // -q^-1 mod 2^64
 };
 
 // A batch of ciphertexts with one shape; either a view of caller memory or a
@@ -66,6 +67,8 @@ struct Buf {
 };
 typedef std::shared_ptr<Buf> BufP;
 
+// Key-switching key, stored in Montgomery form (every word times 2^64 mod its
+// prime) for the inner product's Montgomery reduction.
 struct KeyDev {
   u64* b = nullptr;  // [dnum][L+alpha][N]
   u64* a = nullptr;
@@ -192,6 +195,7 @@ void k_drop_combine(Context& C, const u64* acc, long acc_os, int nx, const Buf& 
                     const u64* pmod, const u64* inv, Buf& out, int B, cudaStream_t st);
 void k_sub_scale(Context& C, const u64* a, long a_os, const u64* dl, long d_os, const u64* scale, const u64* add,
                  long add_os, u64* out, long out_os, int nl, int n_outer, cudaStream_t st);
+void k_to_montgomery(Context& C, u64* data, int npoly, cudaStream_t st);
 void k_ks_ip(Context& C, const u64* d, long d_os, const u64* ext, long ext_os, const KeyDev& K, int level,
              u64* acc, long acc_os, int n_outer, cudaStream_t st);
 void k_automorph(Context& C, const Buf& a, int g, Buf& out, cudaStream_t st);
