@@ -382,14 +382,21 @@ struct LinArgs {
   i64 c[16];
 };
 
-__global__ void k_lincomb_impl(LinArgs A, int nterms, i64 cst, int small, u64* out, int ocap, int N, int ncomp,
-                               int level, const ModDesc* mods) {
-  int poly = blockIdx.y;  // (bt, comp, i)
-  int i = poly % level, comp = (poly / level) % ncomp, bt = poly / (level * ncomp);
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
+// out = sum_t c_t y_t (+ cst on component 0), one word per thread. All term
+// words are loaded before any arithmetic so the loads overlap.
+__global__ void __launch_bounds__(256) k_lincomb_impl(LinArgs A, int nterms, i64 cst, int small, u64* out, int ocap,
+                                                      int N, int ncomp, int level, const ModDesc* mods) {
+  const int poly = blockIdx.y;  // (bt, comp, i)
+  const int i = poly % level, comp = (poly / level) % ncomp, bt = poly / (level * ncomp);
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const Modulus& md = MOD(mods, i);
   const u64 q = md.q;
+  const size_t row = (size_t)(bt * ncomp + comp);
+  u64 y[16];
+#pragma unroll
+  for (int t = 0; t < 16; ++t)
+    if (t < nterms) y[t] = A.ptr[t][(row * A.cap[t] + i) * N + n];
   u64 r;
   if (small) {
     // |c| < 2^32: y * |c| is two 32x32 products; positive and negative terms
@@ -399,36 +406,41 @@ __global__ void k_lincomb_impl(LinArgs A, int nterms, i64 cst, int small, u64* o
     pos.zero();
     neg.zero();
     const int npos = small - 1;
-    for (int t = 0; t < nterms; ++t) {
-      u64 y = A.ptr[t][((size_t)(bt * ncomp + comp) * A.cap[t] + i) * N + n];
-      const i64 c = A.c[t];
-      const uint32_t m = (uint32_t)(t < npos ? c : -c);
-      const u64 p0 = (u64)(uint32_t)y * m, p1 = (u64)(uint32_t)(y >> 32) * m;
-      if (t < npos) {
-        pos.add(p0);
-        pos.add(p1 << 32);
-        pos.hi += p1 >> 32;
-      } else {
-        neg.add(p0);
-        neg.add(p1 << 32);
-        neg.hi += p1 >> 32;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      if (t < nterms) {
+        const i64 c = A.c[t];
+        const uint32_t m = (uint32_t)(t < npos ? c : -c);
+        const u64 p0 = (u64)(uint32_t)y[t] * m, p1 = (u64)(uint32_t)(y[t] >> 32) * m;
+        if (t < npos) {
+          pos.add(p0);
+          pos.add(p1 << 32);
+          pos.hi += p1 >> 32;
+        } else {
+          neg.add(p0);
+          neg.add(p1 << 32);
+          neg.hi += p1 >> 32;
+        }
       }
     }
     if (comp == 0 && cst > 0) pos.add((u64)cst);
     if (comp == 0 && cst < 0) neg.add((u64)(-cst));
     r = sub_mod(barrett_reduce128(pos.hi, pos.lo, md), barrett_reduce128(neg.hi, neg.lo, md), q);
   } else {
+    // |c| < q (checked on the host): c mod q is c or q - |c|
     Acc128 acc;
     acc.zero();
-    for (int t = 0; t < nterms; ++t) {
-      u64 y = A.ptr[t][((size_t)(bt * ncomp + comp) * A.cap[t] + i) * N + n];
-      i64 c = A.c[t];
-      acc.mac(y, c >= 0 ? (u64)c : q - (u64)(-c));
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      if (t < nterms) {
+        const i64 c = A.c[t];
+        acc.mac_wide(y[t], c >= 0 ? (u64)c : q - (u64)(-c));
+      }
     }
     if (comp == 0 && cst != 0) acc.add(cst >= 0 ? (u64)cst : q - (u64)(-cst));
     r = barrett_reduce128(acc.hi, acc.lo, md);
   }
-  out[((size_t)(bt * ncomp + comp) * ocap + i) * N + n] = r;
+  out[(row * ocap + i) * N + n] = r;
 }
 
 // acc_c[l-1] += P * d_c[l-1] (mod q_{l-1}) for c = 0, 1: the last data limb of
@@ -518,6 +530,14 @@ void k_lincomb(Context& C, const std::vector<const Buf*>& ys, const std::vector<
   LinArgs A;
   bool small = cst > -(1LL << 32) && cst < (1LL << 32);
   for (int t = 0; t < nt; ++t) small = small && cs[t] > -(1LL << 32) && cs[t] < (1LL << 32);
+  if (!small) {  // the general path lifts c as c or q - |c|: every |c| must lie below every prime
+    const u64 qmin = 1ULL << (C.prm.bits - 1);
+    for (int t = 0; t <= nt; ++t) {
+      const i64 c = t < nt ? cs[t] : cst;
+      if (c == INT64_MIN || (u64)(c < 0 ? -c : c) >= qmin)
+        throw Error(SS_ERR_PARAM, "linear-combination scalar too large for the primes");
+    }
+  }
   int npos = 0, k2 = 0;
   if (small) {  // non-negative scalars first (the sum does not depend on the order)
     for (int t = 0; t < nt; ++t)

@@ -163,6 +163,16 @@ def test_linear_combination_parity(tiny, nterms, big):
     same(got, ref)
 
 
+def test_linear_combination_rejects_scalars_beyond_the_primes(tiny):
+    import paper_2604_19890_gb300 as ssg
+    g, o = tiny
+    gc, _ = encrypt_both(g, o, np.zeros((1, g.slots)), 2900)
+    for c in (1 << 35, -(1 << 40)):  # the 36-bit primes lie above 2^35
+        with pytest.raises(ssg.SSError) as e:
+            g.linear_combination([gc, gc], [3, c])
+        assert e.value.code == ssg.SS_ERR_PARAM
+
+
 def test_eval_g_reduce_compare_raise_parity(tiny):
     g, o = tiny
     rng = np.random.default_rng(3)
