@@ -13,6 +13,14 @@ from . import build as _build
 _lib = None
 
 
+# Section 4.3 predicates, in the order the C interfaces number them.
+PREDICATES = ["lt", "le", "gt", "ge", "eq", "neq"]
+
+
+def _pred(p):
+    return PREDICATES.index(p) if isinstance(p, str) else int(p)
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -61,6 +69,8 @@ def lib():
             "orc_eval_g": (vp, [vp, vp, i32]),
             "orc_reduce": (i32, [vp, vp, P(vp)]),
             "orc_compare_lt": (vp, [vp, vp, vp]),
+            "orc_compare": (vp, [vp, i32, vp, vp]),
+            "orc_query_where": (vp, [vp, P(vp), P(vp), i32, i32, P(i32), P(vp), P(vp), P(i32)]),
             "orc_raise": (vp, [vp, vp]),
             "orc_rotate_sum": (vp, [vp, vp]),
             "orc_query": (vp, [vp, P(vp), P(vp), P(vp), P(vp), i32, i32]),
@@ -314,6 +324,23 @@ class Oracle:
 
     def compare_lt(self, a, b):
         return Ct(self, lib().orc_compare_lt(self.h, a.h, b.h))
+
+    def compare(self, pred, a, b):
+        """Section 4.3 predicate (PREDICATES name or index) of a against b, at t = p."""
+        return Ct(self, lib().orc_compare(self.h, _pred(pred), a.h, b.h))
+
+    def query_where(self, A, B, conds):
+        """SUM(A*B) over rows where every (pred, X, Y) condition holds; Y may hold one ciphertext."""
+        n, k = len(A), len(conds)
+        arr = lambda xs: (C.c_void_p * len(xs))(*[x.h for x in xs])
+        preds = (C.c_int32 * k)(*[_pred(c[0]) for c in conds])
+        X = (C.c_void_p * (k * n))(*[x.h for c in conds for x in c[1]])
+        Y = (C.c_void_p * (k * n))()
+        for j, c in enumerate(conds):
+            for i, y in enumerate(c[2]):
+                Y[j * n + i] = y.h
+        ny = (C.c_int32 * k)(*[len(c[2]) for c in conds])
+        return Ct(self, lib().orc_query_where(self.h, arr(A), arr(B), n, k, preds, X, Y, ny))
 
     def raise_modulus(self, a):
         return Ct(self, lib().orc_raise(self.h, a.h))

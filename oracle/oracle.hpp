@@ -176,4 +176,16 @@ std::vector<int> rotate_sum_elements(const Context& C);
 Ct query_sum_where_lt(const Context& C, const std::vector<Ct>& A, const std::vector<Ct>& B,
                       const std::vector<Ct>& C1, const std::vector<Ct>& C2, Trace* tr);
 
+// Section 4.3 predicates of a against b, results at t = p.
+enum Pred { PRED_LT = 0, PRED_LE, PRED_GT, PRED_GE, PRED_EQ, PRED_NEQ };
+Ct compare_eq(const Context& C, const Ct& a, const Ct& b, Trace* tr);
+Ct compare(const Context& C, int pred, const Ct& a, const Ct& b, Trace* tr);
+// One condition of a conjunctive WHERE: X[i] pred Y[i] (Y may hold one ciphertext).
+struct Cond {
+  int pred;
+  std::vector<Ct> X, Y;
+};
+Ct query_sum_where(const Context& C, const std::vector<Ct>& A, const std::vector<Ct>& B,
+                   const std::vector<Cond>& conds, Trace* tr);
+
 }  // namespace orc

@@ -242,6 +242,28 @@ void* orc_compare_lt(void* h, void* a, void* b) {
   return guard_ptr([&] { return box(compare_lt(ctx(h), ct(a), ct(b), trace(h))); });
 }
 
+void* orc_compare(void* h, int pred, void* a, void* b) {
+  return guard_ptr([&] { return box(compare(ctx(h), pred, ct(a), ct(b), trace(h))); });
+}
+
+// conds: n_cond (pred, X[n], Y[ny]) triples flattened: preds[k], X[k*n + i], Y[k*n + i] (ny[k] = 1 or n)
+void* orc_query_where(void* h, void** A, void** B, int n, int n_cond, const int* preds, void** X, void** Y,
+                      const int* ny) {
+  return guard_ptr([&] {
+    std::vector<Ct> a, b;
+    for (int i = 0; i < n; ++i) { a.push_back(ct(A[i])); b.push_back(ct(B[i])); }
+    std::vector<Cond> conds;
+    for (int k = 0; k < n_cond; ++k) {
+      Cond c;
+      c.pred = preds[k];
+      for (int i = 0; i < n; ++i) c.X.push_back(ct(X[(size_t)k * n + i]));
+      for (int i = 0; i < ny[k]; ++i) c.Y.push_back(ct(Y[(size_t)k * n + i]));
+      conds.push_back(std::move(c));
+    }
+    return box(query_sum_where(ctx(h), a, b, conds, trace(h)));
+  });
+}
+
 void* orc_raise(void* h, void* a) { return guard_ptr([&] { return box(raise_modulus(ctx(h), ct(a), trace(h))); }); }
 
 void* orc_rotate_sum(void* h, void* a) { return guard_ptr([&] { return box(rotate_sum(ctx(h), ct(a), trace(h))); }); }

@@ -263,6 +263,47 @@ Ct compare_lt(const Context& C, const Ct& a, const Ct& b, Trace* tr) {
   return lt;
 }
 
+// Per-digit EQ against zero alone (Section 4.3, Fermat): F_EQ(x) = 1 - x^(p-1),
+// taken as 1 - y^((p-1)/2) with y = x^2, the power built by the Powers rule.
+static Ct eq_digit(const Context& C, const Ct& x, Trace* tr) {
+  Ct y = mul(C, x, x);
+  Powers P(C, y, tr);
+  Ct eq = add_scalar(C, mul_scalar(C, P.get((C.P.p - 1) / 2), -1), 1);
+  note(tr, "eq digit -> EQ L" + std::to_string(eq.level));
+  return eq;
+}
+
+// Section 4.3, EQ case: d = a - b, digits = Reduce(d), EQ = prod_i F_EQ(d_i),
+// multiplied in from the most significant digit down.
+Ct compare_eq(const Context& C, const Ct& a, const Ct& b, Trace* tr) {
+  int r = C.P.r;
+  int l = std::min(a.level, b.level);
+  std::vector<Ct> dg = reduce_to_digits(C, sub(C, align_to(C, a, l), align_to(C, b, l)), tr);
+  std::vector<Ct> EQ;
+  for (int i = 0; i < r; ++i) EQ.push_back(eq_digit(C, dg[i], tr));
+  Ct eq = EQ[r - 1];
+  for (int i = r - 2; i >= 0; --i) eq = mul(C, eq, EQ[i]);
+  note(tr, "EQ -> L" + std::to_string(eq.level));
+  return eq;
+}
+
+// 1 - x at t = p: complements an indicator
+static Ct complement(const Context& C, const Ct& x) { return add_scalar(C, mul_scalar(C, x, -1), 1); }
+
+// Section 4.3: GT(a, b) = LT(b, a) (the centred range is symmetric); NEQ, GE
+// and LE are 1 - EQ, 1 - LT and 1 - GT.
+Ct compare(const Context& C, int pred, const Ct& a, const Ct& b, Trace* tr) {
+  switch (pred) {
+    case PRED_LT: return compare_lt(C, a, b, tr);
+    case PRED_LE: return complement(C, compare_lt(C, b, a, tr));
+    case PRED_GT: return compare_lt(C, b, a, tr);
+    case PRED_GE: return complement(C, compare_lt(C, a, b, tr));
+    case PRED_EQ: return compare_eq(C, a, b, tr);
+    case PRED_NEQ: return complement(C, compare_eq(C, a, b, tr));
+    default: throw std::runtime_error("unknown predicate");
+  }
+}
+
 // Section 4.4: RaiseModToP2R(k) = G_{p,r}(k-bar) after t <- p^r.
 Ct raise_modulus(const Context& C, const Ct& lt, Trace* tr) {
   if (lt.t_exp != 1) throw std::runtime_error("raise: input must be at t = p");
@@ -297,22 +338,36 @@ Ct rotate_sum(const Context& C, const Ct& a, Trace* tr) {
   return s;
 }
 
-// SUM over rows of A*B where C1 < C2 (Algorithm 4 semantics), per ciphertext:
-// ind = Raise(LT(C1, C2)); R = ind * (A*B); total = rotate_sum(sum R).
-Ct query_sum_where_lt(const Context& C, const std::vector<Ct>& A, const std::vector<Ct>& B,
-                      const std::vector<Ct>& C1, const std::vector<Ct>& C2, Trace* tr) {
+// SUM over rows of A*B where every condition holds, per ciphertext: the
+// indicators of the conditions (t = p) are multiplied in order (AND), raised
+// once, ind = Raise(prod_k cond_k); R = ind * (A*B); total = rotate_sum(sum R).
+Ct query_sum_where(const Context& C, const std::vector<Ct>& A, const std::vector<Ct>& B,
+                   const std::vector<Cond>& conds, Trace* tr) {
   size_t n = A.size();
-  if (B.size() != n || C1.size() != n || (C2.size() != n && C2.size() != 1))
-    throw std::runtime_error("query: column sizes differ");
+  if (B.size() != n || conds.empty()) throw std::runtime_error("query: bad columns");
+  for (auto& c : conds)
+    if (c.X.size() != n || (c.Y.size() != n && c.Y.size() != 1)) throw std::runtime_error("query: column sizes differ");
   Ct total;
   for (size_t i = 0; i < n; ++i) {
-    const Ct& c2 = C2.size() == 1 ? C2[0] : C2[i];
-    Ct ind = raise_modulus(C, compare_lt(C, C1[i], c2, tr), tr);
+    Ct ind;
+    for (size_t k = 0; k < conds.size(); ++k) {
+      const Cond& c = conds[k];
+      Ct v = compare(C, c.pred, c.X[i], c.Y.size() == 1 ? c.Y[0] : c.Y[i], tr);
+      ind = k == 0 ? v : mul(C, ind, v);
+    }
+    ind = raise_modulus(C, ind, tr);
     Ct prod = mul(C, A[i], B[i]);
     Ct R = mul(C, ind, prod);
     total = (i == 0) ? R : add_aligned(C, total, R);
   }
   return rotate_sum(C, total, tr);
+}
+
+// SUM over rows of A*B where C1 < C2 (Algorithm 4 semantics).
+Ct query_sum_where_lt(const Context& C, const std::vector<Ct>& A, const std::vector<Ct>& B,
+                      const std::vector<Ct>& C1, const std::vector<Ct>& C2, Trace* tr) {
+  if (C2.size() != A.size() && C2.size() != 1) throw std::runtime_error("query: column sizes differ");
+  return query_sum_where(C, A, B, {Cond{PRED_LT, C1, C2}}, tr);
 }
 
 }  // namespace orc

@@ -13,6 +13,7 @@ import pytest
 import sympy
 
 import oracle as O
+from oracle import plain
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -436,6 +437,62 @@ def test_compare_all_pairs_p17_r2(small17):
         assert o.noise_budget(lt) > 0
         up = o.raise_modulus(lt)
         assert up.t_exp == 2 and [int(x) for x in o.decrypt_slots(up)] == exp
+
+
+@pytest.mark.parametrize("pred", O.PREDICATES)
+def test_predicates_all_residues_p17_r2(small17, pred):
+    """Section 4.3 predicates against their plaintext definitions on every
+    residue of a - b mod 289 (37 ciphertexts of 8 slots): EQ = prod F_EQ(d_i),
+    GT(a, b) = LT(b, a), NEQ/GE/LE = 1 - EQ/LT/GT."""
+    o = small17
+    t = o.t
+    rng = np.random.default_rng(40 + O.PREDICATES.index(pred))
+    for blk in range(0, t, o.slots):
+        dvals = np.arange(blk, blk + o.slots) % t
+        a = rng.integers(0, t, o.slots)
+        b = (a - dvals) % t
+        r = o.compare(pred, o.encrypt_slots(a.astype(np.uint64), 1), o.encrypt_slots(b.astype(np.uint64), 2))
+        assert r.t_exp == 1
+        exp = [plain.predicate(pred, x, y, t) for x, y in zip(a, b)]
+        assert [int(x) for x in o.decrypt_slots(r)] == exp, (pred, blk)
+    assert o.noise_budget(r) > 0
+
+
+def test_eq_fold_is_digit_product(small17):
+    """EQ of values differing only in the high digit (d = 17 k) is 0 although
+    the low digit of d is 0; d = 0 gives 1."""
+    o = small17
+    t, p = o.t, o.p
+    a = np.array([5, 100, 288, 0, 17, 34, 200, 3], dtype=np.int64)
+    d = np.array([0, p, 2 * p, 5 * p, 1, t - p, 0, p * 8], dtype=np.int64)
+    b = (a - d) % t
+    r = o.compare("eq", o.encrypt_slots((a % t).astype(np.uint64), 3), o.encrypt_slots(b.astype(np.uint64), 4))
+    assert [int(x) for x in o.decrypt_slots(r)] == [1 if x % t == 0 else 0 for x in d]
+
+
+def test_query_where_conjunction(small17):
+    """SUM(a*b) WHERE c1 < c2 AND c3 = k AND c4 >= c5 against its plaintext definition; a single LT
+    condition gives the same ciphertext words as the LT query."""
+    o = small17
+    t = o.t
+    rng = np.random.default_rng(41)
+    n = 2
+    cols = {k: [rng.integers(0, t, o.slots) for _ in range(n)] for k in ("a", "b", "c1", "c2", "c3", "c4", "c5")}
+    cols["c3"][0][:4] = 7  # some rows match the equality
+    cols["c3"][1][2:5] = 7
+    enc = {k: [o.encrypt_slots(np.asarray(v, np.uint64), 100 * j + i) for i, v in enumerate(vs)]
+           for j, (k, vs) in enumerate(cols.items())}
+    kc = [o.encrypt_slots(np.full(o.slots, 7, np.uint64), 999)]
+    conds = [("lt", enc["c1"], enc["c2"]), ("eq", enc["c3"], kc), ("ge", enc["c4"], enc["c5"])]
+    out = o.query_where(enc["a"], enc["b"], conds)
+    exp = plain.query_where(np.array(cols["a"]), np.array(cols["b"]),
+                            [("lt", np.array(cols["c1"]), np.array(cols["c2"])), ("eq", np.array(cols["c3"]), 7),
+                             ("ge", np.array(cols["c4"]), np.array(cols["c5"]))], t)
+    assert [int(x) for x in o.decrypt_slots(out)] == [exp] * o.slots
+    assert o.noise_budget(out) > 0
+    one = o.query_where(enc["a"], enc["b"], [("lt", enc["c1"], enc["c2"])])
+    ref = o.query(enc["a"], enc["b"], enc["c1"], enc["c2"])
+    assert (one.words() == ref.words()).all()
 
 
 def test_raise_clears_high_digits(small17):
