@@ -156,6 +156,15 @@ ss_status ss_eval_g(ss_ctx* ctx, const ss_ct* x, int32_t e, ss_ct* out, ss_strea
 ss_status ss_reduce_to_digits(ss_ctx* ctx, const ss_ct* a, ss_ct* digits, ss_stream stream);
 /* Algorithm 4: out = [centred(a - b) < 0] at t = p; b may have count 1 (broadcast) */
 ss_status ss_compare_lt(ss_ctx* ctx, const ss_ct* a, const ss_ct* b, ss_ct* out, ss_stream stream);
+/* Section 4.3 predicates of a against b, out at t = p (1 where it holds, else 0):
+ *   LT  [centred(a - b) < 0]  (Algorithm 4)     LE  1 - GT
+ *   GT  LT(b, a)                                GE  1 - LT
+ *   EQ  prod_i F_EQ(d_i) over the digits d_i of a - b, F_EQ(x) = 1 - x^(p-1)
+ *   NEQ 1 - EQ
+ * centred() maps Z_{p^r} to [-(p^r-1)/2, (p^r-1)/2]. Either operand may have
+ * count 1 (broadcast against the other). */
+typedef enum { SS_PRED_LT = 0, SS_PRED_LE = 1, SS_PRED_GT = 2, SS_PRED_GE = 3, SS_PRED_EQ = 4, SS_PRED_NEQ = 5 } ss_predicate;
+ss_status ss_compare(ss_ctx* ctx, int32_t pred, const ss_ct* a, const ss_ct* b, ss_ct* out, ss_stream stream);
 /* Section 4.4: t <- p^r, out = G_{p,r}(in) */
 ss_status ss_raise_modulus(ss_ctx* ctx, const ss_ct* in, ss_ct* out, ss_stream stream);
 /* compare-then-SUM query (Section 1, Fig. 1; Section 5.2): one ciphertext whose
@@ -163,6 +172,20 @@ ss_status ss_raise_modulus(ss_ctx* ctx, const ss_ct* in, ss_ct* out, ss_stream s
  * same count; C2 has that count or 1 (an encrypted threshold). */
 ss_status ss_query_sum_where_lt(ss_ctx* ctx, const ss_ct* A, const ss_ct* B, const ss_ct* C1, const ss_ct* C2,
                                 ss_ct* out, ss_stream stream);
+/* Conjunctive WHERE (Section 4.3 predicates joined by AND; the paper's
+ * database workload filters on several columns): one ciphertext whose every
+ * slot holds sum over rows of A*B*prod_k [x_k pred_k y_k] mod p^r. The
+ * conditions' indicators are multiplied at t = p in order and raised once.
+ * Every x_k has A's count; y_k has that count or 1. conds is a host array of
+ * n_conds >= 1 entries; the ciphertexts it points to are device-resident. */
+typedef struct {
+  int32_t pred; /* ss_predicate */
+  int32_t pad;
+  const ss_ct* x;
+  const ss_ct* y;
+} ss_cond;
+ss_status ss_query_sum_where(ss_ctx* ctx, const ss_ct* A, const ss_ct* B, const ss_cond* conds, int32_t n_conds,
+                             ss_ct* out, ss_stream stream);
 /* Same query with every input in HOST memory: copies the four columns to the
  * device, runs the query and copies the result ciphertext back to host_out
  * (uint64[2][out_level][N]); writes its level and t_exp. Synchronous. */

@@ -36,6 +36,10 @@ class ss_ct(C.Structure):
                 ("t_exp", C.c_int32), ("capacity", C.c_int32), ("reserved", C.c_int32)]
 
 
+class ss_cond(C.Structure):
+    _fields_ = [("pred", C.c_int32), ("pad", C.c_int32), ("x", C.POINTER(ss_ct)), ("y", C.POINTER(ss_ct))]
+
+
 class ss_batch_item(C.Structure):
     _fields_ = [("ctx", C.c_int32), ("reduce", C.c_int32), ("a", ss_ct), ("b", ss_ct),
                 ("prod", C.POINTER(ss_ct)), ("digits", C.POINTER(ss_ct))]
@@ -83,6 +87,10 @@ _SIGS = {
     "ss_trace": (C.c_int, [C.c_void_p, C.c_int32]),
     "ss_trace_get": (C.c_int32, [C.c_void_p, C.c_char_p, C.c_int32]),
     "ss_launch_count": (C.c_uint64, [C.c_void_p]),
+    "ss_compare": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(ss_ct), C.POINTER(ss_ct), C.POINTER(ss_ct),
+                             C.c_void_p]),
+    "ss_query_sum_where": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.POINTER(ss_ct), C.POINTER(ss_cond), C.c_int32,
+                                     C.POINTER(ss_ct), C.c_void_p]),
     "ss_stage_stats": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_double)]),
     "ss_alu_probe": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_double)]),
     "ss_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(ss_batch_item), C.c_int32,
@@ -105,6 +113,9 @@ _SIGS = {
 
 KERNEL_CLASSES = ["ntt", "base_conversion", "keyswitch_inner_product", "tensor", "sub_scale", "automorphism",
                   "elementwise", "sampling"]
+# Section 4.3 predicates in ss_predicate order
+PREDICATES = ["lt", "le", "gt", "ge", "eq", "neq"]
+
 QUERY_STAGES = ["reduction", "comparison", "aggregation", "modulus_raising", "masked_product", "sum"]
 
 
@@ -467,6 +478,28 @@ class Context:
 
     def eval_g(self, x, e):
         return self._call1(lib().ss_eval_g, x, self._out(x), C.c_int32(e))
+
+    def compare(self, pred, a, b):
+        """Section 4.3 predicate ('lt', 'le', 'gt', 'ge', 'eq', 'neq' or its index) of a against b, at t = p."""
+        pi = PREDICATES.index(pred) if isinstance(pred, str) else int(pred)
+        out = self._out(a if a.count >= b.count else b, ncomp=2)
+        da, db, do = a.desc(), b.desc(), out.desc()
+        _chk(lib().ss_compare(self.h, pi, C.byref(da), C.byref(db), C.byref(do), _stream(self.torch)))
+        return out.update(do)
+
+    def query_where(self, A, B, conds, stream=None):
+        """SUM(A*B) over the rows where every (pred, X, Y) condition holds (Y may have count 1)."""
+        out = self.empty(1, level=A.level)
+        descs = [(x.desc(), y.desc()) for _, x, y in conds]
+        arr = (ss_cond * len(conds))()
+        for k, (pred, _, _) in enumerate(conds):
+            arr[k].pred = PREDICATES.index(pred) if isinstance(pred, str) else int(pred)
+            arr[k].x = C.pointer(descs[k][0])
+            arr[k].y = C.pointer(descs[k][1])
+        da, db, do = A.desc(), B.desc(), out.desc()
+        _chk(lib().ss_query_sum_where(self.h, C.byref(da), C.byref(db), arr, len(conds), C.byref(do),
+                                      _stream(self.torch, stream)))
+        return out.update(do)
 
     def raise_modulus(self, a):
         return self._call1(lib().ss_raise_modulus, a, self._out(a))

@@ -362,6 +362,17 @@ ss_status ss_compare_lt(ss_ctx* ctx, const ss_ct* a, const ss_ct* b, ss_ct* out,
   });
 }
 
+ss_status ss_compare(ss_ctx* ctx, int32_t pred, const ss_ct* a, const ss_ct* b, ss_ct* out, ss_stream stream) {
+  return guard([&] {
+    need(ctx != nullptr, SS_ERR_PARAM, "null context");
+    need(pred >= SS_PRED_LT && pred <= SS_PRED_NEQ, SS_ERR_PARAM, "unknown predicate");
+    check_ct(ctx->C, a, "null a");
+    check_ct(ctx->C, b, "null b");
+    auto r = ss::ev_compare(ctx->C, pred, ss::view_buf(*a), ss::view_buf(*b), S(stream));
+    deliver(ctx->C, r, out, S(stream));
+  });
+}
+
 ss_status ss_raise_modulus(ss_ctx* ctx, const ss_ct* in, ss_ct* out, ss_stream stream) {
   return guard([&] {
     need(ctx != nullptr, SS_ERR_PARAM, "null context");
@@ -378,6 +389,24 @@ ss_status ss_query_sum_where_lt(ss_ctx* ctx, const ss_ct* A, const ss_ct* B, con
     for (const ss_ct* c : {A, B, C1, C2}) check_ct(ctx->C, c, "null column");
     auto r = ss::ev_query(ctx->C, ss::view_buf(*A), ss::view_buf(*B), ss::view_buf(*C1), ss::view_buf(*C2),
                           S(stream));
+    deliver(ctx->C, r, out, S(stream));
+  });
+}
+
+ss_status ss_query_sum_where(ss_ctx* ctx, const ss_ct* A, const ss_ct* B, const ss_cond* conds, int32_t n_conds,
+                             ss_ct* out, ss_stream stream) {
+  return guard([&] {
+    need(ctx != nullptr && conds != nullptr && n_conds >= 1, SS_ERR_PARAM, "bad argument");
+    check_ct(ctx->C, A, "null column");
+    check_ct(ctx->C, B, "null column");
+    std::vector<ss::QCond> qc;
+    for (int k = 0; k < n_conds; ++k) {
+      need(conds[k].pred >= SS_PRED_LT && conds[k].pred <= SS_PRED_NEQ, SS_ERR_PARAM, "unknown predicate");
+      check_ct(ctx->C, conds[k].x, "null condition column");
+      check_ct(ctx->C, conds[k].y, "null condition column");
+      qc.push_back({conds[k].pred, ss::view_buf(*conds[k].x), ss::view_buf(*conds[k].y)});
+    }
+    auto r = ss::ev_query_where(ctx->C, ss::view_buf(*A), ss::view_buf(*B), qc, S(stream));
     deliver(ctx->C, r, out, S(stream));
   });
 }

@@ -55,7 +55,8 @@ static BufP binary(Context& C, int op, const BufP& a0, const BufP& b0, cudaStrea
   int l = std::min(a0->level, b0->level);
   BufP a = ev_modswitch_to(C, a0, l, st), b = ev_modswitch_to(C, b0, l, st);
   if (a->count == 1 && b->count > 1) {
-    if (op == 1) throw Error(SS_ERR_SHAPE, "broadcast of the left operand of a subtraction");
+    // a - b with a broadcast: -(b - a), the same canonical residues word for word
+    if (op == 1) return ev_scalar(C, 0, binary(C, 1, b, a, st), -1, st);
     std::swap(a, b);
   }
   BufP out = alloc_buf(C, out_count(a, b), a->ncomp, l, a->t_exp, st);
@@ -305,6 +306,57 @@ BufP ev_compare_lt(Context& C, const BufP& a, const BufP& b, cudaStream_t st) {
   return lt;
 }
 
+// Per-digit EQ against zero alone (Section 4.3): F_EQ(x) = 1 - x^(p-1) as
+// 1 - y^((p-1)/2), y = x^2, the power built by the Powers rule.
+static BufP eq_digit(Context& C, const BufP& x, cudaStream_t st) {
+  BufP y = ev_mul(C, x, x, st);
+  Powers P(C, y, st);
+  BufP eq = ev_lincomb(C, {{P.get((C.p - 1) / 2), -1}}, 1, st);
+  note(C, "eq digit -> EQ " + L_(eq->level));
+  return eq;
+}
+
+// Section 4.3, EQ: Reduce(a - b), F_EQ per digit, product from the most
+// significant digit down.
+BufP ev_compare_eq(Context& C, const BufP& a, const BufP& b, cudaStream_t st) {
+  int r = C.r;
+  std::vector<BufP> dg;
+  {
+    StageScope sc(C, ST_REDUCE, st);
+    dg = ev_reduce(C, ev_sub(C, a, b, st), st);
+  }
+  std::vector<BufP> EQ(r);
+  {
+    StageScope sc(C, ST_COMPARE, st);
+    for (int i = 0; i < r; ++i) EQ[i] = eq_digit(C, dg[i], st);
+  }
+  StageScope sc(C, ST_AGGREGATE, st);
+  BufP eq = EQ[r - 1];
+  for (int i = r - 2; i >= 0; --i) eq = ev_mul(C, eq, EQ[i], st);
+  note(C, "EQ -> " + L_(eq->level));
+  return eq;
+}
+
+// 1 - x at t = p
+static BufP complement(Context& C, const BufP& x, cudaStream_t st) {
+  StageScope sc(C, ST_AGGREGATE, st);
+  return ev_lincomb(C, {{x, -1}}, 1, st);
+}
+
+// Section 4.3: GT(a, b) = LT(b, a) on the symmetric centred range; NEQ, GE and
+// LE are 1 - EQ, 1 - LT and 1 - GT.
+BufP ev_compare(Context& C, int pred, const BufP& a, const BufP& b, cudaStream_t st) {
+  switch (pred) {
+    case SS_PRED_LT: return ev_compare_lt(C, a, b, st);
+    case SS_PRED_LE: return complement(C, ev_compare_lt(C, b, a, st), st);
+    case SS_PRED_GT: return ev_compare_lt(C, b, a, st);
+    case SS_PRED_GE: return complement(C, ev_compare_lt(C, a, b, st), st);
+    case SS_PRED_EQ: return ev_compare_eq(C, a, b, st);
+    case SS_PRED_NEQ: return complement(C, ev_compare_eq(C, a, b, st), st);
+    default: throw Error(SS_ERR_PARAM, "unknown predicate");
+  }
+}
+
 // Section 4.4
 BufP ev_raise(Context& C, const BufP& a, cudaStream_t st) {
   if (a->t_exp != 1) throw Error(SS_ERR_TMOD, "raise input must be at t = p");
@@ -338,19 +390,34 @@ static BufP batch_total(Context& C, const BufP& R, cudaStream_t st) {
   return out;
 }
 
-// SUM(A*B WHERE C1 < C2) per ciphertext: ind = Raise(LT(C1, C2)), R = ind*(A*B),
-// total = rotate_sum(sum R). Ciphertexts are processed C.batch at a time.
-BufP ev_query(Context& C, const BufP& A, const BufP& B, const BufP& C1, const BufP& C2, cudaStream_t st) {
+// SUM(A*B) over the rows where every condition holds, per ciphertext: the
+// conditions' indicators (t = p) are multiplied in order (AND) and raised once,
+// ind = Raise(prod_k cond_k), R = ind*(A*B), total = rotate_sum(sum R).
+// Ciphertexts are processed C.batch at a time.
+BufP ev_query_where(Context& C, const BufP& A, const BufP& B, const std::vector<QCond>& conds, cudaStream_t st) {
   int n = A->count;
-  if (B->count != n || C1->count != n || (C2->count != n && C2->count != 1))
-    throw Error(SS_ERR_SHAPE, "column batch sizes differ");
+  if (conds.empty()) throw Error(SS_ERR_PARAM, "a query needs at least one condition");
+  if (B->count != n) throw Error(SS_ERR_SHAPE, "column batch sizes differ");
+  for (auto& c : conds)
+    if (c.X->count != n || (c.Y->count != n && c.Y->count != 1)) throw Error(SS_ERR_SHAPE, "column batch sizes differ");
   BufP total;
   int step = std::max(1, C.batch);
   for (int b0 = 0; b0 < n; b0 += step) {
     int cnt = std::min(step, n - b0);
-    BufP a = slice_buf(A, b0, cnt, C.N), b = slice_buf(B, b0, cnt, C.N), c1 = slice_buf(C1, b0, cnt, C.N);
-    BufP c2 = C2->count == 1 ? C2 : slice_buf(C2, b0, cnt, C.N);
-    BufP ind = ev_raise(C, ev_compare_lt(C, c1, c2, st), st);
+    BufP a = slice_buf(A, b0, cnt, C.N), b = slice_buf(B, b0, cnt, C.N);
+    BufP ind;
+    for (size_t k = 0; k < conds.size(); ++k) {
+      const QCond& c = conds[k];
+      BufP y = c.Y->count == 1 ? c.Y : slice_buf(c.Y, b0, cnt, C.N);
+      BufP v = ev_compare(C, c.pred, slice_buf(c.X, b0, cnt, C.N), y, st);
+      if (k == 0) {
+        ind = v;
+      } else {
+        StageScope sc(C, ST_AGGREGATE, st);
+        ind = ev_mul(C, ind, v, st);
+      }
+    }
+    ind = ev_raise(C, ind, st);
     BufP R;
     {
       StageScope sc(C, ST_PRODUCT, st);
@@ -361,6 +428,12 @@ BufP ev_query(Context& C, const BufP& A, const BufP& B, const BufP& C1, const Bu
     total = total ? ev_add(C, total, part, st) : part;
   }
   return ev_rotate_sum(C, total, st);
+}
+
+BufP ev_query(Context& C, const BufP& A, const BufP& B, const BufP& C1, const BufP& C2, cudaStream_t st) {
+  if (C1->count != A->count || (C2->count != A->count && C2->count != 1))
+    throw Error(SS_ERR_SHAPE, "column batch sizes differ");
+  return ev_query_where(C, A, B, {QCond{SS_PRED_LT, C1, C2}}, st);
 }
 
 int plan_query_depth(Context& C, int level) {

@@ -243,6 +243,13 @@ BufP ev_compare_lt(Context& C, const BufP& a, const BufP& b, cudaStream_t st);
 BufP ev_raise(Context& C, const BufP& a, cudaStream_t st);
 BufP ev_rotate_sum(Context& C, const BufP& a, cudaStream_t st);
 BufP ev_query(Context& C, const BufP& A, const BufP& B, const BufP& C1, const BufP& C2, cudaStream_t st);
+BufP ev_compare_eq(Context& C, const BufP& a, const BufP& b, cudaStream_t st);
+BufP ev_compare(Context& C, int pred, const BufP& a, const BufP& b, cudaStream_t st);
+struct QCond {
+  int pred;
+  BufP X, Y;  // X[i] pred Y[i]; Y may hold one ciphertext
+};
+BufP ev_query_where(Context& C, const BufP& A, const BufP& B, const std::vector<QCond>& conds, cudaStream_t st);
 struct QueryCols {
   BufP A, B, C1, C2;
 };

@@ -226,6 +226,70 @@ def test_query_parity(tiny, n_ct, batch):
     g.set_batch(8)
 
 
+@pytest.mark.parametrize("pred", ["lt", "le", "gt", "ge", "eq", "neq"])
+def test_predicate_parity(tiny, pred):
+    g, o = tiny
+    rng = np.random.default_rng(60 + len(pred))
+    A = rng.integers(0, g.t, (2, g.slots))
+    B = rng.integers(0, g.t, (2, g.slots))
+    B[0, :3] = A[0, :3]  # equal pairs
+    B[1, 3] = (A[1, 3] + g.p) % g.t  # same low digit
+    ga, oa = encrypt_both(g, o, A, 1200)
+    gb, ob = encrypt_both(g, o, B, 1300)
+    got = g.compare(pred, ga, gb)
+    same(got, [o.compare(pred, x, y) for x, y in zip(oa, ob)])
+    exp = [[plain.predicate(pred, x, y, g.t) for x, y in zip(ra, rb)] for ra, rb in zip(A, B)]
+    assert (g.decrypt_slots(got) == np.array(exp)).all()
+
+
+@pytest.mark.parametrize("pred", ["gt", "le", "eq"])
+def test_predicate_broadcast_either_side(tiny, pred):
+    g, o = tiny
+    rng = np.random.default_rng(70)
+    X = rng.integers(0, g.t, (2, g.slots))
+    thr = np.full((1, g.slots), 150)
+    X[1, :2] = 150
+    gx, ox = encrypt_both(g, o, X, 1400)
+    gt_, ot_ = encrypt_both(g, o, thr, 1500)
+    same(g.compare(pred, gx, gt_), [o.compare(pred, x, ot_[0]) for x in ox])
+    same(g.compare(pred, gt_, gx), [o.compare(pred, ot_[0], x) for x in ox])
+
+
+def test_query_where_parity(tiny):
+    g, o = tiny
+    rng = np.random.default_rng(80)
+    n = 3
+    cols = {k: rng.integers(0, g.t, (n, g.slots)) for k in ("a", "b", "c1", "c2", "c3")}
+    cols["c3"][:, ::3] = 7
+    enc = {k: encrypt_both(g, o, v, 5000 + 100 * i) for i, (k, v) in enumerate(cols.items())}
+    gk, ok = encrypt_both(g, o, np.full((1, g.slots), 7), 5900)
+    g.set_batch(2)
+    got = g.query_where(enc["a"][0], enc["b"][0], [("lt", enc["c1"][0], enc["c2"][0]), ("eq", enc["c3"][0], gk)])
+    g.set_batch(8)
+    ref = o.query_where(enc["a"][1], enc["b"][1], [("lt", enc["c1"][1], enc["c2"][1]), ("eq", enc["c3"][1], ok)])
+    same(got, [ref])
+    exp = plain.query_where(cols["a"], cols["b"], [("lt", cols["c1"], cols["c2"]), ("eq", cols["c3"], 7)], g.t)
+    assert (g.decrypt_slots(got) == exp).all()
+    # one LT condition is the LT query, word for word
+    one = g.query_where(enc["a"][0], enc["b"][0], [("lt", enc["c1"][0], enc["c2"][0])])
+    same(one, [o.query(enc["a"][1], enc["b"][1], enc["c1"][1], enc["c2"][1])])
+
+
+def test_eq_schedule_trace_matches_reference(tiny):
+    g, o = tiny
+    rng = np.random.default_rng(9)
+    ga, oa = encrypt_both(g, o, rng.integers(0, g.t, (1, g.slots)), 810)
+    gb, ob = encrypt_both(g, o, rng.integers(0, g.t, (1, g.slots)), 910)
+    g.trace(True)
+    o.trace(True)
+    g.compare("neq", ga, gb)
+    o.compare("neq", oa[0], ob[0])
+    gt, ot = g.trace_text(), o.trace_text()
+    g.trace(False)
+    o.trace(False)
+    assert gt == ot and "eq digit" in gt
+
+
 def test_schedule_trace_matches_reference(tiny):
     g, o = tiny
     rng = np.random.default_rng(5)
