@@ -576,6 +576,61 @@ def run_ours(args):
     return 0 if verified else 1
 
 
+# ------------------------------------------------------------------ LT operator across (p, r)
+# (bit width, p, r) from the paper's LT tables (Section 5) that power-of-two
+# rings with binomial slot factors support (p = 1 mod 4).
+LT_SWEEP = [(8, 5, 4), (8, 17, 2), (12, 17, 3), (16, 17, 4), (16, 41, 3), (16, 257, 2), (20, 17, 5), (20, 37, 4)]
+
+
+def run_lt_sweep(args):
+    """LT(a, b) followed by modulus raising on a batch of ciphertexts for each
+    (p, r): per-stage times (reduction, comparison, aggregation, raising) as in
+    the paper's runtime breakdown, per ciphertext and amortised per slot. The
+    chain is the shortest one the query schedule needs at that (p, r)."""
+    import numpy as np
+    import torch
+
+    import paper_2604_19890_gb300 as ssg
+    from paper_2604_19890_gb300 import build as ssbuild
+    from paper_2604_19890_gb300 import synth
+
+    ssbuild.build()
+    stream = torch.cuda.current_stream()
+    for bw, p, r in LT_SWEEP:
+        base = dict(logN=args.sweep_logn, alpha=2, bits=55, p=p, r=r, h=120, nmax=0, seed=SEED + p * 10 + r)
+        probe = ssg.Context(L=64, **base)
+        L = 64 - probe.query_depth(64) + 1
+        del probe
+        g = ssg.Context(L=L, **base)
+        g.keygen([])
+        vals = synth.table(SEED + bw, args.sweep_ct, g.slots, g.t, columns=("a", "b"))
+        ea = g.encrypt(np.stack([g.encode(x) for x in vals["a"]]), 1)
+        eb = g.encrypt(np.stack([g.encode(x) for x in vals["b"]]), 100)
+        res = g.raise_modulus(g.compare("lt", ea, eb))  # warm-up and check
+        exp = np.array([[1 if ((int(x) - int(y)) % g.t) > g.t // 2 else 0 for x, y in zip(ra, rb)]
+                        for ra, rb in zip(vals["a"], vals["b"])])
+        ok = bool((g.decrypt_slots(res) == exp).all())
+        g.kernel_timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            g.raise_modulus(g.compare("lt", ea, eb))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = g.stage_stats()
+        g.kernel_timing(False)
+        per = args.steps * args.sweep_ct
+        total = e0.elapsed_time(e1) / per
+        stages = {k: st[k][1] / per for k in ("reduction", "comparison", "aggregation", "modulus_raising")}
+        print(json.dumps({"lt_sweep": True, "bit_width": bw, "p": p, "r": r, "t": g.t, "N": g.N, "L": L,
+                          "slots": g.slots, "ciphertexts": args.sweep_ct, "ms_per_ciphertext": stages | {"total": total},
+                          "amortized_ms_per_slot": total / g.slots, "verified": ok}))
+        del g
+        torch.cuda.empty_cache()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -596,7 +651,13 @@ def main():
     ap.add_argument("--batched", action="store_true", help="batched form: 64 mixed-N pairs, graph replay")
     ap.add_argument("--serve-ct", type=int, default=2)
     ap.add_argument("--serve-queries", type=int, default=16)
+    ap.add_argument("--lt-sweep", action="store_true",
+                    help="LT operator + modulus raising across (p, r) at fixed bit widths, per-stage times")
+    ap.add_argument("--sweep-logn", type=int, default=15)
+    ap.add_argument("--sweep-ct", type=int, default=8)
     args = ap.parse_args()
+    if args.lt_sweep:
+        return run_lt_sweep(args)
     if args.serve:
         return run_serve(args)
     if args.batched:

@@ -275,6 +275,21 @@ def test_query_where_parity(tiny):
     same(one, [o.query(enc["a"][1], enc["b"][1], enc["c1"][1], enc["c2"][1])])
 
 
+@pytest.mark.parametrize("p,r", [(5, 4), (41, 3), (37, 4)])
+def test_compare_raise_other_p_r(p, r):
+    """LT then raising at the (p, r) of the LT sweep's other bit widths, 50-bit primes, N = 64."""
+    g, o = make_pair(logN=6, L=60, alpha=2, bits=50, p=p, r=r, h=16, seed=11, galois=[])
+    rng = np.random.default_rng(p * r)
+    A = rng.integers(0, g.t, (2, g.slots))
+    B = rng.integers(0, g.t, (2, g.slots))
+    ga, oa = encrypt_both(g, o, A, 700)
+    gb, ob = encrypt_both(g, o, B, 710)
+    got = g.raise_modulus(g.compare("lt", ga, gb))
+    same(got, [o.raise_modulus(o.compare_lt(x, y)) for x, y in zip(oa, ob)])
+    exp = [[plain.lt(x, y, g.t) for x, y in zip(ra, rb)] for ra, rb in zip(A, B)]
+    assert (g.decrypt_slots(got) == np.array(exp)).all()
+
+
 def test_eq_schedule_trace_matches_reference(tiny):
     g, o = tiny
     rng = np.random.default_rng(9)
