@@ -35,6 +35,8 @@ struct NttArgs {
   const Modulus* mods;
   const u64* tw;     // per prime 4N words: (w, w') pairs forward, then inverse
   const u64* ninv;   // per prime (N^-1, shoup)
+  const u64* src;    // out-of-place first phase: polynomial (o, i) is read at src + o src_os + i N
+  long src_os;
 };
 
 // Blocks walk the polynomials limb-major (all outer copies of limb 0, then of
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, in
 // less than 2q to the bound, so inputs below 4q leave a log2 N <= 16 stage
 // transform below 36q < 2^64 (primes below 2^58), and the last phase brings
 // every word back to [0, q) once (reduce_lazy).
-template <bool FWD, bool COLS, bool LAST, int LOGS>
+template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC = false>
 __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_ntt16(NttArgs A, int logCPB, int m0) {
   extern __shared__ u64 sm[];
   u64* ptr;
@@ -223,6 +225,12 @@ __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_nt
   const int tile = blockIdx.x;
   const int stride = A.N >> LOGS;
   u64* gbase = COLS ? ptr + (long)tile * CPB : ptr + (long)tile * W;
+  const u64* gsrc = gbase;
+  if (SRC) {  // same polynomial, read from the out-of-place source
+    const int i = blockIdx.y / A.n_outer, o = blockIdx.y % A.n_outer;
+    const u64* rb = A.src + (long)o * A.src_os + (long)i * A.N;
+    gsrc = COLS ? rb + (long)tile * CPB : rb + (long)tile * W;
+  }
   constexpr int NR = (LOGS + 3) / 4;
   constexpr int B0 = FWD ? LOGS - 1 : (LOGS < 4 ? LOGS : 4) - 1;
   constexpr int NSL = LOGS - 4 * (NR - 1);
@@ -230,7 +238,7 @@ __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_nt
   constexpr bool DIN = COLS || (B0 - 3 >= 4);
   constexpr bool DOUT = COLS || (BL - 3 >= 4);
   if (!DIN) {
-    for (int lin = tid; lin < W; lin += T) sm[swz(lin)] = gbase[lin];
+    for (int lin = tid; lin < W; lin += T) sm[swz(lin)] = gsrc[lin];
     __syncthreads();
   }
   u64 ni = 0, nip = 0;
@@ -263,7 +271,7 @@ __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_nt
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         int r = rbase + (k << logu);
-        x[k] = COLS ? gbase[(long)r * stride + c] : gbase[(c << LOGS) + r];
+        x[k] = COLS ? gsrc[(long)r * stride + c] : gsrc[(c << LOGS) + r];
       }
     } else {
 #pragma unroll
@@ -338,13 +346,13 @@ __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_nt
   }
 }
 
-template <bool FWD, bool COLS, bool LAST>
+template <bool FWD, bool COLS, bool LAST, bool SRC = false>
 void launch16(int logS, dim3 g, int thr, size_t smem, cudaStream_t st, const NttArgs& A, int logc, int m0) {
   switch (logS) {
-    case 5: k_ntt16<FWD, COLS, LAST, 5><<<g, thr, smem, st>>>(A, logc, m0); break;
-    case 6: k_ntt16<FWD, COLS, LAST, 6><<<g, thr, smem, st>>>(A, logc, m0); break;
-    case 7: k_ntt16<FWD, COLS, LAST, 7><<<g, thr, smem, st>>>(A, logc, m0); break;
-    default: k_ntt16<FWD, COLS, LAST, 8><<<g, thr, smem, st>>>(A, logc, m0); break;
+    case 5: k_ntt16<FWD, COLS, LAST, 5, SRC><<<g, thr, smem, st>>>(A, logc, m0); break;
+    case 6: k_ntt16<FWD, COLS, LAST, 6, SRC><<<g, thr, smem, st>>>(A, logc, m0); break;
+    case 7: k_ntt16<FWD, COLS, LAST, 7, SRC><<<g, thr, smem, st>>>(A, logc, m0); break;
+    default: k_ntt16<FWD, COLS, LAST, 8, SRC><<<g, thr, smem, st>>>(A, logc, m0); break;
   }
 }
 
@@ -364,6 +372,8 @@ NttArgs make_args(Context& C, const PolySet& s) {
   A.mods = reinterpret_cast<const Modulus*>(C.d_mod);
   A.tw = C.d_tw;
   A.ninv = C.d_ninv;
+  A.src = nullptr;
+  A.src_os = 0;
   return A;
 }
 
@@ -386,21 +396,28 @@ int ilog2(int x) {
 
 }  // namespace
 
-static void launch(Context& C, const PolySet& s, bool fwd, cudaStream_t st) {
+// src: optional out-of-place source read by the first phase (inverse only)
+static void launch(Context& C, const PolySet& s, bool fwd, cudaStream_t st, const u64* src = nullptr,
+                   long src_os = 0) {
   int npoly = s.n_outer * s.nl;
   if (npoly == 0) return;
   if (npoly > 65535) throw Error(SS_ERR_SHAPE, "too many polynomials in one transform");
   NttArgs A = make_args(C, s);
   const int N = C.N, logN = C.logN;
-  int kr = kt_begin(C, st);
   auto smem = [](int words) { return (size_t)(words + words / 8) * 8; };
   if (N <= TILE) {
+    if (src)  // one in-place phase: copy first
+      SS_CUDA(cudaMemcpy2DAsync(s.base, (size_t)s.outer_stride * 8, src, (size_t)src_os * 8, (size_t)s.nl * N * 8,
+                                s.n_outer, cudaMemcpyDeviceToDevice, st));
+    int kr = kt_begin(C, st);
     dim3 g(1, npoly);
     int thr = N / 8;
     if (fwd) k_ntt<true, false, true><<<g, thr, smem(N), st>>>(A, logN, 0, 1);
     else k_ntt<false, false, true><<<g, thr, smem(N), st>>>(A, logN, 0, 1);
     ++C.launches;
+    kt_end(C, kr, KC_NTT, 16.0 * N * active_polys(s), st);
   } else {
+    int kr = kt_begin(C, st);
     const int log2n = 8, log1 = logN - log2n;  // N = N1 * N2, N2 = 256
     const int tl = C.ntt_tile_log == 11 ? 11 : 12, tile = 1 << tl;
     const int logc1 = tl - log1, logc2 = tl - log2n;
@@ -409,18 +426,28 @@ static void launch(Context& C, const PolySet& s, bool fwd, cudaStream_t st) {
     if (fwd) {
       launch16<true, true, false>(log1, g1, thr, smem(tile), st, A, logc1, 1);
       launch16<true, false, true>(log2n, g2, thr, smem(tile), st, A, logc2, 1 << log1);
+    } else if (src) {
+      NttArgs A1 = A;
+      A1.src = src;
+      A1.src_os = src_os;
+      launch16<false, false, false, true>(log2n, g2, thr, smem(tile), st, A1, logc2, 1 << log1);
+      launch16<false, true, true>(log1, g1, thr, smem(tile), st, A, logc1, 1);
     } else {
       launch16<false, false, false>(log2n, g2, thr, smem(tile), st, A, logc2, 1 << log1);
       launch16<false, true, true>(log1, g1, thr, smem(tile), st, A, logc1, 1);
     }
     C.launches += 2;
+    kt_end(C, kr, KC_NTT, 16.0 * N * active_polys(s), st);
   }
-  kt_end(C, kr, KC_NTT, 16.0 * N * active_polys(s), st);
   SS_CUDA(cudaGetLastError());
 }
 
 void ntt_forward(Context& C, const PolySet& s, cudaStream_t st) { launch(C, s, true, st); }
 
 void ntt_inverse(Context& C, const PolySet& s, cudaStream_t st) { launch(C, s, false, st); }
+
+void ntt_inverse_from(Context& C, const PolySet& s, const u64* src, long src_os, cudaStream_t st) {
+  launch(C, s, false, st, src, src_os);
+}
 
 }  // namespace ss

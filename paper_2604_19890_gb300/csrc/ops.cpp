@@ -77,11 +77,9 @@ static void keyswitch_impl(Context& C, const Buf& in, int comp, const KeyDev& K,
   const int dn = (l + a - 1) / a, nx = l + a;
   const long in_os = (long)in.ncomp * in.cap * N;
   const u64* d = in.data + (size_t)comp * in.cap * N;
-  // 1. coefficient form of the digit source
+  // 1. coefficient form of the digit source (read in place, written to dc)
   u64* dc = static_cast<u64*>(pool_alloc((size_t)B * l * N * 8, st));
-  SS_CUDA(cudaMemcpy2DAsync(dc, (size_t)l * N * 8, d, (size_t)in_os * 8, (size_t)l * N * 8, B,
-                            cudaMemcpyDeviceToDevice, st));
-  ntt_inverse(C, PolySet{dc, (long)l * N, B, l, 0, l}, st);
+  ntt_inverse_from(C, PolySet{dc, (long)l * N, B, l, 0, l}, d, in_os, st);
   // 2. ModUp of every digit to the other data primes and the special primes
   const long ext_os = (long)dn * nx * N;
   u64* ext = static_cast<u64*>(pool_alloc((size_t)B * ext_os * 8, st));
@@ -159,9 +157,7 @@ void op_relin_drop(Context& C, const Buf& in, Buf& out, cudaStream_t st) {
   const u64* d = in.data + (size_t)2 * in.cap * N;
   // 1-3: ModUp and inner product, as in keyswitch_impl
   u64* dc = static_cast<u64*>(pool_alloc((size_t)B * l * N * 8, st));
-  SS_CUDA(cudaMemcpy2DAsync(dc, (size_t)l * N * 8, d, (size_t)in_os * 8, (size_t)l * N * 8, B,
-                            cudaMemcpyDeviceToDevice, st));
-  ntt_inverse(C, PolySet{dc, (long)l * N, B, l, 0, l}, st);
+  ntt_inverse_from(C, PolySet{dc, (long)l * N, B, l, 0, l}, d, in_os, st);
   const long ext_os = (long)dn * nx * N;
   u64* ext = static_cast<u64*>(pool_alloc((size_t)B * ext_os * 8, st));
   for (int j = 0; j < dn; ++j) {

@@ -180,6 +180,9 @@ struct PolySet {
 };
 void ntt_forward(Context& C, const PolySet& s, cudaStream_t st);
 void ntt_inverse(Context& C, const PolySet& s, cudaStream_t st);
+// Inverse transform of the polynomials at src (same shape as s, outer stride
+// src_os) written to s: the first phase reads src, so src is left unchanged.
+void ntt_inverse_from(Context& C, const PolySet& s, const u64* src, long src_os, cudaStream_t st);
 
 void k_binary(Context& C, int op, const Buf& a, const Buf& b, Buf& out, cudaStream_t st);  // 0 add, 1 sub
 void k_scalar(Context& C, int op, const Buf& a, i64 c, Buf& out, cudaStream_t st);       // 0 mul, 1 add(c0), 2 mul p^-1
