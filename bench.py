@@ -542,8 +542,9 @@ def run_ours(args):
         for _ in range(e_steps):
             out, ol, ot = g.query_host(arrs["a"], arrs["b"], arrs["c1"], arrs["c2"], L)
         dt = (time.perf_counter() - t0) / e_steps
+        e2e_ok = bool((g.decrypt_slots(g.from_words(out[None], ot)) == exp).all())
         e2e = {"value": rows / dt, "unit": "rows/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(2 * ol * g.N * 8), "ms_per_step": dt * 1e3}
+               "d2h_bytes_per_step": int(2 * ol * g.N * 8), "ms_per_step": dt * 1e3, "verified": e2e_ok}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and args.preset == PRESET:

@@ -519,14 +519,14 @@ class Context:
 
     def query_host(self, A, B, C1, C2, level, stream=None):
         """Query on host arrays uint64[count][2][level][N]; returns (words, level, t_exp)."""
-        out = np.zeros((2, level, self.N), dtype=np.uint64)
+        out = np.zeros(2 * level * self.N, dtype=np.uint64)  # filled as uint64[2][out_level][N]
         ol, ot = C.c_int32(), C.c_int32()
         arrs = [np.ascontiguousarray(x, dtype=np.uint64) for x in (A, B, C1, C2)]
         _chk(lib().ss_query_sum_where_lt_host(self.h, *[C.c_void_p(x.ctypes.data) for x in arrs],
                                               arrs[0].shape[0], arrs[3].shape[0], level,
                                               C.c_void_p(out.ctypes.data), C.byref(ol), C.byref(ot),
                                               _stream(self.torch, stream)))
-        return out[:, : ol.value], ol.value, ot.value
+        return out[: 2 * ol.value * self.N].reshape(2, ol.value, self.N), ol.value, ot.value
 
     def query_depth(self, level=None):
         out = C.c_int32()

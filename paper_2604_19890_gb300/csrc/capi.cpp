@@ -421,18 +421,44 @@ ss_status ss_query_sum_where_lt_host(ss_ctx* ctx, const uint64_t* A, const uint6
     need(level >= 1 && level <= C.L, SS_ERR_LEVEL, "bad level");
     cudaStream_t st = S(stream);
     size_t ct_words = (size_t)2 * level * C.N;
-    auto up = [&](const uint64_t* h, int cnt) {
-      ss::BufP b = ss::alloc_buf(C, cnt, 2, level, C.r, st);
-      SS_CUDA(cudaMemcpyAsync(b->data, h, cnt * ct_words * 8, cudaMemcpyHostToDevice, st));
-      return b;
+    // Buffers come from the pool on st. The comparison columns are copied on
+    // st; A and B on a second stream that starts once the allocations are
+    // ordered, so their upload overlaps the comparisons (the first product
+    // waits for it). Everything is freed on st after the final synchronise.
+    ss::BufP a = ss::alloc_buf(C, count, 2, level, C.r, st), b = ss::alloc_buf(C, count, 2, level, C.r, st);
+    ss::BufP c1 = ss::alloc_buf(C, count, 2, level, C.r, st), c2 = ss::alloc_buf(C, count2, 2, level, C.r, st);
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t allocated = nullptr, ab_ready = nullptr;
+    auto cleanup = [&] {
+      if (s2) cudaStreamSynchronize(s2);
+      if (allocated) cudaEventDestroy(allocated);
+      if (ab_ready) cudaEventDestroy(ab_ready);
+      if (s2) cudaStreamDestroy(s2);
     };
-    ss::BufP a = up(A, count), b = up(B, count), c1 = up(C1, count), c2 = up(C2, count2);
-    ss::BufP r = ss::ev_query(C, a, b, c1, c2, st);
-    size_t row = (size_t)r->level * C.N * 8;
-    SS_CUDA(cudaMemcpy2DAsync(host_out, row, r->data, (size_t)r->cap * C.N * 8, row, 2, cudaMemcpyDeviceToHost, st));
-    SS_CUDA(cudaStreamSynchronize(st));
-    if (out_level) *out_level = r->level;
-    if (out_t_exp) *out_t_exp = r->t_exp;
+    try {
+      SS_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+      SS_CUDA(cudaEventCreateWithFlags(&allocated, cudaEventDisableTiming));
+      SS_CUDA(cudaEventCreateWithFlags(&ab_ready, cudaEventDisableTiming));
+      SS_CUDA(cudaMemcpyAsync(c1->data, C1, count * ct_words * 8, cudaMemcpyHostToDevice, st));
+      SS_CUDA(cudaMemcpyAsync(c2->data, C2, count2 * ct_words * 8, cudaMemcpyHostToDevice, st));
+      SS_CUDA(cudaEventRecord(allocated, st));
+      SS_CUDA(cudaStreamWaitEvent(s2, allocated, 0));
+      SS_CUDA(cudaMemcpyAsync(a->data, A, count * ct_words * 8, cudaMemcpyHostToDevice, s2));
+      SS_CUDA(cudaMemcpyAsync(b->data, B, count * ct_words * 8, cudaMemcpyHostToDevice, s2));
+      SS_CUDA(cudaEventRecord(ab_ready, s2));
+      ss::BufP r = ss::ev_query_where(C, a, b, {ss::QCond{SS_PRED_LT, c1, c2}}, st, ab_ready);
+      size_t row = (size_t)r->level * C.N * 8;
+      SS_CUDA(cudaMemcpy2DAsync(host_out, row, r->data, (size_t)r->cap * C.N * 8, row, 2, cudaMemcpyDeviceToHost,
+                                st));
+      SS_CUDA(cudaStreamSynchronize(st));
+      if (out_level) *out_level = r->level;
+      if (out_t_exp) *out_t_exp = r->t_exp;
+    } catch (...) {
+      cudaStreamSynchronize(st);
+      cleanup();
+      throw;
+    }
+    cleanup();
   });
 }
 

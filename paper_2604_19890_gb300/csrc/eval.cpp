@@ -394,7 +394,8 @@ static BufP batch_total(Context& C, const BufP& R, cudaStream_t st) {
 // conditions' indicators (t = p) are multiplied in order (AND) and raised once,
 // ind = Raise(prod_k cond_k), R = ind*(A*B), total = rotate_sum(sum R).
 // Ciphertexts are processed C.batch at a time.
-BufP ev_query_where(Context& C, const BufP& A, const BufP& B, const std::vector<QCond>& conds, cudaStream_t st) {
+BufP ev_query_where(Context& C, const BufP& A, const BufP& B, const std::vector<QCond>& conds, cudaStream_t st,
+                    cudaEvent_t ab_ready) {
   int n = A->count;
   if (conds.empty()) throw Error(SS_ERR_PARAM, "a query needs at least one condition");
   if (B->count != n) throw Error(SS_ERR_SHAPE, "column batch sizes differ");
@@ -418,6 +419,7 @@ BufP ev_query_where(Context& C, const BufP& A, const BufP& B, const std::vector<
       }
     }
     ind = ev_raise(C, ind, st);
+    if (ab_ready && !C.dry && b0 == 0) SS_CUDA(cudaStreamWaitEvent(st, ab_ready, 0));  // A and B still arriving
     BufP R;
     {
       StageScope sc(C, ST_PRODUCT, st);

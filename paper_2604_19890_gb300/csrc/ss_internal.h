@@ -252,7 +252,10 @@ struct QCond {
   int pred;
   BufP X, Y;  // X[i] pred Y[i]; Y may hold one ciphertext
 };
-BufP ev_query_where(Context& C, const BufP& A, const BufP& B, const std::vector<QCond>& conds, cudaStream_t st);
+// ab_ready (optional): event after which A and B hold their data; the first
+// product waits for it, so their upload can overlap the comparisons.
+BufP ev_query_where(Context& C, const BufP& A, const BufP& B, const std::vector<QCond>& conds, cudaStream_t st,
+                    cudaEvent_t ab_ready = nullptr);
 struct QueryCols {
   BufP A, B, C1, C2;
 };

@@ -305,6 +305,20 @@ def test_eq_schedule_trace_matches_reference(tiny):
     assert gt == ot and "eq digit" in gt
 
 
+def test_query_from_host_memory_matches_device_query(tiny):
+    """ss_query_sum_where_lt_host (columns in host memory, A and B uploaded on a
+    second stream while the comparisons run) returns the device query's words."""
+    g, o = tiny
+    rng = np.random.default_rng(90)
+    cols = [rng.integers(0, g.t, (3, g.slots)) for _ in range(4)]
+    enc = [encrypt_both(g, o, v, 6000 + 100 * i)[0] for i, v in enumerate(cols)]
+    ref = g.query(*enc)
+    host = [e.words() for e in enc]
+    out, lvl, te = g.query_host(*host, enc[0].level)
+    assert (lvl, te) == (ref.level, ref.t_exp)
+    assert (out == ref.words()[0]).all()
+
+
 def test_schedule_trace_matches_reference(tiny):
     g, o = tiny
     rng = np.random.default_rng(5)
