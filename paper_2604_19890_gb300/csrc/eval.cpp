@@ -184,19 +184,66 @@ Term bsgs(Context& C, const std::vector<i64>& h, Powers& P, cudaStream_t st) {
   std::vector<i64> c(len, 0);
   std::copy(h.begin(), h.end(), c.begin());
   note(C, "bsgs n+1=" + std::to_string(n1) + " k=" + std::to_string(k) + " len=" + std::to_string(len));
+  auto nonzero = [&](int lo) {
+    std::vector<int> idx;
+    for (int i = 1; i < k; ++i)
+      if (c[lo + i] != 0) idx.push_back(i);
+    return idx;
+  };
+  // Leaf combinations computed ahead, several per pass over the baby steps
+  // (k_lincomb_multi reads each aligned baby step once for up to 16 leaves).
+  // A leaf joins when its terms are among the first leaf's and its common
+  // level is the first leaf's; each result equals its own linear combination.
+  std::map<int, BufP> ahead;
+  auto plan_leaves = [&](const std::vector<int>& idx0, int lvl0) {
+    if (idx0.size() > 16) return;
+    std::vector<int> los;
+    for (int lo = 0; lo < len; lo += k) {
+      std::vector<int> idx = nonzero(lo);
+      if (idx.empty()) continue;
+      bool inside = true;
+      int lvl = 1 << 30;
+      for (int i : idx) {
+        if (!std::binary_search(idx0.begin(), idx0.end(), i)) { inside = false; break; }
+        lvl = std::min(lvl, P.get(i)->level);
+      }
+      if (inside && lvl == lvl0) los.push_back(lo);
+    }
+    if (los.size() < 2) return;
+    std::vector<const Buf*> ys;
+    for (int i : idx0) ys.push_back(P.at_level(i, lvl0).get());
+    const Buf& y0 = *ys[0];
+    for (size_t b = 0; b < los.size(); b += 16) {
+      std::vector<std::vector<i64>> cs;
+      std::vector<Buf*> outs;
+      for (size_t j = b; j < los.size() && j < b + 16; ++j) {
+        std::vector<i64> row;
+        for (int i : idx0) row.push_back(c[los[j] + i]);
+        cs.push_back(row);
+        BufP o = alloc_buf(C, y0.count, 2, lvl0, y0.t_exp, st);
+        ahead[los[j]] = o;
+        outs.push_back(o.get());
+      }
+      if (!C.dry) k_lincomb_multi(C, ys, cs, outs, st);
+    }
+  };
   std::function<Term(int, int)> rec = [&](int lo, int ln) -> Term {
     Term out;
     if (ln == k) {
       out.cst = c[lo];
-      std::vector<int> idx;
-      for (int i = 1; i < k; ++i)
-        if (c[lo + i] != 0) idx.push_back(i);
+      std::vector<int> idx = nonzero(lo);
       if (idx.empty()) return out;
       int lvl = 1 << 30;
       for (int i : idx) lvl = std::min(lvl, P.get(i)->level);
-      std::vector<std::pair<BufP, i64>> terms;
-      for (int i : idx) terms.push_back({P.at_level(i, lvl), c[lo + i]});
-      out.ct = ev_lincomb(C, terms, 0, st);
+      if (lo == 0) plan_leaves(idx, lvl);
+      auto it = ahead.find(lo);
+      if (it != ahead.end()) {
+        out.ct = it->second;
+      } else {
+        std::vector<std::pair<BufP, i64>> terms;
+        for (int i : idx) terms.push_back({P.at_level(i, lvl), c[lo + i]});
+        out.ct = ev_lincomb(C, terms, 0, st);
+      }
       note(C, "baby lo=" + std::to_string(lo) + " terms=" + std::to_string(idx.size()) + " " + L_(lvl));
       return out;
     }
@@ -551,7 +598,8 @@ size_t query_bytes_estimate(const Context& C, int n_ct, int level) {
   const int b = std::min(n_ct, std::max(1, C.batch));
   const int dn = (level + C.alpha - 1) / C.alpha, nx = level + C.alpha;
   const size_t ks = (size_t)b * ((size_t)dn * nx + 4 * (size_t)nx + 2 * (size_t)level) * C.N * 8;
-  return 4 * (size_t)n_ct * ct + (size_t)b * ct * 48 + ks;
+  // columns + live intermediates of a pass (powers, up to 16 leaf combinations computed ahead) + key switch
+  return 4 * (size_t)n_ct * ct + (size_t)b * ct * (48 + 16) + ks;
 }
 
 }  // namespace ss

@@ -443,6 +443,72 @@ __global__ void __launch_bounds__(256) k_lincomb_impl(LinArgs A, int nterms, i64
   out[(row * ocap + i) * N + n] = r;
 }
 
+// Several linear combinations of the same inputs in one pass:
+// out_j = sum_i c[j][i] y_i for j < nout, every y_i read once. Scalars are
+// below 2^32 in magnitude (two 32-bit products per term, positive and
+// negative sums apart) or, with `small` = 0, below the smallest prime.
+struct LinMultiArgs {
+  const u64* ptr[16];
+  int cap[16];
+  u64* out[16];
+  int ocap[16];
+  i64 c[16][16];
+};
+
+__global__ void __launch_bounds__(256) k_lincomb_multi_impl(LinMultiArgs A, int nin, int nout, int small, int N,
+                                                            int ncomp, int level, const ModDesc* mods) {
+  const int poly = blockIdx.y;  // (bt, comp, i)
+  const int i = poly % level, comp = (poly / level) % ncomp, bt = poly / (level * ncomp);
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const Modulus& md = MOD(mods, i);
+  const u64 q = md.q;
+  const size_t row = (size_t)(bt * ncomp + comp);
+  u64 y[16];
+#pragma unroll
+  for (int t = 0; t < 16; ++t)
+    if (t < nin) y[t] = A.ptr[t][(row * A.cap[t] + i) * N + n];
+  for (int j = 0; j < nout; ++j) {
+    u64 r;
+    if (small) {
+      Acc128 pos, neg;
+      pos.zero();
+      neg.zero();
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        if (t < nin) {
+          const i64 c = A.c[j][t];
+          if (c > 0) {
+            const u64 p0 = (u64)(uint32_t)y[t] * (uint32_t)c, p1 = (u64)(uint32_t)(y[t] >> 32) * (uint32_t)c;
+            pos.add(p0);
+            pos.add(p1 << 32);
+            pos.hi += p1 >> 32;
+          } else if (c < 0) {
+            const uint32_t m = (uint32_t)(-c);
+            const u64 p0 = (u64)(uint32_t)y[t] * m, p1 = (u64)(uint32_t)(y[t] >> 32) * m;
+            neg.add(p0);
+            neg.add(p1 << 32);
+            neg.hi += p1 >> 32;
+          }
+        }
+      }
+      r = sub_mod(barrett_reduce128(pos.hi, pos.lo, md), barrett_reduce128(neg.hi, neg.lo, md), q);
+    } else {
+      Acc128 acc;
+      acc.zero();
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        if (t < nin) {
+          const i64 c = A.c[j][t];
+          if (c != 0) acc.mac_wide(y[t], c > 0 ? (u64)c : q - (u64)(-c));
+        }
+      }
+      r = barrett_reduce128(acc.hi, acc.lo, md);
+    }
+    A.out[j][(row * A.ocap[j] + i) * N + n] = r;
+  }
+}
+
 // acc_c[l-1] += P * d_c[l-1] (mod q_{l-1}) for c = 0, 1: the last data limb of
 // the extended ciphertext P*d + acc before it joins the dropped primes.
 __global__ void k_fixup_last_impl(u64* acc, long acc_os, int nx, const u64* d, long d_os, int dcap, int l,
@@ -551,6 +617,38 @@ void k_lincomb(Context& C, const std::vector<const Buf*>& ys, const std::vector<
   TIMED(KC_ELEM, (nt + 1.0) * polys * C.N * 8.0,
         k_lincomb_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(A, nt, cst, small ? npos + 1 : 0, out.data, out.cap, C.N,
                                                               out.ncomp, out.level, C.d_mod));
+  LAUNCHED();
+}
+
+void k_lincomb_multi(Context& C, const std::vector<const Buf*>& ys, const std::vector<std::vector<i64>>& cs,
+                     const std::vector<Buf*>& outs, cudaStream_t st) {
+  const int nin = (int)ys.size(), nout = (int)outs.size();
+  if (nin < 1 || nin > 16 || nout < 1 || nout > 16 || (int)cs.size() != nout)
+    throw Error(SS_ERR_PARAM, "multi-output linear combination of 1..16 inputs and outputs");
+  LinMultiArgs A;
+  bool small = true;
+  const u64 qmin = 1ULL << (C.prm.bits - 1);
+  for (int j = 0; j < nout; ++j) {
+    if ((int)cs[j].size() != nin) throw Error(SS_ERR_PARAM, "coefficient row length");
+    A.out[j] = outs[j]->data;
+    A.ocap[j] = outs[j]->cap;
+    for (int t = 0; t < nin; ++t) {
+      const i64 c = cs[j][t];
+      if (c == INT64_MIN || (u64)(c < 0 ? -c : c) >= qmin)
+        throw Error(SS_ERR_PARAM, "linear-combination scalar too large for the primes");
+      small = small && c > -(1LL << 32) && c < (1LL << 32);
+      A.c[j][t] = c;
+    }
+  }
+  for (int t = 0; t < nin; ++t) {
+    A.ptr[t] = ys[t]->data;
+    A.cap[t] = ys[t]->cap;
+  }
+  const Buf& o0 = *outs[0];
+  const int polys = o0.count * o0.ncomp * o0.level;
+  TIMED(KC_ELEM, (double)(nin + nout) * polys * C.N * 8.0,
+        k_lincomb_multi_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(A, nin, nout, small ? 1 : 0, C.N, o0.ncomp,
+                                                                    o0.level, C.d_mod));
   LAUNCHED();
 }
 

@@ -214,6 +214,9 @@ void k_crt(Context& C, const u64* v, int count, int level, int t_exp, u64* out, 
 void k_ksk_gadget(Context& C, u64* b, const u64* sprime, int j, cudaStream_t st);
 void k_square(Context& C, const u64* a, u64* out, int nprimes, cudaStream_t st);
 void k_batch_sum(Context& C, const Buf& a, Buf& out, cudaStream_t st);
+// outs[j] = sum_i cs[j][i] ys[i]; every input read once (all of one shape and level)
+void k_lincomb_multi(Context& C, const std::vector<const Buf*>& ys, const std::vector<std::vector<i64>>& cs,
+                     const std::vector<Buf*>& outs, cudaStream_t st);
 void k_lincomb(Context& C, const std::vector<const Buf*>& ys, const std::vector<i64>& cs, i64 cst, Buf& out,
                cudaStream_t st);
 
