@@ -27,6 +27,10 @@ namespace {
 
 constexpr int TPB = 256;
 
+#ifndef SS_KSIP_OB
+#define SS_KSIP_OB 2  // ciphertexts per thread in the key-switch inner product
+#endif
+
 static_assert(sizeof(Modulus) == sizeof(ModDesc), "device modulus descriptors share one layout");
 __device__ __forceinline__ const Modulus& MOD(const ModDesc* m, int i) {
   return reinterpret_cast<const Modulus*>(m)[i];
@@ -189,19 +193,23 @@ __global__ void k_sub_scale_impl(const u64* a, long a_os, const u64* dl, long d_
 // ---------------------------------------------------------------- key-switch inner product
 // acc[comp][m] = sum_j ext_j[m] * key_j[comp][g(m)], with ext_j[m] = d[m] on the
 // digit's own primes. 128-bit lazy sum over the digits, one Montgomery
-// reduction (the keys are stored times 2^64 mod q). One
-// thread per (ciphertext o, limb m, coefficient n); the ciphertext index runs
-// fastest over the blocks, so the blocks that read one stretch of the key run
-// back to back and all but the first find it in L2.
+// reduction (the keys are stored times 2^64 mod q). One thread per (group of
+// OB ciphertexts, limb m, coefficient n): each key word is loaded once for
+// the group. The ciphertext group runs fastest over the blocks, so the blocks
+// that read one stretch of the key run back to back and all but the first
+// find it in L2.
+template <int OB>
 __global__ void __launch_bounds__(256) k_ks_ip_impl(const u64* __restrict__ d, long d_os, const u64* __restrict__ ext,
                                                     long ext_os, const u64* __restrict__ kb,
                                                     const u64* __restrict__ ka, int level, int alpha, int L, int T,
                                                     u64* __restrict__ acc, long acc_os, int n_outer, int N,
                                                     const ModDesc* mods) {
-  const int o = blockIdx.x % n_outer;
-  const int n = (blockIdx.x / n_outer) * blockDim.x + threadIdx.x;
+  const int ngroups = (n_outer + OB - 1) / OB;
+  const int o0 = (blockIdx.x % ngroups) * OB;
+  const int n = (blockIdx.x / ngroups) * blockDim.x + threadIdx.x;
   const int m = blockIdx.y;  // local limb over level + alpha
   if (n >= N) return;
+  const int nb = min(OB, n_outer - o0);
   const int g = m < level ? m : L + (m - level);
   const Modulus md = MOD(mods, g);
   const int dn = (level + alpha - 1) / alpha;
@@ -210,21 +218,38 @@ __global__ void __launch_bounds__(256) k_ks_ip_impl(const u64* __restrict__ d, l
   const u64* kbp = kb + (size_t)g * N + n;
   const u64* kap = ka + (size_t)g * N + n;
   const size_t kstride = (size_t)T * N;
-  const u64* ep = ext + o * ext_os + (long)m * N + n;
+  const u64* ep = ext + o0 * ext_os + (long)m * N + n;
+  const u64* dp = d + o0 * d_os + (long)m * N + n;
   const long jstride = (long)nlx * N;
-  Acc128 s0, s1;
-  s0.zero();
-  s1.zero();
-#pragma unroll 4
+  Acc128 s0[OB], s1[OB];
+#pragma unroll
+  for (int b = 0; b < OB; ++b) {
+    s0[b].zero();
+    s1[b].zero();
+  }
   for (int j = 0; j < dn; ++j) {
-    const u64 x = j == jown ? d[o * d_os + (long)m * N + n] : ep[j * jstride];
-    s0.mac_wide(x, __ldg(kbp + j * kstride));
-    s1.mac_wide(x, __ldg(kap + j * kstride));
+    const u64 wb = __ldg(kbp + j * kstride), wa = __ldg(kap + j * kstride);
+    u64 x[OB];
+#pragma unroll
+    for (int b = 0; b < OB; ++b)
+      if (b < nb) x[b] = j == jown ? dp[b * d_os] : ep[b * ext_os + j * jstride];
+#pragma unroll
+    for (int b = 0; b < OB; ++b) {
+      if (b < nb) {
+        s0[b].mac_wide(x[b], wb);
+        s1[b].mac_wide(x[b], wa);
+      }
+    }
   }
   // keys carry 2^64 (Montgomery form); the sum is below dn q^2 < q 2^64
-  u64* out = acc + o * acc_os + (long)m * N + n;
-  out[0] = redc128(s0.hi, s0.lo, md.q, md.qinv);
-  out[(long)nlx * N] = redc128(s1.hi, s1.lo, md.q, md.qinv);
+  u64* out = acc + o0 * acc_os + (long)m * N + n;
+#pragma unroll
+  for (int b = 0; b < OB; ++b) {
+    if (b < nb) {
+      out[b * acc_os] = redc128(s0[b].hi, s0[b].lo, md.q, md.qinv);
+      out[b * acc_os + (long)nlx * N] = redc128(s1[b].hi, s1[b].lo, md.q, md.qinv);
+    }
+  }
 }
 
 // ---------------------------------------------------------------- automorphism
@@ -733,10 +758,11 @@ void k_to_montgomery(Context& C, u64* data, int npoly, cudaStream_t st) {
 void k_ks_ip(Context& C, const u64* d, long d_os, const u64* ext, long ext_os, const KeyDev& K, int level, u64* acc,
              long acc_os, int n_outer, cudaStream_t st) {
   const int dn = (level + C.alpha - 1) / C.alpha;
-  const dim3 grid((unsigned)(n_outer * ((C.N + TPB - 1) / TPB)), (unsigned)(level + C.alpha));
+  constexpr int OB = SS_KSIP_OB;
+  const dim3 grid((unsigned)(((n_outer + OB - 1) / OB) * ((C.N + TPB - 1) / TPB)), (unsigned)(level + C.alpha));
   TIMED(KC_KSIP, ((double)dn * (level + C.alpha) * (n_outer + 2.0) + 2.0 * (level + C.alpha) * n_outer) * (double)C.N * 8.0,
-        k_ks_ip_impl<<<grid, TPB, 0, st>>>(d, d_os, ext, ext_os, K.b, K.a, level, C.alpha, C.L, C.ntot, acc, acc_os,
-                                           n_outer, C.N, C.d_mod));
+        k_ks_ip_impl<OB><<<grid, TPB, 0, st>>>(d, d_os, ext, ext_os, K.b, K.a, level, C.alpha, C.L, C.ntot, acc,
+                                               acc_os, n_outer, C.N, C.d_mod));
   LAUNCHED();
 }
 
