@@ -159,6 +159,15 @@ def query_ntt_count(n_ct_small=(1, 2)):
     return slope, counts[0] - slope
 
 
+def workload_config(logN, L, bits, alpha, p, r, slots, n_ct, batch):
+    """The `config` object both arms print for one workload."""
+    rows = n_ct * slots
+    wl = ("compare-then-SUM query, N=2^%d, L=%d x %d-bit + %d special primes, p^r=%d^%d, %d slots, "
+          "%d ciphertexts per column (%d rows) per GPU" % (logN, L, bits, alpha, p, r, slots, n_ct, rows))
+    return {"workload": wl, "batch": batch,
+            "l2": "inputs (%.1f GB) larger than L2" % (4 * n_ct * 2 * L * (1 << logN) * 8 / 1e9)}
+
+
 def run_reference(args):
     rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
@@ -175,7 +184,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "rows/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": rows / v * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "N=2^16, L=41 x 55-bit + 3 special, p^r=257^3, 32 ct/column (4096 rows)"},
+            "config": workload_config(16, 41, 55, 3, 257, 3, 128, N_CT, args.batch),
             "cpu_baseline": {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
                              "sample": "per step: one tensor+relin+modswitch at level 20 of the N=2^16 chain "
                                        "(%d limb transforms), scaled by the query's %.0f transforms per "
@@ -556,14 +565,11 @@ def run_ours(args):
                          "%.1f s), scaled by the query's %.0f transforms per ciphertext x 32" % (ntts, dt, per_ct)}
 
     if rank == 0:
-        wl = ("compare-then-SUM query, N=2^%d, L=%d x %d-bit + %d special primes, p^r=%d^%d, %d slots, "
-              "%d ciphertexts per column (%d rows) per GPU" % (prm.logN, prm.L, prm.bits, prm.alpha, prm.p, prm.r,
-                                                            g.slots, n_ct, rows))
         line = {"metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-                "config": {"workload": wl, "batch": args.batch,
-                           "l2": "inputs (%.1f GB) larger than L2" % (4 * n_ct * 2 * prm.L * g.N * 8 / 1e9)},
+                "config": workload_config(prm.logN, prm.L, prm.bits, prm.alpha, prm.p, prm.r, g.slots, n_ct,
+                                          args.batch),
                 "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
                                                                                    int(0.99 * len(lat_ms)))]},
                 "verified_against_plaintext": verified,
