@@ -177,17 +177,27 @@ __global__ void __launch_bounds__(256) k_bconv_impl(const u64* __restrict__ src,
 }
 
 // out[m] = (a[m] - d[m]) * scale[m] (+ add[m]); limb m is data prime m.
+// Two consecutive words per thread through 16-byte loads and stores (every
+// limb starts on a 16-byte boundary: N is even and bases are 256-byte aligned).
+__device__ __forceinline__ ulonglong2 ld2(const u64* p) { return *reinterpret_cast<const ulonglong2*>(p); }
+__device__ __forceinline__ void st2(u64* p, u64 x, u64 y) { *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(x, y); }
+
 __global__ void k_sub_scale_impl(const u64* a, long a_os, const u64* dl, long d_os, const u64* scale, const u64* add,
                                  long add_os, u64* out, long out_os, int nl, int N, const ModDesc* mods) {
   int poly = blockIdx.y;
   int m = poly % nl, o = poly / nl;
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  int n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (n >= N) return;
-  u64 q = MOD(mods, m).q;
-  u64 x = sub_mod(a[(long)o * a_os + (long)m * N + n], dl[(long)o * d_os + (long)m * N + n], q);
-  x = shoup(x, __ldg(scale + 2 * m), __ldg(scale + 2 * m + 1), q);
-  if (add) x = add_mod(x, add[(long)o * add_os + (long)m * N + n], q);
-  out[(long)o * out_os + (long)m * N + n] = x;
+  const u64 q = MOD(mods, m).q;
+  const u64 w = __ldg(scale + 2 * m), wp = __ldg(scale + 2 * m + 1);
+  const ulonglong2 av = ld2(a + (long)o * a_os + (long)m * N + n), dv = ld2(dl + (long)o * d_os + (long)m * N + n);
+  u64 x0 = shoup(sub_mod(av.x, dv.x, q), w, wp, q), x1 = shoup(sub_mod(av.y, dv.y, q), w, wp, q);
+  if (add) {
+    const ulonglong2 ad = ld2(add + (long)o * add_os + (long)m * N + n);
+    x0 = add_mod(x0, ad.x, q);
+    x1 = add_mod(x1, ad.y, q);
+  }
+  st2(out + (long)o * out_os + (long)m * N + n, x0, x1);
 }
 
 // ---------------------------------------------------------------- key-switch inner product
@@ -555,13 +565,16 @@ __global__ void k_drop_combine_impl(const u64* acc, long acc_os, int nx, const u
                                     int ocap, int N, const ModDesc* mods) {
   int poly = blockIdx.y;  // (bt, c, i)
   int i = poly % nl, c = (poly / nl) & 1, bt = poly / (2 * nl);
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  int n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (n >= N) return;
-  u64 q = MOD(mods, i).q;
-  u64 x = d[(long)bt * d_os + ((long)c * dcap + i) * N + n];
-  u64 v = add_mod(shoup(x, pmod[2 * i], pmod[2 * i + 1], q), acc[(long)bt * acc_os + ((long)c * nx + i) * N + n], q);
-  v = sub_mod(v, delta[((long)(bt * 2 + c) * nl + i) * N + n], q);
-  out[(long)bt * out_os + ((long)c * ocap + i) * N + n] = shoup(v, inv[2 * i], inv[2 * i + 1], q);
+  const u64 q = MOD(mods, i).q;
+  const u64 pm = pmod[2 * i], pmp = pmod[2 * i + 1], iv = inv[2 * i], ivp = inv[2 * i + 1];
+  const ulonglong2 x = ld2(d + (long)bt * d_os + ((long)c * dcap + i) * N + n);
+  const ulonglong2 s = ld2(acc + (long)bt * acc_os + ((long)c * nx + i) * N + n);
+  const ulonglong2 dl = ld2(delta + ((long)(bt * 2 + c) * nl + i) * N + n);
+  const u64 v0 = sub_mod(add_mod(shoup(x.x, pm, pmp, q), s.x, q), dl.x, q);
+  const u64 v1 = sub_mod(add_mod(shoup(x.y, pm, pmp, q), s.y, q), dl.y, q);
+  st2(out + (long)bt * out_os + ((long)c * ocap + i) * N + n, shoup(v0, iv, ivp, q), shoup(v1, iv, ivp, q));
 }
 
 // out[g] = a[g]^2 for every prime g (evaluation form)
@@ -600,7 +613,7 @@ void k_fixup_last(Context& C, u64* acc, long acc_os, int nx, const Buf& d, int l
 void k_drop_combine(Context& C, const u64* acc, long acc_os, int nx, const Buf& d, const u64* delta, int nl,
                     const u64* pmod, const u64* inv, Buf& out, int B, cudaStream_t st) {
   TIMED(KC_SUBSCALE, 4.0 * 2 * B * nl * C.N * 8.0,
-        k_drop_combine_impl<<<grid_for(C.N, 2 * B * nl), TPB, 0, st>>>(acc, acc_os, nx, d.data,
+        k_drop_combine_impl<<<grid_for(C.N / 2, 2 * B * nl), TPB, 0, st>>>(acc, acc_os, nx, d.data,
                                                                         (long)d.ncomp * d.cap * C.N, d.cap, delta, nl,
                                                                         pmod, inv, out.data,
                                                                         (long)out.ncomp * out.cap * C.N, out.cap, C.N,
@@ -745,7 +758,7 @@ void k_bconv(Context& C, const u64* src, long src_os, int ns, int sp0, const u64
 void k_sub_scale(Context& C, const u64* a, long a_os, const u64* dl, long d_os, const u64* scale, const u64* add,
                  long add_os, u64* out, long out_os, int nl, int n_outer, cudaStream_t st) {
   TIMED(KC_SUBSCALE, (add ? 4.0 : 3.0) * nl * n_outer * (double)C.N * 8.0,
-  k_sub_scale_impl<<<grid_for(C.N, nl * n_outer), TPB, 0, st>>>(a, a_os, dl, d_os, scale, add, add_os, out, out_os,
+  k_sub_scale_impl<<<grid_for(C.N / 2, nl * n_outer), TPB, 0, st>>>(a, a_os, dl, d_os, scale, add, add_os, out, out_os,
                                                                  nl, C.N, C.d_mod));
   LAUNCHED();
 }
