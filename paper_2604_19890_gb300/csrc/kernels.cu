@@ -36,6 +36,11 @@ __device__ __forceinline__ const Modulus& MOD(const ModDesc* m, int i) {
   return reinterpret_cast<const Modulus*>(m)[i];
 }
 
+// Two consecutive words per thread through 16-byte loads and stores (every
+// limb starts on a 16-byte boundary: N is even and bases are 256-byte aligned).
+__device__ __forceinline__ ulonglong2 ld2(const u64* p) { return *reinterpret_cast<const ulonglong2*>(p); }
+__device__ __forceinline__ void st2(u64* p, u64 x, u64 y) { *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(x, y); }
+
 dim3 grid_for(int N, int polys) {
   int bx = (N + TPB - 1) / TPB;
   return dim3(bx, polys);
@@ -46,13 +51,15 @@ __global__ void k_binary_impl(int op, const u64* a, const u64* b, u64* out, int 
                               int bcap, int ocap, int bcast, const ModDesc* mods) {
   int poly = blockIdx.y;  // (bt, c, i)
   int i = poly % level, c = (poly / level) % ncomp, bt = poly / (level * ncomp);
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  int n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (n >= N) return;
   u64 q = MOD(mods, i).q;
   int bb = bcast ? 0 : bt;
-  u64 x = a[((size_t)(bt * ncomp + c) * acap + i) * N + n];
-  u64 y = b[((size_t)(bb * ncomp + c) * bcap + i) * N + n];
-  out[((size_t)(bt * ncomp + c) * ocap + i) * N + n] = op == 0 ? add_mod(x, y, q) : sub_mod(x, y, q);
+  const ulonglong2 x = ld2(a + ((size_t)(bt * ncomp + c) * acap + i) * N + n);
+  const ulonglong2 y = ld2(b + ((size_t)(bb * ncomp + c) * bcap + i) * N + n);
+  u64* o = out + ((size_t)(bt * ncomp + c) * ocap + i) * N + n;
+  if (op == 0) st2(o, add_mod(x.x, y.x, q), add_mod(x.y, y.y, q));
+  else st2(o, sub_mod(x.x, y.x, q), sub_mod(x.y, y.y, q));
 }
 
 // ---------------------------------------------------------------- scalars
@@ -98,21 +105,24 @@ __global__ void k_tensor_impl(const u64* a, const u64* b, u64* out, int N, int l
                               const ModDesc* mods) {
   int poly = blockIdx.y;  // (bt, i)
   int i = poly % level, bt = poly / level;
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  int n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (n >= N) return;
   const Modulus& md = MOD(mods, i);
   size_t la = (size_t)acap * N, lb = (size_t)bcap * N, lo = (size_t)ocap * N;
   const u64* A = a + (size_t)bt * 2 * la + (size_t)i * N + n;
   const u64* B = b + (size_t)bt * 2 * lb + (size_t)i * N + n;
   u64* O = out + (size_t)bt * 3 * lo + (size_t)i * N + n;
-  u64 a0 = A[0], a1 = A[la], b0 = B[0], b1 = B[lb];
-  O[0] = mul_mod(a0, b0, md);
-  Acc128 x;
+  const ulonglong2 a0 = ld2(A), a1 = ld2(A + la), b0 = ld2(B), b1 = ld2(B + lb);
+  st2(O, mul_mod(a0.x, b0.x, md), mul_mod(a0.y, b0.y, md));
+  Acc128 x, y;
   x.zero();
-  x.mac(a0, b1);
-  x.mac(a1, b0);
-  O[lo] = barrett_reduce128(x.hi, x.lo, md);
-  O[2 * lo] = mul_mod(a1, b1, md);
+  y.zero();
+  x.mac_wide(a0.x, b1.x);
+  x.mac_wide(a1.x, b0.x);
+  y.mac_wide(a0.y, b1.y);
+  y.mac_wide(a1.y, b0.y);
+  st2(O + lo, barrett_reduce128(x.hi, x.lo, md), barrett_reduce128(y.hi, y.lo, md));
+  st2(O + 2 * lo, mul_mod(a1.x, b1.x, md), mul_mod(a1.y, b1.y, md));
 }
 
 // ---------------------------------------------------------------- base conversion
@@ -177,11 +187,6 @@ __global__ void __launch_bounds__(256) k_bconv_impl(const u64* __restrict__ src,
 }
 
 // out[m] = (a[m] - d[m]) * scale[m] (+ add[m]); limb m is data prime m.
-// Two consecutive words per thread through 16-byte loads and stores (every
-// limb starts on a 16-byte boundary: N is even and bases are 256-byte aligned).
-__device__ __forceinline__ ulonglong2 ld2(const u64* p) { return *reinterpret_cast<const ulonglong2*>(p); }
-__device__ __forceinline__ void st2(u64* p, u64 x, u64 y) { *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(x, y); }
-
 __global__ void k_sub_scale_impl(const u64* a, long a_os, const u64* dl, long d_os, const u64* scale, const u64* add,
                                  long add_os, u64* out, long out_os, int nl, int N, const ModDesc* mods) {
   int poly = blockIdx.y;
@@ -490,57 +495,70 @@ struct LinMultiArgs {
   i64 c[16][16];
 };
 
+// y * c (|c| < 2^32) added into a 128-bit sum as two 32-bit products
+__device__ __forceinline__ void add_small(Acc128& a, u64 y, uint32_t m) {
+  const u64 p0 = (u64)(uint32_t)y * m, p1 = (u64)(uint32_t)(y >> 32) * m;
+  a.add(p0);
+  a.add(p1 << 32);
+  a.hi += p1 >> 32;
+}
+
+// Two consecutive words per thread.
 __global__ void __launch_bounds__(256) k_lincomb_multi_impl(LinMultiArgs A, int nin, int nout, int small, int N,
                                                             int ncomp, int level, const ModDesc* mods) {
   const int poly = blockIdx.y;  // (bt, comp, i)
   const int i = poly % level, comp = (poly / level) % ncomp, bt = poly / (level * ncomp);
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (n >= N) return;
   const Modulus& md = MOD(mods, i);
   const u64 q = md.q;
   const size_t row = (size_t)(bt * ncomp + comp);
-  u64 y[16];
+  ulonglong2 y[16];
 #pragma unroll
   for (int t = 0; t < 16; ++t)
-    if (t < nin) y[t] = A.ptr[t][(row * A.cap[t] + i) * N + n];
+    if (t < nin) y[t] = ld2(A.ptr[t] + (row * A.cap[t] + i) * N + n);
   for (int j = 0; j < nout; ++j) {
-    u64 r;
+    u64 r0, r1;
     if (small) {
-      Acc128 pos, neg;
-      pos.zero();
-      neg.zero();
+      Acc128 p0, n0, p1, n1;
+      p0.zero();
+      n0.zero();
+      p1.zero();
+      n1.zero();
 #pragma unroll
       for (int t = 0; t < 16; ++t) {
         if (t < nin) {
           const i64 c = A.c[j][t];
           if (c > 0) {
-            const u64 p0 = (u64)(uint32_t)y[t] * (uint32_t)c, p1 = (u64)(uint32_t)(y[t] >> 32) * (uint32_t)c;
-            pos.add(p0);
-            pos.add(p1 << 32);
-            pos.hi += p1 >> 32;
+            add_small(p0, y[t].x, (uint32_t)c);
+            add_small(p1, y[t].y, (uint32_t)c);
           } else if (c < 0) {
-            const uint32_t m = (uint32_t)(-c);
-            const u64 p0 = (u64)(uint32_t)y[t] * m, p1 = (u64)(uint32_t)(y[t] >> 32) * m;
-            neg.add(p0);
-            neg.add(p1 << 32);
-            neg.hi += p1 >> 32;
+            add_small(n0, y[t].x, (uint32_t)(-c));
+            add_small(n1, y[t].y, (uint32_t)(-c));
           }
         }
       }
-      r = sub_mod(barrett_reduce128(pos.hi, pos.lo, md), barrett_reduce128(neg.hi, neg.lo, md), q);
+      r0 = sub_mod(barrett_reduce128(p0.hi, p0.lo, md), barrett_reduce128(n0.hi, n0.lo, md), q);
+      r1 = sub_mod(barrett_reduce128(p1.hi, p1.lo, md), barrett_reduce128(n1.hi, n1.lo, md), q);
     } else {
-      Acc128 acc;
-      acc.zero();
+      Acc128 s0, s1;
+      s0.zero();
+      s1.zero();
 #pragma unroll
       for (int t = 0; t < 16; ++t) {
         if (t < nin) {
           const i64 c = A.c[j][t];
-          if (c != 0) acc.mac_wide(y[t], c > 0 ? (u64)c : q - (u64)(-c));
+          if (c != 0) {
+            const u64 w = c > 0 ? (u64)c : q - (u64)(-c);
+            s0.mac_wide(y[t].x, w);
+            s1.mac_wide(y[t].y, w);
+          }
         }
       }
-      r = barrett_reduce128(acc.hi, acc.lo, md);
+      r0 = barrett_reduce128(s0.hi, s0.lo, md);
+      r1 = barrett_reduce128(s1.hi, s1.lo, md);
     }
-    A.out[j][(row * A.ocap[j] + i) * N + n] = r;
+    st2(A.out[j] + (row * A.ocap[j] + i) * N + n, r0, r1);
   }
 }
 
@@ -685,7 +703,7 @@ void k_lincomb_multi(Context& C, const std::vector<const Buf*>& ys, const std::v
   const Buf& o0 = *outs[0];
   const int polys = o0.count * o0.ncomp * o0.level;
   TIMED(KC_ELEM, (double)(nin + nout) * polys * C.N * 8.0,
-        k_lincomb_multi_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(A, nin, nout, small ? 1 : 0, C.N, o0.ncomp,
+        k_lincomb_multi_impl<<<grid_for(C.N / 2, polys), TPB, 0, st>>>(A, nin, nout, small ? 1 : 0, C.N, o0.ncomp,
                                                                     o0.level, C.d_mod));
   LAUNCHED();
 }
@@ -702,7 +720,7 @@ void k_batch_sum(Context& C, const Buf& a, Buf& out, cudaStream_t st) {
 void k_binary(Context& C, int op, const Buf& a, const Buf& b, Buf& out, cudaStream_t st) {
   int polys = a.count * a.ncomp * a.level;
   TIMED(KC_ELEM, 3.0 * polys * (double)C.N * 8.0,
-  k_binary_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(op, a.data, b.data, out.data, C.N, a.ncomp, a.level, a.cap,
+  k_binary_impl<<<grid_for(C.N / 2, polys), TPB, 0, st>>>(op, a.data, b.data, out.data, C.N, a.ncomp, a.level, a.cap,
                                                        b.cap, out.cap, b.count == 1 && a.count > 1, C.d_mod));
   LAUNCHED();
 }
@@ -725,7 +743,7 @@ void k_copy_limbs(Context& C, const Buf& a, Buf& out, int level, cudaStream_t st
 void k_tensor(Context& C, const Buf& a, const Buf& b, Buf& out, cudaStream_t st) {
   int polys = a.count * a.level;
   TIMED(KC_TENSOR, 7.0 * polys * (double)C.N * 8.0,
-  k_tensor_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(a.data, b.data, out.data, C.N, a.level, a.cap, b.cap, out.cap,
+  k_tensor_impl<<<grid_for(C.N / 2, polys), TPB, 0, st>>>(a.data, b.data, out.data, C.N, a.level, a.cap, b.cap, out.cap,
                                                        C.d_mod));
   LAUNCHED();
 }
