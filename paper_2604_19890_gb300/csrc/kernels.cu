@@ -135,7 +135,9 @@ __global__ void k_tensor_impl(const u64* a, const u64* b, u64* out, int N, int l
 // 128-bit sum of ns products and one Montgomery reduction, which removes the
 // 2^64 and leaves the post factor applied. The sum stays below ns q_s q_g <
 // q_g 2^64 (primes below 2^58, ns <= 64), as the reduction needs.
-template <int NS>
+// V = 2: two consecutive coefficients per thread (16-byte accesses, the
+// staged constants read once for both).
+template <int NS, int V>
 __global__ void __launch_bounds__(256) k_bconv_impl(const u64* __restrict__ src, long src_os, int ns, int sp0, int nsq,
                                                     const u64* __restrict__ c1, const u64* __restrict__ c2, int T,
                                                     u64* __restrict__ dst, long dst_os, int nd, int nq, int L,
@@ -159,16 +161,23 @@ __global__ void __launch_bounds__(256) k_bconv_impl(const u64* __restrict__ src,
   }
   __syncthreads();
   const int o = blockIdx.y;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = V * (blockIdx.x * blockDim.x + threadIdx.x);
   if (n >= N) return;
   constexpr int MAXS = NS > 0 ? NS : 64;
-  u64 y[MAXS];
+  u64 y[V][MAXS];
 #pragma unroll
   for (int s = 0; s < MAXS; ++s) {
     if (s < ns_) {
       const int gs = s < nsq ? sp0 + s : L + (s - nsq);
       const u64 qs = MOD(mods, gs).q;
-      y[s] = shoup(src[o * src_os + (long)s * N + n], c1[2 * s], c1[2 * s + 1], qs);
+      const u64* sp = src + o * src_os + (long)s * N + n;
+      if (V == 2) {
+        const ulonglong2 v = ld2(sp);
+        y[0][s] = shoup(v.x, c1[2 * s], c1[2 * s + 1], qs);
+        y[V - 1][s] = shoup(v.y, c1[2 * s], c1[2 * s + 1], qs);
+      } else {
+        y[0][s] = shoup(*sp, c1[2 * s], c1[2 * s + 1], qs);
+      }
     }
   }
   u64* out = dst + o * dst_os + n;
@@ -176,12 +185,20 @@ __global__ void __launch_bounds__(256) k_bconv_impl(const u64* __restrict__ src,
     const int m0 = part == 0 ? 0 : skip_hi, m1 = part == 0 ? min(skip_lo, nd) : nd;
     for (int m = m0; m < m1; ++m) {
       const u64* e = sh + m * W;
-      Acc128 acc;
-      acc.zero();
+      Acc128 acc[V];
 #pragma unroll
-      for (int s = 0; s < MAXS; ++s)
-        if (s < ns_) acc.mac_wide(y[s], e[2 + s]);
-      out[(long)m * N] = redc128(acc.hi, acc.lo, e[0], e[1]);
+      for (int v = 0; v < V; ++v) acc[v].zero();
+#pragma unroll
+      for (int s = 0; s < MAXS; ++s) {
+        if (s < ns_) {
+          const u64 cs = e[2 + s];
+#pragma unroll
+          for (int v = 0; v < V; ++v) acc[v].mac_wide(y[v][s], cs);
+        }
+      }
+      const u64 qm = e[0], qi = e[1];
+      if (V == 2) st2(out + (long)m * N, redc128(acc[0].hi, acc[0].lo, qm, qi), redc128(acc[V - 1].hi, acc[V - 1].lo, qm, qi));
+      else out[(long)m * N] = redc128(acc[0].hi, acc[0].lo, qm, qi);
     }
   }
 }
@@ -758,15 +775,15 @@ void k_bconv(Context& C, const u64* src, long src_os, int ns, int sp0, const u64
   size_t smem = (size_t)nd * (2 + ns) * 8;
   if (smem > 48 * 1024) throw Error(SS_ERR_PARAM, "base conversion tables exceed 48 KiB of shared memory");
   int kr_ = kt_begin(C, st);
-#define SS_BCONV(NSV)                                                                                     \
-  k_bconv_impl<NSV><<<g, TPB, smem, st>>>(src, src_os, ns, sp0, nsq, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, \
-                                          skip_lo, skip_hi, post, C.N, C.d_mod)
+#define SS_BCONV(NSV, VV)                                                                                        \
+  k_bconv_impl<NSV, VV><<<dim3(g.x / VV + (g.x % VV), g.y), TPB, smem, st>>>(                                       \
+      src, src_os, ns, sp0, nsq, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo, skip_hi, post, C.N, C.d_mod)
   switch (ns) {
-    case 1: SS_BCONV(1); break;
-    case 2: SS_BCONV(2); break;
-    case 3: SS_BCONV(3); break;
-    case 4: SS_BCONV(4); break;
-    default: SS_BCONV(0); break;
+    case 1: SS_BCONV(1, 2); break;
+    case 2: SS_BCONV(2, 2); break;
+    case 3: SS_BCONV(3, 2); break;
+    case 4: SS_BCONV(4, 2); break;
+    default: SS_BCONV(0, 1); break;
   }
 #undef SS_BCONV
   kt_end(C, kr_, KC_BCONV, (double)(ns + nd - (skip_hi - skip_lo)) * n_outer * C.N * 8.0, st);
