@@ -30,6 +30,9 @@ constexpr int TPB = 256;
 #ifndef SS_KSIP_OB
 #define SS_KSIP_OB 2  // ciphertexts per thread in the key-switch inner product
 #endif
+#ifndef SS_KSIP_V
+#define SS_KSIP_V 2  // coefficients per thread in the key-switch inner product
+#endif
 
 static_assert(sizeof(Modulus) == sizeof(ModDesc), "device modulus descriptors share one layout");
 __device__ __forceinline__ const Modulus& MOD(const ModDesc* m, int i) {
@@ -236,9 +239,10 @@ __global__ void __launch_bounds__(256) k_ks_ip_impl(const u64* __restrict__ d, l
                                                     const u64* __restrict__ ka, int level, int alpha, int L, int T,
                                                     u64* __restrict__ acc, long acc_os, int n_outer, int N,
                                                     const ModDesc* mods) {
+  constexpr int V = SS_KSIP_V;  // consecutive coefficients per thread (1 or 2)
   const int ngroups = (n_outer + OB - 1) / OB;
   const int o0 = (blockIdx.x % ngroups) * OB;
-  const int n = (blockIdx.x / ngroups) * blockDim.x + threadIdx.x;
+  const int n = V * ((blockIdx.x / ngroups) * blockDim.x + threadIdx.x);
   const int m = blockIdx.y;  // local limb over level + alpha
   if (n >= N) return;
   const int nb = min(OB, n_outer - o0);
@@ -253,23 +257,48 @@ __global__ void __launch_bounds__(256) k_ks_ip_impl(const u64* __restrict__ d, l
   const u64* ep = ext + o0 * ext_os + (long)m * N + n;
   const u64* dp = d + o0 * d_os + (long)m * N + n;
   const long jstride = (long)nlx * N;
-  Acc128 s0[OB], s1[OB];
+  Acc128 s0[OB][V], s1[OB][V];
 #pragma unroll
-  for (int b = 0; b < OB; ++b) {
-    s0[b].zero();
-    s1[b].zero();
-  }
+  for (int b = 0; b < OB; ++b)
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      s0[b][v].zero();
+      s1[b][v].zero();
+    }
   for (int j = 0; j < dn; ++j) {
-    const u64 wb = __ldg(kbp + j * kstride), wa = __ldg(kap + j * kstride);
-    u64 x[OB];
-#pragma unroll
-    for (int b = 0; b < OB; ++b)
-      if (b < nb) x[b] = j == jown ? dp[b * d_os] : ep[b * ext_os + j * jstride];
+    u64 wb[V], wa[V];
+    if (V == 2) {
+      const ulonglong2 kbv = ld2(kbp + j * kstride), kav = ld2(kap + j * kstride);
+      wb[0] = kbv.x;
+      wb[V - 1] = kbv.y;
+      wa[0] = kav.x;
+      wa[V - 1] = kav.y;
+    } else {
+      wb[0] = __ldg(kbp + j * kstride);
+      wa[0] = __ldg(kap + j * kstride);
+    }
+    u64 x[OB][V];
 #pragma unroll
     for (int b = 0; b < OB; ++b) {
       if (b < nb) {
-        s0[b].mac_wide(x[b], wb);
-        s1[b].mac_wide(x[b], wa);
+        const u64* xp = j == jown ? dp + b * d_os : ep + b * ext_os + j * jstride;
+        if (V == 2) {
+          const ulonglong2 xv = ld2(xp);
+          x[b][0] = xv.x;
+          x[b][V - 1] = xv.y;
+        } else {
+          x[b][0] = *xp;
+        }
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < OB; ++b) {
+      if (b < nb) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          s0[b][v].mac_wide(x[b][v], wb[v]);
+          s1[b][v].mac_wide(x[b][v], wa[v]);
+        }
       }
     }
   }
@@ -278,8 +307,15 @@ __global__ void __launch_bounds__(256) k_ks_ip_impl(const u64* __restrict__ d, l
 #pragma unroll
   for (int b = 0; b < OB; ++b) {
     if (b < nb) {
-      out[b * acc_os] = redc128(s0[b].hi, s0[b].lo, md.q, md.qinv);
-      out[b * acc_os + (long)nlx * N] = redc128(s1[b].hi, s1[b].lo, md.q, md.qinv);
+      if (V == 2) {
+        st2(out + b * acc_os, redc128(s0[b][0].hi, s0[b][0].lo, md.q, md.qinv),
+            redc128(s0[b][V - 1].hi, s0[b][V - 1].lo, md.q, md.qinv));
+        st2(out + b * acc_os + (long)nlx * N, redc128(s1[b][0].hi, s1[b][0].lo, md.q, md.qinv),
+            redc128(s1[b][V - 1].hi, s1[b][V - 1].lo, md.q, md.qinv));
+      } else {
+        out[b * acc_os] = redc128(s0[b][0].hi, s0[b][0].lo, md.q, md.qinv);
+        out[b * acc_os + (long)nlx * N] = redc128(s1[b][0].hi, s1[b][0].lo, md.q, md.qinv);
+      }
     }
   }
 }
@@ -807,7 +843,8 @@ void k_ks_ip(Context& C, const u64* d, long d_os, const u64* ext, long ext_os, c
              long acc_os, int n_outer, cudaStream_t st) {
   const int dn = (level + C.alpha - 1) / C.alpha;
   constexpr int OB = SS_KSIP_OB;
-  const dim3 grid((unsigned)(((n_outer + OB - 1) / OB) * ((C.N + TPB - 1) / TPB)), (unsigned)(level + C.alpha));
+  const int nx_blocks = (C.N / SS_KSIP_V + TPB - 1) / TPB;
+  const dim3 grid((unsigned)(((n_outer + OB - 1) / OB) * nx_blocks), (unsigned)(level + C.alpha));
   TIMED(KC_KSIP, ((double)dn * (level + C.alpha) * (n_outer + 2.0) + 2.0 * (level + C.alpha) * n_outer) * (double)C.N * 8.0,
         k_ks_ip_impl<OB><<<grid, TPB, 0, st>>>(d, d_os, ext, ext_os, K.b, K.a, level, C.alpha, C.L, C.ntot, acc,
                                                acc_os, n_outer, C.N, C.d_mod));
