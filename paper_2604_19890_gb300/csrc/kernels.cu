@@ -44,6 +44,14 @@ __device__ __forceinline__ const Modulus& MOD(const ModDesc* m, int i) {
 __device__ __forceinline__ ulonglong2 ld2(const u64* p) { return *reinterpret_cast<const ulonglong2*>(p); }
 __device__ __forceinline__ void st2(u64* p, u64 x, u64 y) { *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(x, y); }
 
+// y * c (|c| < 2^32) added into a 128-bit sum as two 32-bit products
+__device__ __forceinline__ void add_small(Acc128& a, u64 y, uint32_t m) {
+  const u64 p0 = (u64)(uint32_t)y * m, p1 = (u64)(uint32_t)(y >> 32) * m;
+  a.add(p0);
+  a.add(p1 << 32);
+  a.hi += p1 >> 32;
+}
+
 dim3 grid_for(int N, int polys) {
   int bx = (N + TPB - 1) / TPB;
   return dim3(bx, polys);
@@ -86,13 +94,18 @@ __global__ void k_scalar_impl(int op, const u64* a, i64 c, u64* out, int N, int 
     }
   }
   __syncthreads();
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  int n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);  // two consecutive words per thread
   if (n >= N) return;
-  u64 x = a[((size_t)(bt * ncomp + comp) * acap + i) * N + n];
-  u64 y;
-  if (op == 1) y = comp == 0 ? add_mod(x, sw[0], q) : x;
-  else y = shoup(x, sw[0], sw[1], q);
-  out[((size_t)(bt * ncomp + comp) * ocap + i) * N + n] = y;
+  const ulonglong2 x = ld2(a + ((size_t)(bt * ncomp + comp) * acap + i) * N + n);
+  u64 y0, y1;
+  if (op == 1) {
+    y0 = comp == 0 ? add_mod(x.x, sw[0], q) : x.x;
+    y1 = comp == 0 ? add_mod(x.y, sw[0], q) : x.y;
+  } else {
+    y0 = shoup(x.x, sw[0], sw[1], q);
+    y1 = shoup(x.y, sw[0], sw[1], q);
+  }
+  st2(out + ((size_t)(bt * ncomp + comp) * ocap + i) * N + n, y0, y1);
 }
 
 __global__ void k_copy_impl(const u64* a, u64* out, int N, int ncomp, int level, int acap, int ocap) {
@@ -481,59 +494,73 @@ __global__ void __launch_bounds__(256) k_lincomb_impl(LinArgs A, int nterms, i64
                                                       int N, int ncomp, int level, const ModDesc* mods) {
   const int poly = blockIdx.y;  // (bt, comp, i)
   const int i = poly % level, comp = (poly / level) % ncomp, bt = poly / (level * ncomp);
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);  // two consecutive words per thread
   if (n >= N) return;
   const Modulus& md = MOD(mods, i);
   const u64 q = md.q;
   const size_t row = (size_t)(bt * ncomp + comp);
-  u64 y[16];
+  ulonglong2 y[16];
 #pragma unroll
   for (int t = 0; t < 16; ++t)
-    if (t < nterms) y[t] = A.ptr[t][(row * A.cap[t] + i) * N + n];
-  u64 r;
+    if (t < nterms) y[t] = ld2(A.ptr[t] + (row * A.cap[t] + i) * N + n);
+  u64 r0, r1;
   if (small) {
     // |c| < 2^32: y * |c| is two 32x32 products; positive and negative terms
     // are summed apart (each sum < 2^92) and reduced once each.
     // terms arrive sorted: the first `small` - 1 have c >= 0, the rest c < 0
-    Acc128 pos, neg;
-    pos.zero();
-    neg.zero();
+    Acc128 p0, n0, p1, n1;
+    p0.zero();
+    n0.zero();
+    p1.zero();
+    n1.zero();
     const int npos = small - 1;
 #pragma unroll
     for (int t = 0; t < 16; ++t) {
       if (t < nterms) {
         const i64 c = A.c[t];
         const uint32_t m = (uint32_t)(t < npos ? c : -c);
-        const u64 p0 = (u64)(uint32_t)y[t] * m, p1 = (u64)(uint32_t)(y[t] >> 32) * m;
         if (t < npos) {
-          pos.add(p0);
-          pos.add(p1 << 32);
-          pos.hi += p1 >> 32;
+          add_small(p0, y[t].x, m);
+          add_small(p1, y[t].y, m);
         } else {
-          neg.add(p0);
-          neg.add(p1 << 32);
-          neg.hi += p1 >> 32;
+          add_small(n0, y[t].x, m);
+          add_small(n1, y[t].y, m);
         }
       }
     }
-    if (comp == 0 && cst > 0) pos.add((u64)cst);
-    if (comp == 0 && cst < 0) neg.add((u64)(-cst));
-    r = sub_mod(barrett_reduce128(pos.hi, pos.lo, md), barrett_reduce128(neg.hi, neg.lo, md), q);
+    if (comp == 0 && cst > 0) {
+      p0.add((u64)cst);
+      p1.add((u64)cst);
+    }
+    if (comp == 0 && cst < 0) {
+      n0.add((u64)(-cst));
+      n1.add((u64)(-cst));
+    }
+    r0 = sub_mod(barrett_reduce128(p0.hi, p0.lo, md), barrett_reduce128(n0.hi, n0.lo, md), q);
+    r1 = sub_mod(barrett_reduce128(p1.hi, p1.lo, md), barrett_reduce128(n1.hi, n1.lo, md), q);
   } else {
     // |c| < q (checked on the host): c mod q is c or q - |c|
-    Acc128 acc;
-    acc.zero();
+    Acc128 s0, s1;
+    s0.zero();
+    s1.zero();
 #pragma unroll
     for (int t = 0; t < 16; ++t) {
       if (t < nterms) {
         const i64 c = A.c[t];
-        acc.mac_wide(y[t], c >= 0 ? (u64)c : q - (u64)(-c));
+        const u64 w = c >= 0 ? (u64)c : q - (u64)(-c);
+        s0.mac_wide(y[t].x, w);
+        s1.mac_wide(y[t].y, w);
       }
     }
-    if (comp == 0 && cst != 0) acc.add(cst >= 0 ? (u64)cst : q - (u64)(-cst));
-    r = barrett_reduce128(acc.hi, acc.lo, md);
+    if (comp == 0 && cst != 0) {
+      const u64 w = cst >= 0 ? (u64)cst : q - (u64)(-cst);
+      s0.add(w);
+      s1.add(w);
+    }
+    r0 = barrett_reduce128(s0.hi, s0.lo, md);
+    r1 = barrett_reduce128(s1.hi, s1.lo, md);
   }
-  out[(row * ocap + i) * N + n] = r;
+  st2(out + (row * ocap + i) * N + n, r0, r1);
 }
 
 // Several linear combinations of the same inputs in one pass:
@@ -547,14 +574,6 @@ struct LinMultiArgs {
   int ocap[16];
   i64 c[16][16];
 };
-
-// y * c (|c| < 2^32) added into a 128-bit sum as two 32-bit products
-__device__ __forceinline__ void add_small(Acc128& a, u64 y, uint32_t m) {
-  const u64 p0 = (u64)(uint32_t)y * m, p1 = (u64)(uint32_t)(y >> 32) * m;
-  a.add(p0);
-  a.add(p1 << 32);
-  a.hi += p1 >> 32;
-}
 
 // Two consecutive words per thread.
 __global__ void __launch_bounds__(256) k_lincomb_multi_impl(LinMultiArgs A, int nin, int nout, int small, int N,
@@ -724,7 +743,7 @@ void k_lincomb(Context& C, const std::vector<const Buf*>& ys, const std::vector<
   }
   int polys = out.count * out.ncomp * out.level;
   TIMED(KC_ELEM, (nt + 1.0) * polys * C.N * 8.0,
-        k_lincomb_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(A, nt, cst, small ? npos + 1 : 0, out.data, out.cap, C.N,
+        k_lincomb_impl<<<grid_for(C.N / 2, polys), TPB, 0, st>>>(A, nt, cst, small ? npos + 1 : 0, out.data, out.cap, C.N,
                                                               out.ncomp, out.level, C.d_mod));
   LAUNCHED();
 }
@@ -781,7 +800,7 @@ void k_binary(Context& C, int op, const Buf& a, const Buf& b, Buf& out, cudaStre
 void k_scalar(Context& C, int op, const Buf& a, i64 c, Buf& out, cudaStream_t st) {
   int polys = a.count * a.ncomp * a.level;
   TIMED(KC_ELEM, 2.0 * polys * (double)C.N * 8.0,
-  k_scalar_impl<<<grid_for(C.N, polys), TPB, 0, st>>>(op, a.data, c, out.data, C.N, a.ncomp, a.level, a.cap,
+  k_scalar_impl<<<grid_for(C.N / 2, polys), TPB, 0, st>>>(op, a.data, c, out.data, C.N, a.ncomp, a.level, a.cap,
                                                        out.cap, C.d_mod, C.d_pinv));
   LAUNCHED();
 }
