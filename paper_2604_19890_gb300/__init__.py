@@ -234,7 +234,7 @@ class Batch:
             out.append((prod, ds))
         return out
 
-    def config(self, chunk, nstreams, tile_log=12):
+    def config(self, chunk, nstreams, tile_log=11):
         _chk(lib().ss_batch_config(self.h, chunk, nstreams, tile_log))
 
     def get_config(self):

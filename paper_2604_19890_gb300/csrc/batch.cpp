@@ -29,7 +29,7 @@ struct ss_batch {
   std::vector<ss::Context*> ctxs;
   std::vector<ss_batch_item> items;
   std::vector<Group> groups;
-  int chunk = 64, nstreams = 1, tile_log = 12;
+  int chunk = 64, nstreams = 1, tile_log = SS_NTT_TILE_LOG;
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;
   cudaGraph_t graph = nullptr;
@@ -297,7 +297,7 @@ void ss_batch_destroy(ss_batch* b) {
   ss::drop_graph(*b);
   for (auto s : b->streams) cudaStreamDestroy(s);
   for (auto e : b->events) cudaEventDestroy(e);
-  for (auto* c : b->ctxs) c->ntt_tile_log = 12;
+  for (auto* c : b->ctxs) c->ntt_tile_log = SS_NTT_TILE_LOG;
   delete b;
 }
 

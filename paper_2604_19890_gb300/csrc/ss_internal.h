@@ -104,6 +104,10 @@ struct KTimer {
   double st_ms[ST_N] = {};
 };
 
+#ifndef SS_NTT_TILE_LOG
+#define SS_NTT_TILE_LOG 11
+#endif
+
 struct Context {
   ss_params prm;
   int N = 0, logN = 0, L = 0, alpha = 0, ntot = 0, dnum = 0;
@@ -151,7 +155,7 @@ struct Context {
 
   // evaluator
   int batch = 8;
-  int ntt_tile_log = 12;  // words per CTA tile of the two-phase transform: 2^11 or 2^12
+  int ntt_tile_log = SS_NTT_TILE_LOG;  // words per CTA tile of the two-phase transform: 2^11 or 2^12
   bool dry = false;  // plan only: track levels, launch nothing
   bool trace_on = false;
   std::vector<std::string> trace;
