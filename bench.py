@@ -32,9 +32,9 @@ IMAD_PEAK = 152 * 64 * 2.07e9
 # 32-bit multiplies in one 64-bit Shoup butterfly product (schoolbook minimum):
 # high 64 bits of a*w' (4) + low 64 bits of a*w (3) + low 64 bits of qhat*q (3).
 IMAD_PER_BUTTERFLY = 10
-# DRAM bytes per limb transform (forward, both phases) from the ncu capture in
-# profiles/ntt_n65536_l41.md, over the 1 MB (16 N) it must move.
-NTT_TRAFFIC_PER_ALGO_BYTE = 1.849
+# DRAM bytes per limb transform (forward and inverse, both phases each) from the
+# ncu capture in profiles/ntt_n65536_l41.md, over the 1 MB (16 N) it must move.
+NTT_TRAFFIC_PER_ALGO_BYTE = 1.869
 
 
 def hbm_peak():
