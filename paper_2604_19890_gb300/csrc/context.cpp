@@ -271,7 +271,7 @@ void build_context(Context& C, const ss_params& prm) {
   // twiddles: psi^brv(i) and psi^-brv(i) with Shoup companions
   {
     std::vector<u64> tw((size_t)T * 4 * N);
-    std::vector<u64> ninv(2 * T), pinv(2 * T);
+    std::vector<u64> ninv(4 * T), pinv(2 * T);
     for (int i = 0; i < T; ++i) {
       u64 q = C.primes[i], ps = C.psi[i], pi = nt::inv(ps, q);
       std::vector<u64> fw(N), bw(N);
@@ -286,8 +286,12 @@ void build_context(Context& C, const ss_params& prm) {
         o[2 * N + 2 * k + 1] = nt::shoup(bw[rk], q);
       }
       u64 ni = nt::inv((u64)N % q, q);
-      ninv[2 * i] = ni;
-      ninv[2 * i + 1] = nt::shoup(ni, q);
+      ninv[4 * i] = ni;
+      ninv[4 * i + 1] = nt::shoup(ni, q);
+      // N^-1 times the last inverse stage's twiddle psi^-bitrev(1) = psi^(-N/2)
+      const u64 wni = nt::mul(ni, bw[N / 2], q);
+      ninv[4 * i + 2] = wni;
+      ninv[4 * i + 3] = nt::shoup(wni, q);
       u64 pv = nt::inv((u64)C.p % q, q);
       pinv[2 * i] = pv;
       pinv[2 * i + 1] = nt::shoup(pv, q);

@@ -34,7 +34,7 @@ struct NttArgs {
   int skip_w, skip_mod, skip_level;
   const Modulus* mods;
   const u64* tw;     // per prime 4N words: (w, w') pairs forward, then inverse
-  const u64* ninv;   // per prime (N^-1, shoup)
+  const u64* ninv;   // per prime (N^-1, shoup, N^-1 psi^(-N/2), shoup)
   const u64* src;    // out-of-place first phase: polynomial (o, i) is read at src + o src_os + i N
   long src_os;
 };
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, in
     __syncthreads();
   }
   u64 ni = 0, nip = 0;
-  if (LAST && !FWD) { ni = A.ninv[2 * pidx]; nip = A.ninv[2 * pidx + 1]; }
+  if (LAST && !FWD) { ni = A.ninv[4 * pidx]; nip = A.ninv[4 * pidx + 1]; }
   for (int lin = tid; lin < W; lin += T) {
     u64 v = sm[swz(lin)];
     if (LAST) {
@@ -242,7 +242,13 @@ __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_nt
     __syncthreads();
   }
   u64 ni = 0, nip = 0;
-  if (LAST && !FWD) { ni = A.ninv[2 * pidx]; nip = A.ninv[2 * pidx + 1]; }
+  u64 wni = 0, wnip = 0;
+  if (LAST && !FWD) {
+    ni = A.ninv[4 * pidx];
+    nip = A.ninv[4 * pidx + 1];
+    wni = A.ninv[4 * pidx + 2];
+    wnip = A.ninv[4 * pidx + 3];
+  }
   const int kb = A.mods[pidx].kbits;
   const uint32_t mq = (uint32_t)(A.mods[pidx].mu >> 47);
 #pragma unroll
@@ -290,19 +296,29 @@ __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_nt
         const int d = 1 << j;
         const int logt = logu + j;
         const int sg = LOGS - 1 - logt;
+        // the inverse transform's last stage (one twiddle, psi^(-N/2)) also
+        // applies N^-1: sums times N^-1, differences times N^-1 psi^(-N/2)
+        const bool fold = LAST && !FWD && rho == NR - 1 && jj == ns - 1;
 #pragma unroll
         for (int blk = 0; blk < 8; ++blk) {
           if (blk < 8 / d) {
             const int k0 = blk * 2 * d;
-            const int widx = (mg << sg) + ((rbase + (k0 << logu)) >> (logt + 1));
-            const ulonglong2 wv = __ldg(tw + widx);
-            const u64 w = wv.x, wp = wv.y;
+            u64 w = wni, wp = wnip;
+            if (!fold) {
+              const int widx = (mg << sg) + ((rbase + (k0 << logu)) >> (logt + 1));
+              const ulonglong2 wv = __ldg(tw + widx);
+              w = wv.x;
+              wp = wv.y;
+            }
 #pragma unroll
             for (int p = 0; p < 8; ++p) {
               if (p < d) {
                 const int k = k0 + p;
                 u64 U = x[k], V = x[k + d];
-                if (FWD) {
+                if (fold) {
+                  x[k] = shoup(U + V, ni, nip, q);
+                  x[k + d] = shoup(U - V + q2, w, wp, q);
+                } else if (FWD) {
                   V = shoup_lazy(V, w, wp, q);
                   x[k] = U + V;
                   x[k + d] = U - V + q2;
@@ -323,7 +339,7 @@ __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_nt
       for (int k = 0; k < 16; ++k) {
         int r = rbase + (k << logu);
         u64 v = x[k];
-        if (LAST) v = FWD ? reduce_lazy(v, q, kb, mq) : shoup(v, ni, nip, q);
+        if (LAST && FWD) v = reduce_lazy(v, q, kb, mq);  // the inverse's last stage already reduced and scaled
         if (COLS) gbase[(long)r * stride + c] = v;
         else gbase[(c << LOGS) + r] = v;
       }
@@ -340,7 +356,7 @@ __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_nt
   if (!DOUT) {
     for (int lin = tid; lin < W; lin += T) {
       u64 v = sm[swz(lin)];
-      if (LAST) v = FWD ? reduce_lazy(v, q, kb, mq) : shoup(v, ni, nip, q);
+      if (LAST && FWD) v = reduce_lazy(v, q, kb, mq);
       gbase[lin] = v;
     }
   }
