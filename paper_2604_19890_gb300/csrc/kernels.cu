@@ -30,6 +30,9 @@ constexpr int TPB = 256;
 #ifndef SS_KSIP_OB
 #define SS_KSIP_OB 2  // ciphertexts per thread in the key-switch inner product
 #endif
+#ifndef SS_BCONV_V
+#define SS_BCONV_V 2  // coefficients per thread in base conversion (1 to 4 sources)
+#endif
 #ifndef SS_KSIP_V
 #define SS_KSIP_V 2  // coefficients per thread in the key-switch inner product
 #endif
@@ -43,6 +46,29 @@ __device__ __forceinline__ const Modulus& MOD(const ModDesc* m, int i) {
 // limb starts on a 16-byte boundary: N is even and bases are 256-byte aligned).
 __device__ __forceinline__ ulonglong2 ld2(const u64* p) { return *reinterpret_cast<const ulonglong2*>(p); }
 __device__ __forceinline__ void st2(u64* p, u64 x, u64 y) { *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(x, y); }
+// V consecutive words (V = 1, 2 or 4; 16-byte accesses for V > 1)
+template <int V>
+__device__ __forceinline__ void ldv(const u64* p, u64 (&v)[V]) {
+  if (V == 1) {
+    v[0] = *p;
+  } else {
+#pragma unroll
+    for (int i = 0; i < V; i += 2) {
+      const ulonglong2 t = ld2(p + i);
+      v[i] = t.x;
+      v[i + 1 < V ? i + 1 : i] = t.y;
+    }
+  }
+}
+template <int V>
+__device__ __forceinline__ void stv(u64* p, const u64 (&v)[V]) {
+  if (V == 1) {
+    *p = v[0];
+  } else {
+#pragma unroll
+    for (int i = 0; i < V; i += 2) st2(p + i, v[i], v[i + 1 < V ? i + 1 : i]);
+  }
+}
 
 // y * c (|c| < 2^32) added into a 128-bit sum as two 32-bit products
 __device__ __forceinline__ void add_small(Acc128& a, u64 y, uint32_t m) {
@@ -186,14 +212,10 @@ __global__ void __launch_bounds__(256) k_bconv_impl(const u64* __restrict__ src,
     if (s < ns_) {
       const int gs = s < nsq ? sp0 + s : L + (s - nsq);
       const u64 qs = MOD(mods, gs).q;
-      const u64* sp = src + o * src_os + (long)s * N + n;
-      if (V == 2) {
-        const ulonglong2 v = ld2(sp);
-        y[0][s] = shoup(v.x, c1[2 * s], c1[2 * s + 1], qs);
-        y[V - 1][s] = shoup(v.y, c1[2 * s], c1[2 * s + 1], qs);
-      } else {
-        y[0][s] = shoup(*sp, c1[2 * s], c1[2 * s + 1], qs);
-      }
+      u64 v[V];
+      ldv<V>(src + o * src_os + (long)s * N + n, v);
+#pragma unroll
+      for (int i = 0; i < V; ++i) y[i][s] = shoup(v[i], c1[2 * s], c1[2 * s + 1], qs);
     }
   }
   u64* out = dst + o * dst_os + n;
@@ -213,8 +235,10 @@ __global__ void __launch_bounds__(256) k_bconv_impl(const u64* __restrict__ src,
         }
       }
       const u64 qm = e[0], qi = e[1];
-      if (V == 2) st2(out + (long)m * N, redc128(acc[0].hi, acc[0].lo, qm, qi), redc128(acc[V - 1].hi, acc[V - 1].lo, qm, qi));
-      else out[(long)m * N] = redc128(acc[0].hi, acc[0].lo, qm, qi);
+      u64 r[V];
+#pragma unroll
+      for (int i = 0; i < V; ++i) r[i] = redc128(acc[i].hi, acc[i].lo, qm, qi);
+      stv<V>(out + (long)m * N, r);
     }
   }
 }
@@ -252,7 +276,7 @@ __global__ void __launch_bounds__(256) k_ks_ip_impl(const u64* __restrict__ d, l
                                                     const u64* __restrict__ ka, int level, int alpha, int L, int T,
                                                     u64* __restrict__ acc, long acc_os, int n_outer, int N,
                                                     const ModDesc* mods) {
-  constexpr int V = SS_KSIP_V;  // consecutive coefficients per thread (1 or 2)
+  constexpr int V = SS_KSIP_V;  // consecutive coefficients per thread (1, 2 or 4)
   const int ngroups = (n_outer + OB - 1) / OB;
   const int o0 = (blockIdx.x % ngroups) * OB;
   const int n = V * ((blockIdx.x / ngroups) * blockDim.x + threadIdx.x);
@@ -280,30 +304,12 @@ __global__ void __launch_bounds__(256) k_ks_ip_impl(const u64* __restrict__ d, l
     }
   for (int j = 0; j < dn; ++j) {
     u64 wb[V], wa[V];
-    if (V == 2) {
-      const ulonglong2 kbv = ld2(kbp + j * kstride), kav = ld2(kap + j * kstride);
-      wb[0] = kbv.x;
-      wb[V - 1] = kbv.y;
-      wa[0] = kav.x;
-      wa[V - 1] = kav.y;
-    } else {
-      wb[0] = __ldg(kbp + j * kstride);
-      wa[0] = __ldg(kap + j * kstride);
-    }
+    ldv<V>(kbp + j * kstride, wb);
+    ldv<V>(kap + j * kstride, wa);
     u64 x[OB][V];
 #pragma unroll
-    for (int b = 0; b < OB; ++b) {
-      if (b < nb) {
-        const u64* xp = j == jown ? dp + b * d_os : ep + b * ext_os + j * jstride;
-        if (V == 2) {
-          const ulonglong2 xv = ld2(xp);
-          x[b][0] = xv.x;
-          x[b][V - 1] = xv.y;
-        } else {
-          x[b][0] = *xp;
-        }
-      }
-    }
+    for (int b = 0; b < OB; ++b)
+      if (b < nb) ldv<V>(j == jown ? dp + b * d_os : ep + b * ext_os + j * jstride, x[b]);
 #pragma unroll
     for (int b = 0; b < OB; ++b) {
       if (b < nb) {
@@ -320,15 +326,14 @@ __global__ void __launch_bounds__(256) k_ks_ip_impl(const u64* __restrict__ d, l
 #pragma unroll
   for (int b = 0; b < OB; ++b) {
     if (b < nb) {
-      if (V == 2) {
-        st2(out + b * acc_os, redc128(s0[b][0].hi, s0[b][0].lo, md.q, md.qinv),
-            redc128(s0[b][V - 1].hi, s0[b][V - 1].lo, md.q, md.qinv));
-        st2(out + b * acc_os + (long)nlx * N, redc128(s1[b][0].hi, s1[b][0].lo, md.q, md.qinv),
-            redc128(s1[b][V - 1].hi, s1[b][V - 1].lo, md.q, md.qinv));
-      } else {
-        out[b * acc_os] = redc128(s0[b][0].hi, s0[b][0].lo, md.q, md.qinv);
-        out[b * acc_os + (long)nlx * N] = redc128(s1[b][0].hi, s1[b][0].lo, md.q, md.qinv);
+      u64 r0[V], r1[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        r0[v] = redc128(s0[b][v].hi, s0[b][v].lo, md.q, md.qinv);
+        r1[v] = redc128(s1[b][v].hi, s1[b][v].lo, md.q, md.qinv);
       }
+      stv<V>(out + b * acc_os, r0);
+      stv<V>(out + b * acc_os + (long)nlx * N, r1);
     }
   }
 }
@@ -831,13 +836,13 @@ void k_bconv(Context& C, const u64* src, long src_os, int ns, int sp0, const u64
   if (smem > 48 * 1024) throw Error(SS_ERR_PARAM, "base conversion tables exceed 48 KiB of shared memory");
   int kr_ = kt_begin(C, st);
 #define SS_BCONV(NSV, VV)                                                                                        \
-  k_bconv_impl<NSV, VV><<<dim3(g.x / VV + (g.x % VV), g.y), TPB, smem, st>>>(                                       \
+  k_bconv_impl<NSV, VV><<<dim3((g.x + VV - 1) / VV, g.y), TPB, smem, st>>>(                                       \
       src, src_os, ns, sp0, nsq, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo, skip_hi, post, C.N, C.d_mod)
   switch (ns) {
-    case 1: SS_BCONV(1, 2); break;
-    case 2: SS_BCONV(2, 2); break;
-    case 3: SS_BCONV(3, 2); break;
-    case 4: SS_BCONV(4, 2); break;
+    case 1: SS_BCONV(1, SS_BCONV_V); break;
+    case 2: SS_BCONV(2, SS_BCONV_V); break;
+    case 3: SS_BCONV(3, SS_BCONV_V); break;
+    case 4: SS_BCONV(4, SS_BCONV_V); break;
     default: SS_BCONV(0, 1); break;
   }
 #undef SS_BCONV
