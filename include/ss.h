@@ -261,7 +261,10 @@ ss_status ss_set_batch(ss_ctx* ctx, int32_t batch);
 
 /* ---- raw transform (for kernel-level measurement) ---- */
 /* In-place negacyclic NTT of `npoly` consecutive limbs of N words; limb k uses
- * data prime (first_prime + k % nprimes). */
+ * data prime (first_prime + k % nprimes). Input words must be residues below
+ * their prime (the forward transform keeps lazy sums below 36q, which needs
+ * inputs below 4q); outputs are residues below the prime, forward in the
+ * evaluation order word j = a(psi^(2 bitrev(j) + 1)). */
 ss_status ss_ntt_forward(ss_ctx* ctx, uint64_t* data, int32_t npoly, int32_t first_prime, int32_t nprimes,
                          ss_stream stream);
 ss_status ss_ntt_inverse(ss_ctx* ctx, uint64_t* data, int32_t npoly, int32_t first_prime, int32_t nprimes,
