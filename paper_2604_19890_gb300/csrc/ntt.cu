@@ -20,6 +20,9 @@ namespace {
 constexpr int TILE = 4096;  // words per CTA tile (32 KiB of shared memory)
 
 // resident CTAs per SM the radix-16 phases are compiled for (forward, inverse)
+#ifndef SS_NTT_PREFETCH
+#define SS_NTT_PREFETCH 1  // inverse chunk phase: first-stage twiddles loaded before the staging
+#endif
 #ifndef SS_NTT_MINB_F
 #define SS_NTT_MINB_F 3
 #endif
@@ -237,6 +240,19 @@ __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_nt
   constexpr int BL = FWD ? LOGS - 1 - 4 * (NR - 1) : 4 * (NR - 1) + NSL - 1;
   constexpr bool DIN = COLS || (B0 - 3 >= 4);
   constexpr bool DOUT = COLS || (BL - 3 >= 4);
+  // Inverse chunk phase (staged through shared memory): the first stage's
+  // eight twiddles of this thread are consecutive; load them before the
+  // staging so their latency overlaps it.
+  constexpr bool PRE = SS_NTT_PREFETCH && !FWD && !DIN && !COLS;
+  ulonglong2 pre[PRE ? 8 : 1];
+  if (PRE) {
+    const int logB = LOGS - 4;
+    const int B = tid & ((1 << logB) - 1), c = tid >> logB;
+    const int mg = m0 + tile * CPB + c;
+    const ulonglong2* tp = tw + (mg << (LOGS - 1)) + (B << 3);
+#pragma unroll
+    for (int i = 0; i < (PRE ? 8 : 1); ++i) pre[i] = __ldg(tp + i);
+  }
   if (!DIN) {
     for (int lin = tid; lin < W; lin += T) sm[swz(lin)] = gsrc[lin];
     __syncthreads();
@@ -304,7 +320,10 @@ __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_nt
           if (blk < 8 / d) {
             const int k0 = blk * 2 * d;
             u64 w = wni, wp = wnip;
-            if (!fold) {
+            if (PRE && rho == 0 && jj == 0) {
+              w = pre[PRE ? blk : 0].x;
+              wp = pre[PRE ? blk : 0].y;
+            } else if (!fold) {
               const int widx = (mg << sg) + ((rbase + (k0 << logu)) >> (logt + 1));
               const ulonglong2 wv = __ldg(tw + widx);
               w = wv.x;
