@@ -70,6 +70,13 @@ __device__ __forceinline__ void stv(u64* p, const u64 (&v)[V]) {
   }
 }
 
+// (h 2^32 + l) mod q for 64-bit partial sums h, l (the value is below 2^96)
+__device__ __forceinline__ u64 reduce_split(u64 h, u64 l, const Modulus& md) {
+  const u64 lo = (h << 32) + l;
+  const u64 hi = (h >> 32) + (lo < l ? 1 : 0);
+  return barrett_reduce128(hi, lo, md);
+}
+
 // y * c (|c| < 2^32) added into a 128-bit sum as two 32-bit products
 __device__ __forceinline__ void add_small(Acc128& a, u64 y, uint32_t m) {
   const u64 p0 = (u64)(uint32_t)y * m, p1 = (u64)(uint32_t)(y >> 32) * m;
@@ -581,8 +588,8 @@ struct LinMultiArgs {
 };
 
 // Two consecutive words per thread.
-__global__ void __launch_bounds__(256) k_lincomb_multi_impl(LinMultiArgs A, int nin, int nout, int small, int N,
-                                                            int ncomp, int level, const ModDesc* mods) {
+__global__ void __launch_bounds__(256) k_lincomb_multi_impl(LinMultiArgs A, int nin, int nout, int small, int tiny,
+                                                            int N, int ncomp, int level, const ModDesc* mods) {
   const int poly = blockIdx.y;  // (bt, comp, i)
   const int i = poly % level, comp = (poly / level) % ncomp, bt = poly / (level * ncomp);
   const int n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -596,7 +603,32 @@ __global__ void __launch_bounds__(256) k_lincomb_multi_impl(LinMultiArgs A, int 
     if (t < nin) y[t] = ld2(A.ptr[t] + (row * A.cap[t] + i) * N + n);
   for (int j = 0; j < nout; ++j) {
     u64 r0, r1;
-    if (small) {
+    if (tiny) {
+      // |c| < 2^27, at most 16 terms, words below 2^58: the low and high 32-bit
+      // halves of every word times |c| sum without overflow in 64 bits
+      u64 pl0 = 0, ph0 = 0, nl0 = 0, nh0 = 0, pl1 = 0, ph1 = 0, nl1 = 0, nh1 = 0;
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        if (t < nin) {
+          const i64 c = A.c[j][t];
+          if (c > 0) {
+            const uint32_t m = (uint32_t)c;
+            pl0 += (u64)(uint32_t)y[t].x * m;
+            ph0 += (u64)(uint32_t)(y[t].x >> 32) * m;
+            pl1 += (u64)(uint32_t)y[t].y * m;
+            ph1 += (u64)(uint32_t)(y[t].y >> 32) * m;
+          } else if (c < 0) {
+            const uint32_t m = (uint32_t)(-c);
+            nl0 += (u64)(uint32_t)y[t].x * m;
+            nh0 += (u64)(uint32_t)(y[t].x >> 32) * m;
+            nl1 += (u64)(uint32_t)y[t].y * m;
+            nh1 += (u64)(uint32_t)(y[t].y >> 32) * m;
+          }
+        }
+      }
+      r0 = sub_mod(reduce_split(ph0, pl0, md), reduce_split(nh0, nl0, md), q);
+      r1 = sub_mod(reduce_split(ph1, pl1, md), reduce_split(nh1, nl1, md), q);
+    } else if (small) {
       Acc128 p0, n0, p1, n1;
       p0.zero();
       n0.zero();
@@ -759,7 +791,7 @@ void k_lincomb_multi(Context& C, const std::vector<const Buf*>& ys, const std::v
   if (nin < 1 || nin > 16 || nout < 1 || nout > 16 || (int)cs.size() != nout)
     throw Error(SS_ERR_PARAM, "multi-output linear combination of 1..16 inputs and outputs");
   LinMultiArgs A;
-  bool small = true;
+  bool small = true, tiny = C.prm.bits <= 58;
   const u64 qmin = 1ULL << (C.prm.bits - 1);
   for (int j = 0; j < nout; ++j) {
     if ((int)cs[j].size() != nin) throw Error(SS_ERR_PARAM, "coefficient row length");
@@ -770,6 +802,7 @@ void k_lincomb_multi(Context& C, const std::vector<const Buf*>& ys, const std::v
       if (c == INT64_MIN || (u64)(c < 0 ? -c : c) >= qmin)
         throw Error(SS_ERR_PARAM, "linear-combination scalar too large for the primes");
       small = small && c > -(1LL << 32) && c < (1LL << 32);
+      tiny = tiny && c > -(1LL << 27) && c < (1LL << 27);
       A.c[j][t] = c;
     }
   }
@@ -780,7 +813,8 @@ void k_lincomb_multi(Context& C, const std::vector<const Buf*>& ys, const std::v
   const Buf& o0 = *outs[0];
   const int polys = o0.count * o0.ncomp * o0.level;
   TIMED(KC_ELEM, (double)(nin + nout) * polys * C.N * 8.0,
-        k_lincomb_multi_impl<<<grid_for(C.N / 2, polys), TPB, 0, st>>>(A, nin, nout, small ? 1 : 0, C.N, o0.ncomp,
+        k_lincomb_multi_impl<<<grid_for(C.N / 2, polys), TPB, 0, st>>>(A, nin, nout, small ? 1 : 0, tiny ? 1 : 0, C.N,
+                                                                        o0.ncomp,
                                                                     o0.level, C.d_mod));
   LAUNCHED();
 }
