@@ -502,8 +502,8 @@ struct LinArgs {
 
 // out = sum_t c_t y_t (+ cst on component 0), one word per thread. All term
 // words are loaded before any arithmetic so the loads overlap.
-__global__ void __launch_bounds__(256) k_lincomb_impl(LinArgs A, int nterms, i64 cst, int small, u64* out, int ocap,
-                                                      int N, int ncomp, int level, const ModDesc* mods) {
+__global__ void __launch_bounds__(256) k_lincomb_impl(LinArgs A, int nterms, i64 cst, int small, int tiny, u64* out,
+                                                      int ocap, int N, int ncomp, int level, const ModDesc* mods) {
   const int poly = blockIdx.y;  // (bt, comp, i)
   const int i = poly % level, comp = (poly / level) % ncomp, bt = poly / (level * ncomp);
   const int n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);  // two consecutive words per thread
@@ -516,7 +516,41 @@ __global__ void __launch_bounds__(256) k_lincomb_impl(LinArgs A, int nterms, i64
   for (int t = 0; t < 16; ++t)
     if (t < nterms) y[t] = ld2(A.ptr[t] + (row * A.cap[t] + i) * N + n);
   u64 r0, r1;
-  if (small) {
+  if (tiny) {
+    // |c| < 2^27 (constant included), at most 16 terms, words below 2^58: the
+    // 32-bit halves of every word times |c| sum in 64 bits without overflow;
+    // terms arrive sorted: the first `small` - 1 have c >= 0, the rest c < 0
+    const int npos = small - 1;
+    u64 pl0 = 0, ph0 = 0, nl0 = 0, nh0 = 0, pl1 = 0, ph1 = 0, nl1 = 0, nh1 = 0;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      if (t < nterms) {
+        const i64 c = A.c[t];
+        const uint32_t m = (uint32_t)(t < npos ? c : -c);
+        if (t < npos) {
+          pl0 += (u64)(uint32_t)y[t].x * m;
+          ph0 += (u64)(uint32_t)(y[t].x >> 32) * m;
+          pl1 += (u64)(uint32_t)y[t].y * m;
+          ph1 += (u64)(uint32_t)(y[t].y >> 32) * m;
+        } else {
+          nl0 += (u64)(uint32_t)y[t].x * m;
+          nh0 += (u64)(uint32_t)(y[t].x >> 32) * m;
+          nl1 += (u64)(uint32_t)y[t].y * m;
+          nh1 += (u64)(uint32_t)(y[t].y >> 32) * m;
+        }
+      }
+    }
+    if (comp == 0 && cst > 0) {
+      pl0 += (u64)cst;
+      pl1 += (u64)cst;
+    }
+    if (comp == 0 && cst < 0) {
+      nl0 += (u64)(-cst);
+      nl1 += (u64)(-cst);
+    }
+    r0 = sub_mod(reduce_split(ph0, pl0, md), reduce_split(nh0, nl0, md), q);
+    r1 = sub_mod(reduce_split(ph1, pl1, md), reduce_split(nh1, nl1, md), q);
+  } else if (small) {
     // |c| < 2^32: y * |c| is two 32x32 products; positive and negative terms
     // are summed apart (each sum < 2^92) and reduced once each.
     // terms arrive sorted: the first `small` - 1 have c >= 0, the rest c < 0
@@ -761,6 +795,8 @@ void k_lincomb(Context& C, const std::vector<const Buf*>& ys, const std::vector<
   LinArgs A;
   bool small = cst > -(1LL << 32) && cst < (1LL << 32);
   for (int t = 0; t < nt; ++t) small = small && cs[t] > -(1LL << 32) && cs[t] < (1LL << 32);
+  bool tiny = small && cst > -(1LL << 27) && cst < (1LL << 27);
+  for (int t = 0; t < nt; ++t) tiny = tiny && cs[t] > -(1LL << 27) && cs[t] < (1LL << 27);
   if (!small) {  // the general path lifts c as c or q - |c|: every |c| must lie below every prime
     const u64 qmin = 1ULL << (C.prm.bits - 1);
     for (int t = 0; t <= nt; ++t) {
@@ -780,7 +816,8 @@ void k_lincomb(Context& C, const std::vector<const Buf*>& ys, const std::vector<
   }
   int polys = out.count * out.ncomp * out.level;
   TIMED(KC_ELEM, (nt + 1.0) * polys * C.N * 8.0,
-        k_lincomb_impl<<<grid_for(C.N / 2, polys), TPB, 0, st>>>(A, nt, cst, small ? npos + 1 : 0, out.data, out.cap, C.N,
+        k_lincomb_impl<<<grid_for(C.N / 2, polys), TPB, 0, st>>>(A, nt, cst, small ? npos + 1 : 0, tiny ? 1 : 0, out.data,
+                                                                  out.cap, C.N,
                                                               out.ncomp, out.level, C.d_mod));
   LAUNCHED();
 }

@@ -144,12 +144,14 @@ def test_ops_parity(tiny):
     assert (g.decrypt_slots(gr) == (A * B) % g.t).all()
 
 
-@pytest.mark.parametrize("nterms,big", [(1, False), (3, False), (15, False), (20, False), (4, True)])
-def test_linear_combination_parity(tiny, nterms, big):
+@pytest.mark.parametrize("nterms,lim_bits", [(1, 0), (3, 0), (15, 0), (20, 0), (4, 34), (6, 31)])
+def test_linear_combination_parity(tiny, nterms, lim_bits):
     g, o = tiny
     rng = np.random.default_rng(30 + nterms)
     cts = [encrypt_both(g, o, rng.integers(0, g.t, (2, g.slots)), 2000 + 10 * i) for i in range(nterms)]
-    lim = (1 << 34) if big else g.t // 2  # |c| >= 2^32 takes the general 64-bit product path
+    # |c| < 2^27: 64-bit accumulators of 32-bit halves; below 2^32: two 32-bit
+    # products into 128-bit sums; larger: the general 64-bit product path
+    lim = (1 << lim_bits) if lim_bits else g.t // 2
     coeffs = [int(c) for c in rng.integers(-lim, lim, nterms)]
     cst = int(rng.integers(-100, 100))
     got = g.linear_combination([c[0] for c in cts], coeffs, cst)
