@@ -76,7 +76,10 @@ def lib():
             "orc_query": (vp, [vp, P(vp), P(vp), P(vp), P(vp), i32, i32]),
             "orc_trace": (i32, [vp, i32]),
             "orc_ntt_count": (C.c_ulonglong, [i32]),
+            "orc_set_threads": (i32, [i32]),
             "orc_trace_get": (i32, [vp, C.c_char_p, i32]),
+            "orc_meter": (i32, [vp, i32]),
+            "orc_meter_get": (i32, [vp, C.c_char_p, i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -101,6 +104,16 @@ def _ptr(a, ty=C.c_uint64):
 def _chk(rc):
     if rc != 0:
         raise _err()
+
+
+def set_threads(n=0):
+    """Worker threads of the reference's parallel limb loops (0: one per
+    hardware thread; results do not depend on it). Returns the count in use."""
+    return int(lib().orc_set_threads(int(n)))
+
+
+def threads():
+    return int(lib().orc_set_threads(-1))
 
 
 def ntt_count(reset=False):
@@ -355,6 +368,22 @@ class Oracle:
 
     def trace(self, on=True):
         lib().orc_trace(self.h, 1 if on else 0)
+
+    def meter(self, on=True):
+        """Records the noise budget of every stage result of the space-switching
+        procedures (Algorithms 3 and 4, raising, the query) while on."""
+        lib().orc_meter(self.h, 1 if on else 0)
+
+    def meter_readings(self):
+        """[(stage label, level, budget in bits)] recorded since meter(True)."""
+        n = lib().orc_meter_get(self.h, None, 0)
+        buf = C.create_string_buffer(n + 1)
+        lib().orc_meter_get(self.h, buf, n + 1)
+        out = []
+        for line in buf.value.decode().splitlines():
+            lab, lvl, bits = line.split()
+            out.append((lab, int(lvl[1:]), float(bits)))
+        return out
 
     def trace_text(self):
         n = lib().orc_trace_get(self.h, None, 0)

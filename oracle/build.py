@@ -19,7 +19,7 @@ def build(force: bool = False) -> str:
         if all(os.path.getmtime(d) <= t for d in deps):
             return TARGET
     tmp = TARGET + ".tmp%d" % os.getpid()
-    cmd = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp] + srcs
+    cmd = ["g++", "-O2", "-std=c++17", "-pthread", "-shared", "-fPIC", "-o", tmp] + srcs
     subprocess.run(cmd, check=True)
     os.replace(tmp, TARGET)
     return TARGET

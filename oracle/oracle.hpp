@@ -27,11 +27,14 @@
 //
 // Parity status: the decrypted results are pinned by plaintext definitions and
 // brute force; the exact ciphertext words have no definition outside this
-// code base and are fixed by the conventions written in the design doc (prime
-// choice, root choice, evaluation order of the transform, Philox counters,
-// key-switching decomposition, modulus-switching rule, evaluation schedule).
+// code base and are fixed by conventions that this file and the library each
+// implement on their own (prime choice, root choice, evaluation order of the
+// transform, Philox counters, key-switching decomposition, modulus-switching
+// rule, evaluation schedule).
 #pragma once
+#include <atomic>
 #include <cstdint>
+#include <functional>
 #include <map>
 #include <stdexcept>
 #include <string>
@@ -53,6 +56,16 @@ u64 invmod(u64 a, u64 m);          // extended Euclid; any modulus coprime to a
 u64 lift(i64 c, u64 m);            // integer -> [0, m)
 bool is_prime(u64 n);              // deterministic Miller-Rabin for 64-bit n
 int bitrev(int x, int logn);
+
+// ----------------------------------------------------------------- threads
+// parallel_for(n, f) runs f(0), ..., f(n-1) on the oracle's worker threads
+// (std::thread, dynamic hand-out of indices). Every loop split this way writes
+// disjoint data per index and does the same exact modular arithmetic as the
+// serial loop, so results do not depend on the thread count. A call from
+// inside a worker, or with one thread configured, runs serially.
+void set_threads(int n);  // 0: one per hardware thread
+int threads();
+void parallel_for(int n, const std::function<void(int)>& f);
 
 // --------------------------------------------------------------- big integer
 // Non-negative multi-precision integer, little-endian 64-bit limbs.
@@ -127,7 +140,7 @@ Context make_context(const Params& P);
 void ntt_fwd(const Context& C, int prime_idx, Poly& a);  // coefficients -> evaluation form
 void ntt_inv(const Context& C, int prime_idx, Poly& a);  // evaluation form -> coefficients
 Poly automorph_coeff(const Poly& a, int g, u64 q);        // a(X) -> a(X^g) mod X^N+1
-extern unsigned long long g_ntt_count;                    // limb transforms run so far
+extern std::atomic<unsigned long long> g_ntt_count;      // limb transforms run so far
 
 // -------------------------------------------------------------------- slots
 std::vector<u64> encode(const Context& C, int t_exp, const std::vector<u64>& slots);
@@ -166,7 +179,15 @@ std::vector<i64> flt_table(int p);         // F_LT monomial coefficients, centre
 i64 centre(u64 v, u64 m);
 
 // -------------------------------------------------------- space switching
-struct Trace { std::vector<std::string> ops; bool on = false; };
+// ops: the evaluation schedule, one line per step (when on). noise: when
+// meter is set, the noise budget (noise_budget) of the result of every stage of
+// the space-switching procedures, one "label L<level> <bits>" line per stage.
+struct Trace {
+  std::vector<std::string> ops;
+  bool on = false;
+  bool meter = false;
+  std::vector<std::string> noise;
+};
 Ct eval_g(const Context& C, const Ct& x, int e, Trace* tr);  // G_{p,e}(x)
 std::vector<Ct> reduce_to_digits(const Context& C, const Ct& a, Trace* tr);
 Ct compare_lt(const Context& C, const Ct& a, const Ct& b, Trace* tr);

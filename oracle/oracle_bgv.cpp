@@ -4,6 +4,10 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <exception>
+#include <mutex>
+#include <thread>
 
 namespace orc {
 
@@ -67,6 +71,55 @@ bool is_prime(u64 n) {
     if (comp) return false;
   }
   return true;
+}
+
+// =================================================================== threads
+static int g_threads = 0;  // 0: not set yet (ORC_THREADS or hardware concurrency)
+static thread_local bool t_in_worker = false;
+
+void set_threads(int n) { g_threads = n > 0 ? n : (int)std::max(1u, std::thread::hardware_concurrency()); }
+
+int threads() {
+  if (g_threads <= 0) {
+    const char* e = std::getenv("ORC_THREADS");
+    set_threads(e ? std::atoi(e) : 0);
+  }
+  return g_threads;
+}
+
+void parallel_for(int n, const std::function<void(int)>& f) {
+  int nt = std::min(threads(), n);
+  if (nt <= 1 || t_in_worker) {
+    for (int i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<int> next{0};
+  std::exception_ptr err;
+  std::mutex mu;
+  auto work = [&] {
+    t_in_worker = true;
+    for (int i = next++; i < n; i = next++) {
+      try {
+        f(i);
+      } catch (...) {
+        std::lock_guard<std::mutex> g(mu);
+        if (!err) err = std::current_exception();
+      }
+    }
+    t_in_worker = false;
+  };
+  std::vector<std::thread> pool;
+  for (int k = 1; k < nt; ++k) pool.emplace_back(work);
+  work();
+  for (auto& th : pool) th.join();
+  if (err) std::rethrow_exception(err);
+}
+
+// Splits a loop over limbs (or components) across the workers for rings large
+// enough to pay for the threads; small rings run the plain loop.
+static void limb_for(const Context& C, int n, const std::function<void(int)>& f) {
+  if (C.P.N >= 2048) parallel_for(n, f);
+  else for (int i = 0; i < n; ++i) f(i);
 }
 
 int bitrev(int x, int logn) {
@@ -312,7 +365,7 @@ static void cyclic_ntt(std::vector<u64>& A, u64 omega, u64 q, int logN) {
   A = B;
 }
 
-unsigned long long g_ntt_count = 0;
+std::atomic<unsigned long long> g_ntt_count{0};
 
 void ntt_fwd(const Context& C, int pi, Poly& a) {
   ++g_ntt_count;
@@ -425,7 +478,7 @@ KSKey make_ksk(const Context& C, const std::vector<Poly>& sp_hat, u32 key_id) {
     for (int n = 0; n < P.N; ++n) e[n] = sample_cbd(C, (u32)n, id, TAG_KSK_E);
     K.b[j].resize(nl);
     K.a[j].resize(nl);
-    for (int i = 0; i < nl; ++i) {
+    limb_for(C, nl, [&](int i) {
       u64 q = C.primes[i];
       Poly a(P.N);
       for (int n = 0; n < P.N; ++n) a[n] = sample_uniform(C, (u32)n, (u32)i, id, TAG_KSK_A, q);
@@ -442,7 +495,7 @@ KSKey make_ksk(const Context& C, const std::vector<Poly>& sp_hat, u32 key_id) {
       }
       K.b[j][i] = b;
       K.a[j][i] = a;
-    }
+    });
   }
   return K;
 }
@@ -451,10 +504,10 @@ void secret_keygen(Context& C) {
   int nl = C.P.L + C.P.alpha;
   C.sk = sample_secret(C);
   C.sk_hat.resize(nl);
-  for (int i = 0; i < nl; ++i) {
+  limb_for(C, nl, [&](int i) {
     C.sk_hat[i] = to_limb(C, C.sk, i);
     ntt_fwd(C, i, C.sk_hat[i]);
-  }
+  });
   C.have_keys = true;
 }
 
@@ -464,18 +517,18 @@ void keygen(Context& C, const std::vector<int>& galois) {
   secret_keygen(C);
   // relinearisation key: s' = s^2
   std::vector<Poly> s2(nl);
-  for (int i = 0; i < nl; ++i) {
+  limb_for(C, nl, [&](int i) {
     s2[i].resize(P.N);
     for (int n = 0; n < P.N; ++n) s2[i][n] = mulmod(C.sk_hat[i][n], C.sk_hat[i][n], C.primes[i]);
-  }
+  });
   C.rlk = make_ksk(C, s2, 0);
   C.gk.clear();
   for (int g : galois) {
     std::vector<Poly> sg(nl);
-    for (int i = 0; i < nl; ++i) {
+    limb_for(C, nl, [&](int i) {
       sg[i] = automorph_coeff(to_limb(C, C.sk, i), g, C.primes[i]);
       ntt_fwd(C, i, sg[i]);
-    }
+    });
     C.gk[g] = make_ksk(C, sg, (u32)g);
   }
   C.have_keys = true;
@@ -493,7 +546,7 @@ Ct encrypt(const Context& C, const std::vector<u64>& m, u32 nonce, int t_exp) {
   ct.c.assign(2, std::vector<Poly>(P.L));
   std::vector<i64> e(P.N);
   for (int n = 0; n < P.N; ++n) e[n] = sample_cbd(C, (u32)n, nonce, TAG_ENC_E);
-  for (int i = 0; i < P.L; ++i) {
+  limb_for(C, P.L, [&](int i) {
     u64 q = C.primes[i];
     Poly a(P.N), me(P.N);
     for (int n = 0; n < P.N; ++n) a[n] = sample_uniform(C, (u32)n, (u32)i, nonce, TAG_ENC_A, q);
@@ -504,7 +557,7 @@ Ct encrypt(const Context& C, const std::vector<u64>& m, u32 nonce, int t_exp) {
     for (int n = 0; n < P.N; ++n) c0[n] = submod(me[n], mulmod(a[n], C.sk_hat[i][n], q), q);
     ct.c[0][i] = c0;
     ct.c[1][i] = a;
-  }
+  });
   return ct;
 }
 
@@ -513,7 +566,7 @@ static std::vector<std::pair<bool, Big>> decrypt_raw(const Context& C, const Ct&
   const Params& P = C.P;
   int l = ct.level;
   std::vector<Poly> v(l);
-  for (int i = 0; i < l; ++i) {
+  limb_for(C, l, [&](int i) {
     u64 q = C.primes[i];
     Poly x(P.N);
     for (int n = 0; n < P.N; ++n) {
@@ -525,7 +578,7 @@ static std::vector<std::pair<bool, Big>> decrypt_raw(const Context& C, const Ct&
     }
     ntt_inv(C, i, x);
     v[i] = x;
-  }
+  });
   // CRT: V = sum_i [v_i * (Q/q_i)^{-1}]_{q_i} * (Q/q_i) mod Q
   Big Q = Big::from(1);
   for (int i = 0; i < l; ++i) Q = big_mul_u64(Q, C.primes[i]);
@@ -539,16 +592,20 @@ static std::vector<std::pair<bool, Big>> decrypt_raw(const Context& C, const Ct&
   }
   Big half = big_shr1(Q);
   std::vector<std::pair<bool, Big>> out(P.N);
-  for (int n = 0; n < P.N; ++n) {
-    Big V;
-    for (int i = 0; i < l; ++i) {
-      u64 y = mulmod(v[i][n], Qhat_inv[i], C.primes[i]);
-      V = big_add(V, big_mul_u64(Qhat[i], y));
+  // coefficients in blocks of 256 per worker task
+  const int chunk = 256;
+  limb_for(C, (P.N + chunk - 1) / chunk, [&](int blk) {
+    for (int n = blk * chunk; n < std::min(P.N, (blk + 1) * chunk); ++n) {
+      Big V;
+      for (int i = 0; i < l; ++i) {
+        u64 y = mulmod(v[i][n], Qhat_inv[i], C.primes[i]);
+        V = big_add(V, big_mul_u64(Qhat[i], y));
+      }
+      while (big_cmp(V, Q) >= 0) V = big_sub(V, Q);
+      if (big_cmp(V, half) > 0) out[n] = {true, big_sub(Q, V)};  // negative: -(Q - V)
+      else out[n] = {false, V};
     }
-    while (big_cmp(V, Q) >= 0) V = big_sub(V, Q);
-    if (big_cmp(V, half) > 0) out[n] = {true, big_sub(Q, V)};  // negative: -(Q - V)
-    else out[n] = {false, V};
-  }
+  });
   return out;
 }
 
@@ -585,9 +642,10 @@ Ct add(const Context& C, const Ct& a, const Ct& b) {
   Ct r = a.ncomp >= b.ncomp ? a : b;
   const Ct& o = a.ncomp >= b.ncomp ? b : a;
   for (int c = 0; c < o.ncomp; ++c)
-    for (int i = 0; i < a.level; ++i)
+    limb_for(C, a.level, [&](int i) {
       for (int n = 0; n < C.P.N; ++n)
         r.c[c][i][n] = addmod(r.c[c][i][n], o.c[c][i][n], C.primes[i]);
+    });
   return r;
 }
 
@@ -598,20 +656,20 @@ Ct sub(const Context& C, const Ct& a, const Ct& b) {
 Ct mul_scalar(const Context& C, const Ct& a, i64 s) {
   Ct r = a;
   for (int c = 0; c < a.ncomp; ++c)
-    for (int i = 0; i < a.level; ++i) {
+    limb_for(C, a.level, [&](int i) {
       u64 q = C.primes[i], k = lift(s, q);
       for (int n = 0; n < C.P.N; ++n) r.c[c][i][n] = mulmod(a.c[c][i][n], k, q);
-    }
+    });
   return r;
 }
 
 Ct add_scalar(const Context& C, const Ct& a, i64 s) {
   // the constant polynomial s evaluates to s at every point
   Ct r = a;
-  for (int i = 0; i < a.level; ++i) {
+  limb_for(C, a.level, [&](int i) {
     u64 q = C.primes[i], k = lift(s, q);
     for (int n = 0; n < C.P.N; ++n) r.c[0][i][n] = addmod(r.c[0][i][n], k, q);
-  }
+  });
   return r;
 }
 
@@ -621,7 +679,7 @@ Ct tensor(const Context& C, const Ct& a, const Ct& b) {
   Ct r;
   r.ncomp = 3; r.level = a.level; r.t_exp = a.t_exp;
   r.c.assign(3, std::vector<Poly>(a.level, Poly(C.P.N)));
-  for (int i = 0; i < a.level; ++i) {
+  limb_for(C, a.level, [&](int i) {
     u64 q = C.primes[i];
     for (int n = 0; n < C.P.N; ++n) {
       u64 a0 = a.c[0][i][n], a1 = a.c[1][i][n], b0 = b.c[0][i][n], b1 = b.c[1][i][n];
@@ -629,7 +687,7 @@ Ct tensor(const Context& C, const Ct& a, const Ct& b) {
       r.c[1][i][n] = addmod(mulmod(a0, b1, q), mulmod(a1, b0, q), q);
       r.c[2][i][n] = mulmod(a1, b1, q);
     }
-  }
+  });
   return r;
 }
 
@@ -642,16 +700,16 @@ static std::vector<Poly> scaled_base_conv(const Context& C, const std::vector<Po
                                           u64 t) {
   int N = C.P.N, k = (int)src.size();
   std::vector<Poly> y(k, Poly(N));
-  for (int a = 0; a < k; ++a) {
+  limb_for(C, k, [&](int a) {
     u64 qa = C.primes[src[a]];
     u64 hat = 1;  // Q_src / q_a mod q_a
     for (int b = 0; b < k; ++b) if (b != a) hat = mulmod(hat, C.primes[src[b]] % qa, qa);
     u64 hat_inv = invmod(hat, qa);
     u64 t_inv = invmod(t % qa, qa);
     for (int n = 0; n < N; ++n) y[a][n] = mulmod(mulmod(x[a][n], t_inv, qa), hat_inv, qa);
-  }
+  });
   std::vector<Poly> out(dst.size(), Poly(N));
-  for (size_t m = 0; m < dst.size(); ++m) {
+  limb_for(C, (int)dst.size(), [&](int m) {
     u64 qm = C.primes[dst[m]];
     std::vector<u64> hat_m(k);
     for (int a = 0; a < k; ++a) {
@@ -664,7 +722,7 @@ static std::vector<Poly> scaled_base_conv(const Context& C, const std::vector<Po
       for (int a = 0; a < k; ++a) acc = addmod(acc, mulmod(y[a][n] % qm, hat_m[a], qm), qm);
       out[m][n] = mulmod(acc, t % qm, qm);
     }
-  }
+  });
   return out;
 }
 
@@ -675,7 +733,7 @@ static void keyswitch_acc(const Context& C, const std::vector<Poly>& d, int l, c
   const Params& P = C.P;
   int N = P.N, alpha = P.alpha;
   std::vector<Poly> dc = d;
-  for (int i = 0; i < l; ++i) ntt_inv(C, i, dc[i]);
+  limb_for(C, l, [&](int i) { ntt_inv(C, i, dc[i]); });
   // target primes: the current data primes, then the special primes
   std::vector<int> tgt;
   for (int i = 0; i < l; ++i) tgt.push_back(i);
@@ -683,9 +741,10 @@ static void keyswitch_acc(const Context& C, const std::vector<Poly>& d, int l, c
   acc0.assign(tgt.size(), Poly(N, 0));
   acc1.assign(tgt.size(), Poly(N, 0));
   int dnum = (l + alpha - 1) / alpha;
-  for (int j = 0; j < dnum; ++j) {
-    int lo = j * alpha, hi = std::min((j + 1) * alpha, l);
-    for (size_t m = 0; m < tgt.size(); ++m) {
+  // one worker task per target prime m; it runs over the digits j in order
+  limb_for(C, (int)tgt.size(), [&](int m) {
+    for (int j = 0; j < dnum; ++j) {
+      int lo = j * alpha, hi = std::min((j + 1) * alpha, l);
       int gm = tgt[m];
       u64 qm = C.primes[gm];
       Poly ext(N);
@@ -720,7 +779,7 @@ static void keyswitch_acc(const Context& C, const std::vector<Poly>& d, int l, c
         acc1[m][n] = addmod(acc1[m][n], mulmod(ext[n], K.a[j][gm][n], qm), qm);
       }
     }
-  }
+  });
 }
 
 void keyswitch(const Context& C, const std::vector<Poly>& d, int l, const KSKey& K, int t_exp,
@@ -736,17 +795,17 @@ void keyswitch(const Context& C, const std::vector<Poly>& d, int l, const KSKey&
   for (int i = 0; i < l; ++i) dp.push_back(i);
   auto moddown = [&](std::vector<Poly>& acc, std::vector<Poly>& out) {
     std::vector<Poly> xs(alpha);
-    for (int k = 0; k < alpha; ++k) { xs[k] = acc[l + k]; ntt_inv(C, P.L + k, xs[k]); }
+    limb_for(C, alpha, [&](int k) { xs[k] = acc[l + k]; ntt_inv(C, P.L + k, xs[k]); });
     std::vector<Poly> delta = scaled_base_conv(C, xs, sp, dp, t);
     out.assign(l, Poly(N));
-    for (int i = 0; i < l; ++i) {
+    limb_for(C, l, [&](int i) {
       u64 q = C.primes[i];
       ntt_fwd(C, i, delta[i]);
       u64 Pm = 1;
       for (int k = 0; k < alpha; ++k) Pm = mulmod(Pm, C.primes[P.L + k] % q, q);
       u64 Pinv = invmod(Pm, q);
       for (int n = 0; n < N; ++n) out[i][n] = mulmod(submod(acc[i][n], delta[i][n], q), Pinv, q);
-    }
+    });
   };
   moddown(acc0, k0);
   moddown(acc1, k1);
@@ -759,13 +818,13 @@ Ct relin(const Context& C, const Ct& a) {
   Ct r;
   r.ncomp = 2; r.level = a.level; r.t_exp = a.t_exp;
   r.c.assign(2, std::vector<Poly>(a.level, Poly(C.P.N)));
-  for (int i = 0; i < a.level; ++i) {
+  limb_for(C, a.level, [&](int i) {
     u64 q = C.primes[i];
     for (int n = 0; n < C.P.N; ++n) {
       r.c[0][i][n] = addmod(a.c[0][i][n], k0[i][n], q);
       r.c[1][i][n] = addmod(a.c[1][i][n], k1[i][n], q);
     }
-  }
+  });
   return r;
 }
 
@@ -782,9 +841,9 @@ Ct modswitch(const Context& C, const Ct& a, int drop) {
   r.c.assign(a.ncomp, std::vector<Poly>(nl, Poly(C.P.N)));
   for (int c = 0; c < a.ncomp; ++c) {
     std::vector<Poly> xs(drop);
-    for (int k = 0; k < drop; ++k) { xs[k] = a.c[c][nl + k]; ntt_inv(C, nl + k, xs[k]); }
+    limb_for(C, drop, [&](int k) { xs[k] = a.c[c][nl + k]; ntt_inv(C, nl + k, xs[k]); });
     std::vector<Poly> delta = scaled_base_conv(C, xs, src, dst, t);
-    for (int i = 0; i < nl; ++i) {
+    limb_for(C, nl, [&](int i) {
       u64 q = C.primes[i];
       ntt_fwd(C, i, delta[i]);
       u64 Qd = 1;
@@ -792,7 +851,7 @@ Ct modswitch(const Context& C, const Ct& a, int drop) {
       u64 inv = invmod(Qd, q);
       for (int n = 0; n < C.P.N; ++n)
         r.c[c][i][n] = mulmod(submod(a.c[c][i][n], delta[i][n], q), inv, q);
-    }
+    });
   }
   return r;
 }
@@ -807,24 +866,24 @@ Ct rotate(const Context& C, const Ct& a, int g) {
   auto it = C.gk.find(g);
   if (it == C.gk.end()) throw std::runtime_error("rotate: no Galois key");
   Ct s = a;
-  for (int c = 0; c < 2; ++c)
-    for (int i = 0; i < a.level; ++i) {
-      Poly x = a.c[c][i];
-      ntt_inv(C, i, x);
-      x = automorph_coeff(x, g, C.primes[i]);
-      ntt_fwd(C, i, x);
-      s.c[c][i] = x;
-    }
+  limb_for(C, 2 * a.level, [&](int ci) {
+    int c = ci / a.level, i = ci % a.level;
+    Poly x = a.c[c][i];
+    ntt_inv(C, i, x);
+    x = automorph_coeff(x, g, C.primes[i]);
+    ntt_fwd(C, i, x);
+    s.c[c][i] = x;
+  });
   std::vector<Poly> k0, k1;
   keyswitch(C, s.c[1], a.level, it->second, a.t_exp, k0, k1);
   Ct r = s;
-  for (int i = 0; i < a.level; ++i) {
+  limb_for(C, a.level, [&](int i) {
     u64 q = C.primes[i];
     for (int n = 0; n < C.P.N; ++n) {
       r.c[0][i][n] = addmod(s.c[0][i][n], k0[i][n], q);
       r.c[1][i][n] = k1[i][n];
     }
-  }
+  });
   return r;
 }
 
@@ -832,10 +891,10 @@ Ct divide_by_p(const Context& C, const Ct& a) {
   if (a.t_exp < 2) throw std::runtime_error("divide_by_p: plaintext modulus already p");
   Ct r = a;
   for (int c = 0; c < a.ncomp; ++c)
-    for (int i = 0; i < a.level; ++i) {
+    limb_for(C, a.level, [&](int i) {
       u64 q = C.primes[i], pinv = invmod((u64)C.P.p % q, q);
       for (int n = 0; n < C.P.N; ++n) r.c[c][i][n] = mulmod(a.c[c][i][n], pinv, q);
-    }
+    });
   r.t_exp = a.t_exp - 1;
   return r;
 }
@@ -862,26 +921,28 @@ Ct relin_drop(const Context& C, const Ct& a) {
   for (int c = 0; c < 2; ++c) {
     // c_j on every data prime (index = prime) and special prime (index l + k)
     std::vector<Poly> ext(l + alpha);
-    for (int i = 0; i < l; ++i) {
+    limb_for(C, l, [&](int i) {
       u64 q = C.primes[i], Pm = 1;
       for (int k = 0; k < alpha; ++k) Pm = mulmod(Pm, C.primes[P.L + k] % q, q);
       ext[i].resize(N);
       for (int n = 0; n < N; ++n) ext[i][n] = addmod(mulmod(Pm, a.c[c][i][n], q), acc[c][i][n], q);
-    }
+    });
     for (int k = 0; k < alpha; ++k) ext[l + k] = acc[c][l + k];
-    std::vector<Poly> xs;
-    xs.push_back(ext[l - 1]);
-    ntt_inv(C, l - 1, xs.back());
-    for (int k = 0; k < alpha; ++k) { xs.push_back(ext[l + k]); ntt_inv(C, P.L + k, xs.back()); }
+    // D = {q_{l-1}} and the special primes, in that order, in coefficient form
+    std::vector<Poly> xs(alpha + 1);
+    limb_for(C, alpha + 1, [&](int k) {
+      xs[k] = ext[l - 1 + k];
+      ntt_inv(C, k == 0 ? l - 1 : P.L + k - 1, xs[k]);
+    });
     std::vector<Poly> delta = scaled_base_conv(C, xs, src, dst, t);
-    for (int i = 0; i < l - 1; ++i) {
+    limb_for(C, l - 1, [&](int i) {
       u64 q = C.primes[i];
       ntt_fwd(C, i, delta[i]);
       u64 Dm = C.primes[l - 1] % q;
       for (int k = 0; k < alpha; ++k) Dm = mulmod(Dm, C.primes[P.L + k] % q, q);
       u64 inv = invmod(Dm, q);
       for (int n = 0; n < N; ++n) r.c[c][i][n] = mulmod(submod(ext[i][n], delta[i][n], q), inv, q);
-    }
+    });
   }
   return r;
 }

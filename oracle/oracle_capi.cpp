@@ -277,6 +277,13 @@ void* orc_query(void* h, void** A, void** B, void** C1, void** C2, int n, int n2
   });
 }
 
+// Worker threads of the reference's parallel loops (0: one per hardware
+// thread); returns the count in use.
+int orc_set_threads(int n) {
+  if (n >= 0) set_threads(n);
+  return threads();
+}
+
 unsigned long long orc_ntt_count(int reset) {
   unsigned long long v = g_ntt_count;
   if (reset) g_ntt_count = 0;
@@ -288,6 +295,25 @@ int orc_trace(void* h, int on) {
   t->on = on != 0;
   t->ops.clear();
   return 0;
+}
+
+int orc_meter(void* h, int on) {
+  Trace* t = trace(h);
+  t->meter = on != 0;
+  t->noise.clear();
+  return 0;
+}
+
+// Copies the noise-meter lines (one per stage) into buf; returns the full length.
+int orc_meter_get(void* h, char* buf, int len) {
+  std::string s;
+  for (auto& o : trace(h)->noise) { s += o; s += '\n'; }
+  if (buf && len > 0) {
+    int n = (int)std::min<size_t>(s.size(), (size_t)len - 1);
+    std::memcpy(buf, s.data(), n);
+    buf[n] = 0;
+  }
+  return (int)s.size();
 }
 
 // Copies the trace (one op per line) into buf; returns the full length.

@@ -93,6 +93,15 @@ static void note(Trace* tr, const std::string& s) {
   if (tr && tr->on) tr->ops.push_back(s);
 }
 
+// Noise meter (Section 2.1: decryption is correct while |v| < Q/2): records the
+// budget of a stage's result when the trace's meter is set.
+static void meter(const Context& C, Trace* tr, const std::string& label, const Ct& ct) {
+  if (!tr || !tr->meter) return;
+  char buf[160];
+  std::snprintf(buf, sizeof(buf), "%s L%d %.3f", label.c_str(), ct.level, noise_budget(C, ct));
+  tr->noise.push_back(buf);
+}
+
 static Ct align_to(const Context& C, const Ct& a, int level) { return modswitch_to(C, a, level); }
 
 static Ct add_aligned(const Context& C, const Ct& a, const Ct& b) {
@@ -206,6 +215,7 @@ Ct eval_g(const Context& C, const Ct& x, int e, Trace* tr) {
   Term H = bsgs(C, h, P, tr);
   Ct out = mul_term(C, x, H);
   note(tr, "G done -> L" + std::to_string(out.level));
+  meter(C, tr, "G_e" + std::to_string(e), out);
   return out;
 }
 
@@ -221,6 +231,7 @@ std::vector<Ct> reduce_to_digits(const Context& C, const Ct& a, Trace* tr) {
     Ct diff = sub(C, align_to(C, b, ai.level), ai);
     b = divide_by_p(C, diff);
     note(tr, "digit " + std::to_string(i) + " L" + std::to_string(ai.level));
+    meter(C, tr, "reduce_b" + std::to_string(i + 1), b);
     digits.push_back(ai);
   }
   digits.push_back(b);
@@ -243,6 +254,8 @@ static void compare_digit(const Context& C, const Ct& x, Ct& lt, Ct& eq, Trace* 
   lt = add_aligned(C, mul_term(C, x, H), mul_scalar(C, T, f[p - 1]));
   eq = add_scalar(C, mul_scalar(C, T, -1), 1);
   note(tr, "cmp digit -> LT L" + std::to_string(lt.level) + " EQ L" + std::to_string(eq.level));
+  meter(C, tr, "cmp_lt_digit", lt);
+  meter(C, tr, "cmp_eq_digit", eq);
 }
 
 // Algorithm 4: d = a - b, digits = Reduce(d), per-digit LT_i/EQ_i, then fold
@@ -260,6 +273,7 @@ Ct compare_lt(const Context& C, const Ct& a, const Ct& b, Trace* tr) {
     if (i > 0) eq = mul(C, eq, EQ[i]);
   }
   note(tr, "LT -> L" + std::to_string(lt.level));
+  meter(C, tr, "fold_lt", lt);
   return lt;
 }
 
@@ -311,6 +325,7 @@ Ct raise_modulus(const Context& C, const Ct& lt, Trace* tr) {
   k.t_exp = C.P.r;
   Ct out = eval_g(C, k, C.P.r, tr);
   note(tr, "raise -> L" + std::to_string(out.level));
+  meter(C, tr, "raise", out);
   return out;
 }
 
@@ -358,9 +373,12 @@ Ct query_sum_where(const Context& C, const std::vector<Ct>& A, const std::vector
     ind = raise_modulus(C, ind, tr);
     Ct prod = mul(C, A[i], B[i]);
     Ct R = mul(C, ind, prod);
+    meter(C, tr, "masked_product", R);
     total = (i == 0) ? R : add_aligned(C, total, R);
   }
-  return rotate_sum(C, total, tr);
+  Ct out = rotate_sum(C, total, tr);
+  meter(C, tr, "sum", out);
+  return out;
 }
 
 // SUM over rows of A*B where C1 < C2 (Algorithm 4 semantics).

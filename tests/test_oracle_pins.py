@@ -51,7 +51,7 @@ def test_philox_known_answers():
         f = os.path.join(d, "k.cpp")
         open(f, "w").write(src)
         exe = os.path.join(d, "k")
-        subprocess.run(["g++", "-O1", "-std=c++17", "-I", here, f, os.path.join(here, "oracle_bgv.cpp"), "-o", exe],
+        subprocess.run(["g++", "-O1", "-std=c++17", "-pthread", "-I", here, f, os.path.join(here, "oracle_bgv.cpp"), "-o", exe],
                        check=True)
         for row in rows:
             out = subprocess.run([exe] + row[:6], capture_output=True, text=True, check=True).stdout.split()
@@ -228,6 +228,81 @@ def test_encrypt_is_bgv_relation():
     assert es[0] == es[1] == es[2]
     e = np.array(es[0])
     assert np.abs(e).max() <= 21 and np.abs(e).max() > 0 and 3 < e.var() < 25
+
+
+def _exact_noise_budget(o, ct):
+    """log2(Q_l / 2) - log2 max_n |v_n| with v = c0 + c1 s (+ c2 s^2) lifted to
+    the centred residue modulo Q_l: Python integers throughout, products by the
+    schoolbook negacyclic rule, CRT by the textbook formula."""
+    s = [int(x) for x in o.secret()]
+    w = ct.words()
+    q = [int(x) for x in o.primes()[: ct.level]]
+    Q = math.prod(q)
+    res = []
+    for i, qi in enumerate(q):
+        si = [x % qi for x in s]
+        comps = [[int(x) for x in o.ntt_inv(i, w[c, i])] for c in range(ct.ncomp)]
+        v = comps[0]
+        v = [(x + y) % qi for x, y in zip(v, negacyclic(comps[1], si, qi))]
+        if ct.ncomp == 3:
+            s2 = negacyclic(si, si, qi)
+            v = [(x + y) % qi for x, y in zip(v, negacyclic(comps[2], s2, qi))]
+        res.append(v)
+    mx = 0
+    for n in range(o.N):
+        V = sum(res[i][n] * (Q // qi) * pow(Q // qi, -1, qi) for i, qi in enumerate(q)) % Q
+        if V > Q // 2:
+            V -= Q
+        mx = max(mx, abs(V))
+    return math.log2(Q) - 1 - math.log2(mx), mx
+
+
+def test_noise_budget_exact():
+    """The noise meter (log2(Q/2) - log2 |v|_inf, v the centred c0 + c1 s (+ c2 s^2)
+    mod Q_l, Section 2.1) against its value computed exactly: a fresh encryption,
+    whose v is m + t e with |e| <= 21 (Algorithm 1), a tensor product (three
+    components) and a relinearised, modulus-switched product."""
+    o = tiny(logN=5, L=6, alpha=2)
+    o.keygen([])
+    rng = np.random.default_rng(12)
+    m = o.encode(rng.integers(0, o.t, o.slots, dtype=np.uint64))
+    a = o.encrypt(m, nonce=7)
+    b = o.encrypt_slots(rng.integers(0, o.t, o.slots, dtype=np.uint64), 8)
+    want, mx = _exact_noise_budget(o, a)
+    assert mx <= max(int(x) for x in m) + 21 * o.t
+    assert abs(o.noise_budget(a) - want) < 1e-6
+    for ct in (o.tensor(a, b), o.mul(a, b), o.modswitch(a, 2)):
+        want, _ = _exact_noise_budget(o, ct)
+        assert abs(o.noise_budget(ct) - want) < 1e-6, (ct.ncomp, ct.level)
+
+
+def test_noise_meter_certifies_the_17sq_chain():
+    """The N = 2^13, 17^2 parameter set (36-bit primes, 18 data primes): the
+    noise budget of every stage result of the query (Algorithms 3 and 4,
+    raising, the masked product, the SUM) stays positive down to the last prime,
+    so the chain the query consumes (17 levels) is long enough for its noise,
+    not only for its depth. The meter's readings are the noise_budget values
+    pinned exactly above."""
+    import sys
+    sys.path.insert(0, GOLD)
+    import fullsize_cases as FC
+    prm = FC.PRESETS[0]
+    o = O.Oracle(**prm)
+    o.keygen(o.rotate_sum_elements())
+    case = dict(FC.CASES["query_n8192_17sq"], n_ct=1)
+    cols = FC.query_inputs(case, o.slots, o.t)
+    enc = {k: [o.encrypt(o.encode(r), FC.NONCE[k] + i) for i, r in enumerate(v)] for k, v in cols.items()}
+    o.meter(True)
+    res = o.query(enc["a"], enc["b"], enc["c1"], enc["c2"])
+    readings = o.meter_readings()
+    o.meter(False)
+    labels = [r[0] for r in readings]
+    assert labels[0] == "G_e2" and labels[-1] == "sum" and "raise" in labels and "fold_lt" in labels
+    assert all(bits > 0 for _, _, bits in readings), readings
+    assert readings[-1][1] == res.level == 1
+    assert abs(readings[-1][2] - o.noise_budget(res)) < 1e-3
+    exp = plain.query(cols["a"], cols["b"], cols["c1"], cols["c2"], o.t)
+    assert (o.decrypt_slots(res) == exp).all()
 
 
 def test_ksk_relation():
