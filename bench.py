@@ -32,8 +32,9 @@ IMAD_PEAK = 152 * 64 * 2.07e9
 # 32-bit multiplies in one 64-bit Shoup butterfly product (schoolbook minimum):
 # high 64 bits of a*w' (4) + low 64 bits of a*w (3) + low 64 bits of qhat*q (3).
 IMAD_PER_BUTTERFLY = 10
-# DRAM bytes per limb transform (forward and inverse, both phases each) from the
-# ncu capture in profiles/ntt_n65536_l41.md, over the 1 MB (16 N) it must move.
+# DRAM bytes per limb transform (forward and inverse, both phases each) from one
+# ncu capture of the transform kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum per limb), over the 1 MB (16 N) it must move.
 NTT_TRAFFIC_PER_ALGO_BYTE = 1.869
 
 
@@ -118,27 +119,90 @@ def plain_query(A, B, C1, C2, t):
 
 
 # ------------------------------------------------------------------ CPU reference sample
-def cpu_sample(rows, query_ntts_per_ct, n_ct, level=20):
-    """Times the plain CPU reference on one ciphertext multiply (tensor,
-    relinearisation, modulus switch) at `level` of the N = 2^16, 257^3 chain and
-    scales it to a full query by the query's count of limb transforms (the
-    reference's own count, taken on a small ring where it is the same)."""
+def cpu_reference_sample(seconds, one_thread=False):
+    """The plain CPU reference timed on this host's cores on the benchmark's
+    workload: the parameter set, seeds and nonces of the GPU run, the first
+    ciphertext of columns c1 and c2, d = c1 - c2, then multiplications at the
+    top of the chain (the query's leading operations: the powers of the first
+    G_{p,3} evaluation), repeated until `seconds` have passed. The query's rows
+    per second follow from the reference's own count of limb transforms: the
+    sample's transforms over the transforms the whole query runs per ciphertext
+    of a column (counted on a 256-point ring with the same chain, where the
+    count is the same). With one_thread, one more multiplication at the top
+    level runs on a single thread (the paper's setting, Section 5.1)."""
     import numpy as np
     import oracle as O
-    p = {"logN": 16, "L": level, "alpha": 3, "bits": 55, "p": 257, "r": 3, "h": 120, "seed": SEED}
-    o = O.Oracle(**p)
+    from paper_2604_19890_gb300 import synth
+    prm = dict(logN=16, L=41, alpha=3, bits=55, p=257, r=3, h=120, seed=SEED)
+    slope, fixed = query_ntt_count()
+    per_ct = slope + fixed / N_CT
+    o = O.Oracle(**prm)
     o.keygen([])
-    rng = np.random.default_rng(1)
-    a = o.encrypt_slots(rng.integers(0, o.t, o.slots, dtype=np.uint64), 1)
-    b = o.encrypt_slots(rng.integers(0, o.t, o.slots, dtype=np.uint64), 2)
+    cols = synth.table(SEED, N_CT, o.slots, o.t, columns=("a", "b", "c1", "c2"))
+    c1 = o.encrypt(o.encode(cols["c1"][0]), 3000)
+    c2 = o.encrypt(o.encode(cols["c2"][0]), 4000)
+    d = o.sub(c1, c2)
+    threads = O.threads()
     O.ntt_count(True)
     t0 = time.perf_counter()
-    o.mul(a, b)
+    x, n_mul = d, 0
+    while n_mul == 0 or (time.perf_counter() - t0 < seconds and x.level > 2):
+        x = o.mul(x, x)
+        n_mul += 1
     dt = time.perf_counter() - t0
     ntts = O.ntt_count()
-    per_ntt = dt / ntts
-    t_query = per_ntt * query_ntts_per_ct * n_ct
-    return rows / t_query, dt, ntts
+    res = {"rows_per_s": 128.0 * ntts / per_ct / dt, "seconds": dt, "transforms": ntts, "multiplications": n_mul,
+           "query_transforms_per_ct": per_ct, "threads": threads, "rows": 128.0 * ntts / per_ct}
+    if one_thread:
+        O.set_threads(1)
+        O.ntt_count(True)
+        t0 = time.perf_counter()
+        o.mul(d, d)
+        dt1 = time.perf_counter() - t0
+        n1 = O.ntt_count()
+        O.set_threads(threads)
+        res["one_thread"] = {"rows_per_s": 128.0 * n1 / per_ct / dt1, "seconds": dt1, "transforms": n1}
+    return res
+
+
+def cpu_baseline_entry(r):
+    return {"value": r["rows_per_s"], "unit": "rows/s", "cores": r["threads"], "kind": "oracle",
+            "host_cpus": os.cpu_count(),
+            "sample": "the reference on all %d host threads: %d multiplications at the top of the N=2^16, "
+                      "L=41 chain on the query's first c1 - c2 ciphertext, %.1f s, %d limb transforms = %.4f "
+                      "of the %.0f transforms the query runs per ciphertext of a column"
+                      % (r["threads"], r["multiplications"], r["seconds"], r["transforms"],
+                         r["transforms"] / r["query_transforms_per_ct"], r["query_transforms_per_ct"]),
+            "one_thread": ({"value": r["one_thread"]["rows_per_s"], "unit": "rows/s", "cores": 1,
+                            "sample": "one multiplication at level 41 on one thread, %.1f s"
+                                      % r["one_thread"]["seconds"]} if "one_thread" in r else None)}
+
+
+def run_cpu_full(args):
+    """The whole query on the CPU reference for one ciphertext per column (128
+    rows), all host threads, timed end to end, next to the sample-based rate
+    (validation of the sample's scaling)."""
+    import numpy as np
+    import oracle as O
+    from paper_2604_19890_gb300 import synth
+    prm = dict(logN=16, L=41, alpha=3, bits=55, p=257, r=3, h=120, seed=SEED)
+    o = O.Oracle(**prm)
+    o.keygen(o.rotate_sum_elements())
+    cols = synth.table(SEED, N_CT, o.slots, o.t, columns=("a", "b", "c1", "c2"))
+    cols = {k: v[:1] for k, v in cols.items()}
+    enc = {k: [o.encrypt(o.encode(cols[k][0]), 1000 * (i + 1))] for i, k in enumerate(("a", "b", "c1", "c2"))}
+    O.ntt_count(True)
+    t0 = time.perf_counter()
+    res = o.query(enc["a"], enc["b"], enc["c1"], enc["c2"])
+    dt = time.perf_counter() - t0
+    ntts = O.ntt_count()
+    ok = int(o.decrypt_slots(res)[0]) == plain_query(cols["a"], cols["b"], cols["c1"], cols["c2"], o.t)
+    sample = cpu_reference_sample(args.cpu_seconds)
+    print(json.dumps({"cpu_full_query": True, "threads": O.threads(), "host_cpus": os.cpu_count(), "rows": 128,
+                      "seconds": dt, "rows_per_s": 128 / dt, "transforms": ntts,
+                      "sample_rows_per_s": sample["rows_per_s"], "sample_over_full": sample["rows_per_s"] * dt / 128,
+                      "verified_against_plaintext": bool(ok)}))
+    return 0 if ok else 1
 
 
 def query_ntt_count(n_ct_small=(1, 2)):
@@ -172,23 +236,22 @@ def run_reference(args):
     rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return 0
-    rows = N_CT * 128
-    slope, fixed = query_ntt_count()
-    per_ct = slope + fixed / N_CT
-    vals = []
+    times, rows_done, last = [], 0.0, None
     for i in range(args.warmup + args.steps):
-        v, dt, ntts = cpu_sample(rows, per_ct, N_CT)
+        r = cpu_reference_sample(args.cpu_seconds)
         if i >= args.warmup:
-            vals.append(v)
-    v = sum(vals) / len(vals)
+            times.append(r["seconds"])
+            rows_done += r["rows"]
+            last = r
+    v = rows_done / sum(times)
+    base = cpu_baseline_entry(last)
+    base["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "rows/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rows / v * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(times) / len(times) * 1e3,
+            "rows_per_step": rows_done / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": workload_config(16, 41, 55, 3, 257, 3, 128, N_CT, args.batch),
-            "cpu_baseline": {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
-                             "sample": "per step: one tensor+relin+modswitch at level 20 of the N=2^16 chain "
-                                       "(%d limb transforms), scaled by the query's %.0f transforms per "
-                                       "ciphertext x 32" % (ntts, per_ct)},
+            "cpu_baseline": base,
             "e2e": {"value": v, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -199,7 +262,9 @@ def run_kernel(args):
     """Times one kernel family alone on the benchmark's parameter set (for
     profiling): `ntt` runs forward then inverse transforms over `--limbs` limbs
     of the N = 2^16 chain; `relin` runs tensor + relinearisation + modulus
-    switch on a batch of `--n-ct` ciphertexts at the top level."""
+    switch on a batch of `--n-ct` ciphertexts at the top level; `mul` runs the
+    query's multiplication (tensor, then relinearise-and-drop in one ModDown)
+    on such a batch."""
     import numpy as np
     import torch
 
@@ -233,13 +298,14 @@ def run_kernel(args):
         rng = np.random.default_rng(0)
         a = g.encrypt(np.stack([g.encode(rng.integers(0, g.t, g.slots)) for _ in range(args.n_ct)]), 1)
         b = g.encrypt(np.stack([g.encode(rng.integers(0, g.t, g.slots)) for _ in range(args.n_ct)]), 100)
+        op = (lambda: g.modswitch(g.relin(g.mul(a, b)), 1)) if args.kernel == "relin" else (lambda: g.mul_relin(a, b))
         for _ in range(args.warmup):
-            g.modswitch(g.relin(g.mul(a, b)), 1)
+            op()
         g.kernel_timing(True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            g.modswitch(g.relin(g.mul(a, b)), 1)
+            op()
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / args.steps
         ks = g.kernel_stats()
@@ -255,10 +321,16 @@ def run_kernel(args):
 # ------------------------------------------------------------------ served form
 def run_serve(args):
     """Poisson-arriving compare-then-SUM queries against device-resident tables
-    (N = 2^16, 257^3, `--serve-ct` ciphertexts per column each, keys resident).
-    Compares the plain form (one worker, one query per pass) with the served
-    form (two workers, up to 8 compatible queries merged per pass) at arrival
-    rates relative to the measured single-query capacity and at 10 q/s."""
+    of two parameter sets: N = 2^16 with 257^3 (SUM(a*b) WHERE c1 < c2) and
+    N = 2^15 with 257^2 (SUM(a*b) WHERE c < t, t encrypted), `--serve-ct`
+    ciphertexts per column each, keys of both resident, queries drawn from both
+    at random. Compares the plain form (one worker, one query per pass) with
+    the served form (continuous batching: several workers, compatible queries
+    of one context merged per pass, one HBM budget) at arrival rates relative
+    to the measured capacity and at 10 q/s, `--serve-queries` arrivals per
+    point. A last run submits queries over tables of 2^15 rows (256
+    ciphertexts per column at N = 2^15) mixed with small ones under an HBM
+    budget of two large queries, to show admission by memory."""
     import numpy as np
     import torch
 
@@ -267,59 +339,84 @@ def run_serve(args):
     from paper_2604_19890_gb300 import synth
 
     ssbuild.build()
-    prm = ssg.preset(PRESET)
-    g = ssg.Context(params=prm)
-    g.keygen()
-    g.set_batch(args.batch)
-    n_tables = 8
-    tables = []
-    for i in range(n_tables):
-        cols = synth.table(SEED + 100 + i, args.serve_ct, g.slots, g.t)
-        enc = [g.encrypt(np.stack([g.encode(x) for x in cols[k]]), 10000 * (i + 1) + 100 * j)
+    gs = []
+    for pid in (2, 1):
+        g = ssg.Context(params=ssg.preset(pid))
+        g.keygen()
+        g.set_batch(args.batch)
+        gs.append(g)
+    n_tables = 4
+
+    def make_table(ci, i, n_ct):
+        g = gs[ci]
+        cols = synth.table(SEED + 100 + 10 * ci + i, n_ct, g.slots, g.t)
+        if ci == 1:
+            cols["c2"] = synth.threshold(SEED + 200 + i, g.slots, g.t)
+        enc = [g.encrypt(np.stack([g.encode(x) for x in cols[k]]), 10000 * (i + 1) + 100 * j + 50000 * ci)
                for j, k in enumerate(("a", "b", "c1", "c2"))]
-        tables.append((enc, plain_query(cols["a"], cols["b"], cols["c1"], cols["c2"], g.t)))
-    # single-query service time
-    for _ in range(2):
-        g.query(*tables[0][0])
+        return ci, enc, plain_query(cols["a"], cols["b"], cols["c1"], cols["c2"], g.t)
+
+    tables = [make_table(ci, i, args.serve_ct) for i in range(n_tables) for ci in (0, 1)]
+    # single-query service time over the mix
+    for ci, enc, _ in tables[:2]:
+        gs[ci].query(*enc)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for i in range(3):
-        g.query(*tables[i % n_tables][0])
+    for ci, enc, _ in tables:
+        gs[ci].query(*enc)
     torch.cuda.synchronize()
-    t1 = (time.perf_counter() - t0) / 3
+    t1 = (time.perf_counter() - t0) / len(tables)
     cap = 1.0 / t1
     rng = np.random.default_rng(7)
     out = {"metric": "served compare-then-SUM queries/s and latency", "unit": "queries/s",
-           "config": {"workload": "N=2^16, L=41, p^r=257^3, %d ciphertexts (%d rows) per column per query, "
-                                  "%d device-resident tables" % (args.serve_ct, args.serve_ct * g.slots, n_tables)},
+           "config": {"workload": "mixed: N=2^16/L=41/257^3 and N=2^15/L=30/257^2, %d ciphertexts (%d rows) per "
+                                  "column per query, %d device-resident tables per parameter set"
+                                  % (args.serve_ct, args.serve_ct * 128, n_tables)},
            "single_query_ms": t1 * 1e3, "capacity_qps": cap, "runs": []}
     ok = True
+
+    def run(arrivals, picks, workers, merge, budget=0, check=2):
+        nonlocal ok
+        srv = ssg.Server(gs, workers=workers, max_merge=merge, hbm_budget=budget)
+        tickets = []
+        start = time.perf_counter()
+        for i, at in enumerate(arrivals):
+            now = time.perf_counter() - start
+            if at > now:
+                time.sleep(at - now)
+            ci, enc, exp = picks[i]
+            tickets.append((srv.submit(*enc, ctx_index=ci), time.perf_counter(), i))
+        lat, last = [], 0.0
+        for tk, t_sub, i in tickets:
+            res, q_ms, r_ms = srv.wait(tk, timeout_ms=900000)
+            lat.append(q_ms + r_ms)
+            last = max(last, t_sub - start + (q_ms + r_ms) / 1e3)
+            if i < check:
+                ci, _, exp = picks[i]
+                ok &= bool((gs[ci].decrypt_slots(res) == exp).all())
+        st = srv.stats()
+        srv.close()
+        lat.sort()
+        return {"queries": len(lat), "qps": len(lat) / last, "p50_ms": lat[len(lat) // 2],
+                "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "passes": st["batches"],
+                "peak_inflight_bytes": st["peak_inflight_bytes"]}
+
     for rate in [0.5 * cap, 1.0 * cap, 2.0 * cap, 10.0]:
         gaps = rng.exponential(1.0 / rate, args.serve_queries)
         arrivals = np.cumsum(gaps) - gaps[0]
-        for form, workers, merge in [("plain", 1, 1), ("served", 2, 8)]:
-            srv = ssg.Server(g, workers=workers, max_merge=merge)
-            tickets = []
-            start = time.perf_counter()
-            for i, at in enumerate(arrivals):
-                now = time.perf_counter() - start
-                if at > now:
-                    time.sleep(at - now)
-                tickets.append((srv.submit(*tables[i % n_tables][0]), time.perf_counter(), i))
-            lat, last = [], 0.0
-            for tk, t_sub, i in tickets:
-                res, q_ms, r_ms = srv.wait(tk, timeout_ms=600000)
-                lat.append(q_ms + r_ms)
-                last = max(last, t_sub - start + (q_ms + r_ms) / 1e3)
-                if i < 2:
-                    ok &= bool((g.decrypt_slots(res) == tables[i % n_tables][1]).all())
-            st = srv.stats()
-            srv.close()
-            lat.sort()
-            out["runs"].append({"form": form, "arrival_qps": round(rate, 3), "queries": len(lat),
-                                "qps": len(lat) / last, "p50_ms": lat[len(lat) // 2],
-                                "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                                "passes": st["batches"]})
+        picks = [tables[int(k)] for k in rng.integers(0, len(tables), args.serve_queries)]
+        for form, workers, merge in [("plain", 1, 1), ("served", 3, 8)]:
+            r = run(arrivals, picks, workers, merge)
+            r.update({"form": form, "arrival_qps": round(rate, 3)})
+            out["runs"].append(r)
+    # tables of 2^15 rows at N = 2^15 (256 ciphertexts per column) among small queries
+    big = [make_table(1, 10 + i, 256) for i in range(2)]
+    est = gs[1].query_bytes(256)
+    picks = [big[0]] + tables[:6] + [big[1]] + tables[6:]
+    r = run([0.0] * len(picks), picks, 3, 8, budget=int(2.5 * est), check=len(picks))
+    r.update({"form": "served", "arrival": "burst", "large_queries": 2, "large_rows": 256 * 128,
+              "hbm_budget": int(2.5 * est)})
+    out["runs"].append(r)
     out["verified_against_plaintext"] = ok
     print(json.dumps(out))
     return 0 if ok else 1
@@ -557,12 +654,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and args.preset == PRESET:
-        slope, fixed = query_ntt_count()
-        per_ct = slope + fixed / n_ct
-        v, dt, ntts = cpu_sample(rows, per_ct, n_ct)
-        cpu = {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
-               "sample": "one tensor+relin+modswitch at level 20 of the N=2^16 chain (%d limb transforms, "
-                         "%.1f s), scaled by the query's %.0f transforms per ciphertext x 32" % (ntts, dt, per_ct)}
+        cpu = cpu_baseline_entry(cpu_reference_sample(args.cpu_seconds, one_thread=True))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
@@ -581,6 +673,40 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0 if verified else 1
+
+
+# ------------------------------------------------------------------ tensor-core rates
+def run_mma_rates(args):
+    """Dense matrix-multiply rates of this GPU's tensor cores for the operand
+    types an exact integer contraction could use (int8 -> int32 through
+    torch._int_mm, fp16 and bf16 with fp32 accumulation through torch.matmul),
+    8192^3, best of 10 after warm-up, CUDA events. Context for the choice of
+    the integer pipe for the transforms and the key-switch inner product."""
+    import torch
+    n = args.mma_n
+    out = {"mma_rates": True, "n": n}
+    a8 = torch.randint(-128, 127, (n, n), dtype=torch.int8, device="cuda")
+    b8 = torch.randint(-128, 127, (n, n), dtype=torch.int8, device="cuda").t().contiguous().t()
+    cases = {"int8_int32": lambda: torch._int_mm(a8, b8)}
+    for name, dt in (("fp16_fp32acc", torch.float16), ("bf16_fp32acc", torch.bfloat16)):
+        x = torch.randn(n, n, device="cuda", dtype=dt)
+        y = torch.randn(n, n, device="cuda", dtype=dt)
+        cases[name] = (lambda x=x, y=y: torch.matmul(x, y))
+    for name, f in cases.items():
+        for _ in range(3):
+            f()
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out[name + "_tops"] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+    print(json.dumps(out))
+    return 0
 
 
 # ------------------------------------------------------------------ LT operator across (p, r)
@@ -648,7 +774,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--kernel", choices=["ntt", "relin"], default=None,
+    ap.add_argument("--kernel", choices=["ntt", "relin", "mul"], default=None,
                     help="time one kernel family alone (profiling mode)")
     ap.add_argument("--limbs", type=int, default=512)
     ap.add_argument("--n-ct", type=int, default=N_CT, help="ciphertexts per column")
@@ -657,12 +783,20 @@ def main():
     ap.add_argument("--serve", action="store_true", help="served form: Poisson arrivals, p50/p99")
     ap.add_argument("--batched", action="store_true", help="batched form: 64 mixed-N pairs, graph replay")
     ap.add_argument("--serve-ct", type=int, default=2)
-    ap.add_argument("--serve-queries", type=int, default=16)
+    ap.add_argument("--serve-queries", type=int, default=200)
     ap.add_argument("--lt-sweep", action="store_true",
                     help="LT operator + modulus raising across (p, r) at fixed bit widths, per-stage times")
     ap.add_argument("--sweep-logn", type=int, default=15)
     ap.add_argument("--sweep-ct", type=int, default=8)
+    ap.add_argument("--mma-rates", action="store_true", help="tensor-core int8/fp16/bf16 matmul rates")
+    ap.add_argument("--cpu-seconds", type=float, default=6.0, help="length of one CPU reference sample")
+    ap.add_argument("--cpu-full", action="store_true", help="whole query on the CPU reference, 1 ct per column")
+    ap.add_argument("--mma-n", type=int, default=8192)
     args = ap.parse_args()
+    if args.mma_rates:
+        return run_mma_rates(args)
+    if args.cpu_full:
+        return run_cpu_full(args)
     if args.lt_sweep:
         return run_lt_sweep(args)
     if args.serve:

@@ -23,6 +23,12 @@
  *    its own scratch in a stream-ordered pool (cudaMallocAsync).
  *  - Every call returns an ss_status; ss_last_error() gives a thread-local
  *    message for the last failure. Errors never cross the ABI as exceptions.
+ *  - Calls that run an evaluation schedule (ss_mul_relin, ss_eval_g,
+ *    ss_reduce_to_digits, ss_compare_lt, ss_compare, ss_raise_modulus,
+ *    ss_rotate_sum, ss_query_*) first plan it on the host thread (levels and
+ *    plaintext moduli only): a chain too short for the schedule returns
+ *    SS_ERR_NOISE before anything is enqueued, copied or allocated. Planning
+ *    state is per thread and never affects other threads' calls.
  *  - Keys and contexts are library-owned and released with *_destroy.
  */
 #ifndef SS_H
@@ -123,6 +129,13 @@ ss_status ss_add_scalar(ss_ctx* ctx, const ss_ct* a, int64_t c, ss_ct* out, ss_s
 ss_status ss_mul(ss_ctx* ctx, const ss_ct* a, const ss_ct* b, ss_ct* out, ss_stream stream);
 /* hybrid key switch of c2 with the relinearisation key: 3 -> 2 components */
 ss_status ss_relin(ss_ctx* ctx, const ss_ct* a, ss_ct* out, ss_stream stream);
+/* BGV multiplication as the evaluation schedules run it (Section 2.1: the
+ * product of two ciphertexts, then relinearisation and modulus switching):
+ * both operands are switched to the lower of their levels l, tensored, and the
+ * result is relinearised and divided by q_{l-1} in one ModDown over
+ * {q_{l-1}} and the special primes. 2-component inputs of equal count and
+ * t_exp; out receives 2 components at level l - 1 (capacity >= l - 1). */
+ss_status ss_mul_relin(ss_ctx* ctx, const ss_ct* a, const ss_ct* b, ss_ct* out, ss_stream stream);
 /* Same result as ss_relin, for callers that cannot allocate device memory
  * while they run (a host framework that owns all device memory through its
  * own allocator, or a service that must not risk an allocation stalling or
@@ -146,6 +159,14 @@ ss_status ss_rotate_sum(ss_ctx* ctx, const ss_ct* a, ss_ct* out, ss_stream strea
  * share count, level and t_exp; |coeffs[i]|, |cst| < the smallest prime. */
 ss_status ss_linear_combination(ss_ctx* ctx, const ss_ct* terms, const int64_t* coeffs, int32_t nterms, int64_t cst,
                                 ss_ct* out, ss_stream stream);
+/* Several combinations of the same terms in one pass, as Paterson-Stockmeyer
+ * forms its leaves from one set of baby steps (Theorem 2): for k < nout,
+ * outs[k] = sum_i coeffs[k*nterms + i] * terms[i]. 1 <= nterms, nout <= 16;
+ * every term shares count, level and t_exp; |coeffs| < the smallest prime.
+ * Each term is read once for all outputs; each output equals the
+ * corresponding ss_linear_combination (with cst 0) word for word. */
+ss_status ss_linear_combinations(ss_ctx* ctx, const ss_ct* terms, int32_t nterms, const int64_t* coeffs,
+                                 int32_t nout, ss_ct* outs, ss_stream stream);
 /* DivideByP (Section 4.2): times p^-1 mod Q, t_exp - 1 */
 ss_status ss_divide_by_p(ss_ctx* ctx, const ss_ct* a, ss_ct* out, ss_stream stream);
 
@@ -214,12 +235,16 @@ typedef struct ss_batch ss_batch;
  * data and the output descriptors alive). Items whose reduction does not fit
  * in their remaining levels have it skipped and counted. */
 ss_status ss_batch_create(ss_ctx* const* ctxs, int32_t nctx, const ss_batch_item* items, int32_t n, ss_batch** out);
-/* chunk: ciphertexts per pass; nstreams: 1..8; ntt_tile_log: 11 or 12 (words per transform tile). */
+/* chunk: ciphertexts per pass; nstreams: 1..8 streams, each issuing its own
+ * launches, or 0: merged lanes (each chunk a host thread with its own stream;
+ * the transforms of all lanes, of rings N >= 8192, run together as one
+ * persistent launch per phase over all their tiles); ntt_tile_log: 11 or 12
+ * (words per transform tile). Kernel timing does not cover merged lanes. */
 ss_status ss_batch_config(ss_batch* b, int32_t chunk, int32_t nstreams, int32_t ntt_tile_log);
 ss_status ss_batch_get_config(const ss_batch* b, int32_t* chunk, int32_t* nstreams, int32_t* ntt_tile_log,
                               int32_t* groups, int32_t* skipped);
-/* Autotuner: times the run for chunk in {8, 32, 64} x streams in {1, 3} x tile in {2^11, 2^12} words
- * on this work list and keeps the fastest setting. Synchronous. */
+/* Autotuner: times the run for chunk in {8, 32, 64} x streams in {1, 3, 0 (merged lanes)} x tile in
+ * {2^11, 2^12} words on this work list and keeps the fastest setting. Synchronous. */
 ss_status ss_batch_tune(ss_batch* b, ss_stream stream, int32_t* best_chunk, int32_t* best_streams,
                         int32_t* best_tile_log);
 /* Captures the whole run (current setting) as one CUDA graph on `stream` (not the legacy stream). */
@@ -240,11 +265,24 @@ void ss_batch_destroy(ss_batch* b);
  * server runs. */
 typedef struct ss_server ss_server;
 ss_status ss_server_create(ss_ctx* ctx, int32_t workers, int32_t max_merge, uint64_t hbm_budget, ss_server** out);
+/* A server over several contexts (parameter sets of any ring dimension and
+ * plaintext modulus, keys of all of them resident): queries name their
+ * context at submission (ss_server_submit_to); only queries of the same
+ * context, level and plaintext modulus are merged into one pass, and one HBM
+ * budget admits the queries of all contexts. ss_server_create(ctx, ...) is
+ * the one-context case. */
+ss_status ss_server_create_multi(ss_ctx* const* ctxs, int32_t nctx, int32_t workers, int32_t max_merge,
+                                 uint64_t hbm_budget, ss_server** out);
 /* Queues one query on device-resident columns (as ss_query_sum_where_lt);
  * `out` (count 1, capacity >= the columns' level) receives the result. The
  * caller keeps the columns and *out alive until ss_server_wait returns. */
 ss_status ss_server_submit(ss_server* s, const ss_ct* A, const ss_ct* B, const ss_ct* C1, const ss_ct* C2,
                            ss_ct* out, uint64_t* ticket);
+/* The same for the server's context number ctx_index (0-based, in the order
+ * given to ss_server_create_multi); ss_server_submit is ctx_index 0. A chain
+ * too short for the query is rejected here with SS_ERR_NOISE. */
+ss_status ss_server_submit_to(ss_server* s, int32_t ctx_index, const ss_ct* A, const ss_ct* B, const ss_ct* C1,
+                              const ss_ct* C2, ss_ct* out, uint64_t* ticket);
 /* Waits at most timeout_ms (negative: no bound) for a ticket: SS_ERR_TIMEOUT if
  * it is still running; otherwise releases it and returns its status with the
  * time it waited for admission and the time its batch ran (host clock). */
@@ -256,6 +294,9 @@ void ss_server_destroy(ss_server* s);
 /* Number of levels a query consumes on inputs at `level` (the plan's depth);
  * SS_ERR_NOISE if the chain is too short. */
 ss_status ss_query_depth(ss_ctx* ctx, int32_t level, int32_t* out_level);
+/* Device bytes a query over n_ct ciphertexts per column at `level` holds at
+ * its peak: the estimate the served form admits queries by. */
+ss_status ss_query_bytes(const ss_ctx* ctx, int32_t n_ct, int32_t level, uint64_t* bytes);
 /* Ciphertexts the query evaluates together per pass (memory/throughput knob). */
 ss_status ss_set_batch(ss_ctx* ctx, int32_t batch);
 

@@ -66,6 +66,10 @@ _SIGS = {
     "ss_add_scalar": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.c_int64, C.POINTER(ss_ct), C.c_void_p]),
     "ss_mul": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.POINTER(ss_ct), C.POINTER(ss_ct), C.c_void_p]),
     "ss_relin": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.POINTER(ss_ct), C.c_void_p]),
+    "ss_linear_combinations": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.c_int32, C.POINTER(C.c_int64), C.c_int32,
+                                         C.POINTER(ss_ct), C.c_void_p]),
+    "ss_query_bytes": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_uint64)]),
+    "ss_mul_relin": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.POINTER(ss_ct), C.POINTER(ss_ct), C.c_void_p]),
     "ss_relin_noalloc": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.POINTER(ss_ct), C.c_void_p]),
     "ss_modswitch": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.c_int32, C.POINTER(ss_ct), C.c_void_p]),
     "ss_rotate": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.c_int32, C.POINTER(ss_ct), C.c_void_p]),
@@ -103,6 +107,9 @@ _SIGS = {
     "ss_batch_destroy": (None, [C.c_void_p]),
     "ss_server_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(C.c_void_p)]),
     "ss_server_submit": (C.c_int, [C.c_void_p] + [C.POINTER(ss_ct)] * 5 + [C.POINTER(C.c_uint64)]),
+    "ss_server_create_multi": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
+                                         C.POINTER(C.c_void_p)]),
+    "ss_server_submit_to": (C.c_int, [C.c_void_p, C.c_int32] + [C.POINTER(ss_ct)] * 5 + [C.POINTER(C.c_uint64)]),
     "ss_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "ss_server_stats": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_uint64)] * 3),
     "ss_server_destroy": (None, [C.c_void_p]),
@@ -266,21 +273,25 @@ class Batch:
 
 
 class Server:
-    """Request loop with continuous batching over one context (ss_server_*)."""
+    """Request loop with continuous batching (ss_server_*) over one context or
+    a list of contexts (one HBM budget; queries merge only within a context)."""
 
     def __init__(self, ctx, workers=2, max_merge=8, hbm_budget=0):
-        self.ctx = ctx
+        self.ctxs = list(ctx) if isinstance(ctx, (list, tuple)) else [ctx]
+        self.ctx = self.ctxs[0]
         h = C.c_void_p()
-        _chk(lib().ss_server_create(ctx.h, workers, max_merge, hbm_budget, C.byref(h)))
+        arr = (C.c_void_p * len(self.ctxs))(*[g.h.value for g in self.ctxs])
+        _chk(lib().ss_server_create_multi(arr, len(self.ctxs), workers, max_merge, hbm_budget, C.byref(h)))
         self.h = h
         self._live = {}
 
-    def submit(self, A, B, C1, C2):
-        """Queues a query; returns a ticket. Keeps the descriptors alive until wait()."""
-        out = self.ctx.empty(1, level=A.level)
+    def submit(self, A, B, C1, C2, ctx_index=0):
+        """Queues a query on context ctx_index; returns a ticket. Keeps the
+        descriptors alive until wait()."""
+        out = self.ctxs[ctx_index].empty(1, level=A.level)
         descs = [x.desc() for x in (A, B, C1, C2)] + [out.desc()]
         t = C.c_uint64()
-        _chk(lib().ss_server_submit(self.h, *[C.byref(d) for d in descs], C.byref(t)))
+        _chk(lib().ss_server_submit_to(self.h, ctx_index, *[C.byref(d) for d in descs], C.byref(t)))
         self._live[t.value] = (descs, out, (A, B, C1, C2))
         return t.value
 
@@ -432,6 +443,11 @@ class Context:
     def mul(self, a, b):
         return self._call2(lib().ss_mul, a, b, self._out(a, ncomp=3))
 
+    def mul_relin(self, a, b):
+        """Multiplication as the evaluator runs it: tensor, relinearise, drop one prime."""
+        lvl = min(a.level, b.level) - 1
+        return self._call2(lib().ss_mul_relin, a, b, self.empty(a.count, level=lvl, t_exp=a.t_exp))
+
     def compare_lt(self, a, b):
         return self._call2(lib().ss_compare_lt, a, b, self._out(a, ncomp=2))
 
@@ -472,6 +488,16 @@ class Context:
         do = out.desc()
         _chk(lib().ss_linear_combination(self.h, arr, cf, len(terms), int(cst), C.byref(do), _stream(self.torch)))
         return out.update(do)
+
+    def linear_combinations(self, terms, coeff_rows):
+        """[sum_i row[i] * terms[i] for row in coeff_rows] in one pass (ss_linear_combinations)."""
+        arr = (ss_ct * len(terms))(*[x.desc() for x in terms])
+        flat = [int(c) for row in coeff_rows for c in row]
+        cf = (C.c_int64 * len(flat))(*flat)
+        outs = [self._out(terms[0], ncomp=2) for _ in coeff_rows]
+        od = (ss_ct * len(outs))(*[o.desc() for o in outs])
+        _chk(lib().ss_linear_combinations(self.h, arr, len(terms), cf, len(outs), od, _stream(self.torch)))
+        return [o.update(od[k]) for k, o in enumerate(outs)]
 
     def divide_by_p(self, a):
         return self._call1(lib().ss_divide_by_p, a, self._out(a))
@@ -531,6 +557,12 @@ class Context:
     def query_depth(self, level=None):
         out = C.c_int32()
         _chk(lib().ss_query_depth(self.h, self.L if level is None else level, C.byref(out)))
+        return out.value
+
+    def query_bytes(self, n_ct, level=None):
+        """Peak device bytes of a query over n_ct ciphertexts per column (admission estimate)."""
+        out = C.c_uint64()
+        _chk(lib().ss_query_bytes(self.h, int(n_ct), self.L if level is None else int(level), C.byref(out)))
         return out.value
 
     def set_batch(self, b):

@@ -257,6 +257,39 @@ ss_status ss_linear_combination(ss_ctx* ctx, const ss_ct* terms, const int64_t* 
   });
 }
 
+ss_status ss_linear_combinations(ss_ctx* ctx, const ss_ct* terms, int32_t nterms, const int64_t* coeffs,
+                                 int32_t nout, ss_ct* outs, ss_stream stream) {
+  return guard([&] {
+    need(ctx != nullptr && terms != nullptr && coeffs != nullptr && outs != nullptr, SS_ERR_PARAM, "bad argument");
+    need(nterms >= 1 && nterms <= 16 && nout >= 1 && nout <= 16, SS_ERR_PARAM, "1..16 terms and outputs");
+    std::vector<ss::BufP> keep;
+    std::vector<const ss::Buf*> ys;
+    for (int i = 0; i < nterms; ++i) {
+      check_ct(ctx->C, &terms[i], "null term");
+      need(terms[i].ncomp == 2, SS_ERR_SHAPE, "2-component terms");
+      need(terms[i].level == terms[0].level, SS_ERR_LEVEL, "terms at different levels");
+      need(terms[i].t_exp == terms[0].t_exp, SS_ERR_TMOD, "plaintext moduli differ");
+      need(terms[i].count == terms[0].count, SS_ERR_SHAPE, "batch sizes differ");
+      keep.push_back(ss::view_buf(terms[i]));
+      ys.push_back(keep.back().get());
+    }
+    std::vector<std::vector<int64_t>> cs(nout);
+    std::vector<ss::Buf> ob(nout);
+    std::vector<ss::Buf*> op;
+    for (int k = 0; k < nout; ++k) {
+      cs[k].assign(coeffs + (size_t)k * nterms, coeffs + (size_t)(k + 1) * nterms);
+      check_out(&outs[k], terms[0].count, 2, terms[0].level);
+      ob[k] = as_out(&outs[k]);
+      ob[k].ncomp = 2;
+      ob[k].level = terms[0].level;
+      ob[k].t_exp = terms[0].t_exp;
+      op.push_back(&ob[k]);
+    }
+    ss::k_lincomb_multi(ctx->C, ys, cs, op, S(stream));
+    for (int k = 0; k < nout; ++k) write_back(ob[k], &outs[k]);
+  });
+}
+
 ss_status ss_mul(ss_ctx* ctx, const ss_ct* a, const ss_ct* b, ss_ct* out, ss_stream stream) {
   return guard([&] {
     need(ctx != nullptr, SS_ERR_PARAM, "null context");
@@ -285,6 +318,19 @@ ss_status ss_relin(ss_ctx* ctx, const ss_ct* a, ss_ct* out, ss_stream stream) {
     ss::Buf o = as_out(out);
     ss::op_relin(ctx->C, *ss::view_buf(*a), o, S(stream));
     write_back(o, out);
+  });
+}
+
+ss_status ss_mul_relin(ss_ctx* ctx, const ss_ct* a, const ss_ct* b, ss_ct* out, ss_stream stream) {
+  return guard([&] {
+    need(ctx != nullptr, SS_ERR_PARAM, "null context");
+    check_ct(ctx->C, a, "null a");
+    check_ct(ctx->C, b, "null b");
+    need(a->count == b->count, SS_ERR_SHAPE, "batch sizes differ");
+    auto r = ss::plan_then_run(ctx->C, [&] {
+      return ss::ev_mul(ctx->C, ss::view_buf(*a), ss::view_buf(*b), S(stream));
+    });
+    deliver(ctx->C, r, out, S(stream));
   });
 }
 
@@ -328,7 +374,7 @@ ss_status ss_rotate_sum(ss_ctx* ctx, const ss_ct* a, ss_ct* out, ss_stream strea
   return guard([&] {
     need(ctx != nullptr, SS_ERR_PARAM, "null context");
     check_ct(ctx->C, a, "null a");
-    auto r = ss::ev_rotate_sum(ctx->C, ss::view_buf(*a), S(stream));
+    auto r = ss::plan_then_run(ctx->C, [&] { return ss::ev_rotate_sum(ctx->C, ss::view_buf(*a), S(stream)); });
     deliver(ctx->C, r, out, S(stream));
   });
 }
@@ -338,7 +384,7 @@ ss_status ss_eval_g(ss_ctx* ctx, const ss_ct* x, int32_t e, ss_ct* out, ss_strea
     need(ctx != nullptr, SS_ERR_PARAM, "null context");
     check_ct(ctx->C, x, "null x");
     need(e >= 1 && e <= x->t_exp, SS_ERR_TMOD, "G_{p,e} needs e <= t_exp");
-    auto r = ss::ev_eval_g(ctx->C, ss::view_buf(*x), e, S(stream));
+    auto r = ss::plan_then_run(ctx->C, [&] { return ss::ev_eval_g(ctx->C, ss::view_buf(*x), e, S(stream)); });
     deliver(ctx->C, r, out, S(stream));
   });
 }
@@ -347,7 +393,7 @@ ss_status ss_reduce_to_digits(ss_ctx* ctx, const ss_ct* a, ss_ct* digits, ss_str
   return guard([&] {
     need(ctx != nullptr && digits != nullptr, SS_ERR_PARAM, "null argument");
     check_ct(ctx->C, a, "null a");
-    auto d = ss::ev_reduce(ctx->C, ss::view_buf(*a), S(stream));
+    auto d = ss::plan_then_run(ctx->C, [&] { return ss::ev_reduce(ctx->C, ss::view_buf(*a), S(stream)); });
     for (size_t i = 0; i < d.size(); ++i) deliver(ctx->C, d[i], &digits[i], S(stream));
   });
 }
@@ -357,7 +403,9 @@ ss_status ss_compare_lt(ss_ctx* ctx, const ss_ct* a, const ss_ct* b, ss_ct* out,
     need(ctx != nullptr, SS_ERR_PARAM, "null context");
     check_ct(ctx->C, a, "null a");
     check_ct(ctx->C, b, "null b");
-    auto r = ss::ev_compare_lt(ctx->C, ss::view_buf(*a), ss::view_buf(*b), S(stream));
+    auto r = ss::plan_then_run(ctx->C, [&] {
+      return ss::ev_compare_lt(ctx->C, ss::view_buf(*a), ss::view_buf(*b), S(stream));
+    });
     deliver(ctx->C, r, out, S(stream));
   });
 }
@@ -368,7 +416,9 @@ ss_status ss_compare(ss_ctx* ctx, int32_t pred, const ss_ct* a, const ss_ct* b, 
     need(pred >= SS_PRED_LT && pred <= SS_PRED_NEQ, SS_ERR_PARAM, "unknown predicate");
     check_ct(ctx->C, a, "null a");
     check_ct(ctx->C, b, "null b");
-    auto r = ss::ev_compare(ctx->C, pred, ss::view_buf(*a), ss::view_buf(*b), S(stream));
+    auto r = ss::plan_then_run(ctx->C, [&] {
+      return ss::ev_compare(ctx->C, pred, ss::view_buf(*a), ss::view_buf(*b), S(stream));
+    });
     deliver(ctx->C, r, out, S(stream));
   });
 }
@@ -377,7 +427,7 @@ ss_status ss_raise_modulus(ss_ctx* ctx, const ss_ct* in, ss_ct* out, ss_stream s
   return guard([&] {
     need(ctx != nullptr, SS_ERR_PARAM, "null context");
     check_ct(ctx->C, in, "null input");
-    auto r = ss::ev_raise(ctx->C, ss::view_buf(*in), S(stream));
+    auto r = ss::plan_then_run(ctx->C, [&] { return ss::ev_raise(ctx->C, ss::view_buf(*in), S(stream)); });
     deliver(ctx->C, r, out, S(stream));
   });
 }
@@ -387,8 +437,10 @@ ss_status ss_query_sum_where_lt(ss_ctx* ctx, const ss_ct* A, const ss_ct* B, con
   return guard([&] {
     need(ctx != nullptr, SS_ERR_PARAM, "null context");
     for (const ss_ct* c : {A, B, C1, C2}) check_ct(ctx->C, c, "null column");
-    auto r = ss::ev_query(ctx->C, ss::view_buf(*A), ss::view_buf(*B), ss::view_buf(*C1), ss::view_buf(*C2),
+    auto r = ss::plan_then_run(ctx->C, [&] {
+      return ss::ev_query(ctx->C, ss::view_buf(*A), ss::view_buf(*B), ss::view_buf(*C1), ss::view_buf(*C2),
                           S(stream));
+    });
     deliver(ctx->C, r, out, S(stream));
   });
 }
@@ -406,7 +458,9 @@ ss_status ss_query_sum_where(ss_ctx* ctx, const ss_ct* A, const ss_ct* B, const 
       check_ct(ctx->C, conds[k].y, "null condition column");
       qc.push_back({conds[k].pred, ss::view_buf(*conds[k].x), ss::view_buf(*conds[k].y)});
     }
-    auto r = ss::ev_query_where(ctx->C, ss::view_buf(*A), ss::view_buf(*B), qc, S(stream));
+    auto r = ss::plan_then_run(ctx->C, [&] {
+      return ss::ev_query_where(ctx->C, ss::view_buf(*A), ss::view_buf(*B), qc, S(stream));
+    });
     deliver(ctx->C, r, out, S(stream));
   });
 }
@@ -421,6 +475,11 @@ ss_status ss_query_sum_where_lt_host(ss_ctx* ctx, const uint64_t* A, const uint6
     need(level >= 1 && level <= C.L, SS_ERR_LEVEL, "bad level");
     cudaStream_t st = S(stream);
     size_t ct_words = (size_t)2 * level * C.N;
+    {  // the plan first: a chain too short for the query fails here, before any copy or launch
+      ss::PlanScope ps(C);
+      auto col = [&](int n) { return ss::alloc_buf(C, n, 2, level, C.r, st); };
+      ss::ev_query_where(C, col(count), col(count), {ss::QCond{SS_PRED_LT, col(count), col(count2)}}, st);
+    }
     // Buffers come from the pool on st. The comparison columns are copied on
     // st; A and B on a second stream that starts once the allocations are
     // ordered, so their upload overlaps the comparisons (the first product
@@ -466,6 +525,14 @@ ss_status ss_query_depth(ss_ctx* ctx, int32_t level, int32_t* out_level) {
   return guard([&] {
     need(ctx && out_level, SS_ERR_PARAM, "null argument");
     *out_level = ss::plan_query_depth(ctx->C, level);
+  });
+}
+
+ss_status ss_query_bytes(const ss_ctx* ctx, int32_t n_ct, int32_t level, uint64_t* bytes) {
+  return guard([&] {
+    need(ctx && bytes && n_ct >= 1, SS_ERR_PARAM, "bad argument");
+    need(level >= 1 && level <= ctx->C.L, SS_ERR_LEVEL, "bad level");
+    *bytes = ss::query_bytes_estimate(ctx->C, n_ct, level);
   });
 }
 

@@ -34,7 +34,7 @@ BufP ev_modswitch_to(Context& C, const BufP& a, int level, cudaStream_t st) {
   if (level > a->level) throw Error(SS_ERR_LEVEL, "cannot raise a level");
   if (level < 1) throw Error(SS_ERR_NOISE, "the plan needs more levels than the chain has");
   BufP out = alloc_buf(C, a->count, a->ncomp, level, a->t_exp, st);
-  if (!C.dry) op_modswitch(C, *a, a->level - level, *out, st);
+  if (!is_dry(C)) op_modswitch(C, *a, a->level - level, *out, st);
   return out;
 }
 
@@ -60,7 +60,7 @@ static BufP binary(Context& C, int op, const BufP& a0, const BufP& b0, cudaStrea
     std::swap(a, b);
   }
   BufP out = alloc_buf(C, out_count(a, b), a->ncomp, l, a->t_exp, st);
-  if (!C.dry) k_binary(C, op, *a, *b, *out, st);
+  if (!is_dry(C)) k_binary(C, op, *a, *b, *out, st);
   return out;
 }
 
@@ -69,7 +69,7 @@ BufP ev_sub(Context& C, const BufP& a, const BufP& b, cudaStream_t st) { return 
 
 BufP ev_scalar(Context& C, int op, const BufP& a, i64 c, cudaStream_t st) {
   BufP out = alloc_buf(C, a->count, a->ncomp, a->level, op == 2 ? a->t_exp - 1 : a->t_exp, st);
-  if (!C.dry) k_scalar(C, op, *a, c, *out, st);
+  if (!is_dry(C)) k_scalar(C, op, *a, c, *out, st);
   return out;
 }
 
@@ -106,7 +106,7 @@ BufP ev_lincomb(Context& C, const std::vector<std::pair<BufP, i64>>& terms, i64 
     if (acc) { ys.push_back(acc.get()); cs.push_back(1); }
     while (i < al.size() && ys.size() < 16) { ys.push_back(al[i].get()); cs.push_back(cf[i]); ++i; }
     BufP out = alloc_buf(C, cnt, 2, l, terms[0].first->t_exp, st);
-    if (!C.dry) k_lincomb(C, ys, cs, i == al.size() ? cst : 0, *out, st);
+    if (!is_dry(C)) k_lincomb(C, ys, cs, i == al.size() ? cst : 0, *out, st);
     acc = out;
   }
   return acc;
@@ -121,7 +121,7 @@ BufP ev_mul(Context& C, const BufP& a0, const BufP& b0, cudaStream_t st) {
   if (a->count != b->count) throw Error(SS_ERR_SHAPE, "batch sizes differ");
   BufP t3 = alloc_buf(C, a->count, 3, l, a->t_exp, st);
   BufP out = alloc_buf(C, a->count, 2, l - 1, a->t_exp, st);
-  if (!C.dry) {
+  if (!is_dry(C)) {
     k_tensor(C, *a, *b, *t3, st);
     op_relin_drop(C, *t3, *out, st);
   }
@@ -224,7 +224,7 @@ Term bsgs(Context& C, const std::vector<i64>& h, Powers& P, cudaStream_t st) {
         ahead[los[j]] = o;
         outs.push_back(o.get());
       }
-      if (!C.dry) k_lincomb_multi(C, ys, cs, outs, st);
+      if (!is_dry(C)) k_lincomb_multi(C, ys, cs, outs, st);
     }
   };
   std::function<Term(int, int)> rec = [&](int lo, int ln) -> Term {
@@ -422,7 +422,7 @@ BufP ev_rotate_sum(Context& C, const BufP& a, cudaStream_t st) {
   BufP s = a;
   for (int g : rotate_sum_elements(C)) {
     BufP r = alloc_buf(C, s->count, 2, s->level, s->t_exp, st);
-    if (!C.dry) op_rotate(C, *s, g, *r, st);
+    if (!is_dry(C)) op_rotate(C, *s, g, *r, st);
     s = ev_add(C, s, r, st);
     note(C, "rot " + std::to_string(g));
   }
@@ -433,7 +433,7 @@ static BufP batch_total(Context& C, const BufP& R, cudaStream_t st) {
   if (R->count == 1) return R;
   StageScope sc(C, ST_SUM, st);
   BufP out = alloc_buf(C, 1, R->ncomp, R->level, R->t_exp, st);
-  if (!C.dry) k_batch_sum(C, *R, *out, st);
+  if (!is_dry(C)) k_batch_sum(C, *R, *out, st);
   return out;
 }
 
@@ -466,7 +466,7 @@ BufP ev_query_where(Context& C, const BufP& A, const BufP& B, const std::vector<
       }
     }
     ind = ev_raise(C, ind, st);
-    if (ab_ready && !C.dry && b0 == 0) SS_CUDA(cudaStreamWaitEvent(st, ab_ready, 0));  // A and B still arriving
+    if (ab_ready && !is_dry(C) && b0 == 0) SS_CUDA(cudaStreamWaitEvent(st, ab_ready, 0));  // A and B still arriving
     BufP R;
     {
       StageScope sc(C, ST_PRODUCT, st);
@@ -485,32 +485,21 @@ BufP ev_query(Context& C, const BufP& A, const BufP& B, const BufP& C1, const Bu
   return ev_query_where(C, A, B, {QCond{SS_PRED_LT, C1, C2}}, st);
 }
 
+static thread_local const Context* t_plan_ctx = nullptr;
+
+bool is_dry(const Context& C) { return t_plan_ctx == &C; }
+PlanScope::PlanScope(const Context& C) : prev(t_plan_ctx) { t_plan_ctx = &C; }
+PlanScope::~PlanScope() { t_plan_ctx = prev; }
+
 int plan_query_depth(Context& C, int level) {
-  bool dry = C.dry, tr = C.trace_on;
-  C.dry = true;
-  C.trace_on = false;
-  int out = -1;
-  try {
-    auto mk = [&](int cnt) {
-      auto b = std::make_shared<Buf>();
-      b->count = cnt;
-      b->ncomp = 2;
-      b->level = level;
-      b->t_exp = C.r;
-      b->cap = level;
-      return b;
-    };
-    BufP x = mk(1);
-    BufP r = ev_query(C, x, x, x, x, nullptr);
-    out = r->level;
-  } catch (...) {
-    C.dry = dry;
-    C.trace_on = tr;
-    throw;
-  }
-  C.dry = dry;
-  C.trace_on = tr;
-  return out;
+  PlanScope ps(C);
+  auto x = std::make_shared<Buf>();
+  x->count = 1;
+  x->ncomp = 2;
+  x->level = level;
+  x->t_exp = C.r;
+  x->cap = level;
+  return ev_query(C, x, x, x, x, nullptr)->level;
 }
 
 }  // namespace ss
@@ -524,7 +513,7 @@ BufP ev_concat(Context& C, const std::vector<std::pair<BufP, int>>& parts, cudaS
   for (auto& p : parts) total += p.second;
   const Buf& f = *parts[0].first;
   BufP out = alloc_buf(C, total, f.ncomp, f.level, f.t_exp, st);
-  if (C.dry) return out;
+  if (is_dry(C)) return out;
   const size_t row = (size_t)f.level * C.N * 8, ct = (size_t)f.ncomp * f.level * C.N;
   size_t off = 0;
   for (auto& p : parts) {
@@ -579,7 +568,7 @@ std::vector<BufP> ev_query_multi(Context& C, const std::vector<QueryCols>& qs, c
     for (int k : n) {
       BufP s = slice_buf(R, off, k, C.N);
       BufP part = alloc_buf(C, 1, R->ncomp, R->level, R->t_exp, st);
-      if (!C.dry) k_batch_sum(C, *s, *part, st);
+      if (!is_dry(C)) k_batch_sum(C, *s, *part, st);
       parts.push_back({part, 1});
       off += k;
     }

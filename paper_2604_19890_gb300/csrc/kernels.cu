@@ -7,6 +7,7 @@
 // threads walk the coefficient index n, so every warp touches 32 consecutive
 // 8-byte words of one limb (256 B, fully coalesced).
 #include <cstdio>
+#include <cstring>
 
 #include "modarith.cuh"
 #include "philox.h"
@@ -270,38 +271,24 @@ __global__ void k_sub_scale_impl(const u64* a, long a_os, const u64* dl, long d_
 }
 
 // ---------------------------------------------------------------- key-switch inner product
-// acc[comp][m] = sum_j ext_j[m] * key_j[comp][g(m)], with ext_j[m] = d[m] on the
-// digit's own primes. 128-bit lazy sum over the digits, one Montgomery
-// reduction (the keys are stored times 2^64 mod q). One thread per (group of
-// OB ciphertexts, limb m, coefficient n): each key word is loaded once for
-// the group. The ciphertext group runs fastest over the blocks, so the blocks
-// that read one stretch of the key run back to back and all but the first
-// find it in L2.
-template <int OB>
-__global__ void __launch_bounds__(256) k_ks_ip_impl(const u64* __restrict__ d, long d_os, const u64* __restrict__ ext,
-                                                    long ext_os, const u64* __restrict__ kb,
-                                                    const u64* __restrict__ ka, int level, int alpha, int L, int T,
-                                                    u64* __restrict__ acc, long acc_os, int n_outer, int N,
-                                                    const ModDesc* mods) {
-  constexpr int V = SS_KSIP_V;  // consecutive coefficients per thread (1, 2 or 4)
-  const int ngroups = (n_outer + OB - 1) / OB;
-  const int o0 = (blockIdx.x % ngroups) * OB;
-  const int n = V * ((blockIdx.x / ngroups) * blockDim.x + threadIdx.x);
-  const int m = blockIdx.y;  // local limb over level + alpha
-  if (n >= N) return;
-  const int nb = min(OB, n_outer - o0);
-  const int g = m < level ? m : L + (m - level);
-  const Modulus md = MOD(mods, g);
+// s_c = sum_j ext_j[m] * key_j[c][g(m)] over the digits j, with ext_j[m] = d[m]
+// on the digit's own primes: 128-bit lazy sums for a group of OB ciphertexts
+// and V consecutive coefficients of limb m (each key word is loaded once for
+// the group).
+template <int OB, int V>
+__device__ __forceinline__ void ks_sums(const u64* __restrict__ d, long d_os, const u64* __restrict__ ext,
+                                        long ext_os, const u64* __restrict__ kb, const u64* __restrict__ ka, int m,
+                                        int g, int n, int nb, int level, int alpha, int T, int N, Acc128 (&s0)[OB][V],
+                                        Acc128 (&s1)[OB][V]) {
   const int dn = (level + alpha - 1) / alpha;
   const int nlx = level + alpha;
   const int jown = m < level ? m / alpha : -1;
   const u64* kbp = kb + (size_t)g * N + n;
   const u64* kap = ka + (size_t)g * N + n;
   const size_t kstride = (size_t)T * N;
-  const u64* ep = ext + o0 * ext_os + (long)m * N + n;
-  const u64* dp = d + o0 * d_os + (long)m * N + n;
+  const u64* ep = ext + (long)m * N + n;
+  const u64* dp = d + (long)m * N + n;
   const long jstride = (long)nlx * N;
-  Acc128 s0[OB][V], s1[OB][V];
 #pragma unroll
   for (int b = 0; b < OB; ++b)
 #pragma unroll
@@ -328,19 +315,145 @@ __global__ void __launch_bounds__(256) k_ks_ip_impl(const u64* __restrict__ d, l
       }
     }
   }
-  // keys carry 2^64 (Montgomery form); the sum is below dn q^2 < q 2^64
-  u64* out = acc + o0 * acc_os + (long)m * N + n;
+}
+
+// Arguments of one key-switch inner-product launch (see ks_block).
+struct KsJob {
+  int type;  // 0: reduced sums to acc; 1: fused ModDown by P; 2: fused relinearise-and-drop
+  const u64* d;
+  long d_os;
+  const u64* ext;
+  long ext_os;
+  const u64 *kb, *ka;
+  int level, alpha, L, T;
+  u64* acc;  // type 0
+  long acc_os;
+  int m0, acc_nl;
+  const u64* x;  // types 1, 2
+  long x_os;
+  int x_cap, add_c1;
+  const u64* delta;
+  int nl;
+  const u64 *pm, *scale;
+  u64* out;
+  long out_os;
+  int out_cap;
+  int n_outer, N;
+  const ModDesc* mods;
+  int gx, start;  // blocks along x; first work item (persistent launches)
+};
+
+// One block (bx, by) of a key-switch inner product: one thread per (group of
+// OB ciphertexts, limb, V coefficients); the ciphertext group runs fastest over
+// bx, so the blocks that read one stretch of the key run back to back and all
+// but the first find it in L2. The sums are reduced once (Montgomery: the keys
+// are stored times 2^64 mod q and a sum is below dn q^2 < q 2^64).
+//  TYPE 0: acc[comp][m - m0] = sum_j ext_j[m] * key_j[comp][g(m)] for the limbs
+//          m = m0 + by of the extended basis (data primes, then special
+//          primes); acc holds acc_nl limbs per component.
+//  TYPE 1, 2: the data limb m = by with the ModDown epilogue fused, so these
+//          limbs of the sum never reach memory. With acc_c[m] the reduced sum
+//          and delta_c[m] the converted correction ([ciphertext][2][nl][N],
+//          computed beforehand from the dropped limbs), scale (s, s') Shoup
+//          pairs per limb:
+//    TYPE 2 (relinearise and drop q_{l-1}):
+//          out_c[m] = ((P x_c[m] + acc_c[m]) - delta_c[m]) * (q_{l-1} P)^{-1},
+//          x_c the input's components 0 and 1, P mod q_m in pm;
+//    TYPE 1 (ModDown by P):
+//          out_c[m] = (acc_c[m] - delta_c[m]) * P^{-1} (+ x_c[m] when x is
+//          given; component 1 only when add_c1).
+template <int OB, int TYPE>
+__device__ __forceinline__ void ks_block(const KsJob& J, int bx, int by) {
+  constexpr int V = SS_KSIP_V;  // consecutive coefficients per thread (1, 2 or 4)
+  const int N = J.N;
+  const int ngroups = (J.n_outer + OB - 1) / OB;
+  const int o0 = (bx % ngroups) * OB;
+  const int n = V * ((bx / ngroups) * blockDim.x + threadIdx.x);
+  const int m = TYPE == 0 ? J.m0 + by : by;  // local limb over level + alpha
+  if (n >= N) return;
+  const int nb = min(OB, J.n_outer - o0);
+  const int g = m < J.level ? m : J.L + (m - J.level);
+  const Modulus md = MOD(J.mods, g);
+  Acc128 s0[OB][V], s1[OB][V];
+  ks_sums<OB, V>(J.d + o0 * J.d_os, J.d_os, J.ext + o0 * J.ext_os, J.ext_os, J.kb, J.ka, m, g, n, nb, J.level,
+                 J.alpha, J.T, N, s0, s1);
+  if (TYPE == 0) {
+    u64* out = J.acc + o0 * J.acc_os + (long)(m - J.m0) * N + n;
+#pragma unroll
+    for (int b = 0; b < OB; ++b) {
+      if (b < nb) {
+        u64 r0[V], r1[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          r0[v] = redc128(s0[b][v].hi, s0[b][v].lo, md.q, md.qinv);
+          r1[v] = redc128(s1[b][v].hi, s1[b][v].lo, md.q, md.qinv);
+        }
+        stv<V>(out + b * J.acc_os, r0);
+        stv<V>(out + b * J.acc_os + (long)J.acc_nl * N, r1);
+      }
+    }
+    return;
+  }
+  const u64 q = md.q;
+  const u64 sc = __ldg(J.scale + 2 * m), scp = __ldg(J.scale + 2 * m + 1);
+  u64 pw = 0, pwp = 0;
+  if (TYPE == 2) {
+    pw = __ldg(J.pm + 2 * m);
+    pwp = __ldg(J.pm + 2 * m + 1);
+  }
 #pragma unroll
   for (int b = 0; b < OB; ++b) {
     if (b < nb) {
-      u64 r0[V], r1[V];
+      const int o = o0 + b;
 #pragma unroll
-      for (int v = 0; v < V; ++v) {
-        r0[v] = redc128(s0[b][v].hi, s0[b][v].lo, md.q, md.qinv);
-        r1[v] = redc128(s1[b][v].hi, s1[b][v].lo, md.q, md.qinv);
+      for (int c = 0; c < 2; ++c) {
+        u64 dl[V], r[V];
+        ldv<V>(J.delta + ((long)(o * 2 + c) * J.nl + m) * N + n, dl);
+        u64 xv[V];
+        const bool has_x = J.x != nullptr && (TYPE == 2 || c == 0 || J.add_c1);
+        if (has_x) ldv<V>(J.x + (long)o * J.x_os + ((long)c * J.x_cap + m) * N + n, xv);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const u64 a = redc128(c ? s1[b][v].hi : s0[b][v].hi, c ? s1[b][v].lo : s0[b][v].lo, q, md.qinv);
+          if (TYPE == 2) {
+            r[v] = shoup(sub_mod(add_mod(shoup(xv[v], pw, pwp, q), a, q), dl[v], q), sc, scp, q);
+          } else {
+            r[v] = shoup(sub_mod(a, dl[v], q), sc, scp, q);
+            if (has_x) r[v] = add_mod(r[v], xv[v], q);
+          }
+        }
+        stv<V>(J.out + (long)o * J.out_os + ((long)c * J.out_cap + m) * N + n, r);
       }
-      stv<V>(out + b * acc_os, r0);
-      stv<V>(out + b * acc_os + (long)nlx * N, r1);
+    }
+  }
+}
+
+template <int OB, int TYPE>
+__global__ void __launch_bounds__(256) k_ks_ip_impl(const __grid_constant__ KsJob J) {
+  ks_block<OB, TYPE>(J, blockIdx.x, blockIdx.y);
+}
+
+// Several inner-product launches (any contexts, levels and types) as one
+// persistent launch: the blocks of all jobs form one work list that every
+// CTA walks with stride gridDim.x.
+constexpr int kMaxKsJobs = 16;
+struct KsMulti {
+  int njobs, total;
+  KsJob j[kMaxKsJobs];
+};
+
+template <int OB>
+__global__ void __launch_bounds__(256) k_ks_ip_multi(const __grid_constant__ KsMulti M) {
+  for (int t = blockIdx.x; t < M.total; t += gridDim.x) {
+    int j = 0;
+    while (j + 1 < M.njobs && t >= M.j[j + 1].start) ++j;
+    const KsJob& J = M.j[j];
+    const int local = t - J.start;
+    const int by = local / J.gx, bx = local - by * J.gx;
+    switch (J.type) {
+      case 0: ks_block<OB, 0>(J, bx, by); break;
+      case 1: ks_block<OB, 1>(J, bx, by); break;
+      default: ks_block<OB, 2>(J, bx, by); break;
     }
   }
 }
@@ -706,36 +819,19 @@ __global__ void __launch_bounds__(256) k_lincomb_multi_impl(LinMultiArgs A, int 
 }
 
 // acc_c[l-1] += P * d_c[l-1] (mod q_{l-1}) for c = 0, 1: the last data limb of
-// the extended ciphertext P*d + acc before it joins the dropped primes.
-__global__ void k_fixup_last_impl(u64* acc, long acc_os, int nx, const u64* d, long d_os, int dcap, int l,
-                                  const u64* pmod, int N, const ModDesc* mods) {
+// the extended ciphertext P*d + acc before it joins the dropped primes. That
+// limb is limb acc_limb of acc's nx limbs per component.
+__global__ void k_fixup_last_impl(u64* acc, long acc_os, int nx, int acc_limb, const u64* d, long d_os, int dcap,
+                                  int l, const u64* pmod, int N, const ModDesc* mods) {
   int o = blockIdx.y;  // (bt, c)
   int bt = o >> 1, c = o & 1;
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const int i = l - 1;
   u64 q = MOD(mods, i).q;
-  u64* a = acc + (long)bt * acc_os + ((long)c * nx + i) * N + n;
+  u64* a = acc + (long)bt * acc_os + ((long)c * nx + acc_limb) * N + n;
   u64 x = d[(long)bt * d_os + ((long)c * dcap + i) * N + n];
   *a = add_mod(*a, shoup(x, pmod[2 * i], pmod[2 * i + 1], q), q);
-}
-
-// out_c[i] = ((P d_c[i] + acc_c[i]) - delta_c[i]) * (q_{l-1} P)^{-1}, i < l-1.
-__global__ void k_drop_combine_impl(const u64* acc, long acc_os, int nx, const u64* d, long d_os, int dcap,
-                                    const u64* delta, int nl, const u64* pmod, const u64* inv, u64* out, long out_os,
-                                    int ocap, int N, const ModDesc* mods) {
-  int poly = blockIdx.y;  // (bt, c, i)
-  int i = poly % nl, c = (poly / nl) & 1, bt = poly / (2 * nl);
-  int n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  if (n >= N) return;
-  const u64 q = MOD(mods, i).q;
-  const u64 pm = pmod[2 * i], pmp = pmod[2 * i + 1], iv = inv[2 * i], ivp = inv[2 * i + 1];
-  const ulonglong2 x = ld2(d + (long)bt * d_os + ((long)c * dcap + i) * N + n);
-  const ulonglong2 s = ld2(acc + (long)bt * acc_os + ((long)c * nx + i) * N + n);
-  const ulonglong2 dl = ld2(delta + ((long)(bt * 2 + c) * nl + i) * N + n);
-  const u64 v0 = sub_mod(add_mod(shoup(x.x, pm, pmp, q), s.x, q), dl.x, q);
-  const u64 v1 = sub_mod(add_mod(shoup(x.y, pm, pmp, q), s.y, q), dl.y, q);
-  st2(out + (long)bt * out_os + ((long)c * ocap + i) * N + n, shoup(v0, iv, ivp, q), shoup(v1, iv, ivp, q));
 }
 
 // out[g] = a[g]^2 for every prime g (evaluation form)
@@ -763,22 +859,12 @@ __global__ void k_batch_sum_impl(const u64* a, u64* out, int count, int ncomp, i
 }  // namespace
 
 // ======================================================================= launchers
-void k_fixup_last(Context& C, u64* acc, long acc_os, int nx, const Buf& d, int l, const u64* pmod, int B,
-                  cudaStream_t st) {
+void k_fixup_last(Context& C, u64* acc, long acc_os, int nx, int acc_limb, const Buf& d, int l, const u64* pmod,
+                  int B, cudaStream_t st) {
   TIMED(KC_ELEM, 3.0 * 2 * B * C.N * 8.0,
-        k_fixup_last_impl<<<grid_for(C.N, 2 * B), TPB, 0, st>>>(acc, acc_os, nx, d.data, (long)d.ncomp * d.cap * C.N,
-                                                                 d.cap, l, pmod, C.N, C.d_mod));
-  LAUNCHED();
-}
-
-void k_drop_combine(Context& C, const u64* acc, long acc_os, int nx, const Buf& d, const u64* delta, int nl,
-                    const u64* pmod, const u64* inv, Buf& out, int B, cudaStream_t st) {
-  TIMED(KC_SUBSCALE, 4.0 * 2 * B * nl * C.N * 8.0,
-        k_drop_combine_impl<<<grid_for(C.N / 2, 2 * B * nl), TPB, 0, st>>>(acc, acc_os, nx, d.data,
-                                                                        (long)d.ncomp * d.cap * C.N, d.cap, delta, nl,
-                                                                        pmod, inv, out.data,
-                                                                        (long)out.ncomp * out.cap * C.N, out.cap, C.N,
-                                                                        C.d_mod));
+        k_fixup_last_impl<<<grid_for(C.N, 2 * B), TPB, 0, st>>>(acc, acc_os, nx, acc_limb, d.data,
+                                                                 (long)d.ncomp * d.cap * C.N, d.cap, l, pmod, C.N,
+                                                                 C.d_mod));
   LAUNCHED();
 }
 
@@ -934,16 +1020,116 @@ void k_to_montgomery(Context& C, u64* data, int npoly, cudaStream_t st) {
   LAUNCHED();
 }
 
-void k_ks_ip(Context& C, const u64* d, long d_os, const u64* ext, long ext_os, const KeyDev& K, int level, u64* acc,
-             long acc_os, int n_outer, cudaStream_t st) {
-  const int dn = (level + C.alpha - 1) / C.alpha;
-  constexpr int OB = SS_KSIP_OB;
+static KsJob ks_job(Context& C, int type, const u64* d, long d_os, const u64* ext, long ext_os, const KeyDev& K,
+                    int level, int n_outer, int nlimbs) {
+  KsJob J{};
+  J.type = type;
+  J.d = d;
+  J.d_os = d_os;
+  J.ext = ext;
+  J.ext_os = ext_os;
+  J.kb = K.b;
+  J.ka = K.a;
+  J.level = level;
+  J.alpha = C.alpha;
+  J.L = C.L;
+  J.T = C.ntot;
+  J.n_outer = n_outer;
+  J.N = C.N;
+  J.mods = C.d_mod;
   const int nx_blocks = (C.N / SS_KSIP_V + TPB - 1) / TPB;
-  const dim3 grid((unsigned)(((n_outer + OB - 1) / OB) * nx_blocks), (unsigned)(level + C.alpha));
-  TIMED(KC_KSIP, ((double)dn * (level + C.alpha) * (n_outer + 2.0) + 2.0 * (level + C.alpha) * n_outer) * (double)C.N * 8.0,
-        k_ks_ip_impl<OB><<<grid, TPB, 0, st>>>(d, d_os, ext, ext_os, K.b, K.a, level, C.alpha, C.L, C.ntot, acc,
-                                               acc_os, n_outer, C.N, C.d_mod));
+  J.gx = ((n_outer + SS_KSIP_OB - 1) / SS_KSIP_OB) * nx_blocks;
+  (void)nlimbs;
+  return J;
+}
+
+static_assert(sizeof(KsJob) <= sizeof(KsReq::job), "inner-product job fits the merge request");
+
+static void ks_launch(Context& C, const KsJob& J, int nlimbs, double bytes, cudaStream_t st) {
+  if (ks_merger()) {
+    KsReq r;
+    r.C = &C;
+    r.nlimbs = nlimbs;
+    std::memcpy(r.job, &J, sizeof(J));
+    ks_merger()->submit_ks(r, st);
+    return;
+  }
+  constexpr int OB = SS_KSIP_OB;
+  const dim3 grid((unsigned)J.gx, (unsigned)nlimbs);
+  switch (J.type) {
+    case 0: TIMED(KC_KSIP, bytes, (k_ks_ip_impl<OB, 0><<<grid, TPB, 0, st>>>(J))); break;
+    case 1: TIMED(KC_KSIP, bytes, (k_ks_ip_impl<OB, 1><<<grid, TPB, 0, st>>>(J))); break;
+    default: TIMED(KC_KSIP, bytes, (k_ks_ip_impl<OB, 2><<<grid, TPB, 0, st>>>(J))); break;
+  }
   LAUNCHED();
+}
+
+void k_ks_ip(Context& C, const u64* d, long d_os, const u64* ext, long ext_os, const KeyDev& K, int level, u64* acc,
+             long acc_os, int n_outer, cudaStream_t st, int m0, int nlimbs) {
+  const int dn = (level + C.alpha - 1) / C.alpha;
+  if (nlimbs < 0) nlimbs = level + C.alpha - m0;
+  KsJob J = ks_job(C, 0, d, d_os, ext, ext_os, K, level, n_outer, nlimbs);
+  J.acc = acc;
+  J.acc_os = acc_os;
+  J.m0 = m0;
+  J.acc_nl = nlimbs;
+  // each key limb is read once per launch; ext limbs and the sums once per ciphertext
+  ks_launch(C, J, nlimbs, ((double)dn * nlimbs * (n_outer + 2.0) + 2.0 * nlimbs * n_outer) * (double)C.N * 8.0, st);
+}
+
+void k_ks_ip_fused(Context& C, const u64* d, long d_os, const u64* ext, long ext_os, const KeyDev& K, int level,
+                   int nlimbs, bool drop, const Buf* x, bool add_c1, const u64* delta, int nl, const u64* pm,
+                   const u64* scale, Buf& out, int n_outer, cudaStream_t st) {
+  const int dn = (level + C.alpha - 1) / C.alpha;
+  KsJob J = ks_job(C, drop ? 2 : 1, d, d_os, ext, ext_os, K, level, n_outer, nlimbs);
+  J.x = x ? x->data : nullptr;
+  J.x_os = x ? (long)x->ncomp * x->cap * C.N : 0;
+  J.x_cap = x ? x->cap : 0;
+  J.add_c1 = add_c1 ? 1 : 0;
+  J.delta = delta;
+  J.nl = nl;
+  J.pm = pm;
+  J.scale = scale;
+  J.out = out.data;
+  J.out_os = (long)out.ncomp * out.cap * C.N;
+  J.out_cap = out.cap;
+  const int nx = x ? (drop || add_c1 ? 2 : 1) : 0;
+  ks_launch(C, J, nlimbs,
+            ((double)dn * nlimbs * (n_outer + 2.0) + (4.0 + nx) * nlimbs * n_outer) * (double)C.N * 8.0, st);
+}
+
+KsMerger*& ks_merger() {
+  static thread_local KsMerger* m = nullptr;
+  return m;
+}
+
+// Jobs of several lanes as persistent launches of at most kMaxKsJobs jobs each.
+void ks_multi(const std::vector<KsReq>& reqs, cudaStream_t st) {
+  static int resident = 0;
+  if (!resident) {
+    int dev = 0, sms = 0, per = 0;
+    SS_CUDA(cudaGetDevice(&dev));
+    SS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ks_ip_multi<SS_KSIP_OB>, TPB, 0));
+    resident = sms * std::max(1, per);
+  }
+  for (size_t b0 = 0; b0 < reqs.size(); b0 += kMaxKsJobs) {
+    const size_t b1 = std::min(reqs.size(), b0 + kMaxKsJobs);
+    KsMulti M;
+    M.njobs = 0;
+    M.total = 0;
+    for (size_t r = b0; r < b1; ++r) {
+      KsJob J;
+      std::memcpy(&J, reqs[r].job, sizeof(J));
+      J.start = M.total;
+      M.total += J.gx * reqs[r].nlimbs;
+      M.j[M.njobs++] = J;
+    }
+    if (M.total == 0) continue;
+    k_ks_ip_multi<SS_KSIP_OB><<<std::min(M.total, resident), TPB, 0, st>>>(M);
+    SS_CUDA(cudaGetLastError());
+    ++reqs[b0].C->launches;
+  }
 }
 
 void k_automorph(Context& C, const Buf& a, int g, Buf& out, cudaStream_t st) {

@@ -214,23 +214,24 @@ __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, in
 // less than 2q to the bound, so inputs below 4q leave a log2 N <= 16 stage
 // transform below 36q < 2^64 (primes below 2^58), and the last phase brings
 // every word back to [0, q) once (reduce_lazy).
-template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC = false>
-__global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_ntt16(NttArgs A, int logCPB, int m0) {
+// One CTA tile (`tile` of polynomial `poly`) of one phase; the body of the
+// per-transform kernel k_ntt16 and of the persistent kernel k_ntt16_multi.
+template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC>
+__device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0, int tile, int poly) {
   extern __shared__ u64 sm[];
   u64* ptr;
   int pidx;
-  if (!poly_of(A, blockIdx.y, ptr, pidx)) return;
+  if (!poly_of(A, poly, ptr, pidx)) return;
   const u64 q = A.mods[pidx].q;
   const ulonglong2* tw = reinterpret_cast<const ulonglong2*>(A.tw + (size_t)pidx * 4 * A.N + (FWD ? 0 : 2 * A.N));
   constexpr int S = 1 << LOGS;
   const int CPB = 1 << logCPB, W = S << logCPB;
   const int tid = threadIdx.x, T = blockDim.x;
-  const int tile = blockIdx.x;
   const int stride = A.N >> LOGS;
   u64* gbase = COLS ? ptr + (long)tile * CPB : ptr + (long)tile * W;
   const u64* gsrc = gbase;
   if (SRC) {  // same polynomial, read from the out-of-place source
-    const int i = blockIdx.y / A.n_outer, o = blockIdx.y % A.n_outer;
+    const int i = poly / A.n_outer, o = poly % A.n_outer;
     const u64* rb = A.src + (long)o * A.src_os + (long)i * A.N;
     gsrc = COLS ? rb + (long)tile * CPB : rb + (long)tile * W;
   }
@@ -381,6 +382,55 @@ __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_nt
   }
 }
 
+template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC = false>
+__global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_ntt16(NttArgs A, int logCPB, int m0) {
+  ntt16_tile<FWD, COLS, LAST, LOGS, SRC>(A, logCPB, m0, blockIdx.x, blockIdx.y);
+}
+
+// ---------------------------------------------------------------- persistent multi-transform phase
+// One phase of up to kMaxNttJobs transforms of any ring dimensions N >= 8192
+// (each job: one polynomial set of one context, with its own moduli and
+// twiddles) in one launch: the tiles of all jobs form one work list, job j
+// owning tiles [start_j, start_j + polys_j * tiles_j); every CTA of a grid
+// sized to the resident CTAs of the device walks the list with stride
+// gridDim.x. All jobs share the tile size (blockDim = tile / 16), so tiles
+// of different N run side by side; the sub-transform length of a job's phase
+// (2^logS, 5 <= logS <= 8) selects the instantiation per tile.
+constexpr int kMaxNttJobs = 24;
+struct NttJob {
+  NttArgs A;
+  int logS, logCPB, m0, tiles, start;
+};
+struct NttMulti {
+  int njobs, total;
+  NttJob j[kMaxNttJobs];
+};
+
+// a separate function per instantiation, so each keeps its own register allocation
+template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC>
+__device__ __noinline__ void ntt16_tile_fn(const NttArgs& A, int logCPB, int m0, int tile, int poly) {
+  ntt16_tile<FWD, COLS, LAST, LOGS, SRC>(A, logCPB, m0, tile, poly);
+}
+
+template <bool FWD, bool COLS, bool LAST, bool SRC>
+__global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I)
+    k_ntt16_multi(const __grid_constant__ NttMulti M) {
+  for (int t = blockIdx.x; t < M.total; t += gridDim.x) {
+    int j = 0;
+    while (j + 1 < M.njobs && t >= M.j[j + 1].start) ++j;
+    const NttJob& J = M.j[j];
+    const int local = t - J.start;
+    const int poly = local / J.tiles, tile = local - poly * J.tiles;
+    switch (J.logS) {
+      case 5: ntt16_tile_fn<FWD, COLS, LAST, 5, SRC>(J.A, J.logCPB, J.m0, tile, poly); break;
+      case 6: ntt16_tile_fn<FWD, COLS, LAST, 6, SRC>(J.A, J.logCPB, J.m0, tile, poly); break;
+      case 7: ntt16_tile_fn<FWD, COLS, LAST, 7, SRC>(J.A, J.logCPB, J.m0, tile, poly); break;
+      default: ntt16_tile_fn<FWD, COLS, LAST, 8, SRC>(J.A, J.logCPB, J.m0, tile, poly); break;
+    }
+    __syncthreads();  // the next tile reuses the shared memory
+  }
+}
+
 template <bool FWD, bool COLS, bool LAST, bool SRC = false>
 void launch16(int logS, dim3 g, int thr, size_t smem, cudaStream_t st, const NttArgs& A, int logc, int m0) {
   switch (logS) {
@@ -423,19 +473,22 @@ double active_polys(const PolySet& s) {
   return n;
 }
 
-int ilog2(int x) {
-  int l = 0;
-  while ((1 << l) < x) ++l;
-  return l;
-}
-
 }  // namespace
+
+NttMerger*& ntt_merger() {
+  static thread_local NttMerger* m = nullptr;
+  return m;
+}
 
 // src: optional out-of-place source read by the first phase (inverse only)
 static void launch(Context& C, const PolySet& s, bool fwd, cudaStream_t st, const u64* src = nullptr,
                    long src_os = 0) {
   int npoly = s.n_outer * s.nl;
   if (npoly == 0) return;
+  if (ntt_merger() && C.N > TILE && !is_dry(C)) {
+    ntt_merger()->submit(NttReq{&C, s, src, src_os}, fwd, st);
+    return;
+  }
   if (npoly > 65535) throw Error(SS_ERR_SHAPE, "too many polynomials in one transform");
   NttArgs A = make_args(C, s);
   const int N = C.N, logN = C.logN;
@@ -475,6 +528,74 @@ static void launch(Context& C, const PolySet& s, bool fwd, cudaStream_t st, cons
     kt_end(C, kr, KC_NTT, 16.0 * N * active_polys(s), st);
   }
   SS_CUDA(cudaGetLastError());
+}
+
+static int resident_ctas() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0, sms = 0;
+    SS_CUDA(cudaGetDevice(&dev));
+    SS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    n = sms * SS_NTT_MINB_F;
+  }
+  return n;
+}
+
+template <bool FWD, bool COLS, bool LAST, bool SRC>
+static void launch_multi(const NttMulti& M, int thr, size_t smem, cudaStream_t st) {
+  if (M.total == 0) return;
+  const int grid = std::min(M.total, resident_ctas());
+  k_ntt16_multi<FWD, COLS, LAST, SRC><<<grid, thr, smem, st>>>(M);
+  SS_CUDA(cudaGetLastError());
+}
+
+void ntt_multi(const std::vector<NttReq>& reqs, bool fwd, int tile_log, cudaStream_t st) {
+  const int tl = tile_log == 11 ? 11 : 12, tile = 1 << tl, thr = tile / 16;
+  const size_t smem = (size_t)(tile + tile / 8) * 8;
+  for (size_t b0 = 0; b0 < reqs.size(); b0 += kMaxNttJobs) {
+    const size_t b1 = std::min(reqs.size(), b0 + kMaxNttJobs);
+    // phase 1 (columns forward, chunks inverse) and phase 2 of every job
+    NttMulti P1, P2;
+    P1.njobs = P2.njobs = 0;
+    P1.total = P2.total = 0;
+    double bytes = 0;
+    for (size_t r = b0; r < b1; ++r) {
+      const NttReq& q = reqs[r];
+      Context& C = *q.C;
+      if (C.N < 8192) throw Error(SS_ERR_PARAM, "merged transforms need N >= 8192");
+      const int npoly = q.s.n_outer * q.s.nl;
+      if (npoly == 0) continue;
+      NttArgs A = make_args(C, q.s);
+      const int log1 = C.logN - 8, logc1 = tl - log1, logc2 = tl - 8;
+      NttJob cols{A, log1, logc1, 1, 1 << (8 - logc1), 0};
+      NttJob chunks{A, 8, logc2, 1 << log1, 1 << (log1 - logc2), 0};
+      if (!fwd) {  // the chunk phase reads the source (the polynomials themselves when in place)
+        chunks.A.src = q.src ? q.src : q.s.base;
+        chunks.A.src_os = q.src ? q.src_os : q.s.outer_stride;
+      }
+      NttJob& j1 = P1.j[P1.njobs++];
+      NttJob& j2 = P2.j[P2.njobs++];
+      j1 = fwd ? cols : chunks;
+      j2 = fwd ? chunks : cols;
+      j1.start = P1.total;
+      j2.start = P2.total;
+      P1.total += npoly * j1.tiles;
+      P2.total += npoly * j2.tiles;
+      bytes += 16.0 * C.N * active_polys(q.s);
+    }
+    if (P1.njobs == 0) continue;
+    Context& C0 = *reqs[b0].C;
+    int kr = kt_begin(C0, st);
+    if (fwd) {
+      launch_multi<true, true, false, false>(P1, thr, smem, st);
+      launch_multi<true, false, true, false>(P2, thr, smem, st);
+    } else {
+      launch_multi<false, false, false, true>(P1, thr, smem, st);
+      launch_multi<false, true, true, false>(P2, thr, smem, st);
+    }
+    C0.launches += 2;
+    kt_end(C0, kr, KC_NTT, bytes, st);
+  }
 }
 
 void ntt_forward(Context& C, const PolySet& s, cudaStream_t st) { launch(C, s, true, st); }

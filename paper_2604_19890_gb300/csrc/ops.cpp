@@ -40,7 +40,7 @@ BufP alloc_buf(Context& C, int count, int ncomp, int level, int t_exp, cudaStrea
   b->cap = level;
   b->stream = s;
   b->bytes = (size_t)count * ncomp * level * C.N * sizeof(u64);
-  if (!C.dry) {
+  if (!is_dry(C)) {
     b->data = static_cast<u64*>(pool_alloc(b->bytes, s));
     b->owned = true;
   }
@@ -97,31 +97,23 @@ static void keyswitch_impl(Context& C, const Buf& in, int comp, const KeyDev& K,
   ps.skip_level = l;
   ntt_forward(C, ps, st);
   pool_free(dc, st);
-  // 3. inner product with the key, both components
-  const long acc_os = 2L * nx * N;
-  u64* acc = static_cast<u64*>(pool_alloc((size_t)B * acc_os * 8, st));
-  k_ks_ip(C, d, in_os, ext, ext_os, K, l, acc, acc_os, B, st);
-  pool_free(ext, st);
-  // 4. ModDown: delta = t * conv_P->Q(t^-1 acc mod P); out = (acc - delta) * P^-1 (+ addend)
-  ntt_inverse(C, PolySet{acc + (size_t)l * N, (long)nx * N, 2 * B, a, C.L, 0}, st);
+  // 3. inner product with the key on the special primes (both components)
+  const long sp_os = 2L * a * N;
+  u64* acc = static_cast<u64*>(pool_alloc((size_t)B * sp_os * 8, st));
+  k_ks_ip(C, d, in_os, ext, ext_os, K, l, acc, sp_os, B, st, l, a);
+  // 4. ModDown: delta = t * conv_P->Q(t^-1 acc mod P) on the data primes
+  ntt_inverse(C, PolySet{acc, (long)a * N, 2 * B, a, C.L, 0}, st);
   u64* delta = static_cast<u64*>(pool_alloc((size_t)2 * B * l * N * 8, st));
   const u64* c1 = C.d_tables + C.off_md_c1[in.t_exp];
   const u64* c2 = C.d_tables + C.off_md_c2;
   const u64* post = C.d_tmod + (size_t)in.t_exp * C.ntot * 2;
-  k_bconv(C, acc + (size_t)l * N, (long)nx * N, a, C.L, c1, c2, delta, (long)l * N, l, l, 0, 0, post, 2 * B, st);
+  k_bconv(C, acc, (long)a * N, a, C.L, c1, c2, delta, (long)l * N, l, l, 0, 0, post, 2 * B, st);
   ntt_forward(C, PolySet{delta, (long)l * N, 2 * B, l, 0, l}, st);
-  const u64* pinv = C.d_tables + C.off_md_pinv;
-  for (int c = 0; c < 2; ++c) {
-    const u64* add = nullptr;
-    long add_os = 0;
-    if (addend && (c == 0 || add_c1)) {
-      add = addend->data + (size_t)c * addend->cap * N;
-      add_os = (long)addend->ncomp * addend->cap * N;
-    }
-    k_sub_scale(C, acc + (size_t)c * nx * N, acc_os, delta + (size_t)c * l * N, 2L * l * N, pinv, add, add_os,
-                out.data + (size_t)c * out.cap * N, (long)out.ncomp * out.cap * N, l, B, st);
-  }
   pool_free(acc, st);
+  // 5. inner product on the data primes fused with out = (acc - delta) P^-1 (+ addend)
+  const u64* pinv = C.d_tables + C.off_md_pinv;
+  k_ks_ip_fused(C, d, in_os, ext, ext_os, K, l, l, false, addend, add_c1, delta, l, nullptr, pinv, out, B, st);
+  pool_free(ext, st);
   pool_free(delta, st);
 }
 
@@ -173,24 +165,27 @@ void op_relin_drop(Context& C, const Buf& in, Buf& out, cudaStream_t st) {
   ps.skip_level = l;
   ntt_forward(C, ps, st);
   pool_free(dc, st);
-  const long acc_os = 2L * nx * N;
-  u64* acc = static_cast<u64*>(pool_alloc((size_t)B * acc_os * 8, st));
-  k_ks_ip(C, d, in_os, ext, ext_os, C.rlk, l, acc, acc_os, B, st);
-  pool_free(ext, st);
-  // 4. fused ModDown by q_{l-1} P
+  // 3. inner product on q_{l-1} and the special primes (the limbs the ModDown drops)
+  const int ns = a + 1;
+  const long sp_os = 2L * ns * N;
+  u64* acc = static_cast<u64*>(pool_alloc((size_t)B * sp_os * 8, st));
+  k_ks_ip(C, d, in_os, ext, ext_os, C.rlk, l, acc, sp_os, B, st, l - 1, ns);
+  // 4. ModDown by q_{l-1} P: delta = t conv([t^-1 (P d + acc)]_D) on the first l-1 primes
   const u64* pmod = C.d_tables + C.off_pmod;
-  k_fixup_last(C, acc, acc_os, nx, in, l, pmod, B, st);
-  ntt_inverse(C, PolySet{acc + (size_t)(l - 1) * N, (long)nx * N, 2 * B, a + 1, l - 1, 1}, st);
+  k_fixup_last(C, acc, sp_os, ns, 0, in, l, pmod, B, st);
+  ntt_inverse(C, PolySet{acc, (long)ns * N, 2 * B, ns, l - 1, 1}, st);
   u64* delta = static_cast<u64*>(pool_alloc((size_t)2 * B * nl * N * 8, st));
   const u64* c2 = C.d_tables + C.off_rd[l];
   const u64* inv = c2 + (size_t)(a + 1) * C.ntot;
   const u64* c1 = C.d_tables + C.off_rd_c1.at({l, in.t_exp});
   const u64* post = C.d_tmod + (size_t)in.t_exp * C.ntot * 2;
-  k_bconv(C, acc + (size_t)(l - 1) * N, (long)nx * N, a + 1, l - 1, c1, c2, delta, (long)nl * N, nl, nl, 0, 0, post,
-          2 * B, st, 1);
+  k_bconv(C, acc, (long)ns * N, ns, l - 1, c1, c2, delta, (long)nl * N, nl, nl, 0, 0, post, 2 * B, st, 1);
   ntt_forward(C, PolySet{delta, (long)nl * N, 2 * B, nl, 0, nl}, st);
-  k_drop_combine(C, acc, acc_os, nx, in, delta, nl, pmod, inv, out, B, st);
   pool_free(acc, st);
+  // 5. inner product on the kept primes fused with the combine
+  //    out_c = ((P d_c + acc_c) - delta_c) (q_{l-1} P)^-1
+  k_ks_ip_fused(C, d, in_os, ext, ext_os, C.rlk, l, nl, true, &in, true, delta, nl, pmod, inv, out, B, st);
+  pool_free(ext, st);
   pool_free(delta, st);
 }
 
@@ -360,7 +355,7 @@ static cudaEvent_t kt_event(Context& C) {
 }
 
 int kt_begin(Context& C, cudaStream_t st) {
-  if (!C.kt.on) return -1;
+  if (!C.kt.on || ntt_merger()) return -1;  // no per-launch timing in the batched form's lanes
   KTimer::Rec r;
   r.a = kt_event(C);
   r.b = kt_event(C);
@@ -381,7 +376,7 @@ void kt_end(Context& C, int rec, int cls, double bytes, cudaStream_t st) {
 }
 
 int stage_begin(Context& C, int stage, cudaStream_t st) {
-  if (!C.kt.on || C.dry) return -1;
+  if (!C.kt.on || is_dry(C)) return -1;
   KTimer::SRec r;
   r.a = kt_event(C);
   r.b = kt_event(C);

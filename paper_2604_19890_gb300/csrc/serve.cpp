@@ -1,14 +1,17 @@
-// Served form: a request loop over one context with continuous batching.
+// Served form: a request loop over one or several contexts (parameter sets,
+// e.g. N = 2^15 with 257^2 and N = 2^16 with 257^3) with continuous batching.
 //
-// Queries arrive through ss_server_submit at any time. `workers` host threads
-// each own a CUDA stream. A worker that is free takes the oldest pending query
-// and every other pending query of the same shape (level, plaintext modulus)
-// that still fits the HBM budget, up to `max_merge`, joins them into one batch
-// (ev_query_multi) and runs it on its stream while the other workers run
-// theirs, so queries that arrive while others are on the GPU are admitted as
-// soon as a worker and memory free up and their work overlaps on the device.
-// Keys and tables stay resident in the context. Every result equals the same
-// query run alone (the schedule is per ciphertext).
+// Queries arrive through ss_server_submit(_to) at any time, each for one of
+// the server's contexts. `workers` host threads each own a CUDA stream. A
+// worker that is free takes the oldest pending query and every other pending
+// query of the same context and shape (level, plaintext modulus) that still
+// fits the one HBM budget shared by all contexts, up to `max_merge`, joins
+// them into one batch (ev_query_multi) and runs it on its stream while the
+// other workers run theirs, so queries of any ring dimension that arrive while
+// others are on the GPU are admitted as soon as a worker and memory free up and
+// their work overlaps on the device. Keys and tables of every context stay
+// resident. Every result equals the same query run alone (the schedule is per
+// ciphertext).
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -24,6 +27,7 @@ typedef std::chrono::steady_clock Clock;
 
 struct Request {
   uint64_t id;
+  int ctx = 0;
   QueryCols cols;
   ss_ct* out;
   size_t bytes;
@@ -34,7 +38,7 @@ struct Request {
 };
 
 struct Server {
-  Context* C = nullptr;
+  std::vector<Context*> ctxs;
   int max_merge = 1;
   size_t budget = 0, inflight = 0, peak_inflight = 0;
   std::mutex mu;
@@ -47,7 +51,7 @@ struct Server {
   std::vector<cudaStream_t> streams;
 
   static bool same_shape(const Request& a, const Request& b) {
-    return a.cols.A->level == b.cols.A->level && a.cols.A->t_exp == b.cols.A->t_exp;
+    return a.ctx == b.ctx && a.cols.A->level == b.cols.A->level && a.cols.A->t_exp == b.cols.A->t_exp;
   }
 
   void worker(int w) {
@@ -86,6 +90,7 @@ struct Server {
       ss_status status = SS_OK;
       std::string err;
       try {
+        Context* C = ctxs[group[0]->ctx];
         std::vector<QueryCols> qs;
         for (auto& r : group) qs.push_back(r->cols);
         auto res = ev_query_multi(*C, qs, st);
@@ -143,18 +148,22 @@ void set_error(const std::string& m);
 
 extern "C" {
 
-ss_status ss_server_create(ss_ctx* ctx, int32_t workers, int32_t max_merge, uint64_t hbm_budget, ss_server** out) {
+ss_status ss_server_create_multi(ss_ctx* const* ctxs, int32_t nctx, int32_t workers, int32_t max_merge,
+                                 uint64_t hbm_budget, ss_server** out) {
   try {
-    if (!ctx || !out || workers < 1 || workers > 16 || max_merge < 1) throw ss::Error(SS_ERR_PARAM, "bad argument");
-    ss::Context& C = ss::context_of(ctx);
-    if (!C.have_keys) throw ss::Error(SS_ERR_PARAM, "no keys");
+    if (!ctxs || nctx < 1 || !out || workers < 1 || workers > 16 || max_merge < 1)
+      throw ss::Error(SS_ERR_PARAM, "bad argument");
+    for (int i = 0; i < nctx; ++i) {
+      if (!ctxs[i]) throw ss::Error(SS_ERR_PARAM, "null context");
+      if (!ss::context_of(ctxs[i]).have_keys) throw ss::Error(SS_ERR_PARAM, "no keys");
+    }
     if (hbm_budget == 0) {
       size_t fr = 0, tot = 0;
       SS_CUDA(cudaMemGetInfo(&fr, &tot));
       hbm_budget = fr / 10 * 8;
     }
     auto* s = new ss_server();
-    s->S.C = &C;
+    for (int i = 0; i < nctx; ++i) s->S.ctxs.push_back(&ss::context_of(ctxs[i]));
     s->S.max_merge = max_merge;
     s->S.budget = hbm_budget;
     int dev = 0;
@@ -177,11 +186,16 @@ ss_status ss_server_create(ss_ctx* ctx, int32_t workers, int32_t max_merge, uint
   }
 }
 
-ss_status ss_server_submit(ss_server* s, const ss_ct* A, const ss_ct* B, const ss_ct* C1, const ss_ct* C2, ss_ct* out,
-                           uint64_t* ticket) {
+ss_status ss_server_create(ss_ctx* ctx, int32_t workers, int32_t max_merge, uint64_t hbm_budget, ss_server** out) {
+  return ss_server_create_multi(&ctx, 1, workers, max_merge, hbm_budget, out);
+}
+
+ss_status ss_server_submit_to(ss_server* s, int32_t ctx_index, const ss_ct* A, const ss_ct* B, const ss_ct* C1,
+                              const ss_ct* C2, ss_ct* out, uint64_t* ticket) {
   try {
     if (!s || !A || !B || !C1 || !C2 || !out || !ticket) throw ss::Error(SS_ERR_PARAM, "null argument");
-    ss::Context& C = *s->S.C;
+    if (ctx_index < 0 || ctx_index >= (int)s->S.ctxs.size()) throw ss::Error(SS_ERR_PARAM, "context index out of range");
+    ss::Context& C = *s->S.ctxs[ctx_index];
     for (const ss_ct* c : {A, B, C1, C2})
       if (!c->data || c->level < 2 || c->level > C.L || c->t_exp != C.r || c->ncomp != 2)
         throw ss::Error(SS_ERR_PARAM, "columns must be 2-component ciphertexts at t = p^r");
@@ -190,7 +204,10 @@ ss_status ss_server_submit(ss_server* s, const ss_ct* A, const ss_ct* B, const s
     if (B->count != A->count || C1->count != A->count || (C2->count != A->count && C2->count != 1))
       throw ss::Error(SS_ERR_SHAPE, "column batch sizes differ");
     if (out->count != 1 || !out->data) throw ss::Error(SS_ERR_SHAPE, "result buffer must hold one ciphertext");
+    // the plan first: a chain too short for the query is rejected at submission
+    ss::plan_query_depth(C, A->level);
     auto r = std::make_shared<ss::Request>();
+    r->ctx = ctx_index;
     r->cols = {ss::view_buf(*A), ss::view_buf(*B), ss::view_buf(*C1), ss::view_buf(*C2)};
     r->out = out;
     r->bytes = ss::query_bytes_estimate(C, A->count, A->level);
@@ -208,6 +225,11 @@ ss_status ss_server_submit(ss_server* s, const ss_ct* A, const ss_ct* B, const s
     ss::set_error(e.what());
     return e.code;
   }
+}
+
+ss_status ss_server_submit(ss_server* s, const ss_ct* A, const ss_ct* B, const ss_ct* C1, const ss_ct* C2, ss_ct* out,
+                           uint64_t* ticket) {
+  return ss_server_submit_to(s, 0, A, B, C1, C2, out, ticket);
 }
 
 // Bounded wait: SS_ERR_TIMEOUT if the ticket is not done within timeout_ms

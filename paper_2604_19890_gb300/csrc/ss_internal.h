@@ -156,7 +156,6 @@ struct Context {
   // evaluator
   int batch = 8;
   int ntt_tile_log = SS_NTT_TILE_LOG;  // words per CTA tile of the two-phase transform: 2^11 or 2^12
-  bool dry = false;  // plan only: track levels, launch nothing
   bool trace_on = false;
   std::vector<std::string> trace;
   std::atomic<unsigned long long> launches{0};  // shared by server worker threads
@@ -187,6 +186,40 @@ void ntt_inverse(Context& C, const PolySet& s, cudaStream_t st);
 // Inverse transform of the polynomials at src (same shape as s, outer stride
 // src_os) written to s: the first phase reads src, so src is left unchanged.
 void ntt_inverse_from(Context& C, const PolySet& s, const u64* src, long src_os, cudaStream_t st);
+// Transforms of several contexts (ring dimensions N >= 8192) merged: each
+// phase of all of them runs as one persistent launch over their tiles.
+struct NttReq {
+  Context* C;
+  PolySet s;
+  const u64* src;  // out-of-place source of an inverse transform, or null
+  long src_os;
+};
+void ntt_multi(const std::vector<NttReq>& reqs, bool fwd, int tile_log, cudaStream_t st);
+// Collects the transforms that several cooperating host threads issue (the
+// batched form's lanes) and launches them merged. While a thread's hook is
+// set, its transforms of rings N >= 8192 go to submit(), which returns once
+// the merged launch that includes them is enqueued (ordered after st and
+// before st's later work).
+struct NttMerger {
+  virtual void submit(const NttReq& r, bool fwd, cudaStream_t st) = 0;
+  virtual ~NttMerger() {}
+};
+NttMerger*& ntt_merger();  // this thread's hook (null: launch directly)
+// One key-switch inner-product launch, recorded for merging (its argument
+// block is private to the kernels' file).
+struct KsReq {
+  Context* C;
+  int nlimbs;
+  alignas(16) unsigned char job[256];
+};
+// Inner products of several lanes (any contexts, levels, epilogues) as
+// persistent launches over all their blocks.
+void ks_multi(const std::vector<KsReq>& reqs, cudaStream_t st);
+struct KsMerger {
+  virtual void submit_ks(const KsReq& r, cudaStream_t st) = 0;
+  virtual ~KsMerger() {}
+};
+KsMerger*& ks_merger();  // this thread's hook (null: launch directly)
 
 void k_binary(Context& C, int op, const Buf& a, const Buf& b, Buf& out, cudaStream_t st);  // 0 add, 1 sub
 void k_scalar(Context& C, int op, const Buf& a, i64 c, Buf& out, cudaStream_t st);       // 0 mul, 1 add(c0), 2 mul p^-1
@@ -196,15 +229,21 @@ void k_tensor(Context& C, const Buf& a, const Buf& b, Buf& out, cudaStream_t st)
 void k_bconv(Context& C, const u64* src, long src_os, int ns, int sp0, const u64* c1, const u64* c2, u64* dst,
              long dst_os, int nd, int nq, int skip_lo, int skip_hi, const u64* post, int n_outer, cudaStream_t st,
              int nsq = -1);
-void k_fixup_last(Context& C, u64* acc, long acc_os, int nx, const Buf& d, int l, const u64* pmod, int B,
-                  cudaStream_t st);
-void k_drop_combine(Context& C, const u64* acc, long acc_os, int nx, const Buf& d, const u64* delta, int nl,
-                    const u64* pmod, const u64* inv, Buf& out, int B, cudaStream_t st);
+// acc_c[acc_limb] += P * d_c[l-1] (acc: nx limbs per component)
+void k_fixup_last(Context& C, u64* acc, long acc_os, int nx, int acc_limb, const Buf& d, int l, const u64* pmod,
+                  int B, cudaStream_t st);
 void k_sub_scale(Context& C, const u64* a, long a_os, const u64* dl, long d_os, const u64* scale, const u64* add,
                  long add_os, u64* out, long out_os, int nl, int n_outer, cudaStream_t st);
 void k_to_montgomery(Context& C, u64* data, int npoly, cudaStream_t st);
+// key-switch inner product for the limbs [m0, m0 + nlimbs) of the extended
+// basis (nlimbs < 0: to the end); acc holds nlimbs limbs per component
 void k_ks_ip(Context& C, const u64* d, long d_os, const u64* ext, long ext_os, const KeyDev& K, int level,
-             u64* acc, long acc_os, int n_outer, cudaStream_t st);
+             u64* acc, long acc_os, int n_outer, cudaStream_t st, int m0 = 0, int nlimbs = -1);
+// inner product over the data limbs [0, nlimbs) with the ModDown epilogue
+// (drop: relinearise-and-drop combine; else subtract, scale by P^-1, add x)
+void k_ks_ip_fused(Context& C, const u64* d, long d_os, const u64* ext, long ext_os, const KeyDev& K, int level,
+                   int nlimbs, bool drop, const Buf* x, bool add_c1, const u64* delta, int nl, const u64* pm,
+                   const u64* scale, Buf& out, int n_outer, cudaStream_t st);
 void k_automorph(Context& C, const Buf& a, int g, Buf& out, cudaStream_t st);
 void k_uniform(Context& C, u64* out, long out_os, int n_outer, int nl, int q0, int nq, u32 id0, u32 tag,
                cudaStream_t st);
@@ -293,8 +332,30 @@ struct StageScope {
   ~StageScope() { stage_end(C, rec, st); }
 };
 
+// Plan-only evaluation. While a PlanScope for a context is open on the calling
+// thread, the evaluator tracks shapes, levels and plaintext moduli of that
+// context's operations but allocates, launches and traces nothing. The state is
+// per thread, so planning never affects other threads (server workers) using
+// the same context.
+bool is_dry(const Context& C);
+struct PlanScope {
+  const Context* prev;
+  explicit PlanScope(const Context& C);
+  ~PlanScope();
+};
+// Runs f as a plan first (an error such as SS_ERR_NOISE is thrown before any
+// work is enqueued), then for real.
+template <class F>
+auto plan_then_run(Context& C, F&& f) -> decltype(f()) {
+  {
+    PlanScope ps(C);
+    f();
+  }
+  return f();
+}
+
 inline void note(Context& C, const std::string& s) {
-  if (C.trace_on) C.trace.push_back(s);
+  if (C.trace_on && !is_dry(C)) C.trace.push_back(s);
 }
 
 }  // namespace ss

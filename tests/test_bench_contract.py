@@ -27,7 +27,10 @@ def test_reference_arm_line():
     assert d["higher_is_better"] is True and d["value"] > 0
     assert d["config"] == bench.workload_config(16, 41, 55, 3, 257, 3, 128, bench.N_CT, 32)
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    import oracle as O
+    assert cb["kind"] == "oracle" and cb["cores"] == O.threads() and cb["value"] == d["value"] and cb["sample"]
+    # the line's rate is the measured one: rows per step over the measured time per step
+    assert abs(d["rows_per_step"] / (d["ms_per_step"] / 1e3) - d["value"]) < 1e-6 * d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 

@@ -85,8 +85,12 @@ def test_batch_eager_tuned_graph(world):
     st.synchronize()
     skipped = check(b, refs)
     assert b.get_config()["skipped"] == skipped
+    b.config(2, 0, 11)  # merged lanes (one host thread per chunk)
+    b.run(st)
+    st.synchronize()
+    check(b, refs)
     best = b.tune(st)
-    assert best[0] in (8, 32, 64) and best[1] in (1, 3) and best[2] in (11, 12)
+    assert best[0] in (8, 32, 64) and best[1] in (0, 1, 3) and best[2] in (11, 12)
     b.capture(st)
     for _ in range(2):
         b.run(st)

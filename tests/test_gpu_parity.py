@@ -376,3 +376,71 @@ def test_p257_r3_small_ring():
     same(lt, [o.compare_lt(x, y) for x, y in zip(oa, ob)])
     exp = np.array([[plain.lt(x, y, g.t) for x, y in zip(ra, rb)] for ra, rb in zip(A, B)])
     assert (g.decrypt_slots(lt) == exp).all()
+
+
+def test_short_chain_is_rejected_before_any_launch():
+    """A chain shorter than the schedule's depth fails with SS_ERR_NOISE from
+    the plan, before anything is enqueued: the library's launch count does not
+    move (query, conjunctive query, host-memory query and comparison)."""
+    import paper_2604_19890_gb300 as ssg
+    g, _ = make_pair(L=9, seed=17)  # the 17^2 query consumes 16 levels
+    rng = np.random.default_rng(18)
+    cols = [g.encrypt_slots(rng.integers(0, g.t, (2, g.slots)), 100 * (i + 1)) for i in range(4)]
+    calls = [lambda: g.query(*cols),
+             lambda: g.query_where(cols[0], cols[1], [("lt", cols[2], cols[3]), ("eq", cols[2], cols[3])]),
+             lambda: g.query_host(*[c.words() for c in cols], cols[0].level),
+             lambda: g.compare_lt(cols[2], cols[3])]
+    for call in calls:
+        n0 = g.launches()
+        with pytest.raises(ssg.SSError) as e:
+            call()
+        assert e.value.code == ssg.SS_ERR_NOISE
+        assert g.launches() == n0
+    with pytest.raises(ssg.SSError) as e:
+        g.query_depth()
+    assert e.value.code == ssg.SS_ERR_NOISE
+
+
+def _oracle_lincomb(o, cts, coeffs, cst=0):
+    acc = None
+    for oc, cf in zip(cts, coeffs):
+        term = o.mul_scalar(oc, cf)
+        acc = term if acc is None else o.add(acc, term)
+    return o.add_scalar(acc, cst) if cst else acc
+
+
+def test_linear_combination_at_the_small_scalar_bound(tiny):
+    """16 terms with coefficients of magnitude 2^27 - 1 and mixed signs plus a
+    constant: the largest sums the 64-bit accumulators of 32-bit word halves
+    must hold (the path for scalars below 2^27)."""
+    g, o = tiny
+    rng = np.random.default_rng(91)
+    cts = [encrypt_both(g, o, rng.integers(0, g.t, (2, g.slots)), 7000 + 10 * i) for i in range(16)]
+    lim = (1 << 27) - 1
+    coeffs = [lim if i % 3 else -lim for i in range(16)]
+    got = g.linear_combination([c[0] for c in cts], coeffs, -98765)
+    same(got, [_oracle_lincomb(o, [c[1][b] for c in cts], coeffs, -98765) for b in range(2)])
+
+
+@pytest.mark.parametrize("rows", [
+    # every scalar below 2^27 (32-bit word halves into 64-bit sums), one row at the bound
+    [[(1 << 27) - 1, -((1 << 27) - 1), 5, -7, 1], [3, 1, -1, 0, 2]],
+    # one scalar at 2^27: the launch takes the path for scalars below 2^32
+    [[(1 << 27) - 1, -3, 5, 1 << 27, 1], [-((1 << 31) - 5), 0, 1, 2, -(1 << 27)]],
+    # one scalar at 2^33: the general path (64-bit products; the 36-bit primes lie above 2^35)
+    [[1 << 33, -5, 1, 0, 7], [-((1 << 34) + 3), 2, 0, 1, 1], [1, 1, 1, 1, 1]],
+])
+def test_linear_combinations_parity(tiny, rows):
+    """ss_linear_combinations (several outputs of one set of terms in one pass,
+    the Paterson-Stockmeyer leaves) against the reference's chain of scalar
+    products and additions, on each of its three scalar paths."""
+    g, o = tiny
+    rng = np.random.default_rng(92 + len(rows))
+    n = len(rows[0])
+    cts = [encrypt_both(g, o, rng.integers(0, g.t, (2, g.slots)), 7500 + 10 * i) for i in range(n)]
+    got = g.linear_combinations([c[0] for c in cts], rows)
+    assert len(got) == len(rows)
+    for k, row in enumerate(rows):
+        same(got[k], [_oracle_lincomb(o, [c[1][b] for c in cts], row) for b in range(2)])
+        single = g.linear_combination([c[0] for c in cts], row)
+        assert (single.words() == got[k].words()).all()
