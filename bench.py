@@ -475,18 +475,26 @@ def run_batched(args):
     e1.record(st)
     st.synchronize()
     plain_ms = e0.elapsed_time(e1)
-    best = b.tune(st)
-    b.capture(st)
-    b.run(st)
-    st.synchronize()
-    times = []
-    for _ in range(max(3, args.steps)):
-        e0.record(st)
+    def graph_time():
+        b.capture(st)
         b.run(st)
-        e1.record(st)
         st.synchronize()
-        times.append(e0.elapsed_time(e1))
-    graph_ms = sorted(times)[len(times) // 2]
+        times = []
+        for _ in range(max(3, args.steps)):
+            e0.record(st)
+            b.run(st)
+            e1.record(st)
+            st.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return sorted(times)[len(times) // 2]
+
+    # merged lanes (persistent transforms and inner products over all pairs), best chunk
+    merged = {}
+    for c in (8, 64):
+        b.config(c, 0, 11)
+        merged[c] = graph_time()
+    best = b.tune(st)
+    graph_ms = graph_time()
     # decrypted semantics of every product and digit
     ok = True
     for (ci, _, _, _), (va, vb), (prod, digs) in zip(pairs, plain_vals, b.results()):
@@ -513,6 +521,7 @@ def run_batched(args):
            "plain_ms": plain_ms, "batched_graph_ms": graph_ms, "plain_pairs_per_s": 64 / (plain_ms / 1e3),
            "batched_pairs_per_s": 64 / (graph_ms / 1e3), "speedup": plain_ms / graph_ms,
            "tuned": {"chunk": best[0], "streams": best[1], "ntt_tile_words": 1 << best[2]},
+           "merged_lanes_graph_ms": {"chunk %d" % c: v for c, v in merged.items()},
            "groups": info["groups"], "reductions_skipped": info["skipped"], "verified_against_plaintext": ok}
     print(json.dumps(out))
     return 0 if ok else 1

@@ -297,6 +297,13 @@ ss_status ss_query_depth(ss_ctx* ctx, int32_t level, int32_t* out_level);
 /* Device bytes a query over n_ct ciphertexts per column at `level` holds at
  * its peak: the estimate the served form admits queries by. */
 ss_status ss_query_bytes(const ss_ctx* ctx, int32_t n_ct, int32_t level, uint64_t* bytes);
+/* Coefficients of G_{p,e} used by ss_eval_g, the reduction, the raising and
+ * the queries: 0 = the canonical table (Newton interpolation, centred mod p^e,
+ * the default); 1 = the lattice-reduced representative (Section 4.2, after
+ * Geelen et al.): the odd polynomial equal to G_{p,e} on all of Z_{p^e} with
+ * the least sum of |centred coefficients|, found exactly for e = 2, 3 (other e:
+ * the canonical table). Smaller coefficients grow the noise less. */
+ss_status ss_set_g_table(ss_ctx* ctx, int32_t mode);
 /* Ciphertexts the query evaluates together per pass (memory/throughput knob). */
 ss_status ss_set_batch(ss_ctx* ctx, int32_t batch);
 

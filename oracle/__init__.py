@@ -47,6 +47,8 @@ def lib():
             "orc_decode": (i32, [vp, i32, P(u64), P(u64)]),
             "orc_g_table": (i32, [i32, i32, P(i64)]),
             "orc_flt_table": (i32, [i32, P(i64)]),
+            "orc_g_table_reduced": (i32, [i32, i32, P(i64)]),
+            "orc_set_reduced_g": (i32, [vp, i32]),
             "orc_encrypt": (vp, [vp, P(u64), u32, i32]),
             "orc_ct_info": (i32, [vp, P(i32), P(i32), P(i32)]),
             "orc_ct_export": (i32, [vp, P(u64)]),
@@ -125,6 +127,14 @@ def g_table(p, e):
     D = (e - 1) * (p - 1) + 1
     out = np.zeros(D + 1, dtype=np.int64)
     _chk(lib().orc_g_table(p, e, _ptr(out, C.c_int64)))
+    return out
+
+
+def g_table_reduced(p, e):
+    """An equivalent G_{p,e} with the least sum of |centred coefficients| (e = 2, 3)."""
+    D = (e - 1) * (p - 1) + 1
+    out = np.zeros(D + 1, dtype=np.int64)
+    _chk(lib().orc_g_table_reduced(p, e, _ptr(out, C.c_int64)))
     return out
 
 
@@ -286,6 +296,10 @@ class Oracle:
 
     def decrypt_slots(self, ct):
         return self.decode(self.decrypt(ct), ct.t_exp)
+
+    def set_reduced_g(self, on=True):
+        """Evaluate G_{p,e} with the lattice-reduced coefficients (Section 4.2)."""
+        _chk(lib().orc_set_reduced_g(self.h, 1 if on else 0))
 
     def noise_budget(self, ct):
         return lib().orc_noise_budget(self.h, ct.h)

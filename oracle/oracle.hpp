@@ -129,6 +129,7 @@ struct Context {
   std::vector<Poly> sk_hat;     // NTT(s) per prime (all L + alpha)
   KSKey rlk;
   std::map<int, KSKey> gk;
+  bool reduced_g = false;       // evaluate the lattice-reduced G_{p,e} (g_table_reduced)
 };
 
 // ------------------------------------------------------------- construction
@@ -175,6 +176,7 @@ Ct mul(const Context& C, const Ct& a, const Ct& b);  // align, tensor, relin_dro
 
 // ------------------------------------------------------------ coefficients
 std::vector<i64> g_table(int p, int e);    // G_{p,e} monomial coefficients, centred mod p^e
+std::vector<i64> g_table_reduced(int p, int e);  // an equivalent G_{p,e} with the least sum of |coefficients| (e = 2, 3)
 std::vector<i64> flt_table(int p);         // F_LT monomial coefficients, centred mod p
 i64 centre(u64 v, u64 m);
 

@@ -143,6 +143,17 @@ int orc_g_table(int p, int e, int64_t* out) {
   });
 }
 
+int orc_g_table_reduced(int p, int e, int64_t* out) {
+  return guard([&] {
+    auto g = g_table_reduced(p, e);
+    for (size_t i = 0; i < g.size(); ++i) out[i] = g[i];
+  });
+}
+
+int orc_set_reduced_g(void* h, int on) {
+  return guard([&] { ctx(h).reduced_g = on != 0; });
+}
+
 int orc_flt_table(int p, int64_t* out) {
   return guard([&] {
     auto f = flt_table(p);

@@ -75,6 +75,71 @@ std::vector<i64> g_table(int p, int e) {
   return out;
 }
 
+// Lattice-reduced representative of G_{p,e} (Section 4.2: Geelen et al. replace
+// G_{p,e} by an equivalent polynomial with smaller integer coefficients, which
+// slows noise growth). Two integer polynomials agree on all of Z_{p^e} exactly
+// when their difference is null mod p^e; in the falling-factorial basis the
+// null polynomials are sum_k a_k (x)_k with p^(e - v_p(k!)) | a_k. Up to the
+// degree D = (e-1)(p-1)+1 of G_{p,e}, with (x)_k = (x)_p (x-p)_(k-p) and
+// (x)_p = x^p - x (mod p), the odd null polynomials modulo p^e are
+//   e = 2:  a p (x^p - x),                          a in Z_p;
+//   e = 3:  p^2 * odd part of (x^p - x) R(x),       R in F_p[x], deg R < p.
+// Among G + (odd null polynomial) this returns the one whose centred
+// coefficients have the least sum of absolute values, by exhaustive search.
+// For e = 3, coefficient i (odd) of (x^p - x) R(x) is r_(i-p) - r_(i-1), so
+// only the even-indexed r_m enter: coefficient 1 takes -r_0, p takes
+// r_0 - r_(p-1), 2p-1 takes r_(p-1), and for even 2 <= m <= p-3 coefficient
+// m+1 takes -r_m and p+m takes r_m; the choices of the r_m for 2 <= m <= p-3
+// are independent, and (r_0, r_(p-1)) is searched jointly. Ties keep the
+// smallest parameter (in [0, p), lexicographic for the joint pair). Other e:
+// the canonical table.
+std::vector<i64> g_table_reduced(int p, int e) {
+  std::vector<i64> g = g_table(p, e);
+  if (e != 2 && e != 3) return g;
+  const i64 pe = (i64)ipow_u((u64)p, e);
+  auto cen = [&](i64 v) {
+    i64 z = v % pe;
+    if (z < 0) z += pe;
+    return z > pe / 2 ? z - pe : z;
+  };
+  auto mag = [&](int i, i64 delta) { i64 v = cen(g[i] + delta); return v < 0 ? -v : v; };
+  std::vector<i64> out = g;
+  if (e == 2) {
+    const i64 P = p;
+    i64 best = -1;
+    int ba = 0;
+    for (int a = 0; a < p; ++a) {
+      i64 c = mag(1, -a * P) + mag(p, a * P);
+      if (best < 0 || c < best) { best = c; ba = a; }
+    }
+    out[1] = cen(g[1] - ba * P);
+    out[p] = cen(g[p] + ba * P);
+    return out;
+  }
+  const i64 P2 = (i64)p * p;
+  for (int m = 2; m <= p - 3; m += 2) {
+    i64 best = -1;
+    int br = 0;
+    for (int r = 0; r < p; ++r) {
+      i64 c = mag(m + 1, -r * P2) + mag(p + m, r * P2);
+      if (best < 0 || c < best) { best = c; br = r; }
+    }
+    out[m + 1] = cen(g[m + 1] - br * P2);
+    out[p + m] = cen(g[p + m] + br * P2);
+  }
+  i64 best = -1;
+  int b0 = 0, b1 = 0;
+  for (int r0 = 0; r0 < p; ++r0)
+    for (int r1 = 0; r1 < p; ++r1) {
+      i64 c = mag(1, -r0 * P2) + mag(p, (i64)(r0 - r1) * P2) + mag(2 * p - 1, r1 * P2);
+      if (best < 0 || c < best) { best = c; b0 = r0; b1 = r1; }
+    }
+  out[1] = cen(g[1] - b0 * P2);
+  out[p] = cen(g[p] + (i64)(b0 - b1) * P2);
+  out[2 * p - 1] = cen(g[2 * p - 1] + b1 * P2);
+  return out;
+}
+
 // F_LT (Section 4.3): ((p+1)/2) x^(p-1) + sum_{odd i <= p-2} c_i x^i with
 // c_i = sum_{j=1}^{(p-1)/2} j^(p-1-i), all mod p.
 std::vector<i64> flt_table(int p) {
@@ -205,7 +270,7 @@ static Ct mul_term(const Context& C, const Ct& x, const Term& T) {
 }
 
 Ct eval_g(const Context& C, const Ct& x, int e, Trace* tr) {
-  std::vector<i64> g = g_table(C.P.p, e);
+  std::vector<i64> g = C.reduced_g ? g_table_reduced(C.P.p, e) : g_table(C.P.p, e);
   std::vector<i64> h;
   for (size_t i = 1; i < g.size(); i += 2) h.push_back(g[i]);  // G = x * H(x^2)
   while (h.size() > 1 && h.back() == 0) h.pop_back();

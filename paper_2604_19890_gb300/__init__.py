@@ -69,6 +69,7 @@ _SIGS = {
     "ss_linear_combinations": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.c_int32, C.POINTER(C.c_int64), C.c_int32,
                                          C.POINTER(ss_ct), C.c_void_p]),
     "ss_query_bytes": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_uint64)]),
+    "ss_set_g_table": (C.c_int, [C.c_void_p, C.c_int32]),
     "ss_mul_relin": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.POINTER(ss_ct), C.POINTER(ss_ct), C.c_void_p]),
     "ss_relin_noalloc": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.POINTER(ss_ct), C.c_void_p]),
     "ss_modswitch": (C.c_int, [C.c_void_p, C.POINTER(ss_ct), C.c_int32, C.POINTER(ss_ct), C.c_void_p]),
@@ -564,6 +565,10 @@ class Context:
         out = C.c_uint64()
         _chk(lib().ss_query_bytes(self.h, int(n_ct), self.L if level is None else int(level), C.byref(out)))
         return out.value
+
+    def set_g_table(self, mode):
+        """0: canonical G_{p,e} coefficients; 1: the lattice-reduced representative."""
+        _chk(lib().ss_set_g_table(self.h, int(mode)))
 
     def set_batch(self, b):
         _chk(lib().ss_set_batch(self.h, b))

@@ -536,6 +536,13 @@ ss_status ss_query_bytes(const ss_ctx* ctx, int32_t n_ct, int32_t level, uint64_
   });
 }
 
+ss_status ss_set_g_table(ss_ctx* ctx, int32_t mode) {
+  return guard([&] {
+    need(ctx && (mode == 0 || mode == 1), SS_ERR_PARAM, "G table mode must be 0 or 1");
+    ctx->C.reduced_g = mode == 1;
+  });
+}
+
 ss_status ss_set_batch(ss_ctx* ctx, int32_t batch) {
   return guard([&] {
     need(ctx && batch >= 1, SS_ERR_PARAM, "bad batch");

@@ -157,6 +157,88 @@ std::vector<i64> g_coeffs(int p, int e) {
   return out;
 }
 
+// Lattice-reduced G_{p,e} (Section 4.2, Geelen et al.'s smaller equivalent
+// coefficients) for e = 2, 3: the canonical table plus the odd null polynomial
+// mod p^e that minimises the sum of |centred coefficients|. The odd null
+// polynomials of degree <= (e-1)(p-1)+1 are spanned mod p^e by the generators
+//   e = 2:  p (x^p - x);
+//   e = 3:  p^2 * odd part of (x^p - x) x^m, m = 0, 2, ..., p-1,
+// built here as coefficient vectors. Generators whose supports are disjoint
+// from all others are chosen one at a time (exhaustively over their multiplier
+// 0..p-1); the two that share coefficient p (m = 0 and m = p-1) are chosen
+// jointly. Ties keep the smaller multiplier (the first generator's first). The
+// result agrees with G_{p,e} on all of Z_{p^e}. Other e: the canonical table.
+std::vector<i64> g_coeffs_reduced(int p, int e) {
+  std::vector<i64> g = g_coeffs(p, e);
+  if (e != 2 && e != 3) return g;
+  const int D = (int)g.size() - 1;
+  const i64 pe = (i64)upow((u64)p, e), step = e == 2 ? p : (i64)p * p;
+  // generator vectors (coefficients mod p^e of step * odd part of (x^p - x) x^m)
+  std::vector<std::vector<i64>> gens;
+  for (int m = 0; m <= (e == 2 ? 0 : p - 1); m += 2) {
+    std::vector<i64> v(D + 1, 0);
+    if (m + p <= D && (m + p) % 2 == 1) v[m + p] += step;
+    if (m + 1 <= D && (m + 1) % 2 == 1) v[m + 1] -= step;
+    gens.push_back(v);
+  }
+  auto centre_pe = [&](i64 x) {
+    i64 z = x % pe;
+    if (z < 0) z += pe;
+    return z > pe / 2 ? z - pe : z;
+  };
+  // cost of the coefficients in `idx` after adding sum_k a[k] * gens[ks[k]]
+  auto cost = [&](const std::vector<int>& ks, const std::vector<int>& a, const std::vector<int>& idx) {
+    i64 s = 0;
+    for (int i : idx) {
+      i64 v = g[i];
+      for (size_t k = 0; k < ks.size(); ++k) v += (i64)a[k] * gens[ks[k]][i];
+      v = centre_pe(v);
+      s += v < 0 ? -v : v;
+    }
+    return s;
+  };
+  auto support = [&](int k) {
+    std::vector<int> s;
+    for (int i = 0; i <= D; ++i)
+      if (gens[k][i] != 0) s.push_back(i);
+    return s;
+  };
+  std::vector<int> mult(gens.size(), 0);
+  std::vector<bool> done(gens.size(), false);
+  for (size_t k = 0; k < gens.size(); ++k) {
+    if (done[k]) continue;
+    // generators sharing a coefficient with k
+    std::vector<int> grp{(int)k};
+    for (size_t k2 = k + 1; k2 < gens.size(); ++k2)
+      for (int i : support((int)k))
+        if (gens[k2][i] != 0) { grp.push_back((int)k2); break; }
+    if (grp.size() > 2) throw Error(SS_ERR_PARAM, "reduced G: unexpected generator coupling");
+    std::vector<int> idx;
+    for (int kk : grp)
+      for (int i : support(kk))
+        if (std::find(idx.begin(), idx.end(), i) == idx.end()) idx.push_back(i);
+    i64 best = -1;
+    std::vector<int> ba(grp.size(), 0), a(grp.size(), 0);
+    for (a[0] = 0; a[0] < p; ++a[0])
+      for (int a1 = 0; a1 < (grp.size() > 1 ? p : 1); ++a1) {
+        if (grp.size() > 1) a[1] = a1;
+        i64 c = cost(grp, a, idx);
+        if (best < 0 || c < best) { best = c; ba = a; }
+      }
+    for (size_t j = 0; j < grp.size(); ++j) {
+      mult[grp[j]] = ba[j];
+      done[grp[j]] = true;
+    }
+  }
+  std::vector<i64> out(D + 1, 0);
+  for (int i = 0; i <= D; ++i) {
+    i64 v = g[i];
+    for (size_t k = 0; k < gens.size(); ++k) v += (i64)mult[k] * gens[k][i];
+    out[i] = centre_pe(v);
+  }
+  return out;
+}
+
 // F_LT over Z_p: coefficient of x^(p-1) is (p+1)/2; odd i <= p-2 carry
 // c_i = sum_{j=1}^{(p-1)/2} j^(p-1-i).
 std::vector<i64> flt_coeffs(int p) {

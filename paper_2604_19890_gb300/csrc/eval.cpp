@@ -277,7 +277,7 @@ BufP mul_term(Context& C, const BufP& x, const Term& T, cudaStream_t st) {
 
 // ------------------------------------------------------------------ space switching
 BufP ev_eval_g(Context& C, const BufP& x, int e, cudaStream_t st) {
-  std::vector<i64> g = nt::g_coeffs(C.p, e);
+  std::vector<i64> g = C.reduced_g ? nt::g_coeffs_reduced(C.p, e) : nt::g_coeffs(C.p, e);
   std::vector<i64> h;
   for (size_t i = 1; i < g.size(); i += 2) h.push_back(g[i]);
   while (h.size() > 1 && h.back() == 0) h.pop_back();

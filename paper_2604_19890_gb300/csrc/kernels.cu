@@ -37,6 +37,13 @@ constexpr int TPB = 256;
 #ifndef SS_KSIP_V
 #define SS_KSIP_V 2  // coefficients per thread in the key-switch inner product
 #endif
+#ifndef SS_KSIP_UNROLL
+#define SS_KSIP_UNROLL 0  // digits per iteration of the inner product's loop (0: the compiler's choice)
+#endif
+#ifndef SS_KSIP_MINB
+#define SS_KSIP_MINB 4  // resident CTAs per SM the inner product is compiled for (64 registers)
+#endif
+constexpr int kKsipUnroll = SS_KSIP_UNROLL > 0 ? SS_KSIP_UNROLL : 1;
 
 static_assert(sizeof(Modulus) == sizeof(ModDesc), "device modulus descriptors share one layout");
 __device__ __forceinline__ const Modulus& MOD(const ModDesc* m, int i) {
@@ -296,6 +303,9 @@ __device__ __forceinline__ void ks_sums(const u64* __restrict__ d, long d_os, co
       s0[b][v].zero();
       s1[b][v].zero();
     }
+#if SS_KSIP_UNROLL > 0
+#pragma unroll kKsipUnroll
+#endif
   for (int j = 0; j < dn; ++j) {
     u64 wb[V], wa[V];
     ldv<V>(kbp + j * kstride, wb);
@@ -429,7 +439,7 @@ __device__ __forceinline__ void ks_block(const KsJob& J, int bx, int by) {
 }
 
 template <int OB, int TYPE>
-__global__ void __launch_bounds__(256) k_ks_ip_impl(const __grid_constant__ KsJob J) {
+__global__ void __launch_bounds__(256, SS_KSIP_MINB) k_ks_ip_impl(const __grid_constant__ KsJob J) {
   ks_block<OB, TYPE>(J, blockIdx.x, blockIdx.y);
 }
 
@@ -443,7 +453,7 @@ struct KsMulti {
 };
 
 template <int OB>
-__global__ void __launch_bounds__(256) k_ks_ip_multi(const __grid_constant__ KsMulti M) {
+__global__ void __launch_bounds__(256, SS_KSIP_MINB) k_ks_ip_multi(const __grid_constant__ KsMulti M) {
   for (int t = blockIdx.x; t < M.total; t += gridDim.x) {
     int j = 0;
     while (j + 1 < M.njobs && t >= M.j[j + 1].start) ++j;

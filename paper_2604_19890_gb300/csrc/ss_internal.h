@@ -43,6 +43,7 @@ int brv(int x, int logn);
 std::vector<u64> chain(int bits, u64 step, int count);
 u64 root2n(u64 q, int N);
 std::vector<i64> g_coeffs(int p, int e);  // centred mod p^e, odd, degree (e-1)(p-1)+1
+std::vector<i64> g_coeffs_reduced(int p, int e);  // equivalent, least sum of |coefficients| (e = 2, 3)
 std::vector<i64> flt_coeffs(int p);       // centred mod p
 }  // namespace nt
 
@@ -155,6 +156,7 @@ struct Context {
 
   // evaluator
   int batch = 8;
+  bool reduced_g = false;  // evaluate G_{p,e} with the lattice-reduced coefficients
   int ntt_tile_log = SS_NTT_TILE_LOG;  // words per CTA tile of the two-phase transform: 2^11 or 2^12
   bool trace_on = false;
   std::vector<std::string> trace;

@@ -444,3 +444,31 @@ def test_linear_combinations_parity(tiny, rows):
         same(got[k], [_oracle_lincomb(o, [c[1][b] for c in cts], row) for b in range(2)])
         single = g.linear_combination([c[0] for c in cts], row)
         assert (single.words() == got[k].words()).all()
+
+
+@pytest.mark.parametrize("p,r,logN,L,alpha,bits", [(17, 3, 6, 30, 2, 50), (257, 3, 5, 44, 3, 55)])
+def test_reduced_g_parity(p, r, logN, L, alpha, bits):
+    """The lattice-reduced G_{p,e} (Section 4.2; ss_set_g_table(ctx, 1)) on both
+    sides: G evaluation, Algorithm 3, comparison and raising, word for word,
+    and decrypted against the plaintext definitions."""
+    g, o = make_pair(logN=logN, L=L, alpha=alpha, bits=bits, p=p, r=r, h=8, seed=23)
+    g.set_g_table(1)
+    o.set_reduced_g(True)
+    rng = np.random.default_rng(p + r)
+    A = rng.integers(0, g.t, (2, g.slots))
+    B = rng.integers(0, g.t, (2, g.slots))
+    ga, oa = encrypt_both(g, o, A, 30)
+    gb, ob = encrypt_both(g, o, B, 40)
+    red = g.eval_g(ga, r)
+    same(red, [o.eval_g(x, r) for x in oa])
+    gd = g.reduce(ga)
+    od = [o.reduce(x) for x in oa]
+    for i in range(r):
+        same(gd[i], [d[i] for d in od])
+    up = g.raise_modulus(g.compare_lt(ga, gb))
+    same(up, [o.raise_modulus(o.compare_lt(x, y)) for x, y in zip(oa, ob)])
+    exp = np.array([[plain.lt(x, y, g.t) for x, y in zip(ra, rb)] for ra, rb in zip(A, B)])
+    assert (g.decrypt_slots(up) == exp).all()
+    # the canonical table gives other words for the same input (the test is not vacuous)
+    g.set_g_table(0)
+    assert (g.eval_g(ga, r).words() != red.words()).any()

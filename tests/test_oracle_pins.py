@@ -442,6 +442,54 @@ def test_g_table_257_cubed_sampled():
     assert all(poly_eval(g, x, M) == bal(x, p) % M for x in xs)
 
 
+@pytest.mark.parametrize("p,e", [(3, 3), (5, 3), (7, 3), (13, 3), (17, 2), (17, 3), (257, 2)])
+def test_g_table_reduced_lemma_brute_force(p, e):
+    """The lattice-reduced G_{p,e} (Section 4.2) is still G_{p,e}: Lemma 3 on all
+    of Z_{p^e}, odd, centred, the same degree, and its coefficients' absolute
+    sum is at most the canonical table's."""
+    g, c = O.g_table_reduced(p, e), O.g_table(p, e)
+    M = p ** e
+    assert len(g) == len(c) and int(g[-1]) != 0
+    assert all(int(g[i]) == 0 for i in range(0, len(g), 2))
+    assert all(-M // 2 <= int(x) <= M // 2 for x in g)
+    assert np.abs(g).sum() <= np.abs(c).sum()
+    xs = range(M) if M <= 70000 else range(0, M, 7)
+    assert all(poly_eval(g, x, M) == bal(x, p) % M for x in xs)
+
+
+def test_g_table_reduced_257_cubed_sampled():
+    p, e = 257, 3
+    g = O.g_table_reduced(p, e)
+    M = p ** e
+    rng = np.random.default_rng(1)
+    xs = [int(x) for x in rng.integers(0, M, 3000)] + list(range(0, 3 * p)) + [M - 1, M - 2, M // 2]
+    assert all(poly_eval(g, x, M) == bal(x, p) % M for x in xs)
+    assert np.abs(g).sum() < 0.5 * np.abs(O.g_table(p, e)).sum()
+
+
+@pytest.mark.parametrize("p,e", [(3, 2), (3, 3), (5, 2)])
+def test_g_table_reduced_is_minimal_brute_force(p, e):
+    """Minimality against brute force over the function class itself: every odd
+    polynomial of degree <= (e-1)(p-1)+1 with centred coefficients mod p^e that
+    satisfies Lemma 3 on all of Z_{p^e}; none has a smaller absolute sum."""
+    import itertools
+    M = p ** e
+    D = (e - 1) * (p - 1) + 1
+    odd = list(range(1, D + 1, 2))
+    box = range(-(M // 2), M // 2 + 1)
+    best = None
+    for cs in itertools.product(box, repeat=len(odd)):
+        cost = sum(abs(x) for x in cs)
+        if best is not None and cost >= best:
+            continue
+        poly = [0] * (D + 1)
+        for i, x in zip(odd, cs):
+            poly[i] = x
+        if all(poly_eval(poly, x, M) == bal(x, p) % M for x in range(M)):
+            best = cost
+    assert best == int(np.abs(O.g_table_reduced(p, e)).sum())
+
+
 @pytest.mark.parametrize("p", [5, 13, 17, 41, 257])
 def test_flt_truth_table(p):
     """Section 4.3 closed form of F_LT against the LT0 truth table (Section 2.2)."""
