@@ -351,7 +351,9 @@ ss_status ss_stage_stats(ss_ctx* ctx, int32_t stage, uint64_t* count, double* ms
  * ALU-bound kernels (measurement; the paper has no counterpart). kind 0:
  * 32-bit multiply-adds per second; kind 1: forward butterflies per second
  * (Harvey's form: one conditional subtraction, one 64-bit Shoup product, the
- * lazy add and subtract; residues held in registers, no memory traffic).
+ * lazy add and subtract; residues held in registers, no memory traffic);
+ * kind 2: 32 x 32 -> 64-bit widening multiply-adds per second (the partial
+ * products of a 64-bit modular product).
  * iters in [1, 2^20] sets the loop length (every thread of one full wave of
  * CTAs runs 8 operations per iteration). Allocates and frees a small buffer;
  * synchronises its own stream. */

@@ -626,7 +626,7 @@ ss_status ss_stage_stats(ss_ctx* ctx, int32_t stage, uint64_t* count, double* ms
 
 ss_status ss_alu_probe(int32_t kind, int32_t iters, double* per_second) {
   return guard([&] {
-    need((kind == 0 || kind == 1) && iters >= 1 && iters <= (1 << 20) && per_second, SS_ERR_PARAM, "bad argument");
+    need(kind >= 0 && kind <= 2 && iters >= 1 && iters <= (1 << 20) && per_second, SS_ERR_PARAM, "bad argument");
     *per_second = ss::alu_probe(kind, iters);
   });
 }

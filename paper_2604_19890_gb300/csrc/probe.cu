@@ -2,7 +2,9 @@
 // loops that issue the arithmetic of the transforms with no memory traffic.
 //   kind 0: 32-bit multiply-adds (IMAD) per second;
 //   kind 1: forward butterflies per second in Harvey's form: reduce the upper
-//           input below 2q, one 64-bit Shoup product, lazy add and subtract.
+//           input below 2q, one 64-bit Shoup product, lazy add and subtract;
+//   kind 2: 32 x 32 -> 64-bit widening multiply-adds (IMAD.WIDE) per second,
+//           the partial products a 64-bit modular product is built from.
 // One full wave of CTAs (as many per SM as fit) runs the loop.
 #include "modarith.cuh"
 #include <algorithm>
@@ -23,6 +25,23 @@ __global__ void __launch_bounds__(256) k_probe_imad(uint32_t* out, int iters, ui
     for (int k = 0; k < 8; ++k) a[k] = a[k] * b + c;
   }
   uint32_t x = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x ^= a[k];
+  out[tid] = x;
+}
+
+__global__ void __launch_bounds__(256) k_probe_wide(u64* out, int iters, uint32_t seed) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  u64 a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = (u64)tid * 2654435761u + k;
+  const uint32_t b = seed | 1u;
+  const u64 c = ((u64)seed << 29) | 7u;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = (u64)(uint32_t)a[k] * b + c;  // low 32 bits times b, 64-bit sum
+  }
+  u64 x = 0;
 #pragma unroll
   for (int k = 0; k < 8; ++k) x ^= a[k];
   out[tid] = x;
@@ -61,7 +80,8 @@ double alu_probe(int kind, int iters) {
   const int threads = 256;
   int per_sm = 0;
   if (kind == 0) SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_imad, threads, 0));
-  else SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_butterfly, threads, 0));
+  else if (kind == 1) SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_butterfly, threads, 0));
+  else SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_wide, threads, 0));
   const int blocks = prop.multiProcessorCount * std::max(1, per_sm), n = blocks * threads;
   void* buf = nullptr;
   SS_CUDA(cudaMalloc(&buf, (size_t)n * 8));
@@ -77,7 +97,8 @@ double alu_probe(int kind, int iters) {
   for (int rep = 0; rep < 2; ++rep) {  // the first pass warms up
     SS_CUDA(cudaEventRecord(e0, st));
     if (kind == 0) k_probe_imad<<<blocks, threads, 0, st>>>((uint32_t*)buf, iters, 0x9E3779B9u);
-    else k_probe_butterfly<<<blocks, threads, 0, st>>>((u64*)buf, iters, q, w, wp);
+    else if (kind == 1) k_probe_butterfly<<<blocks, threads, 0, st>>>((u64*)buf, iters, q, w, wp);
+    else k_probe_wide<<<blocks, threads, 0, st>>>((u64*)buf, iters, 0x9E3779B9u);
     SS_CUDA(cudaEventRecord(e1, st));
     SS_CUDA(cudaEventSynchronize(e1));
     SS_CUDA(cudaGetLastError());
@@ -87,7 +108,7 @@ double alu_probe(int kind, int iters) {
   cudaEventDestroy(e1);
   cudaStreamDestroy(st);
   cudaFree(buf);
-  const double ops = (double)n * iters * 8.0;  // 8 IMADs or 8 butterflies per thread and iteration
+  const double ops = (double)n * iters * 8.0;  // 8 operations per thread and iteration
   return ops / (ms * 1e-3);
 }
 

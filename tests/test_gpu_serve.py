@@ -158,3 +158,19 @@ def test_served_mixed_contexts_equal_alone():
         assert ((g1, g2)[ci].decrypt_slots(res) == exp).all()
     assert srv.stats()["completed"] == len(qs)
     srv.close()
+
+
+def test_submit_rejects_a_chain_too_short():
+    """A query whose schedule needs more levels than its columns have is refused
+    at submission with SS_ERR_NOISE (the plan runs before it is queued)."""
+    import paper_2604_19890_gb300 as ssg
+    g = ssg.Context(logN=6, L=9, alpha=2, bits=36, p=17, r=2, h=16, nmax=0, seed=33)
+    g.keygen()
+    rng = np.random.default_rng(5)
+    cols = [g.encrypt_slots(rng.integers(0, g.t, (1, g.slots)), 10 * (i + 1)) for i in range(4)]
+    srv = ssg.Server(g, workers=1, max_merge=1)
+    with pytest.raises(ssg.SSError) as e:
+        srv.submit(*cols)
+    assert e.value.code == ssg.SS_ERR_NOISE
+    assert srv.stats()["completed"] == 0
+    srv.close()
