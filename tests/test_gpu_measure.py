@@ -49,7 +49,9 @@ def test_alu_probes_report_finite_rates():
     bfly = ssg.alu_probe(1, 256)
     assert math.isfinite(imad) and imad > 1e11
     assert math.isfinite(bfly) and bfly > 1e9
+    wide = ssg.alu_probe(2, 1024)  # widening multiply-adds: no faster than 32-bit ones
+    assert math.isfinite(wide) and 1e11 < wide <= imad * 1.05
     with pytest.raises(ssg.SSError):
-        ssg.alu_probe(2, 16)
+        ssg.alu_probe(3, 16)
     with pytest.raises(ssg.SSError):
         ssg.alu_probe(0, 0)
