@@ -434,7 +434,10 @@ def run_batched(args):
     the 17^2 / 36-bit and 257^2 / 55-bit parameter sets: multiply + relinearise
     and, where the levels allow, reduce to digits (Algorithm 3). Plain form:
     one pair at a time on one stream; batched form: autotuned chunks over
-    streams, captured once as a CUDA graph and replayed."""
+    streams or merged lanes, captured once as a CUDA graph and replayed.
+    `--batched-mix small`: 64 pairs at N = 2^14 and levels 8..12 of the 17^2
+    set only (many small items, where launches rather than arithmetic
+    dominate)."""
     import numpy as np
     import torch
 
@@ -443,9 +446,12 @@ def run_batched(args):
 
     ssbuild.build()
     sets = []
-    for logN in (14, 15, 16):
+    small = args.batched_mix == "small"
+    for logN in ((14,) if small else (14, 15, 16)):
         sets.append(dict(logN=logN, L=28, alpha=2, bits=36, p=17, r=2, h=120, nmax=1 << 16, seed=SEED + logN))
-        sets.append(dict(logN=logN, L=28, alpha=2, bits=55, p=257, r=2, h=120, nmax=1 << 16, seed=SEED + 100 + logN))
+        if not small:
+            sets.append(dict(logN=logN, L=28, alpha=2, bits=55, p=257, r=2, h=120, nmax=1 << 16,
+                             seed=SEED + 100 + logN))
     gs = []
     for s in sets:
         g = ssg.Context(**s)
@@ -456,7 +462,7 @@ def run_batched(args):
     for i in range(64):
         ci = int(rng.integers(0, len(gs)))
         g = gs[ci]
-        lvl = int(rng.integers(4, 29))
+        lvl = int(rng.integers(8, 13)) if small else int(rng.integers(4, 29))
         va, vb = rng.integers(0, g.t, g.slots), rng.integers(0, g.t, g.slots)
         ga = g.encrypt(g.encode(va), 10 + 2 * i)
         gb = g.encrypt(g.encode(vb), 11 + 2 * i)
@@ -523,7 +529,8 @@ def run_batched(args):
     for sb in singles:
         sb.close()
     b.close()
-    out = {"metric": "batched multiply+relinearise+reduce, 64 mixed-N pairs", "unit": "pairs/s",
+    out = {"metric": "batched multiply+relinearise+reduce, 64 %s pairs" % ("small N=2^14" if small else "mixed-N"),
+           "unit": "pairs/s",
            "plain_ms": plain_ms, "batched_graph_ms": graph_ms, "plain_pairs_per_s": 64 / (plain_ms / 1e3),
            "batched_pairs_per_s": 64 / (graph_ms / 1e3), "speedup": plain_ms / graph_ms,
            "tuned": {"chunk": best[0], "streams": best[1], "ntt_tile_words": 1 << best[2]},
@@ -804,6 +811,7 @@ def main():
                     help="0: N=2^13, 17^2; 1: N=2^15, 257^2; 2: N=2^16, 257^3 (the headline workload)")
     ap.add_argument("--serve", action="store_true", help="served form: Poisson arrivals, p50/p99")
     ap.add_argument("--batched", action="store_true", help="batched form: 64 mixed-N pairs, graph replay")
+    ap.add_argument("--batched-mix", choices=["mixed", "small"], default="mixed")
     ap.add_argument("--serve-ct", type=int, default=2)
     ap.add_argument("--serve-queries", type=int, default=200)
     ap.add_argument("--lt-sweep", action="store_true",

@@ -1115,13 +1115,15 @@ KsMerger*& ks_merger() {
 
 // Jobs of several lanes as persistent launches of at most kMaxKsJobs jobs each.
 void ks_multi(const std::vector<KsReq>& reqs, cudaStream_t st) {
-  static int resident = 0;
+  static std::atomic<int> resident_{0};
+  int resident = resident_.load();
   if (!resident) {
     int dev = 0, sms = 0, per = 0;
     SS_CUDA(cudaGetDevice(&dev));
     SS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     SS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ks_ip_multi<SS_KSIP_OB>, TPB, 0));
     resident = sms * std::max(1, per);
+    resident_.store(resident);
   }
   for (size_t b0 = 0; b0 < reqs.size(); b0 += kMaxKsJobs) {
     const size_t b1 = std::min(reqs.size(), b0 + kMaxKsJobs);

@@ -531,14 +531,16 @@ static void launch(Context& C, const PolySet& s, bool fwd, cudaStream_t st, cons
 }
 
 static int resident_ctas() {
-  static int n = 0;
-  if (!n) {
+  static std::atomic<int> n{0};
+  int v = n.load();
+  if (!v) {
     int dev = 0, sms = 0;
     SS_CUDA(cudaGetDevice(&dev));
     SS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    n = sms * SS_NTT_MINB_F;
+    v = sms * SS_NTT_MINB_F;
+    n.store(v);
   }
-  return n;
+  return v;
 }
 
 template <bool FWD, bool COLS, bool LAST, bool SRC>

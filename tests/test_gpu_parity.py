@@ -472,3 +472,58 @@ def test_reduced_g_parity(p, r, logN, L, alpha, bits):
     # the canonical table gives other words for the same input (the test is not vacuous)
     g.set_g_table(0)
     assert (g.eval_g(ga, r).words() != red.words()).any()
+
+
+def _random_sets(n, seed):
+    """Seeded parameter sets across the space the library accepts: ring 2^4..2^7,
+    primes of 30..58 bits (58: the lazy-transform bound), 1..3 special primes,
+    plaintext p^r in {5^2, 13^2, 17^2, 17^3, 257, 257^2}."""
+    rng = np.random.default_rng(seed)
+    pr = [(5, 2), (13, 2), (17, 2), (17, 3), (257, 1), (257, 2)]
+    out = []
+    for k in range(n):
+        p, r = pr[k % len(pr)]
+        out.append(dict(logN=int(rng.integers(4, 8)), L=int(rng.integers(4, 9)), alpha=int(rng.integers(1, 4)),
+                        bits=int(rng.choice([30, 36, 45, 50, 55, 58])), p=p, r=r, h=8, seed=int(rng.integers(1, 1 << 30))))
+    return out
+
+
+@pytest.mark.parametrize("prm", _random_sets(12, 2026), ids=lambda d: "N%d_L%d_a%d_b%d_p%d_r%d" % (
+    1 << d["logN"], d["L"], d["alpha"], d["bits"], d["p"], d["r"]))
+def test_random_parameter_sets(prm):
+    """Every BGV operation word for word against the reference on seeded random
+    parameter sets: encryption, tensor, relinearisation, the evaluator's
+    multiplication, modulus switching, every rotate-sum element, DivideByP,
+    a linear combination, and decryption of the product."""
+    import paper_2604_19890_gb300 as ssg
+    try:
+        g = ssg.Context(nmax=0, **prm)
+    except ssg.SSError:
+        pytest.skip("no prime chain of this width for this ring and plaintext modulus")
+    o = O.Oracle(**prm)
+    gal = g.rotate_sum_elements()
+    g.keygen(gal)
+    o.keygen(gal)
+    rng = np.random.default_rng(prm["seed"] % 1000)
+    A = rng.integers(0, g.t, (2, g.slots))
+    B = rng.integers(0, g.t, (2, g.slots))
+    ga, oa = encrypt_both(g, o, A, 50)
+    gb, ob = encrypt_both(g, o, B, 60)
+    same(ga, oa)
+    gt = g.mul(ga, gb)
+    ot = [o.tensor(x, y) for x, y in zip(oa, ob)]
+    same(gt, ot)
+    same(g.relin(gt), [o.relin(x) for x in ot])
+    gm = g.mul_relin(ga, gb)
+    om = [o.mul(x, y) for x, y in zip(oa, ob)]
+    same(gm, om)
+    if prm["L"] > 2:
+        same(g.modswitch(ga, 2), [o.modswitch(x, 2) for x in oa])
+    for gel in gal:
+        same(g.rotate(ga, gel), [o.rotate(x, gel) for x in oa])
+    same(g.linear_combination([ga, gb], [7, -3], 5), [o.add_scalar(o.add(o.mul_scalar(x, 7), o.mul_scalar(y, -3)), 5)
+                                                      for x, y in zip(oa, ob)])
+    if g.r >= 2:
+        gp, op = encrypt_both(g, o, (A * g.p) % g.t, 70)
+        same(g.divide_by_p(gp), [o.divide_by_p(x) for x in op])
+    assert (g.decrypt_slots(gm) == (A.astype(object) * B.astype(object)) % g.t).all()
