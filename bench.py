@@ -671,6 +671,8 @@ def run_ours(args):
         L = enc["a"].level
         h2d = sum(a.nbytes for a in arrs.values())
         ol = None
+        # one untimed call first: the pool grows once for the four uploaded columns
+        g.query_host(arrs["a"], arrs["b"], arrs["c1"], arrs["c2"], L)
         torch.cuda.synchronize()
         e_steps = max(1, min(args.steps, args.e2e_steps))
         t0 = time.perf_counter()
@@ -800,7 +802,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=32)
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--kernel", choices=["ntt", "relin", "mul"], default=None,
