@@ -30,7 +30,8 @@ def lib():
         P = C.POINTER
         sig = {
             "orc_last_error": (C.c_char_p, []),
-            "orc_ctx_new": (vp, [i32, i32, i32, i32, i32, i32, i32, i32, u64]),
+            "orc_ctx_new": (vp, [i32, i32, i32, i32, i32, i32, i32, i32, u64, i32]),
+            "orc_ctx_ring": (i32, [vp, P(i32), P(u64), P(i32)]),
             "orc_ctx_free": (None, [vp]),
             "orc_ctx_info": (i32, [vp, P(i32), P(i32), P(u64), P(u64), P(i32)]),
             "orc_primes": (i32, [vp, P(u64)]),
@@ -186,10 +187,11 @@ class Ct:
 class Oracle:
     """One parameter set of the CPU reference BGV."""
 
-    def __init__(self, logN, L, alpha, bits, p, r, h=120, nmax=0, seed=1):
+    def __init__(self, logN, L, alpha, bits, p, r, h=120, nmax=0, seed=1, m_odd=1):
         self.logN, self.N, self.L, self.alpha, self.bits = logN, 1 << logN, L, alpha, bits
         self.p, self.r, self.h_weight, self.seed = p, r, h, seed
-        self.h = lib().orc_ctx_new(logN, L, alpha, bits, p, r, h, nmax, seed)
+        self.m_odd = m_odd or 1
+        self.h = lib().orc_ctx_new(logN, L, alpha, bits, p, r, h, nmax, seed, self.m_odd)
         if not self.h:
             raise _err()
         s, d, t, w = C.c_int(), C.c_int(), C.c_uint64(), C.c_uint64()
@@ -198,6 +200,12 @@ class Oracle:
         se = np.zeros(self.slots, dtype=np.int32)
         _chk(lib().orc_ctx_info(self.h, C.byref(s), C.byref(d), C.byref(t), C.byref(w), _ptr(se, C.c_int)))
         self.slot_exp = se
+        ri, th, gens = np.zeros(6, dtype=np.int32), np.zeros(2, dtype=np.uint64), np.zeros(64, dtype=np.int32)
+        _chk(lib().orc_ctx_ring(self.h, _ptr(ri, C.c_int), _ptr(th), _ptr(gens, C.c_int)))
+        # cyclotomic index m (2N or 3N); for m = 3N the slot algebra of Phi_M'(X^s) over GR(p^r, 2)
+        self.m, self.Mp, self.s, self.nprime, self.gr_c = (int(x) for x in ri[:5])
+        self.theta = (int(th[0]), int(th[1]))
+        self.gens = [(int(gens[2 * i]), int(gens[2 * i + 1])) for i in range(int(ri[5]))]
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -24,6 +24,7 @@
 //   per-digit aggregation, LT comparison            Section 4.3, Algorithm 4
 //   RaiseModToP2R = G_{p,r} after t <- p^r          Section 4.4
 //   compare-then-aggregate database query           Section 1 (Fig. 1), Section 5.2
+//   cyclotomic ring Phi_m, m = 2N or 3N; slots       Section 2.1, Section 5.1 (l = n / Ord(m, p))
 //
 // Parity status: the decrypted results are pinned by plaintext definitions and
 // brute force; the exact ciphertext words have no definition outside this
@@ -99,6 +100,7 @@ struct Params {
   int h = 0;       // Hamming weight of the ternary secret
   int nmax = 0;    // largest ring dimension the primes must support
   u64 seed = 0;
+  int m_odd = 1;   // odd part of the cyclotomic index m: 1 -> m = 2N, 3 -> m = 3N
 };
 
 typedef std::vector<u64> Poly;  // one RNS limb: N residues
@@ -119,10 +121,18 @@ struct Context {
   Params P;
   u64 t = 0;                    // p^r
   std::vector<u64> primes;      // L data primes then alpha special primes
-  std::vector<u64> psi;         // primitive 2N-th root per prime
+  int m = 0;                    // cyclotomic index: 2N or 3N
+  std::vector<u64> psi;         // per prime: the smallest primitive m-th root of unity
   int slots = 0, d = 0;         // slot count and slot degree: N = slots * d
-  u64 omega = 0;                // primitive 2*slots-th root of unity mod p^r
-  std::vector<int> slot_exp;    // slot j holds the value at omega^slot_exp[j]
+  u64 omega = 0;                // m = 2N: primitive 2*slots-th root of unity mod p^r
+  std::vector<int> slot_exp;    // slot j holds the value at omega^slot_exp[j] (m = 3N: theta^slot_exp[j])
+  // m = 3N slot algebra (Section 2.1, general m): Phi_3N(X) = Phi_M'(X^s) with
+  // M' = 3 * 2^b', and the roots of Phi_M' are theta^e, e in (Z/M')^*, in the
+  // Galois ring GR(p^r, 2) = Z_{p^r}[u] / (u^2 - gr_c).
+  int Mp = 0, s = 0, nprime = 0;  // M', s, deg Phi_M' = N / s
+  u64 gr_c = 0;                   // quadratic non-residue mod p
+  u64 theta[2] = {0, 0};          // primitive M'-th root of unity in GR(p^r, 2): theta[0] + theta[1] u
+  std::vector<std::pair<int, int>> gens;  // slot-group generators (element mod M', order)
   // keys
   bool have_keys = false;
   std::vector<i64> sk;          // ternary secret, coefficient form
@@ -134,13 +144,15 @@ struct Context {
 
 // ------------------------------------------------------------- construction
 std::vector<u64> gen_primes(int bits, u64 M, int count);
-u64 find_psi(u64 q, int N);
+u64 find_psi(u64 q, int N);             // smallest primitive 2N-th root of unity mod q
+u64 find_root3(u64 q, int N);           // smallest primitive 3N-th root of unity mod q
 Context make_context(const Params& P);
 
 // ---------------------------------------------------------------- transform
 void ntt_fwd(const Context& C, int prime_idx, Poly& a);  // coefficients -> evaluation form
 void ntt_inv(const Context& C, int prime_idx, Poly& a);  // evaluation form -> coefficients
 Poly automorph_coeff(const Poly& a, int g, u64 q);        // a(X) -> a(X^g) mod X^N+1
+Poly automorph_coeff(const Context& C, const Poly& a, int g, u64 q);  // a(X) -> a(X^g) mod Phi_m
 extern std::atomic<unsigned long long> g_ntt_count;      // limb transforms run so far
 
 // -------------------------------------------------------------------- slots

@@ -285,16 +285,171 @@ u64 find_psi(u64 q, int N) {
   return best;
 }
 
+// Smallest primitive 3N-th root of unity mod q (q = 1 mod 3N). A unit has
+// order exactly 3N when its 3N-th power is 1 and its 3N/2-th and N-th powers
+// are not (the maximal proper divisors of 3N = 3 * 2^k).
+u64 find_root3(u64 q, int N) {
+  const u64 m = 3 * (u64)N;
+  auto order_m = [&](u64 x) {
+    return powmod(x, m, q) == 1 && powmod(x, m / 2, q) != 1 && powmod(x, m / 3, q) != 1;
+  };
+  u64 c = 0;
+  for (u64 x = 2; !c; ++x) {
+    u64 y = powmod(x, (q - 1) / m, q);
+    if (order_m(y)) c = y;
+  }
+  // the primitive 3N-th roots are c^j, gcd(j, 6) = 1; take the smallest
+  u64 best = c, w = 1;
+  for (u64 j = 1; j < m; ++j) {
+    w = mulmod(w, c, q);
+    if (j % 2 != 0 && j % 3 != 0 && w < best) best = w;
+  }
+  return best;
+}
+
 static u64 ipow(u64 b, int e) { u64 r = 1; while (e-- > 0) r *= b; return r; }
+
+// ------------------------------------------------ Galois ring GR(p^k, 2)
+// Z_{p^k}[u] / (u^2 - c) with c a quadratic non-residue mod p: the unramified
+// degree-2 extension of Z_{p^k}. An element is x[0] + x[1] u.
+struct GR2 {
+  u64 x[2];
+};
+static GR2 gr_mul(const GR2& a, const GR2& b, u64 c, u64 t) {
+  u64 r0 = addmod(mulmod(a.x[0], b.x[0], t), mulmod(c, mulmod(a.x[1], b.x[1], t), t), t);
+  u64 r1 = addmod(mulmod(a.x[0], b.x[1], t), mulmod(a.x[1], b.x[0], t), t);
+  return GR2{{r0, r1}};
+}
+static GR2 gr_add(const GR2& a, const GR2& b, u64 t) { return GR2{{addmod(a.x[0], b.x[0], t), addmod(a.x[1], b.x[1], t)}}; }
+static GR2 gr_sub(const GR2& a, const GR2& b, u64 t) { return GR2{{submod(a.x[0], b.x[0], t), submod(a.x[1], b.x[1], t)}}; }
+static GR2 gr_pow(GR2 a, u64 e, u64 c, u64 t) {
+  GR2 r{{1 % t, 0}};
+  while (e) {
+    if (e & 1) r = gr_mul(r, a, c, t);
+    a = gr_mul(a, a, c, t);
+    e >>= 1;
+  }
+  return r;
+}
+// (a0 + a1 u)^-1 = (a0 - a1 u) / (a0^2 - c a1^2); the norm is a unit for units
+static GR2 gr_inv(const GR2& a, u64 c, u64 t) {
+  u64 nrm = submod(mulmod(a.x[0], a.x[0], t), mulmod(c, mulmod(a.x[1], a.x[1], t), t), t);
+  u64 ni = invmod(nrm, t);
+  return GR2{{mulmod(a.x[0], ni, t), mulmod(submod(0, a.x[1], t), ni, t)}};
+}
+static bool gr_is(const GR2& a, u64 v0, u64 v1) { return a.x[0] == v0 && a.x[1] == v1; }
+
+// Slot algebra of Phi_3N mod p^r (Section 2.1 with m = 3N, N = 2^k).
+// With 2^b the largest power of two dividing p^2 - 1, b' = min(b, k),
+// M' = 3 * 2^b' and s = 3N / M': Phi_3N(X) = Phi_M'(X^s), and Phi_M'(y)
+// splits over GR(p^r, 2) into the linear factors y - theta^e, e in (Z/M')^*,
+// because M' divides p^2 - 1. Frobenius maps theta^e to theta^(e p), so the
+// slots (the factors of Phi_3N over Z_{p^r}) are the orbits of (Z/M')^*
+// under multiplication by p. A plaintext with constant slot values is
+// A(X^s) with A(theta^e) = value of e's slot for every root.
+static void make_slots_m3(Context& C) {
+  const Params& P = C.P;
+  const u64 p = (u64)P.p;
+  int b = 0;
+  for (u64 v = p * p - 1; v % 2 == 0; v /= 2) ++b;
+  const int bp = std::min(b, P.logN);
+  C.Mp = 3 << bp;
+  C.s = 3 * P.N / C.Mp;
+  C.nprime = P.N / C.s;
+  for (u64 c = 2; c < p; ++c)
+    if (powmod(c, (p - 1) / 2, p) == p - 1) { C.gr_c = c; break; }
+  if (!C.gr_c) throw std::runtime_error("no quadratic non-residue");
+  // theta_0: the first element x0 + x1 u of F_{p^2} (index x0 + p x1) of order exactly M'
+  const u64 Mp = (u64)C.Mp;
+  GR2 th0{{0, 0}};
+  for (u64 i = 1; i < p * p; ++i) {
+    GR2 x{{i % p, i / p}};
+    if (gr_is(gr_pow(x, Mp, C.gr_c, p), 1, 0) && !gr_is(gr_pow(x, Mp / 2, C.gr_c, p), 1, 0) &&
+        !gr_is(gr_pow(x, Mp / 3, C.gr_c, p), 1, 0)) { th0 = x; break; }
+  }
+  if (gr_is(th0, 0, 0)) throw std::runtime_error("no primitive M'-th root in F_{p^2}");
+  // Teichmueller lift: theta = theta_0^((p^2)^(r-1)) in GR(p^r, 2), the root of
+  // unity of order M' that reduces to theta_0 mod p
+  GR2 th = th0;
+  for (int i = 1; i < P.r; ++i) th = gr_pow(th, p * p, C.gr_c, C.t);
+  if (!gr_is(gr_pow(th, Mp, C.gr_c, C.t), 1, 0)) throw std::runtime_error("theta lift failed");
+  C.theta[0] = th.x[0];
+  C.theta[1] = th.x[1];
+  // units of Z/M' and the subgroup generated by p
+  auto unit = [&](int e) { return e % 2 != 0 && e % 3 != 0; };
+  std::vector<char> H(C.Mp, 0);
+  for (u64 x = 1 % Mp;;) {
+    if (H[x]) break;
+    H[x] = 1;
+    x = x * (p % Mp) % Mp;
+  }
+  int o = 0;
+  for (int e = 0; e < C.Mp; ++e) o += H[e];
+  C.slots = C.nprime / o;
+  // generators: repeatedly the smallest element of largest order modulo H,
+  // then H <- H <g>
+  C.gens.clear();
+  auto order_mod_H = [&](int g) {
+    int n = 1;
+    for (long x = g; !H[x]; x = x * g % C.Mp) ++n;
+    return n;
+  };
+  int covered = o;
+  while (covered < C.nprime) {
+    int best = -1, bn = 0;
+    for (int g = 1; g < C.Mp; ++g)
+      if (unit(g)) {
+        int n = order_mod_H(g);
+        if (n > bn) { bn = n; best = g; }
+      }
+    C.gens.push_back({best, bn});
+    std::vector<char> H2(C.Mp, 0);
+    for (int h = 0; h < C.Mp; ++h)
+      if (H[h]) {
+        long x = h;
+        for (int j = 0; j < bn; ++j, x = x * best % C.Mp) H2[x] = 1;
+      }
+    H.swap(H2);
+    covered = 0;
+    for (int e = 0; e < C.Mp; ++e) covered += H[e];
+  }
+  // slot j = j_1 + n_1 (j_2 + n_2 (...)) holds the roots theta^(e p^i), e = prod g_i^j_i
+  C.slot_exp.assign(C.slots, 1);
+  for (int j = 0; j < C.slots; ++j) {
+    long e = 1;
+    int rest = j;
+    for (auto& gn : C.gens) {
+      for (int k = 0; k < rest % gn.second; ++k) e = e * gn.first % C.Mp;
+      rest /= gn.second;
+    }
+    C.slot_exp[j] = (int)e;
+  }
+  // slot degree over X: ord_{3N}(p)
+  int d = 1;
+  for (u64 x = p % (3 * (u64)P.N); x != 1; x = x * p % (3 * (u64)P.N)) ++d;
+  C.d = d;
+  if (C.slots * d != P.N) throw std::runtime_error("slot count does not match ord_3N(p)");
+}
 
 Context make_context(const Params& P0) {
   Context C;
   C.P = P0;
   Params& P = C.P;
   if (P.N != (1 << P.logN)) throw std::runtime_error("N must be 2^logN");
+  if (P.m_odd == 0) P.m_odd = 1;
+  if (P.m_odd != 1 && P.m_odd != 3) throw std::runtime_error("m must be 2N or 3N");
   if (P.nmax == 0) P.nmax = P.N;
   if (P.nmax < P.N) throw std::runtime_error("nmax < N");
   C.t = ipow((u64)P.p, P.r);
+  C.m = P.m_odd == 3 ? 3 * P.N : 2 * P.N;
+  if (P.m_odd == 3) {
+    if (P.p % 3 == 0 || P.logN < 3) throw std::runtime_error("m = 3N needs p != 3 and N >= 8");
+    // primes q = 1 mod lcm(3*nmax, p^r) = 3*nmax*p^r (q odd: nmax is even)
+    C.primes = gen_primes(P.bits, 3 * (u64)P.nmax * C.t, P.L + P.alpha);
+    for (u64 q : C.primes) C.psi.push_back(find_root3(q, P.N));
+    make_slots_m3(C);
+    return C;
+  }
   // primes q = 1 mod lcm(2*nmax, p^r); p is odd, so the lcm is the product
   u64 M = 2 * (u64)P.nmax * C.t;
   C.primes = gen_primes(P.bits, M, P.L + P.alpha);
@@ -367,8 +522,65 @@ static void cyclic_ntt(std::vector<u64>& A, u64 omega, u64 q, int logN) {
 
 std::atomic<unsigned long long> g_ntt_count{0};
 
+// m = 3N: Phi_3N(X) = X^N - X^(N/2) + 1 = (X^(N/2) - rho_0)(X^(N/2) - rho_1)
+// with rho_h = omega^(e_h N/2), e_0 = 1, e_1 = 5, omega the primitive 3N-th
+// root (rho_0 is a primitive 6th root of unity, rho_1 = rho_0^5). Half h of
+// the evaluation form holds a mod (X^(N/2) - rho_h) at its roots
+// omega^(e_h + 6k), k < N/2: twist by omega^(e_h i), then the cyclic transform
+// of length N/2 with omega^6; word h N/2 + j = a(omega^(e_h + 6 bitrev(j))).
+static void ntt_fwd_m3(const Context& C, int pi, Poly& a) {
+  const int N = C.P.N, n = N / 2, logn = C.P.logN - 1;
+  const u64 q = C.primes[pi], w = C.psi[pi];
+  Poly out(N);
+  for (int h = 0; h < 2; ++h) {
+    const u64 eh = h == 0 ? 1 : 5;
+    const u64 rho = powmod(w, eh * (u64)n, q), tw = powmod(w, eh, q);
+    std::vector<u64> b(n);
+    u64 pw = 1;
+    for (int i = 0; i < n; ++i) {
+      b[i] = mulmod(addmod(a[i], mulmod(rho, a[i + n], q), q), pw, q);
+      pw = mulmod(pw, tw, q);
+    }
+    cyclic_ntt(b, powmod(w, 6, q), q, logn);
+    for (int j = 0; j < n; ++j) out[(size_t)h * n + j] = b[bitrev(j, logn)];
+  }
+  a = out;
+}
+
+// Inverse of ntt_fwd_m3: per half the inverse cyclic transform and untwist
+// give b_h = a mod (X^(N/2) - rho_h); then the Chinese remainder step
+// a_hi = (b_0 - b_1) / (rho_0 - rho_1), a_lo = b_0 - rho_0 a_hi.
+static void ntt_inv_m3(const Context& C, int pi, Poly& a) {
+  const int N = C.P.N, n = N / 2, logn = C.P.logN - 1;
+  const u64 q = C.primes[pi], w = C.psi[pi];
+  const u64 n_inv = invmod((u64)n, q);
+  std::vector<u64> b[2];
+  u64 rho[2];
+  for (int h = 0; h < 2; ++h) {
+    const u64 eh = h == 0 ? 1 : 5;
+    rho[h] = powmod(w, eh * (u64)n, q);
+    const u64 tw_inv = invmod(powmod(w, eh, q), q);
+    std::vector<u64> B(n);
+    for (int k = 0; k < n; ++k) B[k] = a[(size_t)h * n + bitrev(k, logn)];
+    cyclic_ntt(B, invmod(powmod(w, 6, q), q), q, logn);
+    b[h].resize(n);
+    u64 pw = 1;
+    for (int i = 0; i < n; ++i) {
+      b[h][i] = mulmod(mulmod(B[i], n_inv, q), pw, q);
+      pw = mulmod(pw, tw_inv, q);
+    }
+  }
+  const u64 dinv = invmod(submod(rho[0], rho[1], q), q);
+  for (int i = 0; i < n; ++i) {
+    u64 hi = mulmod(submod(b[0][i], b[1][i], q), dinv, q);
+    a[i] = submod(b[0][i], mulmod(rho[0], hi, q), q);
+    a[i + n] = hi;
+  }
+}
+
 void ntt_fwd(const Context& C, int pi, Poly& a) {
   ++g_ntt_count;
+  if (C.P.m_odd == 3) return ntt_fwd_m3(C, pi, a);
   int N = C.P.N, logN = C.P.logN;
   u64 q = C.primes[pi], psi = C.psi[pi];
   std::vector<u64> b(N);
@@ -380,6 +592,7 @@ void ntt_fwd(const Context& C, int pi, Poly& a) {
 
 void ntt_inv(const Context& C, int pi, Poly& a) {
   ++g_ntt_count;
+  if (C.P.m_odd == 3) return ntt_inv_m3(C, pi, a);
   int N = C.P.N, logN = C.P.logN;
   u64 q = C.primes[pi], psi = C.psi[pi];
   std::vector<u64> A(N);
@@ -405,10 +618,95 @@ Poly automorph_coeff(const Poly& a, int g, u64 q) {
   return out;
 }
 
+// a(X) -> a(X^g) mod Phi_m. For m = 3N: X^(3N/2) = -1 and X^N = X^(N/2) - 1
+// modulo Phi_3N, so X^e (e mod 3N, folded to [0, 3N/2) with a sign) is X^e
+// for e < N and X^(e - N/2) - X^(e - N) for N <= e < 3N/2.
+Poly automorph_coeff(const Context& C, const Poly& a, int g, u64 q) {
+  if (C.P.m_odd != 3) return automorph_coeff(a, g, q);
+  const long N = (long)a.size(), m = 3 * N, half = m / 2;
+  Poly out(N, 0);
+  for (long i = 0; i < N; ++i) {
+    long e = ((long)g * i) % m;
+    u64 v = a[i] % q;
+    if (e >= half) { e -= half; v = (q - v) % q; }
+    if (e < N) {
+      out[e] = addmod(out[e], v, q);
+    } else {
+      out[e - N / 2] = addmod(out[e - N / 2], v, q);
+      out[e - N] = submod(out[e - N], v, q);
+    }
+  }
+  return out;
+}
+
 // ===================================================================== slots
+// m = 3N. Encoding constant slots v: the polynomial A of degree < n' = deg
+// Phi_M' with A(theta^e) = v[slot of e] for every root theta^e of Phi_M',
+// by Lagrange interpolation at the roots written with the node polynomial:
+// A(y) = sum_e v_e Phi_M'(y) / ((y - theta^e) Phi_M''(theta^e)), where
+// Phi_M'(y) = y^n' - y^(n'/2) + 1. The result has coefficients in Z_{p^t}
+// (the values are Frobenius-invariant); m(X) = A(X^s).
+static std::vector<u64> encode_m3(const Context& C, u64 t, const std::vector<u64>& v) {
+  const int n = C.nprime, s = C.s, Mp = C.Mp;
+  const u64 c = C.gr_c;
+  const GR2 th{{C.theta[0] % t, C.theta[1] % t}};
+  // slot of every exponent e in (Z/M')^*: the orbit representatives are slot_exp
+  std::vector<int> slot_of(Mp, -1);
+  for (int j = 0; j < C.slots; ++j) {
+    long e = C.slot_exp[j];
+    for (int k = 0; k < Mp && slot_of[e] < 0; ++k, e = e * (C.P.p % Mp) % Mp) slot_of[e] = j;
+  }
+  std::vector<GR2> A(n, GR2{{0, 0}});
+  const u64 nn = (u64)n % t, nh = (u64)(n / 2) % t;
+  for (int e = 1; e < Mp; ++e) {
+    if (e % 2 == 0 || e % 3 == 0) continue;
+    if (slot_of[e] < 0) throw std::runtime_error("encode: root outside every slot");
+    const GR2 z = gr_pow(th, (u64)e, c, t);
+    // Phi'(z) = n z^(n-1) - (n/2) z^(n/2-1)
+    GR2 d1 = gr_pow(z, (u64)(n - 1), c, t), d2 = gr_pow(z, (u64)(n / 2 - 1), c, t);
+    GR2 dphi = gr_sub(GR2{{mulmod(nn, d1.x[0], t), mulmod(nn, d1.x[1], t)}},
+                      GR2{{mulmod(nh, d2.x[0], t), mulmod(nh, d2.x[1], t)}}, t);
+    GR2 coef = gr_inv(dphi, c, t);
+    const u64 val = v[slot_of[e]] % t;
+    coef = GR2{{mulmod(coef.x[0], val, t), mulmod(coef.x[1], val, t)}};
+    // synthetic division Phi(y) / (y - z): quotient digits from the top
+    GR2 qk{{1 % t, 0}};  // coefficient of y^(n-1)
+    for (int k = n - 1; k >= 0; --k) {
+      A[k] = gr_add(A[k], gr_mul(coef, qk, c, t), t);
+      if (k == 0) break;
+      // q_{k-1} = phi_k + z q_k, phi_k = -1 at k = n/2, else 0 (0 < k < n)
+      GR2 nq = gr_mul(z, qk, c, t);
+      if (k == n / 2) nq = gr_sub(nq, GR2{{1 % t, 0}}, t);
+      qk = nq;
+    }
+  }
+  std::vector<u64> m(C.P.N, 0);
+  for (int k = 0; k < n; ++k) {
+    if (A[k].x[1] != 0) throw std::runtime_error("encode: interpolant leaves Z_{p^t}");
+    m[(size_t)k * s] = A[k].x[0];
+  }
+  return m;
+}
+
+// m = 3N. Slot j's value: A_0(theta^e_j), A_0(y) = sum_k m[k s] y^k, read as
+// its Z_{p^t} coordinate (exact for constant slots).
+static std::vector<u64> decode_m3(const Context& C, u64 t, const std::vector<u64>& coeffs) {
+  const GR2 th{{C.theta[0] % t, C.theta[1] % t}};
+  std::vector<u64> v(C.slots, 0);
+  for (int j = 0; j < C.slots; ++j) {
+    const GR2 z = gr_pow(th, (u64)C.slot_exp[j], C.gr_c, t);
+    GR2 acc{{0, 0}};
+    for (int k = C.nprime - 1; k >= 0; --k)  // Horner
+      acc = gr_add(gr_mul(acc, z, C.gr_c, t), GR2{{coeffs[(size_t)k * C.s] % t, 0}}, t);
+    v[j] = acc.x[0];
+  }
+  return v;
+}
+
 std::vector<u64> encode(const Context& C, int t_exp, const std::vector<u64>& v) {
   u64 t = ipow((u64)C.P.p, t_exp);
   if ((int)v.size() != C.slots) throw std::runtime_error("encode: wrong slot count");
+  if (C.P.m_odd == 3) return encode_m3(C, t, v);
   u64 w = C.omega % t;
   u64 inv_l = invmod((u64)C.slots % t, t);
   std::vector<u64> m(C.P.N, 0);
@@ -427,6 +725,7 @@ std::vector<u64> encode(const Context& C, int t_exp, const std::vector<u64>& v) 
 
 std::vector<u64> decode(const Context& C, int t_exp, const std::vector<u64>& coeffs) {
   u64 t = ipow((u64)C.P.p, t_exp);
+  if (C.P.m_odd == 3) return decode_m3(C, t, coeffs);
   u64 w = C.omega % t;
   int two_l = 2 * C.slots;
   std::vector<u64> v(C.slots, 0);
@@ -526,7 +825,7 @@ void keygen(Context& C, const std::vector<int>& galois) {
   for (int g : galois) {
     std::vector<Poly> sg(nl);
     limb_for(C, nl, [&](int i) {
-      sg[i] = automorph_coeff(to_limb(C, C.sk, i), g, C.primes[i]);
+      sg[i] = automorph_coeff(C, to_limb(C, C.sk, i), g, C.primes[i]);
       ntt_fwd(C, i, sg[i]);
     });
     C.gk[g] = make_ksk(C, sg, (u32)g);
@@ -870,7 +1169,7 @@ Ct rotate(const Context& C, const Ct& a, int g) {
     int c = ci / a.level, i = ci % a.level;
     Poly x = a.c[c][i];
     ntt_inv(C, i, x);
-    x = automorph_coeff(x, g, C.primes[i]);
+    x = automorph_coeff(C, x, g, C.primes[i]);
     ntt_fwd(C, i, x);
     s.c[c][i] = x;
   });

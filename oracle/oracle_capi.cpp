@@ -32,11 +32,11 @@ extern "C" {
 
 const char* orc_last_error() { return g_err.c_str(); }
 
-void* orc_ctx_new(int logN, int L, int alpha, int bits, int p, int r, int h, int nmax, uint64_t seed) {
+void* orc_ctx_new(int logN, int L, int alpha, int bits, int p, int r, int h, int nmax, uint64_t seed, int m_odd) {
   return guard_ptr([&]() -> void* {
     Params P;
     P.logN = logN; P.N = 1 << logN; P.L = L; P.alpha = alpha; P.bits = bits;
-    P.p = p; P.r = r; P.h = h; P.nmax = nmax; P.seed = seed;
+    P.p = p; P.r = r; P.h = h; P.nmax = nmax; P.seed = seed; P.m_odd = m_odd;
     Handle* H = new Handle();
     H->C = make_context(P);
     return H;
@@ -50,6 +50,19 @@ int orc_ctx_info(void* h, int* slots, int* d, uint64_t* t, uint64_t* omega, int*
     Context& C = ctx(h);
     *slots = C.slots; *d = C.d; *t = C.t; *omega = C.omega;
     if (slot_exp) for (int j = 0; j < C.slots; ++j) slot_exp[j] = C.slot_exp[j];
+  });
+}
+
+// m = 3N slot algebra: out[0..5] = m, M', s, n', c, number of generators;
+// theta = (theta[0], theta[1]); gens[2i], gens[2i+1] = generator i and its order.
+int orc_ctx_ring(void* h, int* out, uint64_t* theta, int* gens) {
+  return guard([&] {
+    Context& C = ctx(h);
+    out[0] = C.m; out[1] = C.Mp; out[2] = C.s; out[3] = C.nprime; out[4] = (int)C.gr_c;
+    out[5] = (int)C.gens.size();
+    theta[0] = C.theta[0]; theta[1] = C.theta[1];
+    if (gens)
+      for (size_t i = 0; i < C.gens.size(); ++i) { gens[2 * i] = C.gens[i].first; gens[2 * i + 1] = C.gens[i].second; }
   });
 }
 
@@ -80,7 +93,7 @@ int orc_ntt_inv(void* h, int pi, uint64_t* a) {
 int orc_automorph_coeff(void* h, int pi, int g, uint64_t* a) {
   return guard([&] {
     Poly x(a, a + ctx(h).P.N);
-    x = automorph_coeff(x, g, ctx(h).primes[pi]);
+    x = automorph_coeff(ctx(h), x, g, ctx(h).primes[pi]);
     std::memcpy(a, x.data(), x.size() * 8);
   });
 }

@@ -395,8 +395,23 @@ Ct raise_modulus(const Context& C, const Ct& lt, Trace* tr) {
 }
 
 // Galois elements for a full slot sum: 5^(2^i) for i < log2(slots/2), then -1.
+// m = 3N: for each slot-group generator g_i of order n_i (in the order chosen),
+// g_i^(2^a) mod 3N for a < log2 n_i. Summing x + sigma(x) over these in turn
+// adds up sigma_h(x) over one element h of every slot class, because the
+// products g_1^j_1 g_2^j_2 ... (j_i < n_i) are a transversal of (Z/M')^*/<p>.
 std::vector<int> rotate_sum_elements(const Context& C) {
   std::vector<int> g;
+  if (C.P.m_odd == 3) {
+    const long m = C.m;
+    for (auto& gn : C.gens) {
+      long e = gn.first % m;
+      for (int n = 1; n < gn.second; n *= 2) {
+        g.push_back((int)e);
+        e = e * e % m;
+      }
+    }
+    return g;
+  }
   int twoN = 2 * C.P.N;
   if (C.slots >= 2) {
     long e = 5;
