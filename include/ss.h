@@ -9,13 +9,19 @@
  * back to Z_{p^r} with G_{p,r} (Section 4.4).
  *
  * Conventions shared by every call
- *  - Ring Z[X]/(X^N+1), N a power of two. RNS chain of L data primes
- *    q_0 > ... > q_{L-1} and alpha special primes, all = 1 mod 2*nmax*p^r.
+ *  - Ring Z[X]/Phi_m(X), N a power of two: m = 2N, Phi_m = X^N+1 (the
+ *    default), or m = 3N, Phi_m = X^N - X^(N/2) + 1 (ss_params.m_odd = 3; the
+ *    paper's general cyclotomic m, Section 2.1, with N / Ord(3N, p) slots).
+ *    RNS chain of L data primes q_0 > ... > q_{L-1} and alpha special primes,
+ *    all = 1 mod (m/N)*nmax*p^r.
  *  - A ciphertext batch (ss_ct) lives in caller-owned DEVICE memory laid out
  *    uint64[count][ncomp][capacity][N]: limb i of component c of ciphertext b
  *    starts at data + ((b*ncomp + c)*capacity + i)*N. Limbs are stored in
- *    evaluation (NTT) form: word j of limb i is a(psi_i^(2*bitrev(j)+1)) mod
- *    q_i with psi_i the smallest primitive 2N-th root of unity mod q_i.
+ *    evaluation (NTT) form, psi_i the smallest primitive m-th root of unity
+ *    mod q_i: for m = 2N word j of limb i is a(psi_i^(2*bitrev(j)+1)) mod q_i;
+ *    for m = 3N word h*N/2 + j (h = 0, 1; j < N/2) is
+ *    a(psi_i^(e_h + 6*bitrev(j))) with e_0 = 1, e_1 = 5 and bitrev over
+ *    log2(N/2) bits.
  *    Only limbs 0..level-1 are meaningful. The library never frees caller
  *    memory; outputs must have capacity >= the level they receive.
  *  - Every device call is enqueued on the given stream (NULL = legacy default
@@ -65,6 +71,9 @@ typedef struct {
   int32_t h;        /* Hamming weight of the ternary secret (Section 5.1: 120) */
   int32_t nmax;     /* largest N the prime chain must support (0 = N) */
   uint64_t seed;    /* Philox4x32-10 key for every sampled value */
+  int32_t m_odd;    /* odd part of the cyclotomic index m (Section 2.1, 5.1): 0 or 1 -> m = 2N,
+                       ring Z[X]/(X^N + 1); 3 -> m = 3N, ring Z[X]/(X^N - X^(N/2) + 1) */
+  int32_t reserved; /* 0 */
 } ss_params;
 
 typedef struct {
@@ -95,16 +104,29 @@ ss_status ss_context_info(const ss_ctx* ctx, int32_t* N, int32_t* L, int32_t* al
 
 /* Secret key (ternary, Hamming weight h; Section 2.1 and 5.1), the
  * relinearisation key for s^2 and one Galois key per element of `galois`
- * (odd residues mod 2N). Keys are hybrid key-switching keys over the data and
+ * (units mod m: odd residues mod 2N, or residues mod 3N prime to 6). Keys are hybrid key-switching keys over the data and
  * special primes, device-resident and owned by ctx. Synchronous. */
 ss_status ss_keygen(ss_ctx* ctx, const int32_t* galois, int32_t ngalois);
 
-/* Galois elements ss_rotate_sum uses (5^(2^i) mod 2N for i < log2(slots/2),
- * then 2N-1); returns the count, writes up to cap elements. */
+/* Galois elements ss_rotate_sum uses; returns the count, writes up to cap
+ * elements. m = 2N: 5^(2^i) mod 2N for i < log2(slots/2), then 2N-1.
+ * m = 3N: for each slot-group generator g of order n (below), g^(2^i) mod 3N
+ * for i < log2 n, generators in their order. */
 int32_t ss_rotate_sum_elements(const ss_ctx* ctx, int32_t* out, int32_t cap);
 
 /* Slot encoding over Z_{p^t_exp} (host, synchronous): slots[slots] ->
- * coefficients[N]; slot j is the constant value modulo X^d - zeta_j. */
+ * coefficients[N]. m = 2N: slot j is the constant value modulo X^d - zeta_j.
+ * m = 3N: with 2^b the largest power of two dividing p^2 - 1, b' = min(b,
+ * log2 N), M' = 3*2^b' and s = 3N/M', Phi_3N(X) = Phi_M'(X^s) and Phi_M'
+ * splits over the Galois ring GR(p^r, 2) = Z_{p^r}[u]/(u^2 - c) (c the
+ * smallest quadratic non-residue mod p) at theta^e, e in (Z/M')^*, theta the
+ * root of unity of order M' lifting the first element x0 + x1 u of F_{p^2}
+ * (in the order x0 + p*x1) of that order. Slots are the orbits of (Z/M')^*
+ * under multiplication by p; slot j = j_1 + n_1 (j_2 + n_2 (...)) is the
+ * orbit of g_1^j_1 g_2^j_2 ..., where g_i is the smallest residue of largest
+ * order n_i modulo the subgroup generated by p, g_1, ..., g_{i-1}. The
+ * encoding is A(X^s) with A(theta^e) = the value of e's slot; decoding
+ * returns the Z_{p^t} coordinate of A_0(theta^e_j), A_0 = sum_k c[k s] y^k. */
 ss_status ss_encode(const ss_ctx* ctx, int32_t t_exp, const uint64_t* slots, uint64_t* coeffs);
 ss_status ss_decode(const ss_ctx* ctx, int32_t t_exp, const uint64_t* coeffs, uint64_t* slots);
 
@@ -119,6 +141,7 @@ ss_status ss_encrypt(ss_ctx* ctx, const uint64_t* coeffs, int32_t count, uint32_
  * Only the coefficients at multiples of d are computed (the slot
  * coefficients); the others are written as zero. */
 ss_status ss_decrypt(ss_ctx* ctx, const ss_ct* in, uint64_t* coeffs, ss_stream stream);
+/* (For m = 3N the computed coefficients are those at multiples of s.) */
 
 /* ---- BGV operations (Section 2.1); operands must share level and t_exp ---- */
 ss_status ss_add(ss_ctx* ctx, const ss_ct* a, const ss_ct* b, ss_ct* out, ss_stream stream);
@@ -308,11 +331,11 @@ ss_status ss_set_g_table(ss_ctx* ctx, int32_t mode);
 ss_status ss_set_batch(ss_ctx* ctx, int32_t batch);
 
 /* ---- raw transform (for kernel-level measurement) ---- */
-/* In-place negacyclic NTT of `npoly` consecutive limbs of N words; limb k uses
+/* In-place NTT over the context's ring of `npoly` consecutive limbs of N words; limb k uses
  * data prime (first_prime + k % nprimes). Input words must be residues below
- * their prime (the forward transform keeps lazy sums below 36q, which needs
+ * their prime (the forward transform keeps lazy sums below 40q, which needs
  * inputs below 4q); outputs are residues below the prime, forward in the
- * evaluation order word j = a(psi^(2 bitrev(j) + 1)). */
+ * evaluation order given above. */
 ss_status ss_ntt_forward(ss_ctx* ctx, uint64_t* data, int32_t npoly, int32_t first_prime, int32_t nprimes,
                          ss_stream stream);
 ss_status ss_ntt_inverse(ss_ctx* ctx, uint64_t* data, int32_t npoly, int32_t first_prime, int32_t nprimes,

@@ -28,7 +28,7 @@ class SSError(RuntimeError):
 class ss_params(C.Structure):
     _fields_ = [("logN", C.c_int32), ("L", C.c_int32), ("alpha", C.c_int32), ("bits", C.c_int32),
                 ("p", C.c_int32), ("r", C.c_int32), ("h", C.c_int32), ("nmax", C.c_int32),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("m_odd", C.c_int32), ("reserved", C.c_int32)]
 
 
 class ss_ct(C.Structure):
@@ -342,6 +342,9 @@ class Context:
         self.primes = np.array(list(pr), dtype=np.uint64)
         self.p, self.r = params.p, params.r
         self.t = self.p ** self.r
+        # cyclotomic index: m = 2N (X^N + 1) or 3N (X^N - X^(N/2) + 1)
+        self.m_odd = 3 if params.m_odd == 3 else 1
+        self.m = (3 if self.m_odd == 3 else 2) * self.N
 
     def close(self):
         if getattr(self, "h", None):

@@ -98,6 +98,24 @@ u64 root2n(u64 q, int N) {
   return best;
 }
 
+// Smallest primitive 3N-th root of unity mod q (q = 1 mod 3N): some unit
+// raised to (q-1)/3N whose N-th and 3N/2-th powers differ from 1, then the
+// least of its powers with exponent prime to 6.
+u64 root3n(u64 q, int N) {
+  const u64 m = 3 * (u64)N;
+  u64 g = 0;
+  for (u64 x = 2; !g; ++x) {
+    u64 c = pow(x, (q - 1) / m, q);
+    if (pow(c, (u64)N, q) != 1 && pow(c, m / 2, q) != 1) g = c;
+  }
+  u64 best = g, cur = 1;
+  for (u64 j = 1; j < m; ++j) {
+    cur = mul(cur, g, q);
+    if (j % 6 == 1 || j % 6 == 5) best = std::min(best, cur);
+  }
+  return best;
+}
+
 static u64 upow(u64 b, int e) {
   u64 r = 1;
   for (int i = 0; i < e; ++i) r *= b;
@@ -254,6 +272,113 @@ std::vector<i64> flt_coeffs(int p) {
 
 }  // namespace nt
 
+// ------------------------------------------------------------------ m = 3N slots
+// Degree-2 Galois ring GR(p^k, 2) = Z_{p^k}[u]/(u^2 - c): pairs (a0, a1).
+namespace {
+struct Gr {
+  u64 a0, a1;
+};
+struct GrRing {
+  u64 c, t;
+  Gr mul(Gr x, Gr y) const {
+    return {(nt::mul(x.a0, y.a0, t) + nt::mul(c, nt::mul(x.a1, y.a1, t), t)) % t,
+            (nt::mul(x.a0, y.a1, t) + nt::mul(x.a1, y.a0, t)) % t};
+  }
+  Gr add(Gr x, Gr y) const { return {(x.a0 + y.a0) % t, (x.a1 + y.a1) % t}; }
+  Gr sub(Gr x, Gr y) const { return {(x.a0 + t - y.a0) % t, (x.a1 + t - y.a1) % t}; }
+  Gr scale(Gr x, u64 k) const { return {nt::mul(x.a0, k, t), nt::mul(x.a1, k, t)}; }
+  Gr pow(Gr x, u64 e) const {
+    Gr r{1 % t, 0};
+    for (; e; e >>= 1, x = mul(x, x))
+      if (e & 1) r = mul(r, x);
+    return r;
+  }
+  Gr inv(Gr x) const {  // conjugate over the norm a0^2 - c a1^2
+    u64 nrm = (nt::mul(x.a0, x.a0, t) + t - nt::mul(c, nt::mul(x.a1, x.a1, t), t)) % t;
+    u64 ni = nt::inv(nrm, t);
+    return {nt::mul(x.a0, ni, t), nt::mul((t - x.a1) % t, ni, t)};
+  }
+  static bool one(Gr x) { return x.a0 == 1 && x.a1 == 0; }
+};
+}  // namespace
+
+// Slot structure of Phi_3N over Z_{p^r} (Section 2.1 for m = 3N): M' = 3*2^b'
+// (2^b || p^2 - 1, b' = min(b, log2 N)), s = 3N/M', Phi_3N(X) = Phi_M'(X^s),
+// roots theta^e (e a unit mod M') in GR(p^r, 2); slots = orbits under x p.
+static void build_slots_m3(Context& C) {
+  const u64 p = (u64)C.p;
+  int b = 0;
+  for (u64 v = p * p - 1; !(v & 1); v >>= 1) ++b;
+  const int bp = std::min(b, C.logN);
+  C.Mp = 3 << bp;
+  C.s_stride = 3 * C.N / C.Mp;
+  C.nprime = C.N / C.s_stride;
+  C.gr_c = 0;
+  for (u64 c = 2; c < p && !C.gr_c; ++c)
+    if (nt::pow(c, (p - 1) / 2, p) == p - 1) C.gr_c = c;
+  const u64 Mp = (u64)C.Mp;
+  // theta_0: first x0 + x1 u of F_{p^2} (index x0 + p x1) of order exactly M'
+  GrRing F{C.gr_c, p};
+  Gr th{0, 0};
+  for (u64 i = 1; i < p * p && th.a0 == 0 && th.a1 == 0; ++i) {
+    Gr x{i % p, i / p};
+    if (GrRing::one(F.pow(x, Mp)) && !GrRing::one(F.pow(x, Mp / 2)) && !GrRing::one(F.pow(x, Mp / 3))) th = x;
+  }
+  if (th.a0 == 0 && th.a1 == 0) throw Error(SS_ERR_PARAM, "no root of unity of order M' in F_{p^2}");
+  // Newton's iteration for y^M' = 1 in GR(p^r, 2): y <- y - (y^M' - 1) / (M' y^(M'-1))
+  GrRing R{C.gr_c, C.t};
+  for (int it = 0; it <= C.r; ++it) {
+    Gr f = R.sub(R.pow(th, Mp), Gr{1 % C.t, 0});
+    Gr df = R.scale(R.pow(th, Mp - 1), Mp % C.t);
+    th = R.sub(th, R.mul(f, R.inv(df)));
+  }
+  if (!GrRing::one(R.pow(th, Mp))) throw Error(SS_ERR_PARAM, "root lift failed");
+  C.theta[0] = th.a0;
+  C.theta[1] = th.a1;
+  // slot group (Z/M')^* / <p>: generators, smallest residue of largest order first
+  std::vector<char> inH(Mp, 0);
+  int hsize = 0;
+  for (u64 x = 1; !inH[x]; x = x * (p % Mp) % Mp, ++hsize) inH[x] = 1;
+  C.slots = C.nprime / hsize;
+  C.gens.clear();
+  while (hsize < C.nprime) {
+    int gbest = 0, nbest = 0;
+    for (int g = 1; g < C.Mp; ++g) {
+      if (g % 2 == 0 || g % 3 == 0) continue;
+      int n = 1;
+      for (u64 x = (u64)g; !inH[x]; x = x * (u64)g % Mp) ++n;
+      if (n > nbest) { nbest = n; gbest = g; }
+    }
+    C.gens.push_back({gbest, nbest});
+    std::vector<char> nh(Mp, 0);
+    for (u64 h = 0; h < Mp; ++h) {
+      if (!inH[h]) continue;
+      u64 x = h;
+      for (int j = 0; j < nbest; ++j, x = x * (u64)gbest % Mp) nh[x] = 1;
+    }
+    inH.swap(nh);
+    hsize = 0;
+    for (char v : inH) hsize += v;
+  }
+  C.slot_exp.assign(C.slots, 1);
+  for (int j = 0; j < C.slots; ++j) {
+    u64 e = 1;
+    int rest = j;
+    for (auto& gn : C.gens) {
+      e = e * nt::pow((u64)gn.first, (u64)(rest % gn.second), Mp) % Mp;
+      rest /= gn.second;
+    }
+    C.slot_exp[j] = (int)e;
+  }
+  u64 m = 3 * (u64)C.N, x = p % m;
+  int d = 1;
+  for (; x != 1; x = x * p % m) ++d;
+  C.d = d;
+  if ((long)C.slots * d != C.N) throw Error(SS_ERR_PARAM, "slot count does not match the order of p mod 3N");
+  C.dec_stride = C.s_stride;
+  C.dec_count = C.nprime;
+}
+
 // ------------------------------------------------------------------ context
 static void upload(void** dst, const void* src, size_t bytes) {
   SS_CUDA(cudaMalloc(dst, bytes));
@@ -281,6 +406,8 @@ void build_context(Context& C, const ss_params& prm) {
   if (prm.L < 1 || prm.alpha < 1 || prm.L > 200 || prm.alpha > 16) throw Error(SS_ERR_PARAM, "bad L/alpha");
   if (prm.bits < 20 || prm.bits > 58) throw Error(SS_ERR_PARAM, "bits must be in [20, 58]");
   if (prm.p < 5 || prm.p % 4 != 1 || !nt::prime((u64)prm.p)) throw Error(SS_ERR_PARAM, "p must be a prime = 1 mod 4");
+  if (prm.m_odd != 0 && prm.m_odd != 1 && prm.m_odd != 3) throw Error(SS_ERR_PARAM, "m_odd must be 1 (m = 2N) or 3 (m = 3N)");
+  C.m_odd = prm.m_odd == 3 ? 3 : 1;
   if (prm.r < 1 || prm.r > 8) throw Error(SS_ERR_PARAM, "bad r");
   C.logN = prm.logN;
   C.N = 1 << prm.logN;
@@ -301,12 +428,16 @@ void build_context(Context& C, const ss_params& prm) {
   if ((double)C.dnum * 2.0 >= (double)(1ULL << (63 - prm.bits)))
     throw Error(SS_ERR_PARAM, "too many digits for the lazy inner product at this prime width");
 
-  C.primes = nt::chain(prm.bits, 2 * (u64)nmax * C.t, C.ntot);
+  C.m = C.m_odd == 3 ? 3 * C.N : 2 * C.N;
+  C.primes = nt::chain(prm.bits, (C.m_odd == 3 ? 3 : 2) * (u64)nmax * C.t, C.ntot);
   C.psi.resize(C.ntot);
-  for (int i = 0; i < C.ntot; ++i) C.psi[i] = nt::root2n(C.primes[i], C.N);
+  for (int i = 0; i < C.ntot; ++i)
+    C.psi[i] = C.m_odd == 3 ? nt::root3n(C.primes[i], C.N) : nt::root2n(C.primes[i], C.N);
 
   // slots: d = order of p mod 2N, slots = N/d, X^N+1 = prod (X^d - zeta_j)
-  {
+  if (C.m_odd == 3) {
+    build_slots_m3(C);
+  } else {
     u64 m2 = 2 * (u64)C.N, x = (u64)C.p % m2;
     int d = 1;
     while (x != 1) { x = x * (u64)C.p % m2; ++d; }
@@ -332,6 +463,8 @@ void build_context(Context& C, const ss_params& prm) {
         C.slot_exp[j + h] = (int)((m - g) % m);
       }
     }
+    C.dec_stride = C.d;
+    C.dec_count = C.slots;
   }
 
   const int N = C.N, T = C.ntot;
@@ -350,30 +483,61 @@ void build_context(Context& C, const ss_params& prm) {
   }
   upload((void**)&C.d_mod, md.data(), sizeof(ModDesc) * T);
 
-  // twiddles: psi^brv(i) and psi^-brv(i) with Shoup companions
+  // twiddles: psi^brv(i) and psi^-brv(i) with Shoup companions (m = 2N; m = 3N below)
   {
     std::vector<u64> tw((size_t)T * 4 * N);
     std::vector<u64> ninv(4 * T), pinv(2 * T);
     for (int i = 0; i < T; ++i) {
       u64 q = C.primes[i], ps = C.psi[i], pi = nt::inv(ps, q);
-      std::vector<u64> fw(N), bw(N);
-      u64 a = 1, b = 1;
-      for (int k = 0; k < N; ++k) { fw[k] = a; bw[k] = b; a = nt::mul(a, ps, q); b = nt::mul(b, pi, q); }
       u64* o = &tw[(size_t)i * 4 * N];
-      for (int k = 0; k < N; ++k) {
-        int rk = nt::brv(k, C.logN);
-        o[2 * k] = fw[rk];
-        o[2 * k + 1] = nt::shoup(fw[rk], q);
-        o[2 * N + 2 * k] = bw[rk];
-        o[2 * N + 2 * k + 1] = nt::shoup(bw[rk], q);
-      }
+      auto put = [&](int k, u64 f, u64 bk) {
+        o[2 * k] = f;
+        o[2 * k + 1] = nt::shoup(f, q);
+        o[2 * N + 2 * k] = bk;
+        o[2 * N + 2 * k + 1] = nt::shoup(bk, q);
+      };
       u64 ni = nt::inv((u64)N % q, q);
       ninv[4 * i] = ni;
       ninv[4 * i + 1] = nt::shoup(ni, q);
-      // N^-1 times the last inverse stage's twiddle psi^-bitrev(1) = psi^(-N/2)
-      const u64 wni = nt::mul(ni, bw[N / 2], q);
-      ninv[4 * i + 2] = wni;
-      ninv[4 * i + 3] = nt::shoup(wni, q);
+      if (C.m_odd == 3) {
+        // Phi_3N = (X^(N/2) - rho)(X^(N/2) - rho^5), rho = omega^(N/2): node 1
+        // is that split (forward twiddle rho; the inverse recovers the high
+        // half as (u - v) / (2 rho - 1)). Node k >= 2 at depth l splits
+        // X^(2h) - z^2 into X^h -/+ z for the half e = 1 (k's second bit 0)
+        // or e = 5: z_k = omega^((N/2 >> l) (e + 6 bitrev_{l-1}(j))), j the
+        // index of k within its half at that depth.
+        const u64 m = 3 * (u64)N;
+        std::vector<u64> pw(m);
+        pw[0] = 1;
+        for (u64 e = 1; e < m; ++e) pw[e] = nt::mul(pw[e - 1], ps, q);
+        const u64 rho = pw[N / 2];
+        const u64 wb = nt::inv((2 * rho + q - 1) % q, q);
+        put(0, 1, nt::mul(wb, ni, q));  // inverse word 0: (2 rho - 1)^-1 N^-1 for the fused last stage
+        put(1, rho, wb);
+        for (int k = 2; k < N; ++k) {
+          const int l = 31 - __builtin_clz((unsigned)k);
+          const int h = (k >> (l - 1)) & 1;
+          const int j = k - (1 << l) - (h << (l - 1));
+          const u64 e = (u64)((N / 2) >> l) * ((h ? 5 : 1) + 6 * (u64)nt::brv(j, l - 1)) % m;
+          put(k, pw[e], pw[(m - e) % m]);
+        }
+        // the fused last inverse stage's difference output: 2 (2 rho - 1)^-1 N^-1
+        const u64 c1 = nt::mul(2 % q, nt::mul(wb, ni, q), q);
+        ninv[4 * i + 2] = c1;
+        ninv[4 * i + 3] = nt::shoup(c1, q);
+      } else {
+        std::vector<u64> fw(N), bw(N);
+        u64 a = 1, b = 1;
+        for (int k = 0; k < N; ++k) { fw[k] = a; bw[k] = b; a = nt::mul(a, ps, q); b = nt::mul(b, pi, q); }
+        for (int k = 0; k < N; ++k) {
+          int rk = nt::brv(k, C.logN);
+          put(k, fw[rk], bw[rk]);
+        }
+        // N^-1 times the last inverse stage's twiddle psi^-bitrev(1) = psi^(-N/2)
+        const u64 wni = nt::mul(ni, bw[N / 2], q);
+        ninv[4 * i + 2] = wni;
+        ninv[4 * i + 3] = nt::shoup(wni, q);
+      }
       u64 pv = nt::inv((u64)C.p % q, q);
       pinv[2 * i] = pv;
       pinv[2 * i + 1] = nt::shoup(pv, q);
@@ -539,9 +703,72 @@ static u64 zeta(const Context& C, int j, int power, u64 te) {
   return nt::pow(C.omega % te, e, te);
 }
 
+// m = 3N encoding: the interpolant A (deg < n' = deg Phi_M') with
+// A(theta^e) = V_e, split by the two factors y^(n'/2) - rho_h of Phi_M'
+// (rho_h = theta^(e_h n'/2), e_0 = 1, e_1 = 5): the roots of factor h are
+// theta^(e_h + 6k), so B_h = A mod (y^(n'/2) - rho_h) has the coefficients
+// b_i = (n'/2)^-1 theta^(-e_h i) sum_k V_{e_h+6k} theta^(-6ik) (inverse DFT),
+// and A = A_lo + y^(n'/2) A_hi with A_hi = (B_0 - B_1) / (rho_0 - rho_1),
+// A_lo = B_0 - rho_0 A_hi.
+static std::vector<u64> encode_m3(const Context& C, u64 te, const u64* v) {
+  const GrRing R{C.gr_c, te};
+  const Gr th{C.theta[0] % te, C.theta[1] % te};
+  const int Mp = C.Mp, n = C.nprime, n2 = n / 2;
+  std::vector<int> slot_of(Mp, -1);
+  for (int j = 0; j < C.slots; ++j)
+    for (u64 e = (u64)C.slot_exp[j]; slot_of[e] < 0; e = e * ((u64)C.p % Mp) % Mp) slot_of[e] = j;
+  std::vector<Gr> tpow(Mp);  // theta^e
+  tpow[0] = Gr{1 % te, 0};
+  for (int e = 1; e < Mp; ++e) tpow[e] = R.mul(tpow[e - 1], th);
+  const u64 n2inv = nt::inv((u64)n2 % te, te);
+  std::vector<Gr> B[2];
+  for (int h = 0; h < 2; ++h) {
+    const int eh = h ? 5 : 1;
+    B[h].assign(n2, Gr{0, 0});
+    for (int i = 0; i < n2; ++i) {
+      Gr acc{0, 0};
+      for (int k = 0; k < n2; ++k) {
+        const int e = eh + 6 * k;
+        if (slot_of[e] < 0) throw Error(SS_ERR_PARAM, "encode: root outside the slots");
+        // theta^(-6ik) = theta^(M' - (6ik mod M'))
+        const int ex = (int)((u64)6 * i * k % Mp);
+        acc = R.add(acc, R.scale(tpow[(Mp - ex) % Mp], v[slot_of[e]] % te));
+      }
+      const int tex = (int)((u64)eh * i % Mp);
+      B[h][i] = R.scale(R.mul(acc, tpow[(Mp - tex) % Mp]), n2inv);
+    }
+  }
+  const Gr rho0 = tpow[(u64)n2 % Mp], rho1 = tpow[(u64)5 * n2 % Mp];
+  const Gr dinv = R.inv(R.sub(rho0, rho1));
+  std::vector<u64> m(C.N, 0);
+  for (int i = 0; i < n2; ++i) {
+    const Gr hi = R.mul(R.sub(B[0][i], B[1][i]), dinv);
+    const Gr lo = R.sub(B[0][i], R.mul(rho0, hi));
+    if (hi.a1 != 0 || lo.a1 != 0) throw Error(SS_ERR_PARAM, "encode: interpolant outside Z_{p^t}");
+    m[(size_t)i * C.s_stride] = lo.a0;
+    m[(size_t)(i + n2) * C.s_stride] = hi.a0;
+  }
+  return m;
+}
+
+// m = 3N decoding: slot j reads sum_k c[k s] theta^(e_j k), Z_{p^t} coordinate.
+static std::vector<u64> decode_m3(const Context& C, u64 te, const u64* c) {
+  const GrRing R{C.gr_c, te};
+  const Gr th{C.theta[0] % te, C.theta[1] % te};
+  std::vector<u64> v(C.slots, 0);
+  for (int j = 0; j < C.slots; ++j) {
+    const Gr z = R.pow(th, (u64)C.slot_exp[j]);
+    Gr zk{1 % te, 0}, acc{0, 0};
+    for (int k = 0; k < C.nprime; ++k, zk = R.mul(zk, z)) acc = R.add(acc, R.scale(zk, c[(size_t)k * C.s_stride] % te));
+    v[j] = acc.a0;
+  }
+  return v;
+}
+
 std::vector<u64> encode(const Context& C, int t_exp, const u64* v) {
   if (t_exp < 1 || t_exp > C.r) throw Error(SS_ERR_PARAM, "bad t_exp");
   u64 te = C.tpow[t_exp];
+  if (C.m_odd == 3) return encode_m3(C, te, v);
   u64 il = nt::inv((u64)C.slots % te, te);
   std::vector<u64> m(C.N, 0);
   for (int k = 0; k < C.slots; ++k) {
@@ -556,6 +783,7 @@ std::vector<u64> encode(const Context& C, int t_exp, const u64* v) {
 std::vector<u64> decode(const Context& C, int t_exp, const u64* m) {
   if (t_exp < 1 || t_exp > C.r) throw Error(SS_ERR_PARAM, "bad t_exp");
   u64 te = C.tpow[t_exp];
+  if (C.m_odd == 3) return decode_m3(C, te, m);
   std::vector<u64> v(C.slots, 0);
   for (int j = 0; j < C.slots; ++j) {
     u64 acc = 0;
@@ -567,6 +795,13 @@ std::vector<u64> decode(const Context& C, int t_exp, const u64* m) {
 
 std::vector<int> rotate_sum_elements(const Context& C) {
   std::vector<int> g;
+  if (C.m_odd == 3) {  // g^(2^a) mod 3N for each slot-group generator of order n, a < log2 n
+    for (auto& gn : C.gens) {
+      u64 e = (u64)gn.first % (u64)C.m;
+      for (int n = 1; n < gn.second; n *= 2, e = e * e % (u64)C.m) g.push_back((int)e);
+    }
+    return g;
+  }
   if (C.slots < 2) return g;
   long m = 2L * C.N, e = 5;
   for (int s = 1; s < C.slots / 2; s *= 2, e = e * e % m) g.push_back((int)e);

@@ -469,17 +469,32 @@ __global__ void __launch_bounds__(256, SS_KSIP_MINB) k_ks_ip_multi(const __grid_
 }
 
 // ---------------------------------------------------------------- automorphism
-// evaluation form: word j holds a(psi^(2 brv(j)+1)); sigma_g(a) at that point is
-// a(psi^(g (2 brv(j)+1))), i.e. the word at brv((g (2 brv(j)+1) mod 2N - 1)/2).
+// evaluation form, m = 2N: word j holds a(psi^(2 brv(j)+1)); sigma_g(a) at that
+// point is a(psi^(g (2 brv(j)+1))), i.e. the word at brv((g (2 brv(j)+1) mod 2N - 1)/2).
+// m = 3N: word h N/2 + j holds a(psi^E), E = e_h + 6 brv(j) (e_0 = 1, e_1 = 5,
+// brv over log2(N/2) bits); sigma_g(a) there is the word of exponent g E mod 3N,
+// whose residue mod 6 (1 or 5) gives its half and (gE - e)/6 its index.
+template <bool M3>
 __global__ void k_automorph_impl(const u64* a, u64* out, int g, int N, int logN, int nrows, int acap, int ocap,
                                  int level) {
   int poly = blockIdx.y;  // (bt*ncomp + c, i)
   int i = poly % level, row = poly / level;
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= N) return;
-  unsigned rj = __brev((unsigned)j) >> (32 - logN);
-  unsigned k = (unsigned)(((unsigned long long)g * (2 * rj + 1)) % (2u * (unsigned)N));
-  unsigned src = __brev((k - 1) / 2) >> (32 - logN);
+  unsigned src;
+  if (M3) {
+    const int lh = logN - 1, n2 = N >> 1;
+    const unsigned h = (unsigned)j >> lh, r = (unsigned)j & (unsigned)(n2 - 1);
+    const unsigned E = (h ? 5u : 1u) + 6u * (__brev(r) >> (32 - lh));
+    const unsigned k = (unsigned)(((unsigned long long)g * E) % (3ull * (unsigned)N));
+    const unsigned hs = (k % 6u == 1u) ? 0u : 1u;
+    const unsigned rs = (k - (hs ? 5u : 1u)) / 6u;
+    src = hs * (unsigned)n2 + (__brev(rs) >> (32 - lh));
+  } else {
+    unsigned rj = __brev((unsigned)j) >> (32 - logN);
+    unsigned k = (unsigned)(((unsigned long long)g * (2 * rj + 1)) % (2u * (unsigned)N));
+    src = __brev((k - 1) / 2) >> (32 - logN);
+  }
   out[((size_t)row * ocap + i) * N + j] = a[((size_t)row * acap + i) * N + src];
 }
 
@@ -586,12 +601,12 @@ __global__ void k_dec_dot_impl(const u64* a, int ncomp, int level, int cap, cons
 }
 
 // Garner mixed-radix CRT of one coefficient, centred against (Q-1)/2, mod p^e.
-__global__ void k_crt_impl(const u64* v, int level, int N, int d, int slots, const u64* pinv, const u64* half,
+__global__ void k_crt_impl(const u64* v, int level, int N, int stride, int count, const u64* pinv, const u64* half,
                            const u64* qmodt, u64 te, u64* out, const ModDesc* mods) {
   int bt = blockIdx.y;
   int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= slots) return;
-  int n = k * d;
+  if (k >= count) return;
+  int n = k * stride;
   u64 dig[200];
   for (int i = 0; i < level; ++i) {
     const Modulus& md = MOD(mods, i);
@@ -1147,8 +1162,10 @@ void ks_multi(const std::vector<KsReq>& reqs, cudaStream_t st) {
 void k_automorph(Context& C, const Buf& a, int g, Buf& out, cudaStream_t st) {
   int rows = a.count * a.ncomp;
   TIMED(KC_AUTOMORPH, 2.0 * rows * a.level * (double)C.N * 8.0,
-  k_automorph_impl<<<grid_for(C.N, rows * a.level), TPB, 0, st>>>(a.data, out.data, g, C.N, C.logN, rows, a.cap,
-                                                                   out.cap, a.level));
+  if (C.m_odd == 3) k_automorph_impl<true><<<grid_for(C.N, rows * a.level), TPB, 0, st>>>(
+      a.data, out.data, g, C.N, C.logN, rows, a.cap, out.cap, a.level);
+  else k_automorph_impl<false><<<grid_for(C.N, rows * a.level), TPB, 0, st>>>(
+      a.data, out.data, g, C.N, C.logN, rows, a.cap, out.cap, a.level));
   LAUNCHED();
 }
 
@@ -1212,8 +1229,9 @@ void k_crt(Context& C, const u64* v, int count, int level, int t_exp, u64* out, 
   const u64* pinv = C.d_crt + C.off_crt_pinv;
   const u64* half = C.d_crt + C.off_crt_half[level];
   const u64* qmodt = C.d_crt + C.off_crt_qmodt + (size_t)t_exp * (C.L + 1);
-  dim3 g((C.slots + 127) / 128, count);
-  k_crt_impl<<<g, 128, 0, st>>>(v, level, C.N, C.d, C.slots, pinv, half, qmodt, C.tpow[t_exp], out, C.d_mod);
+  dim3 g((C.dec_count + 127) / 128, count);
+  k_crt_impl<<<g, 128, 0, st>>>(v, level, C.N, C.dec_stride, C.dec_count, pinv, half, qmodt, C.tpow[t_exp], out,
+                                C.d_mod);
   LAUNCHED();
 }
 

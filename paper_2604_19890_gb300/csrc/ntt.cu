@@ -1,8 +1,12 @@
-// Negacyclic NTT / inverse NTT over RNS limbs (Section 2.1 ring arithmetic).
+// NTT / inverse NTT over RNS limbs (Section 2.1 ring arithmetic), for the
+// cyclotomic rings X^N + 1 (m = 2N) and X^N - X^(N/2) + 1 (m = 3N).
 //
 // Forward: merged-twist Cooley-Tukey with twiddles psi^bitrev(m+i); natural
 // coefficients in, evaluation form out with word j = a(psi^(2 bitrev(j)+1)).
 // Inverse: Gentleman-Sande with psi^-bitrev(m+i), then times N^-1.
+// m = 3N: the same trees with node 1 replaced by the split into
+// X^(N/2) - rho and X^(N/2) - rho^5 (R3 kernels) and the subtree twiddles of
+// those two factors; word h N/2 + j = a(omega^(e_h + 6 bitrev(j))).
 //
 // A length-N transform is split N = N1 * N2. Its first log2(N1) stages act on
 // the N2 columns (stride N2) independently, the remaining log2(N2) stages on
@@ -75,7 +79,11 @@ __device__ __forceinline__ u64 reduce_lazy(u64 v, u64 q, int kb, uint32_t mq) {
 // stages have half-distances t = u*2^j for j in [JLO, JHI] and pair the
 // registers (k, k + 2^j). Butterflies of one 2t-block share one twiddle,
 // index (mg << sg) + r/(2t), sg = logS - 1 - log2(t).
-template <bool FWD, int JLO, int JHI>
+// R3 (m = 3N): node 1 (twiddle index 1) is the split of X^N - X^(N/2) + 1 into
+// X^(N/2) - rho and X^(N/2) - rho^5 (rho^5 = 1 - rho): forward (U, V) ->
+// (U + rho V, U + V - rho V); inverse t = (U - V)(2 rho - 1)^-1 ->
+// (U + V - t, 2t), both scaled by N^-1 with the rest afterwards.
+template <bool FWD, int JLO, int JHI, bool R3>
 __device__ __forceinline__ void ntt_round(u64 (&x)[8], int rbase, int logu, int logS, int mg,
                                           const ulonglong2* __restrict__ tw, u64 q) {
   const u64 q2 = 2 * q;
@@ -95,7 +103,21 @@ __device__ __forceinline__ void ntt_round(u64 (&x)[8], int rbase, int logu, int 
       for (int p = 0; p < d; ++p) {
         const int k = k0 + p;
         u64 U = x[k], V = x[k + d];
-        if (FWD) {
+        if (R3 && widx == 1) {
+          if (FWD) {  // residues stay below 4q
+            if (U >= q2) U -= q2;
+            if (V >= q2) V -= q2;
+            const u64 t = shoup_lazy(V, w, wp, q);
+            u64 z = V + q2 - t;
+            if (z >= q2) z -= q2;
+            x[k] = U + t;
+            x[k + d] = U + z;
+          } else {
+            const u64 t = shoup_lazy(U - V + q2, w, wp, q);
+            x[k] = U + V + q2 - t;
+            x[k + d] = t + t;
+          }
+        } else if (FWD) {
           if (U >= q2) U -= q2;
           V = shoup_lazy(V, w, wp, q);
           x[k] = U + V;
@@ -111,16 +133,16 @@ __device__ __forceinline__ void ntt_round(u64 (&x)[8], int rbase, int logu, int 
   }
 }
 
-template <bool FWD>
+template <bool FWD, bool R3>
 __device__ __forceinline__ void ntt_round_dispatch(int jlo, int jhi, u64 (&x)[8], int rbase, int logu, int logS, int mg,
                                                    const ulonglong2* tw, u64 q) {
   switch (jlo * 3 + jhi) {
-    case 0: ntt_round<FWD, 0, 0>(x, rbase, logu, logS, mg, tw, q); break;
-    case 1: ntt_round<FWD, 0, 1>(x, rbase, logu, logS, mg, tw, q); break;
-    case 2: ntt_round<FWD, 0, 2>(x, rbase, logu, logS, mg, tw, q); break;
-    case 4: ntt_round<FWD, 1, 1>(x, rbase, logu, logS, mg, tw, q); break;
-    case 5: ntt_round<FWD, 1, 2>(x, rbase, logu, logS, mg, tw, q); break;
-    default: ntt_round<FWD, 2, 2>(x, rbase, logu, logS, mg, tw, q); break;
+    case 0: ntt_round<FWD, 0, 0, R3>(x, rbase, logu, logS, mg, tw, q); break;
+    case 1: ntt_round<FWD, 0, 1, R3>(x, rbase, logu, logS, mg, tw, q); break;
+    case 2: ntt_round<FWD, 0, 2, R3>(x, rbase, logu, logS, mg, tw, q); break;
+    case 4: ntt_round<FWD, 1, 1, R3>(x, rbase, logu, logS, mg, tw, q); break;
+    case 5: ntt_round<FWD, 1, 2, R3>(x, rbase, logu, logS, mg, tw, q); break;
+    default: ntt_round<FWD, 2, 2, R3>(x, rbase, logu, logS, mg, tw, q); break;
   }
 }
 
@@ -129,7 +151,7 @@ __device__ __forceinline__ void ntt_round_dispatch(int jlo, int jhi, u64 (&x)[8]
 // blockDim = CPB*S/8. Residues stay lazy ([0,4q) forward, [0,2q) inverse)
 // except in the LAST phase, which writes canonical values (times N^-1 for
 // the inverse).
-template <bool FWD, bool COLS, bool LAST>
+template <bool FWD, bool COLS, bool LAST, bool R3 = false>
 __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, int m0) {
   extern __shared__ u64 sm[];
   u64* ptr;
@@ -176,7 +198,7 @@ __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, in
       int r = rbase + (k << logu);
       x[k] = sm[swz(COLS ? (r << logCPB) + c : (c << logS) + r)];
     }
-    ntt_round_dispatch<FWD>(a - logu, b - logu, x, rbase, logu, logS, mg, tw, q);
+    ntt_round_dispatch<FWD, R3>(a - logu, b - logu, x, rbase, logu, logS, mg, tw, q);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       int r = rbase + (k << logu);
@@ -212,11 +234,16 @@ __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, in
 // range is a compile-time constant, so the sixteen words stay in registers.
 // The forward butterfly here never reduces its upper input: each stage adds
 // less than 2q to the bound, so inputs below 4q leave a log2 N <= 16 stage
-// transform below 36q < 2^64 (primes below 2^58), and the last phase brings
-// every word back to [0, q) once (reduce_lazy).
+// transform below 36q (40q with the m = 3N split) < 64q < 2^64 (primes below
+// 2^58), and the last phase brings every word back to [0, q) once (reduce_lazy).
 // One CTA tile (`tile` of polynomial `poly`) of one phase; the body of the
 // per-transform kernel k_ntt16 and of the persistent kernel k_ntt16_multi.
-template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC>
+// R3 (m = 3N, column phases only): the first forward stage and the last
+// inverse stage are node 1, the split of X^N - X^(N/2) + 1 (see ntt_round).
+// Forward it adds up to 6q to the bound, so the transform stays below 40q.
+// Inverse it is fused with N^-1: with c = (2 rho - 1)^-1 N^-1 (inverse
+// twiddle word 0), high = (U - V) 2c, low = (U + V) N^-1 - (U - V) c.
+template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC, bool R3 = false>
 __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0, int tile, int poly) {
   extern __shared__ u64 sm[];
   u64* ptr;
@@ -260,11 +287,17 @@ __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0,
   }
   u64 ni = 0, nip = 0;
   u64 wni = 0, wnip = 0;
+  u64 cni = 0, cnip = 0;
   if (LAST && !FWD) {
     ni = A.ninv[4 * pidx];
     nip = A.ninv[4 * pidx + 1];
     wni = A.ninv[4 * pidx + 2];
     wnip = A.ninv[4 * pidx + 3];
+    if (R3) {
+      const ulonglong2 c0 = __ldg(tw);
+      cni = c0.x;
+      cnip = c0.y;
+    }
   }
   const int kb = A.mods[pidx].kbits;
   const uint32_t mq = (uint32_t)(A.mods[pidx].mu >> 47);
@@ -316,6 +349,7 @@ __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0,
         // the inverse transform's last stage (one twiddle, psi^(-N/2)) also
         // applies N^-1: sums times N^-1, differences times N^-1 psi^(-N/2)
         const bool fold = LAST && !FWD && rho == NR - 1 && jj == ns - 1;
+        const bool split = R3 && COLS && FWD && rho == 0 && jj == 0;
 #pragma unroll
         for (int blk = 0; blk < 8; ++blk) {
           if (blk < 8 / d) {
@@ -335,9 +369,18 @@ __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0,
               if (p < d) {
                 const int k = k0 + p;
                 u64 U = x[k], V = x[k + d];
-                if (fold) {
+                if (fold && R3) {
+                  const u64 dv = U - V + q2;
+                  const u64 lo = shoup(U + V, ni, nip, q), cr = shoup(dv, cni, cnip, q);
+                  x[k] = lo >= cr ? lo - cr : lo + q - cr;
+                  x[k + d] = shoup(dv, w, wp, q);
+                } else if (fold) {
                   x[k] = shoup(U + V, ni, nip, q);
                   x[k + d] = shoup(U - V + q2, w, wp, q);
+                } else if (split) {
+                  const u64 t = shoup_lazy(V, w, wp, q);
+                  x[k] = U + t;
+                  x[k + d] = U + V + q2 - t;
                 } else if (FWD) {
                   V = shoup_lazy(V, w, wp, q);
                   x[k] = U + V;
@@ -382,9 +425,9 @@ __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0,
   }
 }
 
-template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC = false>
+template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC = false, bool R3 = false>
 __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_ntt16(NttArgs A, int logCPB, int m0) {
-  ntt16_tile<FWD, COLS, LAST, LOGS, SRC>(A, logCPB, m0, blockIdx.x, blockIdx.y);
+  ntt16_tile<FWD, COLS, LAST, LOGS, SRC, R3>(A, logCPB, m0, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------- persistent multi-transform phase
@@ -431,13 +474,13 @@ __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I)
   }
 }
 
-template <bool FWD, bool COLS, bool LAST, bool SRC = false>
+template <bool FWD, bool COLS, bool LAST, bool SRC = false, bool R3 = false>
 void launch16(int logS, dim3 g, int thr, size_t smem, cudaStream_t st, const NttArgs& A, int logc, int m0) {
   switch (logS) {
-    case 5: k_ntt16<FWD, COLS, LAST, 5, SRC><<<g, thr, smem, st>>>(A, logc, m0); break;
-    case 6: k_ntt16<FWD, COLS, LAST, 6, SRC><<<g, thr, smem, st>>>(A, logc, m0); break;
-    case 7: k_ntt16<FWD, COLS, LAST, 7, SRC><<<g, thr, smem, st>>>(A, logc, m0); break;
-    default: k_ntt16<FWD, COLS, LAST, 8, SRC><<<g, thr, smem, st>>>(A, logc, m0); break;
+    case 5: k_ntt16<FWD, COLS, LAST, 5, SRC, R3><<<g, thr, smem, st>>>(A, logc, m0); break;
+    case 6: k_ntt16<FWD, COLS, LAST, 6, SRC, R3><<<g, thr, smem, st>>>(A, logc, m0); break;
+    case 7: k_ntt16<FWD, COLS, LAST, 7, SRC, R3><<<g, thr, smem, st>>>(A, logc, m0); break;
+    default: k_ntt16<FWD, COLS, LAST, 8, SRC, R3><<<g, thr, smem, st>>>(A, logc, m0); break;
   }
 }
 
@@ -500,8 +543,13 @@ static void launch(Context& C, const PolySet& s, bool fwd, cudaStream_t st, cons
     int kr = kt_begin(C, st);
     dim3 g(1, npoly);
     int thr = N / 8;
-    if (fwd) k_ntt<true, false, true><<<g, thr, smem(N), st>>>(A, logN, 0, 1);
-    else k_ntt<false, false, true><<<g, thr, smem(N), st>>>(A, logN, 0, 1);
+    if (C.m_odd == 3) {
+      if (fwd) k_ntt<true, false, true, true><<<g, thr, smem(N), st>>>(A, logN, 0, 1);
+      else k_ntt<false, false, true, true><<<g, thr, smem(N), st>>>(A, logN, 0, 1);
+    } else {
+      if (fwd) k_ntt<true, false, true><<<g, thr, smem(N), st>>>(A, logN, 0, 1);
+      else k_ntt<false, false, true><<<g, thr, smem(N), st>>>(A, logN, 0, 1);
+    }
     ++C.launches;
     kt_end(C, kr, KC_NTT, 16.0 * N * active_polys(s), st);
   } else {
@@ -511,18 +559,22 @@ static void launch(Context& C, const PolySet& s, bool fwd, cudaStream_t st, cons
     const int logc1 = tl - log1, logc2 = tl - log2n;
     dim3 g1(1 << (log2n - logc1), npoly), g2(1 << (log1 - logc2), npoly);
     const int thr = tile / 16;
+    const bool r3 = C.m_odd == 3;
     if (fwd) {
-      launch16<true, true, false>(log1, g1, thr, smem(tile), st, A, logc1, 1);
+      if (r3) launch16<true, true, false, false, true>(log1, g1, thr, smem(tile), st, A, logc1, 1);
+      else launch16<true, true, false>(log1, g1, thr, smem(tile), st, A, logc1, 1);
       launch16<true, false, true>(log2n, g2, thr, smem(tile), st, A, logc2, 1 << log1);
-    } else if (src) {
-      NttArgs A1 = A;
-      A1.src = src;
-      A1.src_os = src_os;
-      launch16<false, false, false, true>(log2n, g2, thr, smem(tile), st, A1, logc2, 1 << log1);
-      launch16<false, true, true>(log1, g1, thr, smem(tile), st, A, logc1, 1);
     } else {
-      launch16<false, false, false>(log2n, g2, thr, smem(tile), st, A, logc2, 1 << log1);
-      launch16<false, true, true>(log1, g1, thr, smem(tile), st, A, logc1, 1);
+      if (src) {
+        NttArgs A1 = A;
+        A1.src = src;
+        A1.src_os = src_os;
+        launch16<false, false, false, true>(log2n, g2, thr, smem(tile), st, A1, logc2, 1 << log1);
+      } else {
+        launch16<false, false, false>(log2n, g2, thr, smem(tile), st, A, logc2, 1 << log1);
+      }
+      if (r3) launch16<false, true, true, false, true>(log1, g1, thr, smem(tile), st, A, logc1, 1);
+      else launch16<false, true, true>(log1, g1, thr, smem(tile), st, A, logc1, 1);
     }
     C.launches += 2;
     kt_end(C, kr, KC_NTT, 16.0 * N * active_polys(s), st);
@@ -565,6 +617,7 @@ void ntt_multi(const std::vector<NttReq>& reqs, bool fwd, int tile_log, cudaStre
       const NttReq& q = reqs[r];
       Context& C = *q.C;
       if (C.N < 8192) throw Error(SS_ERR_PARAM, "merged transforms need N >= 8192");
+      if (C.m_odd == 3) throw Error(SS_ERR_PARAM, "merged transforms cover the ring X^N + 1 only");
       const int npoly = q.s.n_outer * q.s.nl;
       if (npoly == 0) continue;
       NttArgs A = make_args(C, q.s);

@@ -115,15 +115,22 @@ struct Context {
   int p = 0, r = 0;
   u64 t = 0;  // p^r
   std::vector<u64> tpow;  // p^e, e = 0..r
-  std::vector<u64> primes, psi;
+  std::vector<u64> primes, psi;  // psi: primitive m-th root of unity per prime
+  int m_odd = 1, m = 0;           // odd part of the cyclotomic index; m = 2N (m_odd 1) or 3N (m_odd 3)
   int slots = 0, d = 0;
   u64 omega = 0;
   std::vector<int> slot_exp;
+  // decryption reconstructs, and decoding reads, the coefficients k * dec_stride, k < dec_count
+  int dec_stride = 0, dec_count = 0;
+  // m = 3N slot algebra: Phi_3N(X) = Phi_M'(X^s), roots theta^e in GR(p^r, 2) = Z_{p^r}[u]/(u^2 - gr_c)
+  int Mp = 0, s_stride = 0, nprime = 0;
+  u64 gr_c = 0, theta[2] = {0, 0};
+  std::vector<std::pair<int, int>> gens;  // slot-group generators mod M' with their orders
 
   // device tables
   ModDesc* d_mod = nullptr;           // [ntot]
   u64* d_tw = nullptr;                // per prime 4N words: (psi_brv, shoup) pairs, then (psiinv_brv, shoup) pairs
-  u64* d_ninv = nullptr;              // [ntot][4] N^{-1}, shoup, N^{-1} psi^{-N/2}, shoup
+  u64* d_ninv = nullptr;              // [ntot][4] N^{-1}, shoup, N^{-1} psi^{-N/2} (m = 3N: 2 N^{-1}), shoup
   u64* d_pinv = nullptr;              // [ntot][2] p^{-1}, shoup
   u64* d_tmod = nullptr;              // [r+1][ntot][2]: p^e mod q, shoup
   u64* d_tables = nullptr;            // base-conversion constants (offsets below)

@@ -1,0 +1,221 @@
+"""The cyclotomic ring m = 3N (Phi_3N = X^N - X^(N/2) + 1; Section 2.1 with a
+general m, Section 5.1's slot count n / Ord(m, p)) on the GPU, word for word
+against the CPU reference through the C-ABI: context tables and slot algebra,
+the transform at every ring size the kernels have (single-phase and the
+two-phase radix-16 form with the split stage), every BGV operation, the
+space-switching procedures and the compare-then-SUM query. All arithmetic is
+exact modular integer arithmetic: the tolerance is zero.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import plain
+
+pytestmark = pytest.mark.gpu
+
+
+def pair(logN=6, L=26, alpha=2, bits=36, p=17, r=2, h=16, seed=7, galois=None, keys=True):
+    import paper_2604_19890_gb300 as ssg
+    g = ssg.Context(logN=logN, L=L, alpha=alpha, bits=bits, p=p, r=r, h=h, nmax=0, seed=seed, m_odd=3)
+    o = O.Oracle(logN=logN, L=L, alpha=alpha, bits=bits, p=p, r=r, h=h, seed=seed, m_odd=3)
+    if keys:
+        gal = g.rotate_sum_elements() if galois is None else galois
+        g.keygen(gal)
+        o.keygen(gal)
+    return g, o
+
+
+def same(gct, oct_list):
+    w = gct.words()
+    assert w.shape[0] == len(oct_list)
+    for b, oc in enumerate(oct_list):
+        assert (gct.ncomp, gct.level, gct.t_exp) == (oc.ncomp, oc.level, oc.t_exp)
+        ow = oc.words()
+        diff = np.argwhere(w[b] != ow)
+        assert diff.size == 0, "first differing word %s of %d" % (diff[0], len(diff))
+
+
+def encrypt_both(g, o, vals, nonce0):
+    vals = np.atleast_2d(np.asarray(vals, dtype=np.uint64))
+    gc = g.encrypt(np.stack([g.encode(v) for v in vals]), nonce0)
+    oc = [o.encrypt(o.encode(v), nonce0 + i) for i, v in enumerate(vals)]
+    return gc, oc
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return pair()
+
+
+@pytest.mark.parametrize("p,r,logN", [(17, 2, 6), (257, 2, 6), (13, 2, 6), (257, 3, 5), (5, 3, 7), (257, 3, 16)])
+def test_context_and_slots_match(p, r, logN):
+    g, o = pair(logN=logN, L=3, alpha=2, bits=55 if p == 257 else 36, p=p, r=r, h=8, keys=False)
+    assert g.m == o.m == 3 * g.N
+    assert (g.primes == o.primes()).all()
+    assert (g.slots, g.d) == (o.slots, o.d)
+    assert g.rotate_sum_elements() == o.rotate_sum_elements()
+    rng = np.random.default_rng(p * r + logN)
+    for te in range(1, r + 1):
+        v = rng.integers(0, p ** te, o.slots)
+        mg, mo = g.encode(v, te), o.encode(v, te)
+        assert (mg == mo).all()
+        assert (g.decode(mg, te) == v).all()
+        c = rng.integers(0, p ** te, g.N).astype(np.uint64)
+        assert (g.decode(c, te) == o.decode(c, te)).all()
+
+
+@pytest.mark.parametrize("logN", [3, 6, 12, 13, 14, 15, 16])
+def test_ntt_parity_3n(logN):
+    import torch
+    import paper_2604_19890_gb300 as ssg
+    L = 3
+    g = ssg.Context(logN=logN, L=L, alpha=1, bits=55, p=257, r=2, h=4, nmax=0, seed=1, m_odd=3)
+    o = O.Oracle(logN=logN, L=L, alpha=1, bits=55, p=257, r=2, h=4, seed=1, m_odd=3)
+    rng = np.random.default_rng(logN)
+    npoly = 2 * L if logN <= 13 else L
+    data = np.stack([rng.integers(0, int(g.primes[i % L]), g.N, dtype=np.uint64) for i in range(npoly)])
+    t = torch.from_numpy(data.view(np.int64).copy()).cuda()
+    g.ntt_forward(t, 0, L)
+    fw = t.cpu().numpy().view(np.uint64).copy()
+    for i in range(npoly):
+        assert (fw[i] == o.ntt_fwd(i % L, data[i])).all(), i
+    g.ntt_inverse(t, 0, L)
+    assert (t.cpu().numpy().view(np.uint64) == data).all()
+
+
+@pytest.mark.parametrize("logN,bits,p", [(6, 58, 257), (13, 58, 257), (16, 58, 257), (16, 30, 5)])
+def test_ntt_extreme_inputs_3n(logN, bits, p):
+    """Words q-1 and 0 everywhere, and the largest and smallest primes: the
+    lazy bounds (below 40q forward) hold at the extremes."""
+    import torch
+    import paper_2604_19890_gb300 as ssg
+    L = 2
+    g = ssg.Context(logN=logN, L=L, alpha=1, bits=bits, p=p, r=2, h=4, nmax=0, seed=1, m_odd=3)
+    o = O.Oracle(logN=logN, L=L, alpha=1, bits=bits, p=p, r=2, h=4, seed=1, m_odd=3)
+    rows = []
+    for i in range(L):
+        q = int(g.primes[i])
+        rows.append(np.full(g.N, q - 1, dtype=np.uint64))
+        alt = np.zeros(g.N, dtype=np.uint64)
+        alt[::2] = q - 1
+        rows.append(alt)
+    data = np.stack(rows)
+    order = [0, 0, 1, 1]  # prime of each row
+    t = torch.from_numpy(data.view(np.int64).copy()).cuda()
+    for k, pi in enumerate(order):
+        g.ntt_forward(t[k:k + 1], pi, 1)
+    fw = t.cpu().numpy().view(np.uint64).copy()
+    for k, pi in enumerate(order):
+        assert (fw[k] == o.ntt_fwd(pi, data[k])).all(), k
+    for k, pi in enumerate(order):
+        g.ntt_inverse(t[k:k + 1], pi, 1)
+    assert (t.cpu().numpy().view(np.uint64) == data).all()
+
+
+def test_ops_parity_3n(tiny):
+    g, o = tiny
+    rng = np.random.default_rng(2)
+    A = rng.integers(0, g.t, (2, g.slots))
+    B = rng.integers(0, g.t, (2, g.slots))
+    ga, oa = encrypt_both(g, o, A, 100)
+    gb, ob = encrypt_both(g, o, B, 200)
+    same(ga, oa)
+    assert (g.decrypt_slots(ga) == A).all()
+    same(g.add(ga, gb), [o.add(x, y) for x, y in zip(oa, ob)])
+    same(g.mul_scalar(ga, -12345), [o.mul_scalar(x, -12345) for x in oa])
+    gt = g.mul(ga, gb)
+    ot = [o.tensor(x, y) for x, y in zip(oa, ob)]
+    same(gt, ot)
+    gr = g.relin(gt)
+    orl = [o.relin(x) for x in ot]
+    same(gr, orl)
+    same(g.mul_relin(ga, gb), [o.mul(x, y) for x, y in zip(oa, ob)])
+    for drop in (1, 3):
+        same(g.modswitch(gr, drop), [o.modswitch(x, drop) for x in orl])
+    for gel in g.rotate_sum_elements():
+        same(g.rotate(ga, gel), [o.rotate(x, gel) for x in oa])
+    same(g.rotate_sum(ga), [o.rotate_sum(x) for x in oa])
+    assert (g.decrypt_slots(g.rotate_sum(ga)) == (A.astype(object).sum(axis=1) % g.t)[:, None]).all()
+    gm, om = encrypt_both(g, o, (A * g.p) % g.t, 300)
+    same(g.divide_by_p(gm), [o.divide_by_p(x) for x in om])
+    assert (g.decrypt_slots(gr) == (A * B) % g.t).all()
+
+
+def test_reduce_compare_raise_parity_3n(tiny):
+    g, o = tiny
+    rng = np.random.default_rng(3)
+    A = rng.integers(0, g.t, (2, g.slots))
+    B = rng.integers(0, g.t, (2, g.slots))
+    ga, oa = encrypt_both(g, o, A, 400)
+    gb, ob = encrypt_both(g, o, B, 500)
+    gd = g.reduce(ga)
+    od = [o.reduce(x) for x in oa]
+    for i in range(g.r):
+        same(gd[i], [d[i] for d in od])
+    lt = g.compare_lt(ga, gb)
+    olt = [o.compare_lt(x, y) for x, y in zip(oa, ob)]
+    same(lt, olt)
+    up = g.raise_modulus(lt)
+    same(up, [o.raise_modulus(x) for x in olt])
+    exp = np.array([[plain.lt(x, y, g.t) for x, y in zip(ra, rb)] for ra, rb in zip(A, B)])
+    assert (g.decrypt_slots(up) == exp).all()
+
+
+@pytest.mark.parametrize("n_ct,batch", [(1, 8), (3, 2)])
+def test_query_parity_3n(tiny, n_ct, batch):
+    g, o = tiny
+    rng = np.random.default_rng(10 + n_ct)
+    cols = {k: rng.integers(0, g.t, (n_ct, g.slots)) for k in ("a", "b", "c1")}
+    thr = np.full((1, g.slots), 150)
+    gA, oA = encrypt_both(g, o, cols["a"], 1000)
+    gB, oB = encrypt_both(g, o, cols["b"], 2000)
+    gC, oC = encrypt_both(g, o, cols["c1"], 3000)
+    gT, oT = encrypt_both(g, o, thr, 4000)
+    g.set_batch(batch)
+    res = g.query(gA, gB, gC, gT)
+    same(res, [o.query(oA, oB, oC, oT)])
+    assert (g.decrypt_slots(res) == plain.query(cols["a"], cols["b"], cols["c1"], thr, g.t)).all()
+    g.set_batch(8)
+
+
+def test_p257_r3_query_3n():
+    """257^3 on the small ring: slots in pairs of conjugate roots over GR(257^3, 2)."""
+    g, o = pair(logN=5, L=44, alpha=3, bits=55, p=257, r=3, h=16, seed=9)
+    rng = np.random.default_rng(5)
+    cols = {k: rng.integers(0, g.t, (1, g.slots)) for k in ("a", "b", "c1", "c2")}
+    enc = {k: encrypt_both(g, o, v, 100 * (i + 1)) for i, (k, v) in enumerate(cols.items())}
+    res = g.query(*(enc[k][0] for k in ("a", "b", "c1", "c2")))
+    same(res, [o.query(*(enc[k][1] for k in ("a", "b", "c1", "c2")))])
+    assert (g.decrypt_slots(res) == plain.query(cols["a"], cols["b"], cols["c1"], cols["c2"], g.t)).all()
+
+
+@pytest.mark.parametrize("prm,count", [
+    (dict(logN=13, L=18, alpha=2, bits=36, p=17, r=2, h=120, seed=601), 2),
+    (dict(logN=14, L=11, alpha=3, bits=55, p=257, r=2, h=120, seed=602), 3),
+], ids=["n8192", "n16384"])
+def test_keyswitch_parity_two_phase_3n(prm, count):
+    """Key switching on the two-phase transform with the split stage: ModUp's
+    out-of-place inverse and digit-skipping forward transforms, ModDown, the
+    fused drop, and rotations by every rotate-sum element and X -> X^(3N-1)."""
+    g, o = pair(**prm, galois=[])
+    gal = g.rotate_sum_elements() + [3 * g.N - 1]
+    g.keygen(gal)
+    o.keygen(gal)
+    rng = np.random.default_rng(prm["seed"])
+    A = rng.integers(0, g.t, (count, g.slots))
+    B = rng.integers(0, g.t, (count, g.slots))
+    ga, oa = encrypt_both(g, o, A, 10)
+    gb, ob = encrypt_both(g, o, B, 20)
+    same(ga, oa)
+    gt = g.mul(ga, gb)
+    ot = [o.tensor(x, y) for x, y in zip(oa, ob)]
+    same(g.relin(gt), [o.relin(x) for x in ot])
+    gm = g.mul_relin(ga, gb)
+    om = [o.mul(x, y) for x, y in zip(oa, ob)]
+    same(gm, om)
+    same(g.modswitch(ga, 2), [o.modswitch(x, 2) for x in oa])
+    for gel in gal:
+        same(g.rotate(gm, gel), [o.rotate(x, gel) for x in om])
+    same(g.rotate_sum(gm), [o.rotate_sum(x) for x in om])
+    assert (g.decrypt_slots(gm) == (A.astype(object) * B.astype(object)) % g.t).all()
