@@ -229,11 +229,12 @@ def query_ntt_count(n_ct_small=(1, 2)):
     return slope, counts[0] - slope
 
 
-def workload_config(logN, L, bits, alpha, p, r, slots, n_ct, batch):
+def workload_config(logN, L, bits, alpha, p, r, slots, n_ct, batch, m_odd=1):
     """The `config` object both arms print for one workload."""
     rows = n_ct * slots
-    wl = ("compare-then-SUM query, N=2^%d, L=%d x %d-bit + %d special primes, p^r=%d^%d, %d slots, "
-          "%d ciphertexts per column (%d rows) per GPU" % (logN, L, bits, alpha, p, r, slots, n_ct, rows))
+    ring = "m=3N ring X^N-X^(N/2)+1" if m_odd == 3 else "ring X^N+1"
+    wl = ("compare-then-SUM query, N=2^%d, %s, L=%d x %d-bit + %d special primes, p^r=%d^%d, %d slots, "
+          "%d ciphertexts per column (%d rows) per GPU" % (logN, ring, L, bits, alpha, p, r, slots, n_ct, rows))
     return {"workload": wl, "batch": batch,
             "l2": "inputs (%.1f GB) larger than L2" % (4 * n_ct * 2 * L * (1 << logN) * 8 / 1e9)}
 
@@ -692,7 +693,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                 "config": workload_config(prm.logN, prm.L, prm.bits, prm.alpha, prm.p, prm.r, g.slots, n_ct,
-                                          args.batch),
+                                          args.batch, prm.m_odd),
                 "latency_ms": {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1,
                                                                                    int(0.99 * len(lat_ms)))]},
                 "verified_against_plaintext": verified,
@@ -809,8 +810,9 @@ def main():
                     help="time one kernel family alone (profiling mode)")
     ap.add_argument("--limbs", type=int, default=512)
     ap.add_argument("--n-ct", type=int, default=N_CT, help="ciphertexts per column")
-    ap.add_argument("--preset", type=int, default=PRESET, choices=[0, 1, 2],
-                    help="0: N=2^13, 17^2; 1: N=2^15, 257^2; 2: N=2^16, 257^3 (the headline workload)")
+    ap.add_argument("--preset", type=int, default=PRESET, choices=[0, 1, 2, 3],
+                    help="0: N=2^13, 17^2; 1: N=2^15, 257^2; 2: N=2^16, 257^3 (the headline workload); "
+                         "3: as 2 on the ring m = 3N (256 slots)")
     ap.add_argument("--serve", action="store_true", help="served form: Poisson arrivals, p50/p99")
     ap.add_argument("--batched", action="store_true", help="batched form: 64 mixed-N pairs, graph replay")
     ap.add_argument("--batched-mix", choices=["mixed", "small"], default="mixed")

@@ -101,6 +101,8 @@ ss_status ss_params_preset(int id, ss_params* out) {
       case 0: p.logN = 13; p.bits = 36; p.alpha = 2; p.p = 17; p.r = 2; p.L = 18; break;
       case 1: p.logN = 15; p.bits = 55; p.alpha = 2; p.p = 257; p.r = 2; p.L = 30; break;
       case 2: p.logN = 16; p.bits = 55; p.alpha = 3; p.p = 257; p.r = 3; p.L = 41; break;
+      // N = 2^16 on the ring m = 3N: 256 slots for 257^3 (128 on X^N + 1)
+      case 3: p.logN = 16; p.bits = 55; p.alpha = 3; p.p = 257; p.r = 3; p.L = 41; p.m_odd = 3; break;
       default: throw ss::Error(SS_ERR_PARAM, "unknown preset");
     }
     *out = p;

@@ -443,6 +443,7 @@ constexpr int kMaxNttJobs = 24;
 struct NttJob {
   NttArgs A;
   int logS, logCPB, m0, tiles, start;
+  int r3;  // ring m = 3N: the column phases take the split stage
 };
 struct NttMulti {
   int njobs, total;
@@ -450,9 +451,9 @@ struct NttMulti {
 };
 
 // a separate function per instantiation, so each keeps its own register allocation
-template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC>
+template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC, bool R3 = false>
 __device__ __noinline__ void ntt16_tile_fn(const NttArgs& A, int logCPB, int m0, int tile, int poly) {
-  ntt16_tile<FWD, COLS, LAST, LOGS, SRC>(A, logCPB, m0, tile, poly);
+  ntt16_tile<FWD, COLS, LAST, LOGS, SRC, R3>(A, logCPB, m0, tile, poly);
 }
 
 template <bool FWD, bool COLS, bool LAST, bool SRC>
@@ -464,6 +465,18 @@ __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I)
     const NttJob& J = M.j[j];
     const int local = t - J.start;
     const int poly = local / J.tiles, tile = local - poly * J.tiles;
+    if constexpr (COLS) {
+      if (J.r3) {
+        switch (J.logS) {
+          case 5: ntt16_tile_fn<FWD, COLS, LAST, 5, SRC, true>(J.A, J.logCPB, J.m0, tile, poly); break;
+          case 6: ntt16_tile_fn<FWD, COLS, LAST, 6, SRC, true>(J.A, J.logCPB, J.m0, tile, poly); break;
+          case 7: ntt16_tile_fn<FWD, COLS, LAST, 7, SRC, true>(J.A, J.logCPB, J.m0, tile, poly); break;
+          default: ntt16_tile_fn<FWD, COLS, LAST, 8, SRC, true>(J.A, J.logCPB, J.m0, tile, poly); break;
+        }
+        __syncthreads();
+        continue;
+      }
+    }
     switch (J.logS) {
       case 5: ntt16_tile_fn<FWD, COLS, LAST, 5, SRC>(J.A, J.logCPB, J.m0, tile, poly); break;
       case 6: ntt16_tile_fn<FWD, COLS, LAST, 6, SRC>(J.A, J.logCPB, J.m0, tile, poly); break;
@@ -617,13 +630,13 @@ void ntt_multi(const std::vector<NttReq>& reqs, bool fwd, int tile_log, cudaStre
       const NttReq& q = reqs[r];
       Context& C = *q.C;
       if (C.N < 8192) throw Error(SS_ERR_PARAM, "merged transforms need N >= 8192");
-      if (C.m_odd == 3) throw Error(SS_ERR_PARAM, "merged transforms cover the ring X^N + 1 only");
       const int npoly = q.s.n_outer * q.s.nl;
       if (npoly == 0) continue;
       NttArgs A = make_args(C, q.s);
       const int log1 = C.logN - 8, logc1 = tl - log1, logc2 = tl - 8;
-      NttJob cols{A, log1, logc1, 1, 1 << (8 - logc1), 0};
-      NttJob chunks{A, 8, logc2, 1 << log1, 1 << (log1 - logc2), 0};
+      const int r3 = C.m_odd == 3 ? 1 : 0;
+      NttJob cols{A, log1, logc1, 1, 1 << (8 - logc1), 0, r3};
+      NttJob chunks{A, 8, logc2, 1 << log1, 1 << (log1 - logc2), 0, 0};
       if (!fwd) {  // the chunk phase reads the source (the polynomials themselves when in place)
         chunks.A.src = q.src ? q.src : q.s.base;
         chunks.A.src_os = q.src ? q.src_os : q.s.outer_stride;

@@ -15,12 +15,15 @@ import numpy as np
 
 from paper_2604_19890_gb300 import synth
 
-# The three named parameter sets (N = 2^13 / 17^2, N = 2^15 / 257^2,
-# N = 2^16 / 257^3), chain lengths as the query needs them, seed 0x5EED0000 + id.
+# The named parameter sets (N = 2^13 / 17^2, N = 2^15 / 257^2, N = 2^16 /
+# 257^3 on X^N + 1 and on m = 3N), chain lengths as the query needs them,
+# seed 0x5EED0000 + id.
 PRESETS = {
     0: dict(logN=13, L=18, alpha=2, bits=36, p=17, r=2, h=120, seed=0x5EED0000),
     1: dict(logN=15, L=30, alpha=2, bits=55, p=257, r=2, h=120, seed=0x5EED0001),
     2: dict(logN=16, L=41, alpha=3, bits=55, p=257, r=3, h=120, seed=0x5EED0002),
+    # the same on the cyclotomic ring m = 3N (X^N - X^(N/2) + 1): 256 slots
+    3: dict(logN=16, L=41, alpha=3, bits=55, p=257, r=3, h=120, seed=0x5EED0003, m_odd=3),
 }
 
 # Nonces of the encrypted inputs: column k uses nonce base + row index.
@@ -39,6 +42,9 @@ CASES = {
     # SUM(a*b) WHERE c1 < c2 (column against column), 1 ciphertext per column.
     "query_n65536_257cubed": dict(kind="query", params=PRESETS[2], value_seed=0x5EED3002, n_ct=1,
                                   threshold=None, square=False),
+    # the same query on m = 3N, 256 slots
+    "query_n65536_257cubed_m3n": dict(kind="query", params=PRESETS[3], value_seed=0x5EED3003, n_ct=1,
+                                      threshold=None, square=False),
 }
 
 # Results of the "ops" case, in the order they are computed:

@@ -219,3 +219,64 @@ def test_keyswitch_parity_two_phase_3n(prm, count):
         same(g.rotate(gm, gel), [o.rotate(x, gel) for x in om])
     same(g.rotate_sum(gm), [o.rotate_sum(x) for x in om])
     assert (g.decrypt_slots(gm) == (A.astype(object) * B.astype(object)) % g.t).all()
+
+
+def test_batch_mixed_rings():
+    """Batched form over an m = 3N context (N = 2^14, 17^2) and an X^N + 1
+    context (N = 2^15, 257^2): products and Algorithm 3's digits equal the
+    reference word for word, on streams, with merged transform lanes, and from
+    the replayed graph."""
+    import torch
+    import paper_2604_19890_gb300 as ssg
+    sets = [dict(logN=14, L=14, alpha=2, bits=36, p=17, r=2, h=120, seed=521, m_odd=3),
+            dict(logN=15, L=14, alpha=2, bits=55, p=257, r=2, h=120, seed=522, m_odd=1)]
+    gs, os_ = [], []
+    for s in sets:
+        g = ssg.Context(nmax=0, **s)
+        o = O.Oracle(**s)
+        g.keygen([])
+        o.keygen([])
+        gs.append(g)
+        os_.append(o)
+    rng = np.random.default_rng(6)
+    plan = [(0, 14, True), (1, 14, True), (0, 9, False), (1, 6, False), (0, 12, True)]
+    pairs, refs = [], []
+    for i, (ci, lvl, red) in enumerate(plan):
+        g, o = gs[ci], os_[ci]
+        va, vb = rng.integers(0, g.t, g.slots), rng.integers(0, g.t, g.slots)
+        ga, gb = g.encrypt(g.encode(va), 100 + 2 * i), g.encrypt(g.encode(vb), 101 + 2 * i)
+        oa, ob = o.encrypt(o.encode(va), 100 + 2 * i), o.encrypt(o.encode(vb), 101 + 2 * i)
+        if lvl < g.L:
+            ga, gb = g.modswitch(ga, g.L - lvl), g.modswitch(gb, g.L - lvl)
+            oa, ob = o.modswitch(oa, g.L - lvl), o.modswitch(ob, g.L - lvl)
+        op = o.mul(oa, ob)
+        od = None
+        if red:
+            try:
+                od = o.reduce(op)
+            except O.OracleError:
+                od = "skip"
+        pairs.append((ci, ga, gb, red))
+        refs.append((op, od))
+    b = ssg.Batch(gs, pairs)
+    st = torch.cuda.Stream()
+
+    def verify():
+        for (prod, digs), (op, od) in zip(b.results(), refs):
+            same(prod, [op])
+            if isinstance(od, list):
+                assert len(digs) == len(od)
+                for d, ref in zip(digs, od):
+                    same(d, [ref])
+
+    for chunk, nstr in ((2, 3), (1, 0), (4, 0)):
+        b.config(chunk, nstr, 11)
+        b.run(st)
+        st.synchronize()
+        verify()
+    b.capture(st)
+    for _ in range(2):
+        b.run(st)
+        st.synchronize()
+        verify()
+    b.close()
