@@ -745,6 +745,8 @@ def run_mma_rates(args):
 # (bit width, p, r) from the paper's LT tables (Section 5) that power-of-two
 # rings with binomial slot factors support (p = 1 mod 4).
 LT_SWEEP = [(8, 5, 4), (8, 17, 2), (12, 17, 3), (16, 17, 4), (16, 41, 3), (16, 257, 2), (20, 17, 5), (20, 37, 4)]
+# on the ring m = 3N also the paper's plaintext primes p = 3 mod 4 (its LT table)
+LT_SWEEP_3N = LT_SWEEP + [(8, 7, 3), (12, 7, 5), (12, 11, 4), (12, 67, 2), (20, 131, 3)]
 
 
 def run_lt_sweep(args):
@@ -761,8 +763,10 @@ def run_lt_sweep(args):
 
     ssbuild.build()
     stream = torch.cuda.current_stream()
-    for bw, p, r in LT_SWEEP:
-        base = dict(logN=args.sweep_logn, alpha=2, bits=55, p=p, r=r, h=120, nmax=0, seed=SEED + p * 10 + r)
+    m_odd = 3 if args.sweep_ring == "3n" else 1
+    for bw, p, r in (LT_SWEEP_3N if m_odd == 3 else LT_SWEEP):
+        base = dict(logN=args.sweep_logn, alpha=2, bits=55, p=p, r=r, h=120, nmax=0, seed=SEED + p * 10 + r,
+                    m_odd=m_odd)
         probe = ssg.Context(L=64, **base)
         L = 64 - probe.query_depth(64) + 1
         del probe
@@ -788,7 +792,7 @@ def run_lt_sweep(args):
         per = args.steps * args.sweep_ct
         total = e0.elapsed_time(e1) / per
         stages = {k: st[k][1] / per for k in ("reduction", "comparison", "aggregation", "modulus_raising")}
-        print(json.dumps({"lt_sweep": True, "bit_width": bw, "p": p, "r": r, "t": g.t, "N": g.N, "L": L,
+        print(json.dumps({"lt_sweep": True, "bit_width": bw, "p": p, "r": r, "t": g.t, "N": g.N, "m": g.m, "L": L,
                           "slots": g.slots, "ciphertexts": args.sweep_ct, "ms_per_ciphertext": stages | {"total": total},
                           "amortized_ms_per_slot": total / g.slots, "verified": ok}))
         del g
@@ -821,6 +825,7 @@ def main():
     ap.add_argument("--lt-sweep", action="store_true",
                     help="LT operator + modulus raising across (p, r) at fixed bit widths, per-stage times")
     ap.add_argument("--sweep-logn", type=int, default=15)
+    ap.add_argument("--sweep-ring", choices=["2n", "3n"], default="2n", help="LT sweep ring: m = 2N or 3N")
     ap.add_argument("--sweep-ct", type=int, default=8)
     ap.add_argument("--mma-rates", action="store_true", help="tensor-core int8/fp16/bf16 matmul rates")
     ap.add_argument("--cpu-seconds", type=float, default=6.0, help="length of one CPU reference sample")

@@ -66,7 +66,7 @@ typedef struct {
   int32_t L;        /* data primes */
   int32_t alpha;    /* special primes = key-switching digit width */
   int32_t bits;     /* primes lie in (2^(bits-1), 2^bits); 20 <= bits <= 58 */
-  int32_t p;        /* plaintext prime, p = 1 mod 4 */
+  int32_t p;        /* plaintext prime >= 5; p = 1 mod 4 when m = 2N */
   int32_t r;        /* plaintext modulus p^r */
   int32_t h;        /* Hamming weight of the ternary secret (Section 5.1: 120) */
   int32_t nmax;     /* largest N the prime chain must support (0 = N) */

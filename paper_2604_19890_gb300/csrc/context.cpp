@@ -405,8 +405,11 @@ void build_context(Context& C, const ss_params& prm) {
   if (prm.logN < 3 || prm.logN > 16) throw Error(SS_ERR_PARAM, "logN must be in [3, 16]");
   if (prm.L < 1 || prm.alpha < 1 || prm.L > 200 || prm.alpha > 16) throw Error(SS_ERR_PARAM, "bad L/alpha");
   if (prm.bits < 20 || prm.bits > 58) throw Error(SS_ERR_PARAM, "bits must be in [20, 58]");
-  if (prm.p < 5 || prm.p % 4 != 1 || !nt::prime((u64)prm.p)) throw Error(SS_ERR_PARAM, "p must be a prime = 1 mod 4");
   if (prm.m_odd != 0 && prm.m_odd != 1 && prm.m_odd != 3) throw Error(SS_ERR_PARAM, "m_odd must be 1 (m = 2N) or 3 (m = 3N)");
+  // X^N + 1 splits into binomial slot factors over Z_p only for p = 1 mod 4; the
+  // m = 3N slot algebra (over GR(p^r, 2)) takes any prime p >= 5
+  if (prm.p < 5 || !nt::prime((u64)prm.p) || (prm.m_odd != 3 && prm.p % 4 != 1))
+    throw Error(SS_ERR_PARAM, "p must be a prime >= 5, = 1 mod 4 on the ring X^N + 1");
   C.m_odd = prm.m_odd == 3 ? 3 : 1;
   if (prm.r < 1 || prm.r > 8) throw Error(SS_ERR_PARAM, "bad r");
   C.logN = prm.logN;

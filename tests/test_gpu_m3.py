@@ -280,3 +280,57 @@ def test_batch_mixed_rings():
         st.synchronize()
         verify()
     b.close()
+
+
+@pytest.mark.parametrize("p,r,L", [(7, 3, 30), (11, 4, 44)])
+def test_compare_raise_p3mod4_3n(p, r, L):
+    """Plaintext primes p = 3 mod 4 (the paper's (7, 3) and (11, 4)) on m = 3N:
+    Algorithm 3's digits, Algorithm 4 and raising word for word."""
+    g, o = pair(logN=7, L=L, alpha=3, bits=55, p=p, r=r, h=16, seed=13, galois=[])
+    rng = np.random.default_rng(p)
+    A = rng.integers(0, g.t, (2, g.slots))
+    B = rng.integers(0, g.t, (2, g.slots))
+    ga, oa = encrypt_both(g, o, A, 50)
+    gb, ob = encrypt_both(g, o, B, 60)
+    gd = g.reduce(ga)
+    od = [o.reduce(x) for x in oa]
+    for i in range(r):
+        same(gd[i], [d[i] for d in od])
+    lt = g.compare_lt(ga, gb)
+    olt = [o.compare_lt(x, y) for x, y in zip(oa, ob)]
+    same(lt, olt)
+    up = g.raise_modulus(lt)
+    same(up, [o.raise_modulus(x) for x in olt])
+    exp = np.array([[plain.lt(x, y, g.t) for x, y in zip(ra, rb)] for ra, rb in zip(A, B)])
+    assert (g.decrypt_slots(up) == exp).all()
+
+
+def test_served_mixed_rings_equal_alone():
+    """One server over an m = 3N context and an X^N + 1 context (N = 2^13,
+    17^2 both): interleaved queries merge only within their context and each
+    result equals the same query run alone, word for word."""
+    import paper_2604_19890_gb300 as ssg
+    g1 = ssg.Context(logN=13, L=18, alpha=2, bits=36, p=17, r=2, h=120, nmax=0, seed=51, m_odd=3)
+    g2 = ssg.Context(logN=13, L=18, alpha=2, bits=36, p=17, r=2, h=120, nmax=0, seed=52)
+    for g in (g1, g2):
+        g.keygen()
+    assert g1.slots == 2 * g2.slots
+    rng = np.random.default_rng(8)
+    qs = []
+    for i, n in enumerate([1, 2, 2, 1, 1, 2]):
+        ci = i % 2
+        g = (g1, g2)[ci]
+        cols = {k: rng.integers(0, g.t, (n, g.slots)) for k in ("a", "b", "c1")}
+        c2 = np.full((1, g.slots), int(rng.integers(0, g.t)))
+        enc = lambda v, nonce: g.encrypt(np.stack([g.encode(x) for x in v]), nonce)
+        A, B, C1, C2 = (enc(cols["a"], 100 * i + 1), enc(cols["b"], 100 * i + 20), enc(cols["c1"], 100 * i + 40),
+                        enc(c2, 100 * i + 60))
+        qs.append((ci, (A, B, C1, C2), plain.query(cols["a"], cols["b"], cols["c1"], c2, g.t)))
+    alone = [(g1, g2)[ci].query(*cols).words() for ci, cols, _ in qs]
+    srv = ssg.Server([g1, g2], workers=2, max_merge=4)
+    tickets = [srv.submit(*cols, ctx_index=ci) for ci, cols, _ in qs]
+    for t, (ci, cols, exp), ref in zip(tickets, qs, alone):
+        res, _, _ = srv.wait(t, timeout_ms=120000)
+        assert (res.words() == ref).all()
+        assert ((g1, g2)[ci].decrypt_slots(res) == exp).all()
+    srv.close()

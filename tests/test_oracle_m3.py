@@ -144,8 +144,10 @@ class GR2:
 
 
 # (p, r, logN): both slot shapes -- p = 2 mod 3 (pairs of conjugate roots per
-# slot) and p = 1 mod 12 (one root per slot) -- and s = 1 as well as s > 1
-SLOT_CASES = [(17, 2, 5), (257, 2, 6), (13, 2, 6), (5, 3, 7), (41, 2, 6), (37, 2, 5)]
+# slot) and p = 1 mod 12 (one root per slot) -- s = 1 as well as s > 1, and
+# p = 3 mod 4 (7, 11, 131), which X^N + 1 cannot split into binomial slots
+SLOT_CASES = [(17, 2, 5), (257, 2, 6), (13, 2, 6), (5, 3, 7), (41, 2, 6), (37, 2, 5), (7, 3, 6), (11, 2, 5),
+              (131, 2, 6)]
 
 
 @pytest.mark.parametrize("p,r,logN", SLOT_CASES)
@@ -236,3 +238,16 @@ def test_query_and_rotate_sum_3n(logN, p, r, L, bits):
     res = o.query([enc(a, 10)], [enc(b, 20)], [enc(c1, 30)], [enc(c2, 40)])
     assert (o.decrypt_slots(res) == plain.query([a], [b], [c1], [c2], t)).all()
     assert o.noise_budget(res) > 5
+
+
+@pytest.mark.parametrize("p,r,L", [(7, 3, 30), (11, 4, 44), (67, 2, 30), (131, 3, 60)])
+def test_lt_and_raise_p3mod4_3n(p, r, L):
+    """The paper's (p, r) pairs with p = 3 mod 4 (Section 5, LT table) on m = 3N:
+    Algorithm 4 then raising, decrypted against the plaintext definition."""
+    o = ctx(logN=6, p=p, r=r, L=L, alpha=3, bits=58 if p == 131 else 55)
+    o.keygen([])
+    t = o.t
+    rng = np.random.default_rng(p)
+    A, B = rng.integers(0, t, o.slots), rng.integers(0, t, o.slots)
+    lt = o.raise_modulus(o.compare_lt(o.encrypt(o.encode(A), 1), o.encrypt(o.encode(B), 2)))
+    assert (o.decrypt_slots(lt) == np.array([plain.lt(x, y, t) for x, y in zip(A, B)])).all()
