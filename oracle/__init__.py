@@ -200,11 +200,13 @@ class Oracle:
         se = np.zeros(self.slots, dtype=np.int32)
         _chk(lib().orc_ctx_info(self.h, C.byref(s), C.byref(d), C.byref(t), C.byref(w), _ptr(se, C.c_int)))
         self.slot_exp = se
-        ri, th, gens = np.zeros(6, dtype=np.int32), np.zeros(2, dtype=np.uint64), np.zeros(64, dtype=np.int32)
+        ri, th, gens = np.zeros(6, dtype=np.int32), np.zeros(6, dtype=np.uint64), np.zeros(64, dtype=np.int32)
         _chk(lib().orc_ctx_ring(self.h, _ptr(ri, C.c_int), _ptr(th), _ptr(gens, C.c_int)))
         # cyclotomic index m (2N or 3N); for m = 3N the slot algebra of Phi_M'(X^s) over GR(p^r, 2)
         self.m, self.Mp, self.s, self.nprime, self.gr_c = (int(x) for x in ri[:5])
-        self.theta = (int(th[0]), int(th[1]))
+        # m = 3N: theta = (t0, t1) in GR(p^r, 2); m = 5N/2: theta = (t0, t1, t2, t3) in GR(p^r, 4), gr_w = w
+        self.theta = tuple(int(x) for x in th[:4]) if self.m_odd == 5 else (int(th[0]), int(th[1]))
+        self.gr_w = (int(th[4]), int(th[5]))
         self.gens = [(int(gens[2 * i]), int(gens[2 * i + 1])) for i in range(int(ri[5]))]
 
     def __del__(self):

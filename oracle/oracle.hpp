@@ -24,7 +24,7 @@
 //   per-digit aggregation, LT comparison            Section 4.3, Algorithm 4
 //   RaiseModToP2R = G_{p,r} after t <- p^r          Section 4.4
 //   compare-then-aggregate database query           Section 1 (Fig. 1), Section 5.2
-//   cyclotomic ring Phi_m, m = 2N or 3N; slots       Section 2.1, Section 5.1 (l = n / Ord(m, p))
+//   cyclotomic ring Phi_m, m = 2N, 3N or 5N/2; slots Section 2.1, Section 5.1 (l = n / Ord(m, p))
 //
 // Parity status: the decrypted results are pinned by plaintext definitions and
 // brute force; the exact ciphertext words have no definition outside this
@@ -100,7 +100,7 @@ struct Params {
   int h = 0;       // Hamming weight of the ternary secret
   int nmax = 0;    // largest ring dimension the primes must support
   u64 seed = 0;
-  int m_odd = 1;   // odd part of the cyclotomic index m: 1 -> m = 2N, 3 -> m = 3N
+  int m_odd = 1;   // odd part of the cyclotomic index m: 1 -> m = 2N, 3 -> m = 3N, 5 -> m = 5N/2
 };
 
 typedef std::vector<u64> Poly;  // one RNS limb: N residues
@@ -133,6 +133,9 @@ struct Context {
   u64 gr_c = 0;                   // quadratic non-residue mod p
   u64 theta[2] = {0, 0};          // primitive M'-th root of unity in GR(p^r, 2): theta[0] + theta[1] u
   std::vector<std::pair<int, int>> gens;  // slot-group generators (element mod M', order)
+  // m = 5N/2: Phi_m(X) = Phi_M'(X^s), M' = 5 * 2^b'; roots in GR(p^r, 4) = GR(p^r, 2)[v] / (v^2 - w)
+  u64 gr_w[2] = {0, 0};           // w: the first non-square of F_{p^2} (index x0 + p x1)
+  u64 theta4[4] = {0, 0, 0, 0};   // theta = (t0 + t1 u) + (t2 + t3 u) v
   // keys
   bool have_keys = false;
   std::vector<i64> sk;          // ternary secret, coefficient form
@@ -146,6 +149,7 @@ struct Context {
 std::vector<u64> gen_primes(int bits, u64 M, int count);
 u64 find_psi(u64 q, int N);             // smallest primitive 2N-th root of unity mod q
 u64 find_root3(u64 q, int N);           // smallest primitive 3N-th root of unity mod q
+u64 find_root5(u64 q, int N);           // smallest primitive (5N/2)-th root of unity mod q
 Context make_context(const Params& P);
 
 // ---------------------------------------------------------------- transform

@@ -431,17 +431,193 @@ static void make_slots_m3(Context& C) {
   if (C.slots * d != P.N) throw std::runtime_error("slot count does not match ord_3N(p)");
 }
 
+// Smallest primitive (5N/2)-th root of unity mod q (q = 1 mod 5N/2): order
+// exactly m = 5 * 2^k means x^m = 1, x^(m/2) != 1 and x^(m/5) != 1.
+u64 find_root5(u64 q, int N) {
+  const u64 m = 5 * (u64)N / 2;
+  auto order_m = [&](u64 x) {
+    return powmod(x, m, q) == 1 && powmod(x, m / 2, q) != 1 && powmod(x, m / 5, q) != 1;
+  };
+  u64 c = 0;
+  for (u64 x = 2; !c; ++x) {
+    u64 y = powmod(x, (q - 1) / m, q);
+    if (order_m(y)) c = y;
+  }
+  u64 best = c, w = 1;
+  for (u64 j = 1; j < m; ++j) {
+    w = mulmod(w, c, q);
+    if (j % 2 != 0 && j % 5 != 0 && w < best) best = w;
+  }
+  return best;
+}
+
+// ------------------------------------------------ Galois ring GR(p^k, 4)
+// The tower GR(p^k, 2)[v] / (v^2 - w), w a non-square of F_{p^2}: an element
+// is a + b v with a, b in GR(p^k, 2).
+struct GR4 {
+  GR2 a, b;
+};
+struct GR4Ring {
+  u64 c, t;
+  GR2 w;
+  GR4 mul(const GR4& x, const GR4& y) const {
+    GR2 ac = gr_mul(x.a, y.a, c, t), bd = gr_mul(x.b, y.b, c, t);
+    GR2 ad = gr_mul(x.a, y.b, c, t), bc = gr_mul(x.b, y.a, c, t);
+    return GR4{gr_add(ac, gr_mul(bd, w, c, t), t), gr_add(ad, bc, t)};
+  }
+  GR4 add(const GR4& x, const GR4& y) const { return GR4{gr_add(x.a, y.a, t), gr_add(x.b, y.b, t)}; }
+  GR4 sub(const GR4& x, const GR4& y) const { return GR4{gr_sub(x.a, y.a, t), gr_sub(x.b, y.b, t)}; }
+  GR4 one() const { return GR4{GR2{{1 % t, 0}}, GR2{{0, 0}}}; }
+  GR4 pow(GR4 x, u64 e) const {
+    GR4 r = one();
+    while (e) {
+      if (e & 1) r = mul(r, x);
+      x = mul(x, x);
+      e >>= 1;
+    }
+    return r;
+  }
+  // (a + b v)^-1 = (a - b v) / (a^2 - b^2 w)
+  GR4 inv(const GR4& x) const {
+    GR2 nrm = gr_sub(gr_mul(x.a, x.a, c, t), gr_mul(gr_mul(x.b, x.b, c, t), w, c, t), t);
+    GR2 ni = gr_inv(nrm, c, t);
+    return GR4{gr_mul(x.a, ni, c, t), gr_mul(gr_sub(GR2{{0, 0}}, x.b, t), ni, c, t)};
+  }
+  GR4 scale(const GR4& x, u64 k) const {
+    return GR4{GR2{{mulmod(x.a.x[0], k, t), mulmod(x.a.x[1], k, t)}}, GR2{{mulmod(x.b.x[0], k, t), mulmod(x.b.x[1], k, t)}}};
+  }
+  static bool is(const GR4& x, u64 v) { return x.a.x[0] == v && x.a.x[1] == 0 && x.b.x[0] == 0 && x.b.x[1] == 0; }
+  static u64 index(const GR4& x, u64 p) { return x.a.x[0] + p * (x.a.x[1] + p * (x.b.x[0] + p * x.b.x[1])); }
+};
+
+// Slot algebra of Phi_m, m = 5N/2 = 5 * 2^k (Section 2.1 with m = 5N/2):
+// with 2^b the largest power of two dividing p^4 - 1, b' = min(b, k),
+// M' = 5 * 2^b' and s = m / M', Phi_m(X) = Phi_M'(X^s) and Phi_M' splits
+// over GR(p^r, 4) at theta^e, e in (Z/M')^*, because M' divides p^4 - 1.
+// theta reduces to the element of smallest index of order exactly M' in
+// F_{p^4} and is its Teichmueller lift. Slots, generators and slot order as
+// for m = 3N.
+static void make_slots_m5(Context& C) {
+  const Params& P = C.P;
+  const u64 p = (u64)P.p;
+  int b = 0;
+  const u64 p4 = p * p * p * p;
+  for (u64 v = p4 - 1; v % 2 == 0; v /= 2) ++b;
+  const int k = P.logN - 1;
+  const int bp = std::min(b, k);
+  C.Mp = 5 << bp;
+  C.s = (5 << k) / C.Mp;
+  C.nprime = P.N / C.s;
+  for (u64 c = 2; c < p; ++c)
+    if (powmod(c, (p - 1) / 2, p) == p - 1) { C.gr_c = c; break; }
+  // w: first x0 + x1 u (index x0 + p x1) that is not a square in F_{p^2}
+  GR2 w{{0, 0}};
+  for (u64 i = 1; i < p * p; ++i) {
+    GR2 x{{i % p, i / p}};
+    if (!gr_is(gr_pow(x, (p * p - 1) / 2, C.gr_c, p), 1, 0)) { w = x; break; }
+  }
+  C.gr_w[0] = w.x[0];
+  C.gr_w[1] = w.x[1];
+  const GR4Ring F{C.gr_c, p, w};
+  const u64 Mp = (u64)C.Mp;
+  auto order_Mp = [&](const GR4& x) {
+    return GR4Ring::is(F.pow(x, Mp), 1) && !GR4Ring::is(F.pow(x, Mp / 2), 1) && !GR4Ring::is(F.pow(x, Mp / 5), 1);
+  };
+  // one element of order M', then the smallest index among its powers prime to M'
+  GR4 y{};
+  bool found = false;
+  for (u64 i = 1; !found; ++i) {
+    u64 r = i;
+    GR4 x{GR2{{r % p, (r / p) % p}}, GR2{{(r / (p * p)) % p, (r / (p * p * p)) % p}}};
+    GR4 cand = F.pow(x, (p4 - 1) / Mp);
+    if (order_Mp(cand)) { y = cand; found = true; }
+  }
+  GR4 th0 = y, cur = F.one();
+  u64 best = ~0ULL;
+  for (u64 j = 1; j < Mp; ++j) {
+    cur = F.mul(cur, y);
+    if (j % 2 != 0 && j % 5 != 0 && GR4Ring::index(cur, p) < best) { best = GR4Ring::index(cur, p); th0 = cur; }
+  }
+  // Teichmueller lift: theta = theta_0^((p^4)^(r-1)) in GR(p^r, 4)
+  const GR4Ring R{C.gr_c, C.t, w};
+  GR4 th = th0;
+  for (int i = 1; i < P.r; ++i) th = R.pow(th, p4);
+  if (!GR4Ring::is(R.pow(th, Mp), 1)) throw std::runtime_error("theta lift failed");
+  C.theta4[0] = th.a.x[0];
+  C.theta4[1] = th.a.x[1];
+  C.theta4[2] = th.b.x[0];
+  C.theta4[3] = th.b.x[1];
+  auto unit = [&](int e) { return e % 2 != 0 && e % 5 != 0; };
+  std::vector<char> H(C.Mp, 0);
+  for (u64 x = 1 % Mp;;) {
+    if (H[x]) break;
+    H[x] = 1;
+    x = x * (p % Mp) % Mp;
+  }
+  int o = 0;
+  for (int e = 0; e < C.Mp; ++e) o += H[e];
+  C.slots = C.nprime / o;
+  C.gens.clear();
+  auto order_mod_H = [&](int g) {
+    int n = 1;
+    for (long x = g; !H[x]; x = x * g % C.Mp) ++n;
+    return n;
+  };
+  int covered = o;
+  while (covered < C.nprime) {
+    int bestg = -1, bn = 0;
+    for (int g = 1; g < C.Mp; ++g)
+      if (unit(g)) {
+        int n = order_mod_H(g);
+        if (n > bn) { bn = n; bestg = g; }
+      }
+    C.gens.push_back({bestg, bn});
+    std::vector<char> H2(C.Mp, 0);
+    for (int h = 0; h < C.Mp; ++h)
+      if (H[h]) {
+        long x = h;
+        for (int j = 0; j < bn; ++j, x = x * bestg % C.Mp) H2[x] = 1;
+      }
+    H.swap(H2);
+    covered = 0;
+    for (int e = 0; e < C.Mp; ++e) covered += H[e];
+  }
+  C.slot_exp.assign(C.slots, 1);
+  for (int j = 0; j < C.slots; ++j) {
+    long e = 1;
+    int rest = j;
+    for (auto& gn : C.gens) {
+      for (int kk = 0; kk < rest % gn.second; ++kk) e = e * gn.first % C.Mp;
+      rest /= gn.second;
+    }
+    C.slot_exp[j] = (int)e;
+  }
+  const u64 m = 5 * (u64)P.N / 2;
+  int d = 1;
+  for (u64 x = p % m; x != 1; x = x * p % m) ++d;
+  C.d = d;
+  if (C.slots * d != P.N) throw std::runtime_error("slot count does not match ord_m(p)");
+}
+
 Context make_context(const Params& P0) {
   Context C;
   C.P = P0;
   Params& P = C.P;
   if (P.N != (1 << P.logN)) throw std::runtime_error("N must be 2^logN");
   if (P.m_odd == 0) P.m_odd = 1;
-  if (P.m_odd != 1 && P.m_odd != 3) throw std::runtime_error("m must be 2N or 3N");
+  if (P.m_odd != 1 && P.m_odd != 3 && P.m_odd != 5) throw std::runtime_error("m must be 2N, 3N or 5N/2");
   if (P.nmax == 0) P.nmax = P.N;
   if (P.nmax < P.N) throw std::runtime_error("nmax < N");
   C.t = ipow((u64)P.p, P.r);
-  C.m = P.m_odd == 3 ? 3 * P.N : 2 * P.N;
+  C.m = P.m_odd == 3 ? 3 * P.N : P.m_odd == 5 ? 5 * P.N / 2 : 2 * P.N;
+  if (P.m_odd == 5) {
+    if (P.p == 5 || P.p >= 32768 || P.logN < 3) throw std::runtime_error("m = 5N/2 needs p != 5, p < 2^15 and N >= 8");
+    // primes q = 1 mod lcm(5*nmax/2, p^r) = 5*nmax*p^r/2
+    C.primes = gen_primes(P.bits, 5 * (u64)P.nmax / 2 * C.t, P.L + P.alpha);
+    for (u64 q : C.primes) C.psi.push_back(find_root5(q, P.N));
+    make_slots_m5(C);
+    return C;
+  }
   if (P.m_odd == 3) {
     if (P.p % 3 == 0 || P.logN < 3) throw std::runtime_error("m = 3N needs p != 3 and N >= 8");
     // primes q = 1 mod lcm(3*nmax, p^r) = 3*nmax*p^r (q odd: nmax is even)
@@ -578,9 +754,87 @@ static void ntt_inv_m3(const Context& C, int pi, Poly& a) {
   }
 }
 
+// m = 5N/2: Phi_m(X) = Phi_10(X^(N/4)) = prod_h (X^(N/4) - xi^(e_h)), xi =
+// omega^(N/4) a primitive 10th root, e = (1, 3, 7, 9). Quarter h of the
+// evaluation form holds a mod (X^(N/4) - xi^(e_h)) = sum_j xi^(e_h j) a_j
+// (a_j the j-th quarter of the coefficients) at its roots omega^(e_h + 10k):
+// twist by omega^(e_h i), cyclic transform of length N/4 with omega^10; word
+// h N/4 + j = a(omega^(e_h + 10 bitrev(j))).
+static const u64 kE5[4] = {1, 3, 7, 9};
+static void ntt_fwd_m5(const Context& C, int pi, Poly& a) {
+  const int N = C.P.N, n = N / 4, logn = C.P.logN - 2;
+  const u64 q = C.primes[pi], w = C.psi[pi];
+  const u64 xi = powmod(w, (u64)n, q);
+  Poly out(N);
+  for (int h = 0; h < 4; ++h) {
+    const u64 eh = kE5[h], x = powmod(xi, eh, q), tw = powmod(w, eh, q);
+    std::vector<u64> b(n);
+    u64 pw = 1;
+    for (int i = 0; i < n; ++i) {
+      u64 v = 0, xj = 1;
+      for (int j = 0; j < 4; ++j, xj = mulmod(xj, x, q)) v = addmod(v, mulmod(xj, a[i + (size_t)j * n], q), q);
+      b[i] = mulmod(v, pw, q);
+      pw = mulmod(pw, tw, q);
+    }
+    cyclic_ntt(b, powmod(w, 10, q), q, logn);
+    for (int j = 0; j < n; ++j) out[(size_t)h * n + j] = b[bitrev(j, logn)];
+  }
+  a = out;
+}
+
+// Inverse of ntt_fwd_m5: b_h = a mod (X^(N/4) - x_h) per quarter, then the
+// quarters a_j by Lagrange interpolation through the nodes x_h = xi^(e_h):
+// sum_j a_j y^j = sum_h b_h prod_{h' != h} (y - x_h') / (x_h - x_h').
+static void ntt_inv_m5(const Context& C, int pi, Poly& a) {
+  const int N = C.P.N, n = N / 4, logn = C.P.logN - 2;
+  const u64 q = C.primes[pi], w = C.psi[pi];
+  const u64 xi = powmod(w, (u64)n, q), n_inv = invmod((u64)n, q);
+  std::vector<u64> b[4];
+  u64 x[4];
+  for (int h = 0; h < 4; ++h) {
+    const u64 eh = kE5[h];
+    x[h] = powmod(xi, eh, q);
+    const u64 tw_inv = invmod(powmod(w, eh, q), q);
+    std::vector<u64> B(n);
+    for (int k = 0; k < n; ++k) B[k] = a[(size_t)h * n + bitrev(k, logn)];
+    cyclic_ntt(B, invmod(powmod(w, 10, q), q), q, logn);
+    b[h].resize(n);
+    u64 pw = 1;
+    for (int i = 0; i < n; ++i) {
+      b[h][i] = mulmod(mulmod(B[i], n_inv, q), pw, q);
+      pw = mulmod(pw, tw_inv, q);
+    }
+  }
+  // Lagrange basis coefficients L[h][j]
+  u64 L[4][4];
+  for (int h = 0; h < 4; ++h) {
+    std::vector<u64> poly{1};  // prod_{h' != h} (y - x_h'), low degree first
+    u64 den = 1;
+    for (int h2 = 0; h2 < 4; ++h2) {
+      if (h2 == h) continue;
+      std::vector<u64> np(poly.size() + 1, 0);
+      for (size_t i = 0; i < poly.size(); ++i) {
+        np[i + 1] = addmod(np[i + 1], poly[i], q);
+        np[i] = submod(np[i], mulmod(poly[i], x[h2], q), q);
+      }
+      poly = np;
+      den = mulmod(den, submod(x[h], x[h2], q), q);
+    }
+    const u64 di = invmod(den, q);
+    for (int j = 0; j < 4; ++j) L[h][j] = mulmod(poly[j], di, q);
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < 4; ++j) {
+      u64 v = 0;
+      for (int h = 0; h < 4; ++h) v = addmod(v, mulmod(L[h][j], b[h][i], q), q);
+      a[i + (size_t)j * n] = v;
+    }
+}
+
 void ntt_fwd(const Context& C, int pi, Poly& a) {
   ++g_ntt_count;
   if (C.P.m_odd == 3) return ntt_fwd_m3(C, pi, a);
+  if (C.P.m_odd == 5) return ntt_fwd_m5(C, pi, a);
   int N = C.P.N, logN = C.P.logN;
   u64 q = C.primes[pi], psi = C.psi[pi];
   std::vector<u64> b(N);
@@ -593,6 +847,7 @@ void ntt_fwd(const Context& C, int pi, Poly& a) {
 void ntt_inv(const Context& C, int pi, Poly& a) {
   ++g_ntt_count;
   if (C.P.m_odd == 3) return ntt_inv_m3(C, pi, a);
+  if (C.P.m_odd == 5) return ntt_inv_m5(C, pi, a);
   int N = C.P.N, logN = C.P.logN;
   u64 q = C.primes[pi], psi = C.psi[pi];
   std::vector<u64> A(N);
@@ -622,6 +877,25 @@ Poly automorph_coeff(const Poly& a, int g, u64 q) {
 // modulo Phi_3N, so X^e (e mod 3N, folded to [0, 3N/2) with a sign) is X^e
 // for e < N and X^(e - N/2) - X^(e - N) for N <= e < 3N/2.
 Poly automorph_coeff(const Context& C, const Poly& a, int g, u64 q) {
+  if (C.P.m_odd == 5) {
+    // X^(5N/4) = -1 and X^N = X^(3N/4) - X^(N/2) + X^(N/4) - 1 modulo Phi_(5N/2)
+    const long N = (long)a.size(), m = 5 * N / 2, half = m / 2;
+    Poly out(N, 0);
+    for (long i = 0; i < N; ++i) {
+      long e = ((long)g * i) % m;
+      u64 v = a[i] % q;
+      if (e >= half) { e -= half; v = (q - v) % q; }
+      if (e < N) {
+        out[e] = addmod(out[e], v, q);
+      } else {
+        out[e - N / 4] = addmod(out[e - N / 4], v, q);
+        out[e - N / 2] = submod(out[e - N / 2], v, q);
+        out[e - 3 * N / 4] = addmod(out[e - 3 * N / 4], v, q);
+        out[e - N] = submod(out[e - N], v, q);
+      }
+    }
+    return out;
+  }
   if (C.P.m_odd != 3) return automorph_coeff(a, g, q);
   const long N = (long)a.size(), m = 3 * N, half = m / 2;
   Poly out(N, 0);
@@ -703,10 +977,72 @@ static std::vector<u64> decode_m3(const Context& C, u64 t, const std::vector<u64
   return v;
 }
 
+// m = 5N/2. As encode_m3 over GR(p^t, 4), with the node polynomial
+// Phi_M'(y) = y^(4h) - y^(3h) + y^(2h) - y^h + 1, h = n'/4.
+static std::vector<u64> encode_m5(const Context& C, u64 t, const std::vector<u64>& v) {
+  const int n = C.nprime, s = C.s, Mp = C.Mp, h = n / 4;
+  const GR4Ring R{C.gr_c, t, GR2{{C.gr_w[0] % t, C.gr_w[1] % t}}};
+  const GR4 th{GR2{{C.theta4[0] % t, C.theta4[1] % t}}, GR2{{C.theta4[2] % t, C.theta4[3] % t}}};
+  std::vector<int> slot_of(Mp, -1);
+  for (int j = 0; j < C.slots; ++j) {
+    long e = C.slot_exp[j];
+    for (int k = 0; k < Mp && slot_of[e] < 0; ++k, e = e * (C.P.p % Mp) % Mp) slot_of[e] = j;
+  }
+  std::vector<GR4> A(n, GR4{});
+  auto phi_k = [&](int k) -> long { return k == 3 * h ? -1 : k == 2 * h ? 1 : k == h ? -1 : 0; };
+  for (int e = 1; e < Mp; ++e) {
+    if (e % 2 == 0 || e % 5 == 0) continue;
+    if (slot_of[e] < 0) throw std::runtime_error("encode: root outside every slot");
+    const GR4 z = R.pow(th, (u64)e);
+    // Phi'(z) = 4h z^(4h-1) - 3h z^(3h-1) + 2h z^(2h-1) - h z^(h-1)
+    GR4 dphi{};
+    const long cs[4] = {4, -3, 2, -1};
+    for (int i = 0; i < 4; ++i) {
+      const int deg = (4 - i) * h;
+      GR4 term = R.scale(R.pow(z, (u64)(deg - 1)), (u64)deg % t);
+      dphi = cs[i] > 0 ? R.add(dphi, term) : R.sub(dphi, term);
+    }
+    GR4 coef = R.scale(R.inv(dphi), v[slot_of[e]] % t);
+    GR4 qk = R.one();  // quotient coefficient of y^(n-1)
+    for (int k = n - 1; k >= 0; --k) {
+      A[k] = R.add(A[k], R.mul(coef, qk));
+      if (k == 0) break;
+      GR4 nq = R.mul(z, qk);
+      const long ph = phi_k(k);
+      if (ph > 0) nq = R.add(nq, R.one());
+      if (ph < 0) nq = R.sub(nq, R.one());
+      qk = nq;
+    }
+  }
+  std::vector<u64> m(C.P.N, 0);
+  for (int k = 0; k < n; ++k) {
+    if (A[k].a.x[1] || A[k].b.x[0] || A[k].b.x[1]) throw std::runtime_error("encode: interpolant leaves Z_{p^t}");
+    m[(size_t)k * s] = A[k].a.x[0];
+  }
+  return m;
+}
+
+static std::vector<u64> decode_m5(const Context& C, u64 t, const std::vector<u64>& coeffs) {
+  const GR4Ring R{C.gr_c, t, GR2{{C.gr_w[0] % t, C.gr_w[1] % t}}};
+  const GR4 th{GR2{{C.theta4[0] % t, C.theta4[1] % t}}, GR2{{C.theta4[2] % t, C.theta4[3] % t}}};
+  std::vector<u64> v(C.slots, 0);
+  for (int j = 0; j < C.slots; ++j) {
+    const GR4 z = R.pow(th, (u64)C.slot_exp[j]);
+    GR4 acc{};
+    for (int k = C.nprime - 1; k >= 0; --k) {
+      acc = R.mul(acc, z);
+      acc.a.x[0] = addmod(acc.a.x[0], coeffs[(size_t)k * C.s] % t, t);
+    }
+    v[j] = acc.a.x[0];
+  }
+  return v;
+}
+
 std::vector<u64> encode(const Context& C, int t_exp, const std::vector<u64>& v) {
   u64 t = ipow((u64)C.P.p, t_exp);
   if ((int)v.size() != C.slots) throw std::runtime_error("encode: wrong slot count");
   if (C.P.m_odd == 3) return encode_m3(C, t, v);
+  if (C.P.m_odd == 5) return encode_m5(C, t, v);
   u64 w = C.omega % t;
   u64 inv_l = invmod((u64)C.slots % t, t);
   std::vector<u64> m(C.P.N, 0);
@@ -726,6 +1062,7 @@ std::vector<u64> encode(const Context& C, int t_exp, const std::vector<u64>& v) 
 std::vector<u64> decode(const Context& C, int t_exp, const std::vector<u64>& coeffs) {
   u64 t = ipow((u64)C.P.p, t_exp);
   if (C.P.m_odd == 3) return decode_m3(C, t, coeffs);
+  if (C.P.m_odd == 5) return decode_m5(C, t, coeffs);
   u64 w = C.omega % t;
   int two_l = 2 * C.slots;
   std::vector<u64> v(C.slots, 0);

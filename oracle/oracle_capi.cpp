@@ -55,12 +55,18 @@ int orc_ctx_info(void* h, int* slots, int* d, uint64_t* t, uint64_t* omega, int*
 
 // m = 3N slot algebra: out[0..5] = m, M', s, n', c, number of generators;
 // theta = (theta[0], theta[1]); gens[2i], gens[2i+1] = generator i and its order.
+// m = 5N/2: theta[0..3] = theta4, theta[4..5] = w.
 int orc_ctx_ring(void* h, int* out, uint64_t* theta, int* gens) {
   return guard([&] {
     Context& C = ctx(h);
     out[0] = C.m; out[1] = C.Mp; out[2] = C.s; out[3] = C.nprime; out[4] = (int)C.gr_c;
     out[5] = (int)C.gens.size();
-    theta[0] = C.theta[0]; theta[1] = C.theta[1];
+    if (C.P.m_odd == 5) {
+      for (int i = 0; i < 4; ++i) theta[i] = C.theta4[i];
+      theta[4] = C.gr_w[0]; theta[5] = C.gr_w[1];
+    } else {
+      theta[0] = C.theta[0]; theta[1] = C.theta[1];
+    }
     if (gens)
       for (size_t i = 0; i < C.gens.size(); ++i) { gens[2 * i] = C.gens[i].first; gens[2 * i + 1] = C.gens[i].second; }
   });

@@ -401,7 +401,7 @@ Ct raise_modulus(const Context& C, const Ct& lt, Trace* tr) {
 // products g_1^j_1 g_2^j_2 ... (j_i < n_i) are a transversal of (Z/M')^*/<p>.
 std::vector<int> rotate_sum_elements(const Context& C) {
   std::vector<int> g;
-  if (C.P.m_odd == 3) {
+  if (C.P.m_odd == 3 || C.P.m_odd == 5) {
     const long m = C.m;
     for (auto& gn : C.gens) {
       long e = gn.first % m;
