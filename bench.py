@@ -232,7 +232,7 @@ def query_ntt_count(n_ct_small=(1, 2)):
 def workload_config(logN, L, bits, alpha, p, r, slots, n_ct, batch, m_odd=1):
     """The `config` object both arms print for one workload."""
     rows = n_ct * slots
-    ring = "m=3N ring X^N-X^(N/2)+1" if m_odd == 3 else "ring X^N+1"
+    ring = {3: "m=3N ring X^N-X^(N/2)+1", 5: "m=5N/2 ring Phi_10(X^(N/4))"}.get(m_odd, "ring X^N+1")
     wl = ("compare-then-SUM query, N=2^%d, %s, L=%d x %d-bit + %d special primes, p^r=%d^%d, %d slots, "
           "%d ciphertexts per column (%d rows) per GPU" % (logN, ring, L, bits, alpha, p, r, slots, n_ct, rows))
     return {"workload": wl, "batch": batch,
@@ -763,8 +763,9 @@ def run_lt_sweep(args):
 
     ssbuild.build()
     stream = torch.cuda.current_stream()
-    m_odd = 3 if args.sweep_ring == "3n" else 1
-    for bw, p, r in (LT_SWEEP_3N if m_odd == 3 else LT_SWEEP):
+    m_odd = {"3n": 3, "5n2": 5}.get(args.sweep_ring, 1)
+    sweep = LT_SWEEP if m_odd == 1 else [x for x in LT_SWEEP_3N if not (m_odd == 5 and x[1] == 5)]
+    for bw, p, r in sweep:
         base = dict(logN=args.sweep_logn, alpha=2, bits=55, p=p, r=r, h=120, nmax=0, seed=SEED + p * 10 + r,
                     m_odd=m_odd)
         probe = ssg.Context(L=64, **base)
@@ -814,9 +815,9 @@ def main():
                     help="time one kernel family alone (profiling mode)")
     ap.add_argument("--limbs", type=int, default=512)
     ap.add_argument("--n-ct", type=int, default=N_CT, help="ciphertexts per column")
-    ap.add_argument("--preset", type=int, default=PRESET, choices=[0, 1, 2, 3],
+    ap.add_argument("--preset", type=int, default=PRESET, choices=[0, 1, 2, 3, 4],
                     help="0: N=2^13, 17^2; 1: N=2^15, 257^2; 2: N=2^16, 257^3 (the headline workload); "
-                         "3: as 2 on the ring m = 3N (256 slots)")
+                         "3: as 2 on the ring m = 3N (256 slots); 4: on m = 5N/2 (512 slots)")
     ap.add_argument("--serve", action="store_true", help="served form: Poisson arrivals, p50/p99")
     ap.add_argument("--batched", action="store_true", help="batched form: 64 mixed-N pairs, graph replay")
     ap.add_argument("--batched-mix", choices=["mixed", "small"], default="mixed")
@@ -825,7 +826,7 @@ def main():
     ap.add_argument("--lt-sweep", action="store_true",
                     help="LT operator + modulus raising across (p, r) at fixed bit widths, per-stage times")
     ap.add_argument("--sweep-logn", type=int, default=15)
-    ap.add_argument("--sweep-ring", choices=["2n", "3n"], default="2n", help="LT sweep ring: m = 2N or 3N")
+    ap.add_argument("--sweep-ring", choices=["2n", "3n", "5n2"], default="2n", help="LT sweep ring: m = 2N, 3N or 5N/2")
     ap.add_argument("--sweep-ct", type=int, default=8)
     ap.add_argument("--mma-rates", action="store_true", help="tensor-core int8/fp16/bf16 matmul rates")
     ap.add_argument("--cpu-seconds", type=float, default=6.0, help="length of one CPU reference sample")

@@ -90,8 +90,9 @@ const char* ss_last_error(void);
 
 /* Named parameter sets. id 0: N=2^13, 36-bit primes, p^r=17^2 (toy);
  * 1: N=2^15, 55-bit, 257^2; 2: N=2^16, 55-bit, 257^3; 3: as 2 on the ring
- * m = 3N (256 slots). The chain length L is the one the query needs (the
- * depth of Algorithms 3/4, raise and SUM). */
+ * m = 3N (256 slots); 4: as 2 on the ring m = 5N/2 (512 slots). The chain
+ * length L is the one the query needs (the depth of Algorithms 3/4, raise and
+ * SUM). */
 ss_status ss_params_preset(int id, ss_params* out);
 
 /* Builds the prime chain, transform tables, base-conversion constants and

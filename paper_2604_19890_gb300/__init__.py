@@ -342,9 +342,9 @@ class Context:
         self.primes = np.array(list(pr), dtype=np.uint64)
         self.p, self.r = params.p, params.r
         self.t = self.p ** self.r
-        # cyclotomic index: m = 2N (X^N + 1) or 3N (X^N - X^(N/2) + 1)
-        self.m_odd = 3 if params.m_odd == 3 else 1
-        self.m = (3 if self.m_odd == 3 else 2) * self.N
+        # cyclotomic index: m = 2N (X^N + 1), 3N (X^N - X^(N/2) + 1) or 5N/2 (Phi_10(X^(N/4)))
+        self.m_odd = params.m_odd if params.m_odd in (3, 5) else 1
+        self.m = {1: 2 * self.N, 3: 3 * self.N, 5: 5 * self.N // 2}[self.m_odd]
 
     def close(self):
         if getattr(self, "h", None):

@@ -103,6 +103,8 @@ ss_status ss_params_preset(int id, ss_params* out) {
       case 2: p.logN = 16; p.bits = 55; p.alpha = 3; p.p = 257; p.r = 3; p.L = 41; break;
       // N = 2^16 on the ring m = 3N: 256 slots for 257^3 (128 on X^N + 1)
       case 3: p.logN = 16; p.bits = 55; p.alpha = 3; p.p = 257; p.r = 3; p.L = 41; p.m_odd = 3; break;
+      // the same on the ring m = 5N/2: 512 slots
+      case 4: p.logN = 16; p.bits = 55; p.alpha = 3; p.p = 257; p.r = 3; p.L = 41; p.m_odd = 5; break;
       default: throw ss::Error(SS_ERR_PARAM, "unknown preset");
     }
     *out = p;

@@ -116,6 +116,24 @@ u64 root3n(u64 q, int N) {
   return best;
 }
 
+// Smallest primitive (5N/2)-th root of unity mod q: a unit raised to
+// (q-1)/m whose m/2-th and m/5-th powers differ from 1, then the least of its
+// powers with exponent prime to 10.
+u64 root5n(u64 q, int N) {
+  const u64 m = 5 * (u64)N / 2;
+  u64 g = 0;
+  for (u64 x = 2; !g; ++x) {
+    u64 c = pow(x, (q - 1) / m, q);
+    if (pow(c, m / 2, q) != 1 && pow(c, m / 5, q) != 1) g = c;
+  }
+  u64 best = g, cur = 1;
+  for (u64 j = 1; j < m; ++j) {
+    cur = mul(cur, g, q);
+    if (j % 2 != 0 && j % 5 != 0) best = std::min(best, cur);
+  }
+  return best;
+}
+
 static u64 upow(u64 b, int e) {
   u64 r = 1;
   for (int i = 0; i < e; ++i) r *= b;
@@ -379,6 +397,132 @@ static void build_slots_m3(Context& C) {
   C.dec_count = C.nprime;
 }
 
+// ------------------------------------------------------------------ m = 5N/2 slots
+namespace {
+// GR(p^k, 4) as GR(p^k, 2)[v]/(v^2 - w): pairs (a, b) of GR(p^k, 2) elements.
+struct Gr4 {
+  Gr a, b;
+};
+struct Gr4Ring {
+  GrRing R;
+  Gr w;
+  Gr4 mul(const Gr4& x, const Gr4& y) const {
+    return {R.add(R.mul(x.a, y.a), R.mul(R.mul(x.b, y.b), w)), R.add(R.mul(x.a, y.b), R.mul(x.b, y.a))};
+  }
+  Gr4 add(const Gr4& x, const Gr4& y) const { return {R.add(x.a, y.a), R.add(x.b, y.b)}; }
+  Gr4 sub(const Gr4& x, const Gr4& y) const { return {R.sub(x.a, y.a), R.sub(x.b, y.b)}; }
+  Gr4 scale(const Gr4& x, u64 k) const { return {R.scale(x.a, k), R.scale(x.b, k)}; }
+  Gr4 one() const { return {Gr{1 % R.t, 0}, Gr{0, 0}}; }
+  Gr4 pow(Gr4 x, u64 e) const {
+    Gr4 r = one();
+    for (; e; e >>= 1, x = mul(x, x))
+      if (e & 1) r = mul(r, x);
+    return r;
+  }
+  Gr4 inv(const Gr4& x) const {  // (a - b v) / (a^2 - b^2 w)
+    Gr ni = R.inv(R.sub(R.mul(x.a, x.a), R.mul(R.mul(x.b, x.b), w)));
+    return {R.mul(x.a, ni), R.mul(R.sub(Gr{0, 0}, x.b), ni)};
+  }
+  static bool is_one(const Gr4& x) { return x.a.a0 == 1 && x.a.a1 == 0 && x.b.a0 == 0 && x.b.a1 == 0; }
+};
+const int kE5[4] = {1, 3, 7, 9};
+}  // namespace
+
+// Slot structure of Phi_m, m = 5N/2 = 5*2^k (Section 2.1): M' = 5*2^b'
+// (2^b || p^4 - 1, b' = min(b, k)), s = m/M', Phi_m(X) = Phi_M'(X^s), roots
+// theta^e (e a unit mod M') in GR(p^r, 4); theta reduces to the element of
+// smallest index x0 + p x1 + p^2 x2 + p^3 x3 of order M' in F_{p^4}.
+static void build_slots_m5(Context& C) {
+  const u64 p = (u64)C.p, p4 = p * p * p * p;
+  int b = 0;
+  for (u64 v = p4 - 1; !(v & 1); v >>= 1) ++b;
+  const int k = C.logN - 1;
+  const int bp = std::min(b, k);
+  C.Mp = 5 << bp;
+  C.s_stride = (5 << k) / C.Mp;
+  C.nprime = C.N / C.s_stride;
+  C.gr_c = 0;
+  for (u64 c = 2; c < p && !C.gr_c; ++c)
+    if (nt::pow(c, (p - 1) / 2, p) == p - 1) C.gr_c = c;
+  const GrRing F2{C.gr_c, p};
+  Gr w{0, 0};
+  for (u64 i = 1; i < p * p && w.a0 == 0 && w.a1 == 0; ++i) {
+    Gr x{i % p, i / p};
+    if (!GrRing::one(F2.pow(x, (p * p - 1) / 2))) w = x;
+  }
+  C.gr_w[0] = w.a0;
+  C.gr_w[1] = w.a1;
+  const Gr4Ring F{F2, w};
+  const u64 Mp = (u64)C.Mp;
+  auto index = [&](const Gr4& x) { return x.a.a0 + p * (x.a.a1 + p * (x.b.a0 + p * x.b.a1)); };
+  Gr4 y{};
+  bool found = false;
+  for (u64 i = 1; !found; ++i) {
+    Gr4 x{Gr{i % p, (i / p) % p}, Gr{(i / (p * p)) % p, (i / (p * p * p)) % p}};
+    Gr4 c = F.pow(x, (p4 - 1) / Mp);
+    if (!Gr4Ring::is_one(F.pow(c, Mp / 2)) && !Gr4Ring::is_one(F.pow(c, Mp / 5))) { y = c; found = true; }
+  }
+  Gr4 th = y, cur = F.one();
+  u64 best = ~0ULL;
+  for (u64 j = 1; j < Mp; ++j) {
+    cur = F.mul(cur, y);
+    if (j % 2 && j % 5 && index(cur) < best) { best = index(cur); th = cur; }
+  }
+  // Newton's iteration for y^M' = 1 in GR(p^r, 4)
+  const Gr4Ring R{GrRing{C.gr_c, C.t}, w};
+  for (int it = 0; it <= C.r; ++it) {
+    Gr4 f = R.sub(R.pow(th, Mp), R.one());
+    Gr4 df = R.scale(R.pow(th, Mp - 1), Mp % C.t);
+    th = R.sub(th, R.mul(f, R.inv(df)));
+  }
+  if (!Gr4Ring::is_one(R.pow(th, Mp))) throw Error(SS_ERR_PARAM, "root lift failed");
+  C.theta4[0] = th.a.a0;
+  C.theta4[1] = th.a.a1;
+  C.theta4[2] = th.b.a0;
+  C.theta4[3] = th.b.a1;
+  std::vector<char> inH(Mp, 0);
+  int hsize = 0;
+  for (u64 x = 1; !inH[x]; x = x * (p % Mp) % Mp, ++hsize) inH[x] = 1;
+  C.slots = C.nprime / hsize;
+  C.gens.clear();
+  while (hsize < C.nprime) {
+    int gbest = 0, nbest = 0;
+    for (int g = 1; g < C.Mp; ++g) {
+      if (g % 2 == 0 || g % 5 == 0) continue;
+      int n = 1;
+      for (u64 x = (u64)g; !inH[x]; x = x * (u64)g % Mp) ++n;
+      if (n > nbest) { nbest = n; gbest = g; }
+    }
+    C.gens.push_back({gbest, nbest});
+    std::vector<char> nh(Mp, 0);
+    for (u64 h = 0; h < Mp; ++h) {
+      if (!inH[h]) continue;
+      u64 x = h;
+      for (int j = 0; j < nbest; ++j, x = x * (u64)gbest % Mp) nh[x] = 1;
+    }
+    inH.swap(nh);
+    hsize = 0;
+    for (char v : inH) hsize += v;
+  }
+  C.slot_exp.assign(C.slots, 1);
+  for (int j = 0; j < C.slots; ++j) {
+    u64 e = 1;
+    int rest = j;
+    for (auto& gn : C.gens) {
+      e = e * nt::pow((u64)gn.first, (u64)(rest % gn.second), Mp) % Mp;
+      rest /= gn.second;
+    }
+    C.slot_exp[j] = (int)e;
+  }
+  u64 m = 5 * (u64)C.N / 2, x = p % m;
+  int d = 1;
+  for (; x != 1; x = x * p % m) ++d;
+  C.d = d;
+  if ((long)C.slots * d != C.N) throw Error(SS_ERR_PARAM, "slot count does not match the order of p mod m");
+  C.dec_stride = C.s_stride;
+  C.dec_count = C.nprime;
+}
+
 // ------------------------------------------------------------------ context
 static void upload(void** dst, const void* src, size_t bytes) {
   SS_CUDA(cudaMalloc(dst, bytes));
@@ -389,6 +533,7 @@ Context::~Context() {
   cudaFree(d_mod);
   cudaFree(d_tw);
   cudaFree(d_ninv);
+  cudaFree(d_split);
   cudaFree(d_pinv);
   cudaFree(d_tmod);
   cudaFree(d_tables);
@@ -405,12 +550,16 @@ void build_context(Context& C, const ss_params& prm) {
   if (prm.logN < 3 || prm.logN > 16) throw Error(SS_ERR_PARAM, "logN must be in [3, 16]");
   if (prm.L < 1 || prm.alpha < 1 || prm.L > 200 || prm.alpha > 16) throw Error(SS_ERR_PARAM, "bad L/alpha");
   if (prm.bits < 20 || prm.bits > 58) throw Error(SS_ERR_PARAM, "bits must be in [20, 58]");
-  if (prm.m_odd != 0 && prm.m_odd != 1 && prm.m_odd != 3) throw Error(SS_ERR_PARAM, "m_odd must be 1 (m = 2N) or 3 (m = 3N)");
+  if (prm.m_odd != 0 && prm.m_odd != 1 && prm.m_odd != 3 && prm.m_odd != 5)
+    throw Error(SS_ERR_PARAM, "m_odd must be 1 (m = 2N), 3 (m = 3N) or 5 (m = 5N/2)");
   // X^N + 1 splits into binomial slot factors over Z_p only for p = 1 mod 4; the
-  // m = 3N slot algebra (over GR(p^r, 2)) takes any prime p >= 5
-  if (prm.p < 5 || !nt::prime((u64)prm.p) || (prm.m_odd != 3 && prm.p % 4 != 1))
+  // m = 3N and 5N/2 slot algebras (over GR(p^r, 2) and GR(p^r, 4)) take any
+  // prime p >= 5 (p != 5 for 5N/2, whose Galois ring needs p^4 < 2^64)
+  if (prm.p < 5 || !nt::prime((u64)prm.p) || (prm.m_odd <= 1 && prm.p % 4 != 1))
     throw Error(SS_ERR_PARAM, "p must be a prime >= 5, = 1 mod 4 on the ring X^N + 1");
-  C.m_odd = prm.m_odd == 3 ? 3 : 1;
+  if (prm.m_odd == 5 && (prm.p == 5 || prm.p >= 32768 || prm.logN < 5))
+    throw Error(SS_ERR_PARAM, "m = 5N/2 needs p != 5, p < 2^15 and N >= 32");
+  C.m_odd = prm.m_odd == 3 || prm.m_odd == 5 ? prm.m_odd : 1;
   if (prm.r < 1 || prm.r > 8) throw Error(SS_ERR_PARAM, "bad r");
   C.logN = prm.logN;
   C.N = 1 << prm.logN;
@@ -431,15 +580,21 @@ void build_context(Context& C, const ss_params& prm) {
   if ((double)C.dnum * 2.0 >= (double)(1ULL << (63 - prm.bits)))
     throw Error(SS_ERR_PARAM, "too many digits for the lazy inner product at this prime width");
 
-  C.m = C.m_odd == 3 ? 3 * C.N : 2 * C.N;
-  C.primes = nt::chain(prm.bits, (C.m_odd == 3 ? 3 : 2) * (u64)nmax * C.t, C.ntot);
+  C.m = C.m_odd == 3 ? 3 * C.N : C.m_odd == 5 ? 5 * C.N / 2 : 2 * C.N;
+  // primes = 1 mod (m/N) * nmax * p^r
+  const u64 step = C.m_odd == 3 ? 3 * (u64)nmax : C.m_odd == 5 ? 5 * (u64)nmax / 2 : 2 * (u64)nmax;
+  C.primes = nt::chain(prm.bits, step * C.t, C.ntot);
   C.psi.resize(C.ntot);
   for (int i = 0; i < C.ntot; ++i)
-    C.psi[i] = C.m_odd == 3 ? nt::root3n(C.primes[i], C.N) : nt::root2n(C.primes[i], C.N);
+    C.psi[i] = C.m_odd == 3   ? nt::root3n(C.primes[i], C.N)
+               : C.m_odd == 5 ? nt::root5n(C.primes[i], C.N)
+                              : nt::root2n(C.primes[i], C.N);
 
   // slots: d = order of p mod 2N, slots = N/d, X^N+1 = prod (X^d - zeta_j)
   if (C.m_odd == 3) {
     build_slots_m3(C);
+  } else if (C.m_odd == 5) {
+    build_slots_m5(C);
   } else {
     u64 m2 = 2 * (u64)C.N, x = (u64)C.p % m2;
     int d = 1;
@@ -490,6 +645,7 @@ void build_context(Context& C, const ss_params& prm) {
   {
     std::vector<u64> tw((size_t)T * 4 * N);
     std::vector<u64> ninv(4 * T), pinv(2 * T);
+    std::vector<u64> split(C.m_odd == 5 ? (size_t)T * 56 : 0);
     for (int i = 0; i < T; ++i) {
       u64 q = C.primes[i], ps = C.psi[i], pi = nt::inv(ps, q);
       u64* o = &tw[(size_t)i * 4 * N];
@@ -502,7 +658,60 @@ void build_context(Context& C, const ss_params& prm) {
       u64 ni = nt::inv((u64)N % q, q);
       ninv[4 * i] = ni;
       ninv[4 * i + 1] = nt::shoup(ni, q);
-      if (C.m_odd == 3) {
+      if (C.m_odd == 5) {
+        // Phi_m = prod_h (X^(N/4) - x_h), x_h = xi^(e_h), xi = omega^(N/4), e =
+        // (1, 3, 7, 9): nodes 1..3 are replaced by the four-way split (table
+        // d_split); node k >= 4 at depth l in quarter h, index j there, splits
+        // with z_k = omega^(((N/4) >> (l-1)) (e_h + 10 bitrev_{l-2}(j))).
+        const u64 m = 5 * (u64)N / 2;
+        std::vector<u64> pw(m);
+        pw[0] = 1;
+        for (u64 e = 1; e < m; ++e) pw[e] = nt::mul(pw[e - 1], ps, q);
+        for (int k = 0; k < 4; ++k) put(k, 1, 1);
+        for (int k = 4; k < N; ++k) {
+          const int l = 31 - __builtin_clz((unsigned)k);
+          const int h = (k >> (l - 2)) & 3;
+          const int j = k - (1 << l) - (h << (l - 2));
+          const u64 e = (u64)((N / 4) >> (l - 1)) * (kE5[h] + 10 * (u64)nt::brv(j, l - 2)) % m;
+          put(k, pw[e], pw[(m - e) % m]);
+        }
+        // split: forward x_h^j (j = 1..3), inverse (V^-1)[j][h] * 4/N, V[h][j] = x_h^j
+        u64 V[4][8];
+        for (int h = 0; h < 4; ++h)
+          for (int j = 0; j < 4; ++j) {
+            V[h][j] = pw[(u64)(N / 4) * kE5[h] * j % m];
+            V[h][4 + j] = h == j ? 1 : 0;
+          }
+        for (int c = 0; c < 4; ++c) {  // Gauss-Jordan mod q
+          int r = c;
+          while (V[r][c] == 0) ++r;
+          for (int j = 0; j < 8; ++j) std::swap(V[c][j], V[r][j]);
+          const u64 iv = nt::inv(V[c][c], q);
+          for (int j = 0; j < 8; ++j) V[c][j] = nt::mul(V[c][j], iv, q);
+          for (int r2 = 0; r2 < 4; ++r2) {
+            if (r2 == c || V[r2][c] == 0) continue;
+            const u64 f = V[r2][c];
+            for (int j = 0; j < 8; ++j) V[r2][j] = (V[r2][j] + q - nt::mul(f, V[c][j], q)) % q;
+          }
+        }
+        // V now holds [I | V^-1] with rows indexed by j: (V^-1)[j][h] = V[j][4 + h]
+        u64* sp = &split[(size_t)i * 56];
+        for (int h = 0; h < 4; ++h)
+          for (int j = 1; j < 4; ++j) {
+            const u64 v = pw[(u64)(N / 4) * kE5[h] * j % m];
+            sp[2 * (3 * h + j - 1)] = v;
+            sp[2 * (3 * h + j - 1) + 1] = nt::shoup(v, q);
+          }
+        const u64 four_ni = nt::mul(4 % q, ni, q);
+        for (int j = 0; j < 4; ++j)
+          for (int h = 0; h < 4; ++h) {
+            const u64 v = nt::mul(V[j][4 + h], four_ni, q);
+            sp[24 + 2 * (4 * j + h)] = v;
+            sp[24 + 2 * (4 * j + h) + 1] = nt::shoup(v, q);
+          }
+        ninv[4 * i + 2] = 0;
+        ninv[4 * i + 3] = 0;
+      } else if (C.m_odd == 3) {
         // Phi_3N = (X^(N/2) - rho)(X^(N/2) - rho^5), rho = omega^(N/2): node 1
         // is that split (forward twiddle rho; the inverse recovers the high
         // half as (u - v) / (2 rho - 1)). Node k >= 2 at depth l splits
@@ -547,6 +756,7 @@ void build_context(Context& C, const ss_params& prm) {
     }
     upload((void**)&C.d_tw, tw.data(), tw.size() * 8);
     upload((void**)&C.d_ninv, ninv.data(), ninv.size() * 8);
+    if (C.m_odd == 5) upload((void**)&C.d_split, split.data(), split.size() * 8);
     upload((void**)&C.d_pinv, pinv.data(), pinv.size() * 8);
     std::vector<u64> tm((size_t)(C.r + 1) * T * 2);
     for (int e = 0; e <= C.r; ++e)
@@ -768,10 +978,83 @@ static std::vector<u64> decode_m3(const Context& C, u64 te, const u64* c) {
   return v;
 }
 
+// m = 5N/2 encoding: Phi_M'(y) = prod_q (y^h - x_q), h = n'/4, x_q =
+// theta^(h e_q), e = (1, 3, 7, 9); factor q has the roots theta^(e_q + 10k),
+// so B_q = A mod (y^h - x_q) has b_i = h^-1 theta^(-e_q i) sum_k
+// V_{e_q+10k} theta^(-10ik); then A = sum_j y^(jh) A_j with B_q = sum_j x_q^j
+// A_j, solved by Gauss-Jordan elimination over GR(p^t, 4).
+static std::vector<u64> encode_m5(const Context& C, u64 te, const u64* v) {
+  const Gr4Ring R{GrRing{C.gr_c, te}, Gr{C.gr_w[0] % te, C.gr_w[1] % te}};
+  const Gr4 th{Gr{C.theta4[0] % te, C.theta4[1] % te}, Gr{C.theta4[2] % te, C.theta4[3] % te}};
+  const int Mp = C.Mp, n = C.nprime, h = n / 4;
+  std::vector<int> slot_of(Mp, -1);
+  for (int j = 0; j < C.slots; ++j)
+    for (u64 e = (u64)C.slot_exp[j]; slot_of[e] < 0; e = e * ((u64)C.p % Mp) % Mp) slot_of[e] = j;
+  std::vector<Gr4> tp(Mp);
+  tp[0] = R.one();
+  for (int e = 1; e < Mp; ++e) tp[e] = R.mul(tp[e - 1], th);
+  const u64 hinv = nt::inv((u64)h % te, te);
+  std::vector<Gr4> B[4];
+  for (int qq = 0; qq < 4; ++qq) {
+    const int eq = kE5[qq];
+    B[qq].assign(h, Gr4{});
+    for (int i = 0; i < h; ++i) {
+      Gr4 acc{};
+      for (int k = 0; k < h; ++k) {
+        const int e = eq + 10 * k;
+        if (slot_of[e] < 0) throw Error(SS_ERR_PARAM, "encode: root outside the slots");
+        const int ex = (int)((u64)10 * i * k % Mp);
+        acc = R.add(acc, R.scale(tp[(Mp - ex) % Mp], v[slot_of[e]] % te));
+      }
+      const int tex = (int)((u64)eq * i % Mp);
+      B[qq][i] = R.scale(R.mul(acc, tp[(Mp - tex) % Mp]), hinv);
+    }
+  }
+  // [V | I] -> [I | V^-1], V[q][j] = x_q^j
+  Gr4 M[4][8];
+  for (int qq = 0; qq < 4; ++qq)
+    for (int j = 0; j < 4; ++j) {
+      M[qq][j] = tp[(u64)h * kE5[qq] * j % Mp];
+      M[qq][4 + j] = qq == j ? R.one() : Gr4{};
+    }
+  for (int c = 0; c < 4; ++c) {
+    const Gr4 iv = R.inv(M[c][c]);  // distinct roots of unity: every pivot is a unit
+    for (int j = 0; j < 8; ++j) M[c][j] = R.mul(M[c][j], iv);
+    for (int r2 = 0; r2 < 4; ++r2) {
+      if (r2 == c) continue;
+      const Gr4 f = M[r2][c];
+      for (int j = 0; j < 8; ++j) M[r2][j] = R.sub(M[r2][j], R.mul(f, M[c][j]));
+    }
+  }
+  std::vector<u64> m(C.N, 0);
+  for (int j = 0; j < 4; ++j)
+    for (int i = 0; i < h; ++i) {
+      Gr4 a{};
+      for (int qq = 0; qq < 4; ++qq) a = R.add(a, R.mul(M[j][4 + qq], B[qq][i]));
+      if (a.a.a1 || a.b.a0 || a.b.a1) throw Error(SS_ERR_PARAM, "encode: interpolant outside Z_{p^t}");
+      m[(size_t)(j * h + i) * C.s_stride] = a.a.a0;
+    }
+  return m;
+}
+
+static std::vector<u64> decode_m5(const Context& C, u64 te, const u64* c) {
+  const Gr4Ring R{GrRing{C.gr_c, te}, Gr{C.gr_w[0] % te, C.gr_w[1] % te}};
+  const Gr4 th{Gr{C.theta4[0] % te, C.theta4[1] % te}, Gr{C.theta4[2] % te, C.theta4[3] % te}};
+  std::vector<u64> v(C.slots, 0);
+  for (int j = 0; j < C.slots; ++j) {
+    const Gr4 z = R.pow(th, (u64)C.slot_exp[j]);
+    Gr4 zk = R.one(), acc{};
+    for (int k = 0; k < C.nprime; ++k, zk = R.mul(zk, z)) acc = R.add(acc, R.scale(zk, c[(size_t)k * C.s_stride] % te));
+    v[j] = acc.a.a0;
+  }
+  return v;
+}
+
 std::vector<u64> encode(const Context& C, int t_exp, const u64* v) {
   if (t_exp < 1 || t_exp > C.r) throw Error(SS_ERR_PARAM, "bad t_exp");
   u64 te = C.tpow[t_exp];
   if (C.m_odd == 3) return encode_m3(C, te, v);
+  if (C.m_odd == 5) return encode_m5(C, te, v);
   u64 il = nt::inv((u64)C.slots % te, te);
   std::vector<u64> m(C.N, 0);
   for (int k = 0; k < C.slots; ++k) {
@@ -787,6 +1070,7 @@ std::vector<u64> decode(const Context& C, int t_exp, const u64* m) {
   if (t_exp < 1 || t_exp > C.r) throw Error(SS_ERR_PARAM, "bad t_exp");
   u64 te = C.tpow[t_exp];
   if (C.m_odd == 3) return decode_m3(C, te, m);
+  if (C.m_odd == 5) return decode_m5(C, te, m);
   std::vector<u64> v(C.slots, 0);
   for (int j = 0; j < C.slots; ++j) {
     u64 acc = 0;
@@ -798,7 +1082,7 @@ std::vector<u64> decode(const Context& C, int t_exp, const u64* m) {
 
 std::vector<int> rotate_sum_elements(const Context& C) {
   std::vector<int> g;
-  if (C.m_odd == 3) {  // g^(2^a) mod 3N for each slot-group generator of order n, a < log2 n
+  if (C.m_odd == 3 || C.m_odd == 5) {  // g^(2^a) mod m for each slot-group generator of order n, a < log2 n
     for (auto& gn : C.gens) {
       u64 e = (u64)gn.first % (u64)C.m;
       for (int n = 1; n < gn.second; n *= 2, e = e * e % (u64)C.m) g.push_back((int)e);

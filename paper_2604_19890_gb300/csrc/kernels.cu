@@ -474,7 +474,9 @@ __global__ void __launch_bounds__(256, SS_KSIP_MINB) k_ks_ip_multi(const __grid_
 // m = 3N: word h N/2 + j holds a(psi^E), E = e_h + 6 brv(j) (e_0 = 1, e_1 = 5,
 // brv over log2(N/2) bits); sigma_g(a) there is the word of exponent g E mod 3N,
 // whose residue mod 6 (1 or 5) gives its half and (gE - e)/6 its index.
-template <bool M3>
+// m = 5N/2: word h N/4 + j holds a(psi^E), E = e_h + 10 brv(j), e = (1, 3, 7, 9),
+// brv over log2(N/4) bits; the residue of g E mod 10 gives the source quarter.
+template <int RING>
 __global__ void k_automorph_impl(const u64* a, u64* out, int g, int N, int logN, int nrows, int acap, int ocap,
                                  int level) {
   int poly = blockIdx.y;  // (bt*ncomp + c, i)
@@ -482,7 +484,15 @@ __global__ void k_automorph_impl(const u64* a, u64* out, int g, int N, int logN,
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= N) return;
   unsigned src;
-  if (M3) {
+  if (RING == 5) {
+    const int lq = logN - 2, n4 = N >> 2;
+    const unsigned h = (unsigned)j >> lq, r = (unsigned)j & (unsigned)(n4 - 1);
+    const unsigned E = (2u * h + 1u + (h >= 2u ? 2u : 0u)) + 10u * (__brev(r) >> (32 - lq));  // e_h = 1, 3, 7, 9
+    const unsigned k = (unsigned)(((unsigned long long)g * E) % (5ull * (unsigned)N / 2ull));
+    const unsigned km = k % 10u;  // 1, 3, 7 or 9
+    const unsigned hs = km < 5u ? km / 2u : (km - 3u) / 2u;
+    src = hs * (unsigned)n4 + (__brev((k - km) / 10u) >> (32 - lq));
+  } else if (RING == 3) {
     const int lh = logN - 1, n2 = N >> 1;
     const unsigned h = (unsigned)j >> lh, r = (unsigned)j & (unsigned)(n2 - 1);
     const unsigned E = (h ? 5u : 1u) + 6u * (__brev(r) >> (32 - lh));
@@ -1162,9 +1172,11 @@ void ks_multi(const std::vector<KsReq>& reqs, cudaStream_t st) {
 void k_automorph(Context& C, const Buf& a, int g, Buf& out, cudaStream_t st) {
   int rows = a.count * a.ncomp;
   TIMED(KC_AUTOMORPH, 2.0 * rows * a.level * (double)C.N * 8.0,
-  if (C.m_odd == 3) k_automorph_impl<true><<<grid_for(C.N, rows * a.level), TPB, 0, st>>>(
+  if (C.m_odd == 5) k_automorph_impl<5><<<grid_for(C.N, rows * a.level), TPB, 0, st>>>(
       a.data, out.data, g, C.N, C.logN, rows, a.cap, out.cap, a.level);
-  else k_automorph_impl<false><<<grid_for(C.N, rows * a.level), TPB, 0, st>>>(
+  else if (C.m_odd == 3) k_automorph_impl<3><<<grid_for(C.N, rows * a.level), TPB, 0, st>>>(
+      a.data, out.data, g, C.N, C.logN, rows, a.cap, out.cap, a.level);
+  else k_automorph_impl<1><<<grid_for(C.N, rows * a.level), TPB, 0, st>>>(
       a.data, out.data, g, C.N, C.logN, rows, a.cap, out.cap, a.level));
   LAUNCHED();
 }

@@ -33,6 +33,9 @@ constexpr int TILE = 4096;  // words per CTA tile (32 KiB of shared memory)
 #ifndef SS_NTT_MINB_I
 #define SS_NTT_MINB_I 3
 #endif
+#ifndef SS_NTT_MINB_R5
+#define SS_NTT_MINB_R5 2  // m = 5N/2 column phases: the four-way split needs more registers
+#endif
 
 struct NttArgs {
   u64* base;
@@ -42,6 +45,7 @@ struct NttArgs {
   const Modulus* mods;
   const u64* tw;     // per prime 4N words: (w, w') pairs forward, then inverse
   const u64* ninv;   // per prime (N^-1, shoup, N^-1 psi^(-N/2), shoup)
+  const u64* split;  // m = 5N/2: per prime 28 (value, shoup) pairs: forward x_h^j (3h + j - 1), inverse (12 + 4j + h)
   const u64* src;    // out-of-place first phase: polynomial (o, i) is read at src + o src_os + i N
   long src_os;
 };
@@ -74,6 +78,46 @@ __device__ __forceinline__ u64 reduce_lazy(u64 v, u64 q, int kb, uint32_t mq) {
   return r >= q ? r - q : r;
 }
 
+// m = 5N/2: the four-way split of Phi_10(X^(N/4)) on four words a_j (the
+// quarters' words at one position). Forward b_h = a_0 + sum_j x_h^j a_j, lazy:
+// a_0 below 4q gives b_h below 10q. Inverse a_j = sum_h W_jh b_h with
+// W = V^-1 * 4/N (V_hj = x_h^j), canonical.
+__device__ __forceinline__ void split4_fwd(u64& a0, u64& a1, u64& a2, u64& a3, const ulonglong2* __restrict__ c,
+                                           u64 q) {
+  const u64 x0 = a0, x1 = a1, x2 = a2, x3 = a3;
+  u64 o[4];
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    const ulonglong2 c1 = __ldg(c + 3 * h), c2 = __ldg(c + 3 * h + 1), c3 = __ldg(c + 3 * h + 2);
+    o[h] = x0 + shoup_lazy(x1, c1.x, c1.y, q) + shoup_lazy(x2, c2.x, c2.y, q) + shoup_lazy(x3, c3.x, c3.y, q);
+  }
+  a0 = o[0];
+  a1 = o[1];
+  a2 = o[2];
+  a3 = o[3];
+}
+__device__ __forceinline__ void split4_inv(u64& b0, u64& b1, u64& b2, u64& b3, const ulonglong2* __restrict__ c,
+                                           u64 q) {
+  const u64 y[4] = {b0, b1, b2, b3};
+  u64 o[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    u64 v = 0;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const ulonglong2 w = __ldg(c + 12 + 4 * j + h);
+      v += shoup(y[h], w.x, w.y, q);
+    }
+    if (v >= 2 * q) v -= 2 * q;
+    if (v >= q) v -= q;
+    o[j] = v;
+  }
+  b0 = o[0];
+  b1 = o[1];
+  b2 = o[2];
+  b3 = o[3];
+}
+
 // One round of up to three radix-2 stages held in registers. The thread owns
 // the eight words r_k = rbase + k*u (rbase = B*8u + o, o < u); the round's
 // stages have half-distances t = u*2^j for j in [JLO, JHI] and pair the
@@ -83,7 +127,7 @@ __device__ __forceinline__ u64 reduce_lazy(u64 v, u64 q, int kb, uint32_t mq) {
 // X^(N/2) - rho and X^(N/2) - rho^5 (rho^5 = 1 - rho): forward (U, V) ->
 // (U + rho V, U + V - rho V); inverse t = (U - V)(2 rho - 1)^-1 ->
 // (U + V - t, 2t), both scaled by N^-1 with the rest afterwards.
-template <bool FWD, int JLO, int JHI, bool R3>
+template <bool FWD, int JLO, int JHI, int RING>
 __device__ __forceinline__ void ntt_round(u64 (&x)[8], int rbase, int logu, int logS, int mg,
                                           const ulonglong2* __restrict__ tw, u64 q) {
   const u64 q2 = 2 * q;
@@ -103,7 +147,7 @@ __device__ __forceinline__ void ntt_round(u64 (&x)[8], int rbase, int logu, int 
       for (int p = 0; p < d; ++p) {
         const int k = k0 + p;
         u64 U = x[k], V = x[k + d];
-        if (R3 && widx == 1) {
+        if (RING == 3 && widx == 1) {
           if (FWD) {  // residues stay below 4q
             if (U >= q2) U -= q2;
             if (V >= q2) V -= q2;
@@ -133,16 +177,16 @@ __device__ __forceinline__ void ntt_round(u64 (&x)[8], int rbase, int logu, int 
   }
 }
 
-template <bool FWD, bool R3>
+template <bool FWD, int RING>
 __device__ __forceinline__ void ntt_round_dispatch(int jlo, int jhi, u64 (&x)[8], int rbase, int logu, int logS, int mg,
                                                    const ulonglong2* tw, u64 q) {
   switch (jlo * 3 + jhi) {
-    case 0: ntt_round<FWD, 0, 0, R3>(x, rbase, logu, logS, mg, tw, q); break;
-    case 1: ntt_round<FWD, 0, 1, R3>(x, rbase, logu, logS, mg, tw, q); break;
-    case 2: ntt_round<FWD, 0, 2, R3>(x, rbase, logu, logS, mg, tw, q); break;
-    case 4: ntt_round<FWD, 1, 1, R3>(x, rbase, logu, logS, mg, tw, q); break;
-    case 5: ntt_round<FWD, 1, 2, R3>(x, rbase, logu, logS, mg, tw, q); break;
-    default: ntt_round<FWD, 2, 2, R3>(x, rbase, logu, logS, mg, tw, q); break;
+    case 0: ntt_round<FWD, 0, 0, RING>(x, rbase, logu, logS, mg, tw, q); break;
+    case 1: ntt_round<FWD, 0, 1, RING>(x, rbase, logu, logS, mg, tw, q); break;
+    case 2: ntt_round<FWD, 0, 2, RING>(x, rbase, logu, logS, mg, tw, q); break;
+    case 4: ntt_round<FWD, 1, 1, RING>(x, rbase, logu, logS, mg, tw, q); break;
+    case 5: ntt_round<FWD, 1, 2, RING>(x, rbase, logu, logS, mg, tw, q); break;
+    default: ntt_round<FWD, 2, 2, RING>(x, rbase, logu, logS, mg, tw, q); break;
   }
 }
 
@@ -151,7 +195,7 @@ __device__ __forceinline__ void ntt_round_dispatch(int jlo, int jhi, u64 (&x)[8]
 // blockDim = CPB*S/8. Residues stay lazy ([0,4q) forward, [0,2q) inverse)
 // except in the LAST phase, which writes canonical values (times N^-1 for
 // the inverse).
-template <bool FWD, bool COLS, bool LAST, bool R3 = false>
+template <bool FWD, bool COLS, bool LAST, int RING = 1>
 __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, int m0) {
   extern __shared__ u64 sm[];
   u64* ptr;
@@ -170,6 +214,27 @@ __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, in
     sm[swz(lin)] = ptr[g];
   }
   __syncthreads();
+  // m = 5N/2 (one phase over CPB = 4 chunks, the four factors): the split
+  // first, residues brought below 2q for the rounds
+  const ulonglong2* spl = RING == 5 ? reinterpret_cast<const ulonglong2*>(A.split + (size_t)pidx * 56) : nullptr;
+  if (RING == 5 && FWD) {
+    const int n4 = W >> 2;
+    for (int i = tid; i < n4; i += T) {
+      u64 a0 = sm[swz(i)], a1 = sm[swz(i + n4)], a2 = sm[swz(i + 2 * n4)], a3 = sm[swz(i + 3 * n4)];
+      if (a0 >= 2 * q) a0 -= 2 * q;
+      if (a0 >= 2 * q) a0 -= 2 * q;
+      split4_fwd(a0, a1, a2, a3, spl, q);
+      u64* o4[4] = {&a0, &a1, &a2, &a3};
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        u64 v = *o4[h];  // below 8q
+        if (v >= 4 * q) v -= 4 * q;
+        if (v >= 2 * q) v -= 2 * q;
+        sm[swz(i + h * n4)] = v;
+      }
+    }
+    __syncthreads();
+  }
   const int rounds = (logS + 2) / 3;
   for (int rho = 0; rho < rounds; ++rho) {
     // log2 of the smallest (a) and largest (b) half-distance of this round
@@ -198,11 +263,23 @@ __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, in
       int r = rbase + (k << logu);
       x[k] = sm[swz(COLS ? (r << logCPB) + c : (c << logS) + r)];
     }
-    ntt_round_dispatch<FWD, R3>(a - logu, b - logu, x, rbase, logu, logS, mg, tw, q);
+    ntt_round_dispatch<FWD, RING>(a - logu, b - logu, x, rbase, logu, logS, mg, tw, q);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       int r = rbase + (k << logu);
       sm[swz(COLS ? (r << logCPB) + c : (c << logS) + r)] = x[k];
+    }
+    __syncthreads();
+  }
+  if (RING == 5 && !FWD) {  // the split last, with the 4/N scaling: canonical
+    const int n4 = W >> 2;
+    for (int i = tid; i < n4; i += T) {
+      u64 b0 = sm[swz(i)], b1 = sm[swz(i + n4)], b2 = sm[swz(i + 2 * n4)], b3 = sm[swz(i + 3 * n4)];
+      split4_inv(b0, b1, b2, b3, spl, q);
+      sm[swz(i)] = b0;
+      sm[swz(i + n4)] = b1;
+      sm[swz(i + 2 * n4)] = b2;
+      sm[swz(i + 3 * n4)] = b3;
     }
     __syncthreads();
   }
@@ -214,7 +291,7 @@ __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, in
       if (FWD) {
         if (v >= 2 * q) v -= 2 * q;
         if (v >= q) v -= q;
-      } else {
+      } else if (RING != 5) {
         v = shoup(v, ni, nip, q);
       }
     }
@@ -243,7 +320,7 @@ __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, in
 // Forward it adds up to 6q to the bound, so the transform stays below 40q.
 // Inverse it is fused with N^-1: with c = (2 rho - 1)^-1 N^-1 (inverse
 // twiddle word 0), high = (U - V) 2c, low = (U + V) N^-1 - (U - V) c.
-template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC, bool R3 = false>
+template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC, int RING = 1>
 __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0, int tile, int poly) {
   extern __shared__ u64 sm[];
   u64* ptr;
@@ -293,7 +370,7 @@ __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0,
     nip = A.ninv[4 * pidx + 1];
     wni = A.ninv[4 * pidx + 2];
     wnip = A.ninv[4 * pidx + 3];
-    if (R3) {
+    if (RING == 3) {
       const ulonglong2 c0 = __ldg(tw);
       cni = c0.x;
       cnip = c0.y;
@@ -349,7 +426,26 @@ __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0,
         // the inverse transform's last stage (one twiddle, psi^(-N/2)) also
         // applies N^-1: sums times N^-1, differences times N^-1 psi^(-N/2)
         const bool fold = LAST && !FWD && rho == NR - 1 && jj == ns - 1;
-        const bool split = R3 && COLS && FWD && rho == 0 && jj == 0;
+        const bool split = RING == 3 && COLS && FWD && rho == 0 && jj == 0;
+        // m = 5N/2: the first two forward stages and the last two inverse
+        // stages of the column phase are the four-way split on the registers
+        // k, k+4, k+8, k+12 (the quarters), k < 4
+        if (RING == 5 && COLS && FWD && rho == 0 && jj < 2) {
+          if (jj == 0) {
+            const ulonglong2* spl = reinterpret_cast<const ulonglong2*>(A.split + (size_t)pidx * 56);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) split4_fwd(x[k], x[k + 4], x[k + 8], x[k + 12], spl, q);
+          }
+          continue;
+        }
+        if (RING == 5 && COLS && LAST && !FWD && rho == NR - 1 && jj >= ns - 2) {
+          if (jj == ns - 1) {
+            const ulonglong2* spl = reinterpret_cast<const ulonglong2*>(A.split + (size_t)pidx * 56);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) split4_inv(x[k], x[k + 4], x[k + 8], x[k + 12], spl, q);
+          }
+          continue;
+        }
 #pragma unroll
         for (int blk = 0; blk < 8; ++blk) {
           if (blk < 8 / d) {
@@ -369,7 +465,7 @@ __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0,
               if (p < d) {
                 const int k = k0 + p;
                 u64 U = x[k], V = x[k + d];
-                if (fold && R3) {
+                if (fold && RING == 3) {
                   const u64 dv = U - V + q2;
                   const u64 lo = shoup(U + V, ni, nip, q), cr = shoup(dv, cni, cnip, q);
                   x[k] = lo >= cr ? lo - cr : lo + q - cr;
@@ -425,9 +521,10 @@ __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0,
   }
 }
 
-template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC = false, bool R3 = false>
-__global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I) k_ntt16(NttArgs A, int logCPB, int m0) {
-  ntt16_tile<FWD, COLS, LAST, LOGS, SRC, R3>(A, logCPB, m0, blockIdx.x, blockIdx.y);
+template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC = false, int RING = 1>
+__global__ void __launch_bounds__(256, RING == 5 ? SS_NTT_MINB_R5 : (FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I))
+    k_ntt16(NttArgs A, int logCPB, int m0) {
+  ntt16_tile<FWD, COLS, LAST, LOGS, SRC, RING>(A, logCPB, m0, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------- persistent multi-transform phase
@@ -443,7 +540,7 @@ constexpr int kMaxNttJobs = 24;
 struct NttJob {
   NttArgs A;
   int logS, logCPB, m0, tiles, start;
-  int r3;  // ring m = 3N: the column phases take the split stage
+  int ring;  // the context's m_odd: 3 (m = 3N) or 5 (m = 5N/2) give the column phase its split; 1 none
 };
 struct NttMulti {
   int njobs, total;
@@ -451,9 +548,9 @@ struct NttMulti {
 };
 
 // a separate function per instantiation, so each keeps its own register allocation
-template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC, bool R3 = false>
+template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC, int RING = 1>
 __device__ __noinline__ void ntt16_tile_fn(const NttArgs& A, int logCPB, int m0, int tile, int poly) {
-  ntt16_tile<FWD, COLS, LAST, LOGS, SRC, R3>(A, logCPB, m0, tile, poly);
+  ntt16_tile<FWD, COLS, LAST, LOGS, SRC, RING>(A, logCPB, m0, tile, poly);
 }
 
 template <bool FWD, bool COLS, bool LAST, bool SRC>
@@ -466,12 +563,20 @@ __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I)
     const int local = t - J.start;
     const int poly = local / J.tiles, tile = local - poly * J.tiles;
     if constexpr (COLS) {
-      if (J.r3) {
-        switch (J.logS) {
-          case 5: ntt16_tile_fn<FWD, COLS, LAST, 5, SRC, true>(J.A, J.logCPB, J.m0, tile, poly); break;
-          case 6: ntt16_tile_fn<FWD, COLS, LAST, 6, SRC, true>(J.A, J.logCPB, J.m0, tile, poly); break;
-          case 7: ntt16_tile_fn<FWD, COLS, LAST, 7, SRC, true>(J.A, J.logCPB, J.m0, tile, poly); break;
-          default: ntt16_tile_fn<FWD, COLS, LAST, 8, SRC, true>(J.A, J.logCPB, J.m0, tile, poly); break;
+      if (J.ring == 3 || J.ring == 5) {
+        if (J.ring == 3) {
+          switch (J.logS) {
+            case 5: ntt16_tile_fn<FWD, COLS, LAST, 5, SRC, 3>(J.A, J.logCPB, J.m0, tile, poly); break;
+            case 6: ntt16_tile_fn<FWD, COLS, LAST, 6, SRC, 3>(J.A, J.logCPB, J.m0, tile, poly); break;
+            case 7: ntt16_tile_fn<FWD, COLS, LAST, 7, SRC, 3>(J.A, J.logCPB, J.m0, tile, poly); break;
+            default: ntt16_tile_fn<FWD, COLS, LAST, 8, SRC, 3>(J.A, J.logCPB, J.m0, tile, poly); break;
+          }
+        } else {
+          switch (J.logS) {
+            case 6: ntt16_tile_fn<FWD, COLS, LAST, 6, SRC, 5>(J.A, J.logCPB, J.m0, tile, poly); break;
+            case 7: ntt16_tile_fn<FWD, COLS, LAST, 7, SRC, 5>(J.A, J.logCPB, J.m0, tile, poly); break;
+            default: ntt16_tile_fn<FWD, COLS, LAST, 8, SRC, 5>(J.A, J.logCPB, J.m0, tile, poly); break;
+          }
         }
         __syncthreads();
         continue;
@@ -487,13 +592,13 @@ __global__ void __launch_bounds__(256, FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I)
   }
 }
 
-template <bool FWD, bool COLS, bool LAST, bool SRC = false, bool R3 = false>
+template <bool FWD, bool COLS, bool LAST, bool SRC = false, int RING = 1>
 void launch16(int logS, dim3 g, int thr, size_t smem, cudaStream_t st, const NttArgs& A, int logc, int m0) {
   switch (logS) {
-    case 5: k_ntt16<FWD, COLS, LAST, 5, SRC, R3><<<g, thr, smem, st>>>(A, logc, m0); break;
-    case 6: k_ntt16<FWD, COLS, LAST, 6, SRC, R3><<<g, thr, smem, st>>>(A, logc, m0); break;
-    case 7: k_ntt16<FWD, COLS, LAST, 7, SRC, R3><<<g, thr, smem, st>>>(A, logc, m0); break;
-    default: k_ntt16<FWD, COLS, LAST, 8, SRC, R3><<<g, thr, smem, st>>>(A, logc, m0); break;
+    case 5: k_ntt16<FWD, COLS, LAST, 5, SRC, RING><<<g, thr, smem, st>>>(A, logc, m0); break;
+    case 6: k_ntt16<FWD, COLS, LAST, 6, SRC, RING><<<g, thr, smem, st>>>(A, logc, m0); break;
+    case 7: k_ntt16<FWD, COLS, LAST, 7, SRC, RING><<<g, thr, smem, st>>>(A, logc, m0); break;
+    default: k_ntt16<FWD, COLS, LAST, 8, SRC, RING><<<g, thr, smem, st>>>(A, logc, m0); break;
   }
 }
 
@@ -513,6 +618,7 @@ NttArgs make_args(Context& C, const PolySet& s) {
   A.mods = reinterpret_cast<const Modulus*>(C.d_mod);
   A.tw = C.d_tw;
   A.ninv = C.d_ninv;
+  A.split = C.d_split;
   A.src = nullptr;
   A.src_os = 0;
   return A;
@@ -536,6 +642,11 @@ NttMerger*& ntt_merger() {
   return m;
 }
 
+// log2 of the chunk length N2 of the two-phase split: 256, except that the
+// m = 5N/2 ring needs at least 64 column words (its inverse split takes the
+// column phase's last two stages in one register round)
+static int chunk_log(const Context& C) { return C.m_odd == 5 && C.logN - 8 < 6 ? C.logN - 6 : 8; }
+
 // src: optional out-of-place source read by the first phase (inverse only)
 static void launch(Context& C, const PolySet& s, bool fwd, cudaStream_t st, const u64* src = nullptr,
                    long src_os = 0) {
@@ -556,9 +667,12 @@ static void launch(Context& C, const PolySet& s, bool fwd, cudaStream_t st, cons
     int kr = kt_begin(C, st);
     dim3 g(1, npoly);
     int thr = N / 8;
-    if (C.m_odd == 3) {
-      if (fwd) k_ntt<true, false, true, true><<<g, thr, smem(N), st>>>(A, logN, 0, 1);
-      else k_ntt<false, false, true, true><<<g, thr, smem(N), st>>>(A, logN, 0, 1);
+    if (C.m_odd == 5) {  // the split, then the four factors as chunks of N/4 (nodes 4..7 and below)
+      if (fwd) k_ntt<true, false, true, 5><<<g, thr, smem(N), st>>>(A, logN - 2, 2, 4);
+      else k_ntt<false, false, true, 5><<<g, thr, smem(N), st>>>(A, logN - 2, 2, 4);
+    } else if (C.m_odd == 3) {
+      if (fwd) k_ntt<true, false, true, 3><<<g, thr, smem(N), st>>>(A, logN, 0, 1);
+      else k_ntt<false, false, true, 3><<<g, thr, smem(N), st>>>(A, logN, 0, 1);
     } else {
       if (fwd) k_ntt<true, false, true><<<g, thr, smem(N), st>>>(A, logN, 0, 1);
       else k_ntt<false, false, true><<<g, thr, smem(N), st>>>(A, logN, 0, 1);
@@ -567,14 +681,14 @@ static void launch(Context& C, const PolySet& s, bool fwd, cudaStream_t st, cons
     kt_end(C, kr, KC_NTT, 16.0 * N * active_polys(s), st);
   } else {
     int kr = kt_begin(C, st);
-    const int log2n = 8, log1 = logN - log2n;  // N = N1 * N2, N2 = 256
+    const int log2n = chunk_log(C), log1 = logN - log2n;  // N = N1 * N2, N2 = 2^log2n
     const int tl = C.ntt_tile_log == 11 ? 11 : 12, tile = 1 << tl;
     const int logc1 = tl - log1, logc2 = tl - log2n;
     dim3 g1(1 << (log2n - logc1), npoly), g2(1 << (log1 - logc2), npoly);
     const int thr = tile / 16;
-    const bool r3 = C.m_odd == 3;
     if (fwd) {
-      if (r3) launch16<true, true, false, false, true>(log1, g1, thr, smem(tile), st, A, logc1, 1);
+      if (C.m_odd == 3) launch16<true, true, false, false, 3>(log1, g1, thr, smem(tile), st, A, logc1, 1);
+      else if (C.m_odd == 5) launch16<true, true, false, false, 5>(log1, g1, thr, smem(tile), st, A, logc1, 1);
       else launch16<true, true, false>(log1, g1, thr, smem(tile), st, A, logc1, 1);
       launch16<true, false, true>(log2n, g2, thr, smem(tile), st, A, logc2, 1 << log1);
     } else {
@@ -586,7 +700,8 @@ static void launch(Context& C, const PolySet& s, bool fwd, cudaStream_t st, cons
       } else {
         launch16<false, false, false>(log2n, g2, thr, smem(tile), st, A, logc2, 1 << log1);
       }
-      if (r3) launch16<false, true, true, false, true>(log1, g1, thr, smem(tile), st, A, logc1, 1);
+      if (C.m_odd == 3) launch16<false, true, true, false, 3>(log1, g1, thr, smem(tile), st, A, logc1, 1);
+      else if (C.m_odd == 5) launch16<false, true, true, false, 5>(log1, g1, thr, smem(tile), st, A, logc1, 1);
       else launch16<false, true, true>(log1, g1, thr, smem(tile), st, A, logc1, 1);
     }
     C.launches += 2;
@@ -633,10 +748,9 @@ void ntt_multi(const std::vector<NttReq>& reqs, bool fwd, int tile_log, cudaStre
       const int npoly = q.s.n_outer * q.s.nl;
       if (npoly == 0) continue;
       NttArgs A = make_args(C, q.s);
-      const int log1 = C.logN - 8, logc1 = tl - log1, logc2 = tl - 8;
-      const int r3 = C.m_odd == 3 ? 1 : 0;
-      NttJob cols{A, log1, logc1, 1, 1 << (8 - logc1), 0, r3};
-      NttJob chunks{A, 8, logc2, 1 << log1, 1 << (log1 - logc2), 0, 0};
+      const int l2 = chunk_log(C), log1 = C.logN - l2, logc1 = tl - log1, logc2 = tl - l2;
+      NttJob cols{A, log1, logc1, 1, 1 << (l2 - logc1), 0, C.m_odd};
+      NttJob chunks{A, l2, logc2, 1 << log1, 1 << (log1 - logc2), 0, 1};
       if (!fwd) {  // the chunk phase reads the source (the polynomials themselves when in place)
         chunks.A.src = q.src ? q.src : q.s.base;
         chunks.A.src_os = q.src ? q.src_os : q.s.outer_stride;

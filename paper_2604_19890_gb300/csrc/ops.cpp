@@ -301,7 +301,7 @@ void op_keygen(Context& C, const std::vector<int>& galois) {
   cudaStream_t st = nullptr;
   const int N = C.N, T = C.ntot;
   for (int g : galois)
-    if (g <= 0 || g >= C.m || g % 2 == 0 || (C.m_odd == 3 && g % 3 == 0))
+    if (g <= 0 || g >= C.m || g % 2 == 0 || (C.m_odd > 1 && g % C.m_odd == 0))
       throw Error(SS_ERR_PARAM, "Galois element must be a unit in (0, m)");
   C.sk = sample_secret(C);
   // s in evaluation form on every prime

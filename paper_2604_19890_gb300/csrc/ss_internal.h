@@ -116,7 +116,7 @@ struct Context {
   u64 t = 0;  // p^r
   std::vector<u64> tpow;  // p^e, e = 0..r
   std::vector<u64> primes, psi;  // psi: primitive m-th root of unity per prime
-  int m_odd = 1, m = 0;           // odd part of the cyclotomic index; m = 2N (m_odd 1) or 3N (m_odd 3)
+  int m_odd = 1, m = 0;           // odd part of the cyclotomic index; m = 2N (m_odd 1), 3N (3) or 5N/2 (5)
   int slots = 0, d = 0;
   u64 omega = 0;
   std::vector<int> slot_exp;
@@ -125,12 +125,15 @@ struct Context {
   // m = 3N slot algebra: Phi_3N(X) = Phi_M'(X^s), roots theta^e in GR(p^r, 2) = Z_{p^r}[u]/(u^2 - gr_c)
   int Mp = 0, s_stride = 0, nprime = 0;
   u64 gr_c = 0, theta[2] = {0, 0};
+  // m = 5N/2: Phi_m(X) = Phi_M'(X^s), M' = 5*2^b', roots theta4 in GR(p^r, 4) = GR(p^r, 2)[v]/(v^2 - gr_w)
+  u64 gr_w[2] = {0, 0}, theta4[4] = {0, 0, 0, 0};
   std::vector<std::pair<int, int>> gens;  // slot-group generators mod M' with their orders
 
   // device tables
   ModDesc* d_mod = nullptr;           // [ntot]
   u64* d_tw = nullptr;                // per prime 4N words: (psi_brv, shoup) pairs, then (psiinv_brv, shoup) pairs
   u64* d_ninv = nullptr;              // [ntot][4] N^{-1}, shoup, N^{-1} psi^{-N/2} (m = 3N: 2 N^{-1}), shoup
+  u64* d_split = nullptr;             // m = 5N/2: [ntot][28][2] four-way split constants (forward 12, inverse 16)
   u64* d_pinv = nullptr;              // [ntot][2] p^{-1}, shoup
   u64* d_tmod = nullptr;              // [r+1][ntot][2]: p^e mod q, shoup
   u64* d_tables = nullptr;            // base-conversion constants (offsets below)

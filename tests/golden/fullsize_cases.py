@@ -24,6 +24,8 @@ PRESETS = {
     2: dict(logN=16, L=41, alpha=3, bits=55, p=257, r=3, h=120, seed=0x5EED0002),
     # the same on the cyclotomic ring m = 3N (X^N - X^(N/2) + 1): 256 slots
     3: dict(logN=16, L=41, alpha=3, bits=55, p=257, r=3, h=120, seed=0x5EED0003, m_odd=3),
+    # and on m = 5N/2 (X^N - X^(3N/4) + X^(N/2) - X^(N/4) + 1): 512 slots
+    4: dict(logN=16, L=41, alpha=3, bits=55, p=257, r=3, h=120, seed=0x5EED0004, m_odd=5),
 }
 
 # Nonces of the encrypted inputs: column k uses nonce base + row index.
@@ -45,6 +47,9 @@ CASES = {
     # the same query on m = 3N, 256 slots
     "query_n65536_257cubed_m3n": dict(kind="query", params=PRESETS[3], value_seed=0x5EED3003, n_ct=1,
                                       threshold=None, square=False),
+    # on m = 5N/2, 512 slots
+    "query_n65536_257cubed_m5n2": dict(kind="query", params=PRESETS[4], value_seed=0x5EED3004, n_ct=1,
+                                       threshold=None, square=False),
 }
 
 # Results of the "ops" case, in the order they are computed:

@@ -75,7 +75,7 @@ def test_ops_n65536_257cubed():
 
 
 @pytest.mark.parametrize("name", ["query_n8192_17sq", "query_n32768_257sq", "query_n65536_257cubed",
-                                  "query_n65536_257cubed_m3n"])
+                                  "query_n65536_257cubed_m3n", "query_n65536_257cubed_m5n2"])
 def test_query_fullsize(name):
     from oracle import plain
     case = FC.CASES[name]
