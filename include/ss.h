@@ -10,8 +10,9 @@
  *
  * Conventions shared by every call
  *  - Ring Z[X]/Phi_m(X), N a power of two: m = 2N, Phi_m = X^N+1 (the
- *    default), or m = 3N, Phi_m = X^N - X^(N/2) + 1 (ss_params.m_odd = 3; the
- *    paper's general cyclotomic m, Section 2.1, with N / Ord(3N, p) slots).
+ *    default), m = 3N, Phi_m = X^N - X^(N/2) + 1 (ss_params.m_odd = 3), or
+ *    m = 5N/2, Phi_m = Phi_10(X^(N/4)) (m_odd = 5): the paper's general
+ *    cyclotomic m, Section 2.1, with N / Ord(m, p) slots.
  *    RNS chain of L data primes q_0 > ... > q_{L-1} and alpha special primes,
  *    all = 1 mod (m/N)*nmax*p^r.
  *  - A ciphertext batch (ss_ct) lives in caller-owned DEVICE memory laid out
@@ -21,7 +22,8 @@
  *    mod q_i: for m = 2N word j of limb i is a(psi_i^(2*bitrev(j)+1)) mod q_i;
  *    for m = 3N word h*N/2 + j (h = 0, 1; j < N/2) is
  *    a(psi_i^(e_h + 6*bitrev(j))) with e_0 = 1, e_1 = 5 and bitrev over
- *    log2(N/2) bits.
+ *    log2(N/2) bits; for m = 5N/2 word h*N/4 + j (h = 0..3; j < N/4) is
+ *    a(psi_i^(e_h + 10*bitrev(j))), e = (1, 3, 7, 9), bitrev over log2(N/4).
  *    Only limbs 0..level-1 are meaningful. The library never frees caller
  *    memory; outputs must have capacity >= the level they receive.
  *  - Every device call is enqueued on the given stream (NULL = legacy default
@@ -66,13 +68,14 @@ typedef struct {
   int32_t L;        /* data primes */
   int32_t alpha;    /* special primes = key-switching digit width */
   int32_t bits;     /* primes lie in (2^(bits-1), 2^bits); 20 <= bits <= 58 */
-  int32_t p;        /* plaintext prime >= 5; p = 1 mod 4 when m = 2N */
+  int32_t p;        /* plaintext prime >= 5; p = 1 mod 4 when m = 2N; p != 5, p < 2^15 when m = 5N/2 */
   int32_t r;        /* plaintext modulus p^r */
   int32_t h;        /* Hamming weight of the ternary secret (Section 5.1: 120) */
   int32_t nmax;     /* largest N the prime chain must support (0 = N) */
   uint64_t seed;    /* Philox4x32-10 key for every sampled value */
   int32_t m_odd;    /* odd part of the cyclotomic index m (Section 2.1, 5.1): 0 or 1 -> m = 2N,
-                       ring Z[X]/(X^N + 1); 3 -> m = 3N, ring Z[X]/(X^N - X^(N/2) + 1) */
+                       ring Z[X]/(X^N + 1); 3 -> m = 3N, ring Z[X]/(X^N - X^(N/2) + 1);
+                       5 -> m = 5N/2, ring Z[X]/(X^N - X^(3N/4) + X^(N/2) - X^(N/4) + 1), N >= 32 */
   int32_t reserved; /* 0 */
 } ss_params;
 
@@ -106,14 +109,14 @@ ss_status ss_context_info(const ss_ctx* ctx, int32_t* N, int32_t* L, int32_t* al
 
 /* Secret key (ternary, Hamming weight h; Section 2.1 and 5.1), the
  * relinearisation key for s^2 and one Galois key per element of `galois`
- * (units mod m: odd residues mod 2N, or residues mod 3N prime to 6). Keys are hybrid key-switching keys over the data and
+ * (units mod m: residues prime to m). Keys are hybrid key-switching keys over the data and
  * special primes, device-resident and owned by ctx. Synchronous. */
 ss_status ss_keygen(ss_ctx* ctx, const int32_t* galois, int32_t ngalois);
 
 /* Galois elements ss_rotate_sum uses; returns the count, writes up to cap
  * elements. m = 2N: 5^(2^i) mod 2N for i < log2(slots/2), then 2N-1.
- * m = 3N: for each slot-group generator g of order n (below), g^(2^i) mod 3N
- * for i < log2 n, generators in their order. */
+ * m = 3N, 5N/2: for each slot-group generator g of order n (below), g^(2^i)
+ * mod m for i < log2 n, generators in their order. */
 int32_t ss_rotate_sum_elements(const ss_ctx* ctx, int32_t* out, int32_t cap);
 
 /* Slot encoding over Z_{p^t_exp} (host, synchronous): slots[slots] ->
@@ -128,7 +131,11 @@ int32_t ss_rotate_sum_elements(const ss_ctx* ctx, int32_t* out, int32_t cap);
  * orbit of g_1^j_1 g_2^j_2 ..., where g_i is the smallest residue of largest
  * order n_i modulo the subgroup generated by p, g_1, ..., g_{i-1}. The
  * encoding is A(X^s) with A(theta^e) = the value of e's slot; decoding
- * returns the Z_{p^t} coordinate of A_0(theta^e_j), A_0 = sum_k c[k s] y^k. */
+ * returns the Z_{p^t} coordinate of A_0(theta^e_j), A_0 = sum_k c[k s] y^k.
+ * m = 5N/2: the same with 2^b || p^4 - 1, b' = min(b, log2 N - 1), M' =
+ * 5*2^b', s = m/M', units prime to 10, and GR(p^r, 4) = GR(p^r, 2)[v]/(v^2 -
+ * w), w the first non-square x0 + x1 u of F_{p^2}; theta lifts the element of
+ * smallest index x0 + p x1 + p^2 x2 + p^3 x3 (basis 1, u, v, uv) of order M'. */
 ss_status ss_encode(const ss_ctx* ctx, int32_t t_exp, const uint64_t* slots, uint64_t* coeffs);
 ss_status ss_decode(const ss_ctx* ctx, int32_t t_exp, const uint64_t* coeffs, uint64_t* slots);
 
@@ -143,7 +150,7 @@ ss_status ss_encrypt(ss_ctx* ctx, const uint64_t* coeffs, int32_t count, uint32_
  * Only the coefficients at multiples of d are computed (the slot
  * coefficients); the others are written as zero. */
 ss_status ss_decrypt(ss_ctx* ctx, const ss_ct* in, uint64_t* coeffs, ss_stream stream);
-/* (For m = 3N the computed coefficients are those at multiples of s.) */
+/* (For m = 3N and 5N/2 the computed coefficients are those at multiples of s.) */
 
 /* ---- BGV operations (Section 2.1); operands must share level and t_exp ---- */
 ss_status ss_add(ss_ctx* ctx, const ss_ct* a, const ss_ct* b, ss_ct* out, ss_stream stream);
