@@ -645,7 +645,7 @@ void build_context(Context& C, const ss_params& prm) {
   {
     std::vector<u64> tw((size_t)T * 4 * N);
     std::vector<u64> ninv(4 * T), pinv(2 * T);
-    std::vector<u64> split(C.m_odd == 5 ? (size_t)T * 56 : 0);
+    std::vector<u64> split(C.m_odd == 5 ? (size_t)T * 24 : 0);
     for (int i = 0; i < T; ++i) {
       u64 q = C.primes[i], ps = C.psi[i], pi = nt::inv(ps, q);
       u64* o = &tw[(size_t)i * 4 * N];
@@ -675,40 +675,20 @@ void build_context(Context& C, const ss_params& prm) {
           const u64 e = (u64)((N / 4) >> (l - 1)) * (kE5[h] + 10 * (u64)nt::brv(j, l - 2)) % m;
           put(k, pw[e], pw[(m - e) % m]);
         }
-        // split: forward x_h^j (j = 1..3), inverse (V^-1)[j][h] * 4/N, V[h][j] = x_h^j
-        u64 V[4][8];
-        for (int h = 0; h < 4; ++h)
-          for (int j = 0; j < 4; ++j) {
-            V[h][j] = pw[(u64)(N / 4) * kE5[h] * j % m];
-            V[h][4 + j] = h == j ? 1 : 0;
-          }
-        for (int c = 0; c < 4; ++c) {  // Gauss-Jordan mod q
-          int r = c;
-          while (V[r][c] == 0) ++r;
-          for (int j = 0; j < 8; ++j) std::swap(V[c][j], V[r][j]);
-          const u64 iv = nt::inv(V[c][c], q);
-          for (int j = 0; j < 8; ++j) V[c][j] = nt::mul(V[c][j], iv, q);
-          for (int r2 = 0; r2 < 4; ++r2) {
-            if (r2 == c || V[r2][c] == 0) continue;
-            const u64 f = V[r2][c];
-            for (int j = 0; j < 8; ++j) V[r2][j] = (V[r2][j] + q - nt::mul(f, V[c][j], q)) % q;
-          }
+        // split constants (the factored four-way split through the quadratics
+        // y^2 - c y + 1, c = xi^e + xi^-e): forward c_1, xi, xi^3, xi^7, xi^9;
+        // inverse (xi - xi^9)^-1, xi, (xi^3 - xi^7)^-1, xi^3, (1 - 2 c_1)^-1 4/N, 4/N, c_1
+        const u64 x1 = pw[N / 4], x3 = pw[(u64)3 * N / 4], x7 = pw[(u64)7 * N / 4 % m], x9 = pw[(u64)9 * N / 4 % m];
+        const u64 c1 = (x1 + x9) % q;
+        const u64 sigma = nt::mul(4 % q, ni, q);
+        const u64 dsig = nt::mul(nt::inv((1 + 2 * q - 2 * c1) % q, q), sigma, q);
+        const u64 vals[12] = {c1, x1, x3, x7, x9, nt::inv((x1 + q - x9) % q, q), x1, nt::inv((x3 + q - x7) % q, q), x3,
+                              dsig, sigma, c1};
+        u64* sp = &split[(size_t)i * 24];
+        for (int k2 = 0; k2 < 12; ++k2) {
+          sp[2 * k2] = vals[k2];
+          sp[2 * k2 + 1] = nt::shoup(vals[k2], q);
         }
-        // V now holds [I | V^-1] with rows indexed by j: (V^-1)[j][h] = V[j][4 + h]
-        u64* sp = &split[(size_t)i * 56];
-        for (int h = 0; h < 4; ++h)
-          for (int j = 1; j < 4; ++j) {
-            const u64 v = pw[(u64)(N / 4) * kE5[h] * j % m];
-            sp[2 * (3 * h + j - 1)] = v;
-            sp[2 * (3 * h + j - 1) + 1] = nt::shoup(v, q);
-          }
-        const u64 four_ni = nt::mul(4 % q, ni, q);
-        for (int j = 0; j < 4; ++j)
-          for (int h = 0; h < 4; ++h) {
-            const u64 v = nt::mul(V[j][4 + h], four_ni, q);
-            sp[24 + 2 * (4 * j + h)] = v;
-            sp[24 + 2 * (4 * j + h) + 1] = nt::shoup(v, q);
-          }
         ninv[4 * i + 2] = 0;
         ninv[4 * i + 3] = 0;
       } else if (C.m_odd == 3) {

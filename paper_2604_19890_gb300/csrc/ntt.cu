@@ -34,7 +34,7 @@ constexpr int TILE = 4096;  // words per CTA tile (32 KiB of shared memory)
 #define SS_NTT_MINB_I 3
 #endif
 #ifndef SS_NTT_MINB_R5
-#define SS_NTT_MINB_R5 2  // m = 5N/2 column phases: the four-way split needs more registers
+#define SS_NTT_MINB_R5 3  // m = 5N/2 column phases (the factored split fits the same 80 registers)
 #endif
 
 struct NttArgs {
@@ -45,7 +45,7 @@ struct NttArgs {
   const Modulus* mods;
   const u64* tw;     // per prime 4N words: (w, w') pairs forward, then inverse
   const u64* ninv;   // per prime (N^-1, shoup, N^-1 psi^(-N/2), shoup)
-  const u64* split;  // m = 5N/2: per prime 28 (value, shoup) pairs: forward x_h^j (3h + j - 1), inverse (12 + 4j + h)
+  const u64* split;  // m = 5N/2: per prime 12 (value, shoup) pairs of the four-way split (split4_fwd/inv)
   const u64* src;    // out-of-place first phase: polynomial (o, i) is read at src + o src_os + i N
   long src_os;
 };
@@ -79,43 +79,55 @@ __device__ __forceinline__ u64 reduce_lazy(u64 v, u64 q, int kb, uint32_t mq) {
 }
 
 // m = 5N/2: the four-way split of Phi_10(X^(N/4)) on four words a_j (the
-// quarters' words at one position). Forward b_h = a_0 + sum_j x_h^j a_j, lazy:
-// a_0 below 4q gives b_h below 10q. Inverse a_j = sum_h W_jh b_h with
-// W = V^-1 * 4/N (V_hj = x_h^j), canonical.
+// quarters' words at one position), factored through the quadratics
+// y^2 - c y + 1 = (y - xi^e)(y - xi^-e), c = xi^e + xi^-e, e = 1 and 3. Both
+// c are roots of c^2 = c + 1 (c_1 + c_3 = 1, c_1 c_3 = -1), so a mod the
+// quadratic is (a0 - a2 - c a3) + (a1 + c (a2 + a3)) y and the two
+// quadratics share the products c_1 a3 and c_1 (a2 + a3); each remainder is
+// then evaluated at its two roots. Forward: 6 Shoup products per 4 words,
+// inputs below 4q give outputs below 16q, in the order xi^1, xi^3, xi^7, xi^9.
+// Inverse (inputs below 2q): the remainders from the root values, then
+// a3 = (r0 - s0) / (1 - 2 c_1), a2 + a3 = (s1 - r1) / (1 - 2 c_1),
+// a1 = r1 - c_1 (a2 + a3), a0 = r0 + a2 + c_1 a3, scaled by 4/N: 10 products,
+// canonical. Constants per prime (value, Shoup pairs): forward c_1, xi, xi^3,
+// xi^7, xi^9; inverse (xi - xi^9)^-1, xi, (xi^3 - xi^7)^-1, xi^3,
+// (1 - 2 c_1)^-1 4/N, 4/N, c_1.
+constexpr int kSplitWords = 24;
 __device__ __forceinline__ void split4_fwd(u64& a0, u64& a1, u64& a2, u64& a3, const ulonglong2* __restrict__ c,
                                            u64 q) {
-  const u64 x0 = a0, x1 = a1, x2 = a2, x3 = a3;
-  u64 o[4];
-#pragma unroll
-  for (int h = 0; h < 4; ++h) {
-    const ulonglong2 c1 = __ldg(c + 3 * h), c2 = __ldg(c + 3 * h + 1), c3 = __ldg(c + 3 * h + 2);
-    o[h] = x0 + shoup_lazy(x1, c1.x, c1.y, q) + shoup_lazy(x2, c2.x, c2.y, q) + shoup_lazy(x3, c3.x, c3.y, q);
-  }
-  a0 = o[0];
-  a1 = o[1];
-  a2 = o[2];
-  a3 = o[3];
+  const ulonglong2 c1 = __ldg(c);
+  const u64 t3 = shoup_lazy(a3, c1.x, c1.y, q);
+  const u64 t23 = shoup_lazy(a2 + a3, c1.x, c1.y, q);
+  const u64 r0 = a0 + 6 * q - a2 - t3;
+  const u64 r1 = a1 + t23;
+  const u64 s0 = a0 + t3 + 8 * q - a2 - a3;
+  const u64 s1 = a1 + a2 + a3 + 2 * q - t23;
+  const ulonglong2 x1 = __ldg(c + 1), x3 = __ldg(c + 2), x7 = __ldg(c + 3), x9 = __ldg(c + 4);
+  a0 = r0 + shoup_lazy(r1, x1.x, x1.y, q);
+  a3 = r0 + shoup_lazy(r1, x9.x, x9.y, q);
+  a1 = s0 + shoup_lazy(s1, x3.x, x3.y, q);
+  a2 = s0 + shoup_lazy(s1, x7.x, x7.y, q);
 }
 __device__ __forceinline__ void split4_inv(u64& b0, u64& b1, u64& b2, u64& b3, const ulonglong2* __restrict__ c,
                                            u64 q) {
-  const u64 y[4] = {b0, b1, b2, b3};
-  u64 o[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    u64 v = 0;
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      const ulonglong2 w = __ldg(c + 12 + 4 * j + h);
-      v += shoup(y[h], w.x, w.y, q);
-    }
-    if (v >= 2 * q) v -= 2 * q;
-    if (v >= q) v -= q;
-    o[j] = v;
-  }
-  b0 = o[0];
-  b1 = o[1];
-  b2 = o[2];
-  b3 = o[3];
+  const ulonglong2 k1 = __ldg(c + 5), x1 = __ldg(c + 6), k3 = __ldg(c + 7), x3 = __ldg(c + 8);
+  const u64 r1 = shoup(b0 - b3 + 2 * q, k1.x, k1.y, q);
+  const u64 r0 = b0 + q - shoup(r1, x1.x, x1.y, q);
+  const u64 s1 = shoup(b1 - b2 + 2 * q, k3.x, k3.y, q);
+  const u64 s0 = b1 + q - shoup(s1, x3.x, x3.y, q);
+  const ulonglong2 d = __ldg(c + 9), sg = __ldg(c + 10), c1 = __ldg(c + 11);
+  const u64 a3 = shoup(r0 - s0 + 3 * q, d.x, d.y, q);
+  const u64 S = shoup(s1 - r1 + q, d.x, d.y, q);
+  const u64 a2 = S >= a3 ? S - a3 : S + q - a3;
+  const u64 u1 = shoup(r1, sg.x, sg.y, q), v1 = shoup(S, c1.x, c1.y, q);
+  const u64 a1 = u1 >= v1 ? u1 - v1 : u1 + q - v1;
+  u64 a0 = shoup(r0, sg.x, sg.y, q) + a2 + shoup(a3, c1.x, c1.y, q);
+  if (a0 >= 2 * q) a0 -= 2 * q;
+  if (a0 >= q) a0 -= q;
+  b0 = a0;
+  b1 = a1;
+  b2 = a2;
+  b3 = a3;
 }
 
 // One round of up to three radix-2 stages held in registers. The thread owns
@@ -216,18 +228,17 @@ __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, in
   __syncthreads();
   // m = 5N/2 (one phase over CPB = 4 chunks, the four factors): the split
   // first, residues brought below 2q for the rounds
-  const ulonglong2* spl = RING == 5 ? reinterpret_cast<const ulonglong2*>(A.split + (size_t)pidx * 56) : nullptr;
+  const ulonglong2* spl = RING == 5 ? reinterpret_cast<const ulonglong2*>(A.split + (size_t)pidx * kSplitWords) : nullptr;
   if (RING == 5 && FWD) {
     const int n4 = W >> 2;
     for (int i = tid; i < n4; i += T) {
       u64 a0 = sm[swz(i)], a1 = sm[swz(i + n4)], a2 = sm[swz(i + 2 * n4)], a3 = sm[swz(i + 3 * n4)];
-      if (a0 >= 2 * q) a0 -= 2 * q;
-      if (a0 >= 2 * q) a0 -= 2 * q;
       split4_fwd(a0, a1, a2, a3, spl, q);
       u64* o4[4] = {&a0, &a1, &a2, &a3};
 #pragma unroll
       for (int h = 0; h < 4; ++h) {
-        u64 v = *o4[h];  // below 8q
+        u64 v = *o4[h];  // below 16q
+        if (v >= 8 * q) v -= 8 * q;
         if (v >= 4 * q) v -= 4 * q;
         if (v >= 2 * q) v -= 2 * q;
         sm[swz(i + h * n4)] = v;
@@ -311,7 +322,7 @@ __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, in
 // range is a compile-time constant, so the sixteen words stay in registers.
 // The forward butterfly here never reduces its upper input: each stage adds
 // less than 2q to the bound, so inputs below 4q leave a log2 N <= 16 stage
-// transform below 36q (40q with the m = 3N split) < 64q < 2^64 (primes below
+// transform below 36q (40q with the m = 3N split, 44q with m = 5N/2's) < 64q < 2^64 (primes below
 // 2^58), and the last phase brings every word back to [0, q) once (reduce_lazy).
 // One CTA tile (`tile` of polynomial `poly`) of one phase; the body of the
 // per-transform kernel k_ntt16 and of the persistent kernel k_ntt16_multi.
@@ -432,7 +443,7 @@ __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0,
         // k, k+4, k+8, k+12 (the quarters), k < 4
         if (RING == 5 && COLS && FWD && rho == 0 && jj < 2) {
           if (jj == 0) {
-            const ulonglong2* spl = reinterpret_cast<const ulonglong2*>(A.split + (size_t)pidx * 56);
+            const ulonglong2* spl = reinterpret_cast<const ulonglong2*>(A.split + (size_t)pidx * kSplitWords);
 #pragma unroll
             for (int k = 0; k < 4; ++k) split4_fwd(x[k], x[k + 4], x[k + 8], x[k + 12], spl, q);
           }
@@ -440,7 +451,7 @@ __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0,
         }
         if (RING == 5 && COLS && LAST && !FWD && rho == NR - 1 && jj >= ns - 2) {
           if (jj == ns - 1) {
-            const ulonglong2* spl = reinterpret_cast<const ulonglong2*>(A.split + (size_t)pidx * 56);
+            const ulonglong2* spl = reinterpret_cast<const ulonglong2*>(A.split + (size_t)pidx * kSplitWords);
 #pragma unroll
             for (int k = 0; k < 4; ++k) split4_inv(x[k], x[k + 4], x[k + 8], x[k + 12], spl, q);
           }

@@ -133,7 +133,7 @@ struct Context {
   ModDesc* d_mod = nullptr;           // [ntot]
   u64* d_tw = nullptr;                // per prime 4N words: (psi_brv, shoup) pairs, then (psiinv_brv, shoup) pairs
   u64* d_ninv = nullptr;              // [ntot][4] N^{-1}, shoup, N^{-1} psi^{-N/2} (m = 3N: 2 N^{-1}), shoup
-  u64* d_split = nullptr;             // m = 5N/2: [ntot][28][2] four-way split constants (forward 12, inverse 16)
+  u64* d_split = nullptr;             // m = 5N/2: [ntot][12][2] four-way split constants (forward 5, inverse 7)
   u64* d_pinv = nullptr;              // [ntot][2] p^{-1}, shoup
   u64* d_tmod = nullptr;              // [r+1][ntot][2]: p^e mod q, shoup
   u64* d_tables = nullptr;            // base-conversion constants (offsets below)
