@@ -279,10 +279,10 @@ def run_kernel(args):
     from paper_2604_19890_gb300 import build as ssbuild
 
     ssbuild.build()
-    prm = ssg.preset(PRESET)
+    prm = ssg.preset(args.preset)
     g = ssg.Context(params=prm)
     peak, kind = hbm_peak()
-    out = {"kernel": args.kernel}
+    out = {"kernel": args.kernel, "preset": args.preset}
     if args.kernel == "ntt":
         L = g.L
         n = args.limbs - args.limbs % L
