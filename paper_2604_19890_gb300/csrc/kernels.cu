@@ -258,6 +258,80 @@ __global__ void __launch_bounds__(256) k_bconv_impl(const u64* __restrict__ src,
   }
 }
 
+// Base conversion from more than four sources (a modulus switch that drops
+// many primes at once): the same staged constants and arithmetic as
+// k_bconv_impl, but the sources stream through registers once per chunk of TC
+// targets, so a thread holds TC x V 128-bit sums instead of every source word.
+// The sums are exact, so the outputs are the same words in any order.
+template <int TC, int V>
+__global__ void __launch_bounds__(256) k_bconv_many_impl(const u64* __restrict__ src, long src_os, int ns, int sp0,
+                                                         int nsq, const u64* __restrict__ c1,
+                                                         const u64* __restrict__ c2, int T, u64* __restrict__ dst,
+                                                         long dst_os, int nd, int nq, int L, int skip_lo, int skip_hi,
+                                                         const u64* __restrict__ post, int N, const ModDesc* mods) {
+  extern __shared__ u64 sh[];
+  const int W = 2 + ns;
+  for (int m = threadIdx.x; m < nd; m += blockDim.x) {
+    const int g = m < nq ? m : L + (m - nq);
+    const Modulus& md = MOD(mods, g);
+    u64* e = sh + m * W;
+    e[0] = md.q;
+    e[1] = md.qinv;
+    const u64 R = barrett_reduce128(1, 0, md);  // 2^64 mod q
+    for (int s = 0; s < ns; ++s) {
+      u64 v = c2[(long)s * T + g];
+      if (post) v = shoup(v, post[2 * g], post[2 * g + 1], md.q);
+      e[2 + s] = mul_mod(v, R, md);
+    }
+  }
+  __syncthreads();
+  const int o = blockIdx.y;
+  const int n = V * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (n >= N) return;
+  const int lo_end = min(skip_lo, nd);
+  const int nt = lo_end + (nd - skip_hi);  // targets [0, skip_lo) and [skip_hi, nd)
+  const u64* sp = src + o * src_os + n;
+  u64* out = dst + o * dst_os + n;
+  for (int t0 = 0; t0 < nt; t0 += TC) {
+    int tm[TC];
+#pragma unroll
+    for (int c = 0; c < TC; ++c) {
+      const int t = min(t0 + c, nt - 1);
+      tm[c] = t < lo_end ? t : skip_hi + (t - lo_end);
+    }
+    Acc128 acc[TC][V];
+#pragma unroll
+    for (int c = 0; c < TC; ++c)
+#pragma unroll
+      for (int i = 0; i < V; ++i) acc[c][i].zero();
+    for (int s = 0; s < ns; ++s) {
+      const int gs = s < nsq ? sp0 + s : L + (s - nsq);
+      const u64 qs = MOD(mods, gs).q;
+      const u64 w = __ldg(c1 + 2 * s), wp = __ldg(c1 + 2 * s + 1);
+      u64 v[V];
+      ldv<V>(sp + (long)s * N, v);
+#pragma unroll
+      for (int i = 0; i < V; ++i) v[i] = shoup(v[i], w, wp, qs);
+#pragma unroll
+      for (int c = 0; c < TC; ++c) {
+        const u64 cs = sh[tm[c] * W + 2 + s];
+#pragma unroll
+        for (int i = 0; i < V; ++i) acc[c][i].mac_wide(v[i], cs);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < TC; ++c) {
+      if (t0 + c < nt) {
+        const u64* e = sh + tm[c] * W;
+        u64 r[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) r[i] = redc128(acc[c][i].hi, acc[c][i].lo, e[0], e[1]);
+        stv<V>(out + (long)tm[c] * N, r);
+      }
+    }
+  }
+}
+
 // out[m] = (a[m] - d[m]) * scale[m] (+ add[m]); limb m is data prime m.
 __global__ void k_sub_scale_impl(const u64* a, long a_os, const u64* dl, long d_os, const u64* scale, const u64* add,
                                  long add_os, u64* out, long out_os, int nl, int N, const ModDesc* mods) {
@@ -1035,7 +1109,10 @@ void k_bconv(Context& C, const u64* src, long src_os, int ns, int sp0, const u64
     case 2: SS_BCONV(2, SS_BCONV_V); break;
     case 3: SS_BCONV(3, SS_BCONV_V); break;
     case 4: SS_BCONV(4, SS_BCONV_V); break;
-    default: SS_BCONV(0, 1); break;
+    default:
+      k_bconv_many_impl<4, 2><<<dim3((g.x + 1) / 2, g.y), TPB, smem, st>>>(
+          src, src_os, ns, sp0, nsq, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo, skip_hi, post, C.N, C.d_mod);
+      break;
   }
 #undef SS_BCONV
   kt_end(C, kr_, KC_BCONV, (double)(ns + nd - (skip_hi - skip_lo)) * n_outer * C.N * 8.0, st);

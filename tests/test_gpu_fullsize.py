@@ -144,6 +144,28 @@ def test_keyswitch_parity_two_phase(prm, count):
     assert (g.decrypt_slots(gm) == (A.astype(object) * B.astype(object)) % g.t).all()
 
 
+@pytest.mark.parametrize("drop", [5, 8, 17, 38, 40])
+def test_modswitch_many_primes_two_phase(drop):
+    """Modulus switching by many primes at once (the query aligns operands
+    down by up to 39 levels): base conversion from more than four primes, to
+    one up to 36 remaining primes, at N = 2^14 on the 41-prime 55-bit chain."""
+    import paper_2604_19890_gb300 as ssg
+    prm = dict(logN=14, L=41, alpha=3, bits=55, p=257, r=3, h=120, seed=521)
+    g = ssg.Context(nmax=0, **prm)
+    o = O.Oracle(**prm)
+    g.keygen([])
+    o.keygen([])
+    rng = np.random.default_rng(drop)
+    A = rng.integers(0, g.t, (2, g.slots))
+    ga = g.encrypt(np.stack([g.encode(v) for v in A]), 30)
+    oa = [o.encrypt(o.encode(v), 30 + i) for i, v in enumerate(A)]
+    same(ga, oa)
+    gs = g.modswitch(ga, drop)
+    same(gs, [o.modswitch(x, drop) for x in oa])
+    assert gs.level == prm["L"] - drop
+    assert (g.decrypt_slots(gs) == A).all()
+
+
 BATCH_SETS = [dict(logN=14, L=14, alpha=2, bits=36, p=17, r=2, h=120, seed=511),
               dict(logN=15, L=14, alpha=2, bits=55, p=257, r=2, h=120, seed=512)]
 
