@@ -74,6 +74,37 @@ def test_ops_n65536_257cubed():
         check(name, ct, exp[name])
 
 
+def test_ops_n65536_257cubed_inside_a_ragged_batch():
+    """The digest case's ciphertexts as element 1 of batches of three (the
+    others random): every batched operation at N = 2^16, level 41 runs its
+    launches over three ciphertexts (an odd count, so the inner product's last
+    ciphertext pair is ragged) and element 1 must still give the reference's
+    words for the case alone."""
+    case = FC.CASES["ops_n65536_257cubed"]
+    exp = DIGESTS["ops_n65536_257cubed"]["results"]
+    g = gpu_ctx(case["params"])
+    va, vb = FC.ops_inputs(case, g.slots, g.t)
+    rng = np.random.default_rng(77)
+    A = np.stack([rng.integers(0, g.t, g.slots), va, rng.integers(0, g.t, g.slots)])
+    B = np.stack([rng.integers(0, g.t, g.slots), vb, rng.integers(0, g.t, g.slots)])
+    a = g.encrypt(np.stack([g.encode(v) for v in A]), 0)  # element 1: nonce 1, as enc_a
+    b = g.encrypt(np.stack([g.encode(v) for v in B]), 1)  # element 1: nonce 2, as enc_b
+    check("enc_a", a, exp["enc_a"], b=1)
+    check("enc_b", b, exp["enc_b"], b=1)
+    t = g.mul(a, b)
+    check("tensor", t, exp["tensor"], b=1)
+    check("relin", g.relin(t), exp["relin"], b=1)
+    m = g.mul_relin(a, b)
+    check("mul", m, exp["mul"], b=1)
+    check("modswitch_3", g.modswitch(a, 3), exp["modswitch_3"], b=1)
+    check("rotate_5", g.rotate(a, 5), exp["rotate_5"], b=1)
+    check("rotate_sum", g.rotate_sum(m), exp["rotate_sum"], b=1)
+    for i, d in enumerate(g.reduce(a)):
+        check("digit_%d" % i, d, exp["digit_%d" % i], b=1)
+    got = g.decrypt_slots(m)
+    assert (got == (A.astype(object) * B.astype(object)) % g.t).all()
+
+
 @pytest.mark.parametrize("name", ["query_n8192_17sq", "query_n32768_257sq", "query_n65536_257cubed",
                                   "query_n65536_257cubed_m3n", "query_n65536_257cubed_m5n2"])
 def test_query_fullsize(name):
