@@ -408,7 +408,10 @@ def run_serve(args):
                 "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "passes": st["batches"],
                 "peak_inflight_bytes": st["peak_inflight_bytes"]}
 
-    for rate in [0.5 * cap, 1.0 * cap, 2.0 * cap, 10.0]:
+    rates = []
+    for tok in args.serve_rates.split(","):  # "2c": twice the measured capacity; "10": 10 q/s
+        rates.append(float(tok[:-1]) * cap if tok.endswith("c") else float(tok))
+    for rate in rates:
         gaps = rng.exponential(1.0 / rate, args.serve_queries)
         arrivals = np.cumsum(gaps) - gaps[0]
         picks = [tables[int(k)] for k in rng.integers(0, len(tables), args.serve_queries)]
@@ -416,14 +419,15 @@ def run_serve(args):
             r = run(arrivals, picks, workers, merge)
             r.update({"form": form, "arrival_qps": round(rate, 3)})
             out["runs"].append(r)
-    # tables of 2^15 rows at N = 2^15 (256 ciphertexts per column) among small queries
-    big = [make_table(1, 10 + i, 256) for i in range(2)]
-    est = gs[1].query_bytes(256)
-    picks = [big[0]] + tables[:6] + [big[1]] + tables[6:]
-    r = run([0.0] * len(picks), picks, 3, 8, budget=int(2.5 * est), check=len(picks))
-    r.update({"form": "served", "arrival": "burst", "large_queries": 2, "large_rows": 256 * 128,
-              "hbm_budget": int(2.5 * est)})
-    out["runs"].append(r)
+    if not args.no_serve_burst:
+        # tables of 2^15 rows at N = 2^15 (256 ciphertexts per column) among small queries
+        big = [make_table(1, 10 + i, 256) for i in range(2)]
+        est = gs[1].query_bytes(256)
+        picks = [big[0]] + tables[:6] + [big[1]] + tables[6:]
+        r = run([0.0] * len(picks), picks, 3, 8, budget=int(2.5 * est), check=len(picks))
+        r.update({"form": "served", "arrival": "burst", "large_queries": 2, "large_rows": 256 * 128,
+                  "hbm_budget": int(2.5 * est)})
+        out["runs"].append(r)
     out["verified_against_plaintext"] = ok
     print(json.dumps(out))
     return 0 if ok else 1
@@ -541,6 +545,52 @@ def run_batched(args):
     return 0 if ok else 1
 
 
+# ------------------------------------------------------------------ short served and batched runs
+def _sub_json(argv, timeout):
+    """Runs this script with `argv` in a child process (its own CUDA context,
+    so nothing it allocates stays behind) and returns its JSON line."""
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__)] + argv, capture_output=True, text=True,
+                           timeout=timeout, cwd=ROOT)
+    except subprocess.TimeoutExpired:
+        return None, "timed out after %d s" % timeout
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    if r.returncode != 0 or not lines:
+        return None, "exit %d: %s" % (r.returncode, (r.stderr or r.stdout).strip().splitlines()[-1:] or "")
+    return json.loads(lines[-1]), None
+
+
+def run_extras():
+    """The served and batched forms in short runs beside the headline number
+    (before it, in child processes): the served form at twice the measured
+    capacity with 100 Poisson arrivals over both parameter sets, plain and
+    served; the batched form of 64 mixed-N pairs, one at a time against the
+    tuned, graph-replayed batch. The full sweeps are `--serve` and `--batched`."""
+    out = {}
+    t0 = time.perf_counter()
+    sv, err = _sub_json(["--serve", "--serve-queries", "100", "--serve-rates", "2c", "--no-serve-burst"], 600)
+    if sv is None:
+        out["served"] = {"error": err}
+    else:
+        runs = {r["form"]: {k: round(r[k], 2) for k in ("qps", "p50_ms", "p99_ms")} for r in sv["runs"]}
+        out["served"] = {"workload": sv["config"]["workload"], "unit": "queries/s",
+                         "capacity_qps": round(sv["capacity_qps"], 2), "arrivals": sv["runs"][0]["queries"],
+                         "arrival_qps": sv["runs"][0]["arrival_qps"], "plain": runs.get("plain"),
+                         "served": runs.get("served"), "verified_against_plaintext": sv["verified_against_plaintext"]}
+    bt, err = _sub_json(["--batched", "--steps", "3"], 600)
+    if bt is None:
+        out["batched"] = {"error": err}
+    else:
+        out["batched"] = {"workload": bt["metric"], "unit": "pairs/s",
+                          "plain_pairs_per_s": round(bt["plain_pairs_per_s"], 1),
+                          "batched_pairs_per_s": round(bt["batched_pairs_per_s"], 1),
+                          "speedup": round(bt["speedup"], 3), "tuned": bt["tuned"],
+                          "merged_lanes_graph_ms": bt["merged_lanes_graph_ms"],
+                          "verified_against_plaintext": bt["verified_against_plaintext"]}
+    out["extras_s"] = round(time.perf_counter() - t0, 1)
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     import numpy as np
@@ -550,10 +600,14 @@ def run_ours(args):
     from paper_2604_19890_gb300 import build as ssbuild
     from paper_2604_19890_gb300 import synth
 
+    ssbuild.build()
+    extras = {}
+    if (int(os.environ.get("WORLD_SIZE", "1")) == 1 and not args.no_extras and args.preset == PRESET
+            and args.n_ct == N_CT and args.batch == 32):
+        extras = run_extras()
     rank, world = dist_init()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    ssbuild.build()
     prm = ssg.preset(args.preset)
     prm.seed = SEED + 1000 * rank
     g = ssg.Context(params=prm)
@@ -615,6 +669,7 @@ def run_ours(args):
     step()
     torch.cuda.synchronize()
     ks = g.kernel_stats()
+    ntt_products = g.ntt_products()
     stages = {k: round(v[1], 3) for k, v in g.stage_stats().items()}
     g.kernel_timing(False)
     # measured integer-pipe ceilings (register-only loops, no memory traffic)
@@ -633,17 +688,19 @@ def run_ours(args):
 
     n_l, ms_l, b_l = ks[dom]
     if dom == "ntt":
-        # integer-multiply roofline of the transform: butterflies = limbs * N/2 * log2 N
-        limbs = b_l / (16.0 * g.N)
-        bfly = limbs * g.N / 2 * int(np.log2(g.N))
+        # integer-multiply roofline of the transform: the Shoup products its
+        # launches performed (N/2 per stage and limb; fewer where the ModUp base
+        # conversion applied the first twiddle), counted by the library
+        bfly = ntt_products
         achieved = bfly * slots_per_bfly / (ms_l / 1e3) / 1e12
         peak_alu = IMAD_PEAK / 1e12
         roof = {"kernel": "ntt", "bound": "alu", "achieved": achieved, "peak": peak_alu,
                 "unit": "T multiply issue slots/s", "frac": achieved / peak_alu,
                 "traffic": (NTT_TRAFFIC_PER_ALGO_BYTE * b_l / n_l) if NTT_TRAFFIC_PER_ALGO_BYTE else None,
-                "peak_source": "derived: 152 SMs x 64 multiply issue slots/clk x 2070 MHz; per Shoup butterfly "
+                "peak_source": "derived: 152 SMs x 64 multiply issue slots/clk x 2070 MHz; per Shoup product "
                                "10 multiplies = 5 single-slot + 5 widening at the measured slot ratio "
                                "(%.2f slots each), %.2f slots" % (wide_slots, slots_per_bfly),
+                "shoup_products": bfly,
                 "frac_at_one_slot_per_multiply": bfly * IMAD_PER_BUTTERFLY / (ms_l / 1e3) / IMAD_PEAK,
                 "measured_imad_per_s": imad_rate, "measured_wide_imad_per_s": wide_rate,
                 "measured_butterflies_per_s": bfly_rate,
@@ -700,6 +757,7 @@ def run_ours(args):
                 "roofline": roof, "kernel_classes": classes, "stages_ms": stages,
                 "ntt_gbs": gbs("ntt"), "keyswitch_ip_gbs": gbs("keyswitch_inner_product"),
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+        line.update(extras)
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
@@ -823,6 +881,11 @@ def main():
     ap.add_argument("--batched-mix", choices=["mixed", "small"], default="mixed")
     ap.add_argument("--serve-ct", type=int, default=2)
     ap.add_argument("--serve-queries", type=int, default=200)
+    ap.add_argument("--serve-rates", default="0.5c,1c,2c,10",
+                    help="arrival rates: q/s, or a multiple of the measured capacity with a 'c' suffix")
+    ap.add_argument("--no-serve-burst", action="store_true", help="skip the burst of 2^15-row tables")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline run without the short served- and batched-form measurements")
     ap.add_argument("--lt-sweep", action="store_true",
                     help="LT operator + modulus raising across (p, r) at fixed bit widths, per-stage times")
     ap.add_argument("--sweep-logn", type=int, default=15)

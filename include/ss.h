@@ -368,6 +368,17 @@ int32_t ss_trace_get(ss_ctx* ctx, char* buf, int32_t len);
 ss_status ss_kernel_timing(ss_ctx* ctx, int32_t on);
 ss_status ss_kernel_stats(ss_ctx* ctx, int32_t cls, uint64_t* launches, double* ms, double* bytes);
 
+/* Shoup products (one 64-bit modular product by a precomputed constant each)
+ * that the timed transform launches performed since kernel timing was switched
+ * on: per polynomial N/2 log2 N forward, less N/2 when a ModUp base conversion
+ * already applied the first stage's twiddle (ring X^N + 1), and
+ * N/2 (log2 N + 1) inverse (the last stage also scales the sums by N^-1). The
+ * split stages of the m = 3N and 5N/2 rings count as the radix-2 stages they
+ * replace. Written to *products; SS_ERR_PARAM on a null argument. The paper has
+ * no counterpart of this call; it is measurement (the work term of the
+ * transform's integer-multiply roofline). */
+ss_status ss_ntt_products(ss_ctx* ctx, double* products);
+
 /* Per-stage breakdown of the query while kernel timing is on, mirroring the
  * runtime breakdown of LT in Section 5 (reduction, comparison, aggregation,
  * modulus raising) plus the rest of the query:

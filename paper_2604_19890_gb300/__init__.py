@@ -115,6 +115,7 @@ _SIGS = {
     "ss_server_stats": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_uint64)] * 3),
     "ss_server_destroy": (None, [C.c_void_p]),
     "ss_kernel_timing": (C.c_int, [C.c_void_p, C.c_int32]),
+    "ss_ntt_products": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "ss_kernel_stats": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_double),
                                   C.POINTER(C.c_double)]),
 }
@@ -611,6 +612,12 @@ class Context:
             _chk(lib().ss_kernel_stats(self.h, i, C.byref(n), C.byref(ms), C.byref(b)))
             out[name] = (n.value, ms.value, b.value)
         return out
+
+    def ntt_products(self):
+        """Shoup products the timed transforms performed since timing was switched on."""
+        v = C.c_double()
+        _chk(lib().ss_ntt_products(self.h, C.byref(v)))
+        return v.value
 
     def stage_stats(self):
         """{stage: (runs, total ms)} of the query since timing was switched on."""

@@ -601,6 +601,7 @@ ss_status ss_kernel_timing(ss_ctx* ctx, int32_t on) {
     ss::kt_collect(C);
     if (on) {
       for (int k = 0; k < ss::KC_N; ++k) { C.kt.launches[k] = 0; C.kt.ms[k] = 0; C.kt.bytes[k] = 0; }
+      C.kt.ntt_products = 0;
       for (int k = 0; k < ss::ST_N; ++k) { C.kt.st_count[k] = 0; C.kt.st_ms[k] = 0; }
     }
     C.kt.on = on != 0;
@@ -615,6 +616,13 @@ ss_status ss_kernel_stats(ss_ctx* ctx, int32_t cls, uint64_t* launches, double* 
     if (launches) *launches = C.kt.launches[cls];
     if (ms) *ms = C.kt.ms[cls];
     if (bytes) *bytes = C.kt.bytes[cls];
+  });
+}
+
+ss_status ss_ntt_products(ss_ctx* ctx, double* products) {
+  return guard([&] {
+    need(ctx != nullptr && products != nullptr, SS_ERR_PARAM, "null argument");
+    *products = ctx->C.kt.ntt_products;
   });
 }
 

@@ -8,6 +8,7 @@
 // 8-byte words of one limb (256 B, fully coalesced).
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "modarith.cuh"
 #include "philox.h"
@@ -42,6 +43,12 @@ constexpr int TPB = 256;
 #endif
 #ifndef SS_KSIP_MINB
 #define SS_KSIP_MINB 4  // resident CTAs per SM the inner product is compiled for (64 registers)
+#endif
+#ifndef SS_KSIP_STAGES
+#define SS_KSIP_STAGES 3  // digits in flight per thread of the inner product (cp.async ring; 0: direct loads)
+#endif
+#ifndef SS_KSIP_ASYNC_MINB
+#define SS_KSIP_ASYNC_MINB 4  // resident CTAs per SM of the cp.async inner product (48 KiB ring each, 64 registers)
 #endif
 constexpr int kKsipUnroll = SS_KSIP_UNROLL > 0 ? SS_KSIP_UNROLL : 1;
 
@@ -194,22 +201,30 @@ __global__ void k_tensor_impl(const u64* a, const u64* b, u64* out, int N, int l
 // q_g 2^64 (primes below 2^58, ns <= 64), as the reduction needs.
 // V = 2: two consecutive coefficients per thread (16-byte accesses, the
 // staged constants read once for both).
+// tw != null (ModUp on the ring X^N + 1): outputs of the upper half
+// (coefficients n >= N/2) also carry the forward transform's node-1 twiddle
+// w_1 = psi^(N/2) of their prime, so the transform skips its first stage's
+// product (PolySet::pre_w1). A block's V*blockDim coefficients lie in one
+// half (the host checks that they divide N/2), so a block of the upper half
+// stages c2'[s] w_1 2^64 instead (the factor 2^64 w_1 mod q comes from the
+// per-prime table r64 beside 2^64 mod q; no product per output).
 template <int NS, int V>
 __global__ void __launch_bounds__(256) k_bconv_impl(const u64* __restrict__ src, long src_os, int ns, int sp0, int nsq,
                                                     const u64* __restrict__ c1, const u64* __restrict__ c2, int T,
                                                     u64* __restrict__ dst, long dst_os, int nd, int nq, int L,
                                                     int skip_lo, int skip_hi, const u64* __restrict__ post, int N,
-                                                    const ModDesc* mods) {
+                                                    const ModDesc* mods, const u64* __restrict__ r64, int pre) {
   extern __shared__ u64 sh[];
   const int ns_ = NS > 0 ? NS : ns;
   const int W = 2 + ns_;
+  const int upper = pre && 2 * V * blockIdx.x * blockDim.x >= N ? 1 : 0;  // block-uniform
   for (int m = threadIdx.x; m < nd; m += blockDim.x) {
     const int g = m < nq ? m : L + (m - nq);
     const Modulus& md = MOD(mods, g);
     u64* e = sh + m * W;
     e[0] = md.q;
     e[1] = md.qinv;
-    const u64 R = barrett_reduce128(1, 0, md);  // 2^64 mod q
+    const u64 R = __ldg(r64 + 2 * g + upper);  // 2^64 (times w_1) mod q
     for (int s = 0; s < ns_; ++s) {
       u64 v = c2[(long)s * T + g];
       if (post) v = shoup(v, post[2 * g], post[2 * g + 1], md.q);
@@ -262,22 +277,25 @@ __global__ void __launch_bounds__(256) k_bconv_impl(const u64* __restrict__ src,
 // many primes at once): the same staged constants and arithmetic as
 // k_bconv_impl, but the sources stream through registers once per chunk of TC
 // targets, so a thread holds TC x V 128-bit sums instead of every source word.
-// The sums are exact, so the outputs are the same words in any order.
+// The sums are exact, so the outputs are the same words in any order. pre: the
+// node-1 twiddle folded into the upper half, as in k_bconv_impl.
 template <int TC, int V>
 __global__ void __launch_bounds__(256) k_bconv_many_impl(const u64* __restrict__ src, long src_os, int ns, int sp0,
                                                          int nsq, const u64* __restrict__ c1,
                                                          const u64* __restrict__ c2, int T, u64* __restrict__ dst,
                                                          long dst_os, int nd, int nq, int L, int skip_lo, int skip_hi,
-                                                         const u64* __restrict__ post, int N, const ModDesc* mods) {
+                                                         const u64* __restrict__ post, int N, const ModDesc* mods,
+                                                         const u64* __restrict__ r64, int pre) {
   extern __shared__ u64 sh[];
   const int W = 2 + ns;
+  const int upper = pre && 2 * V * blockIdx.x * blockDim.x >= N ? 1 : 0;  // block-uniform
   for (int m = threadIdx.x; m < nd; m += blockDim.x) {
     const int g = m < nq ? m : L + (m - nq);
     const Modulus& md = MOD(mods, g);
     u64* e = sh + m * W;
     e[0] = md.q;
     e[1] = md.qinv;
-    const u64 R = barrett_reduce128(1, 0, md);  // 2^64 mod q
+    const u64 R = __ldg(r64 + 2 * g + upper);  // 2^64 (times w_1) mod q
     for (int s = 0; s < ns; ++s) {
       u64 v = c2[(long)s * T + g];
       if (post) v = shoup(v, post[2 * g], post[2 * g + 1], md.q);
@@ -401,6 +419,79 @@ __device__ __forceinline__ void ks_sums(const u64* __restrict__ d, long d_os, co
   }
 }
 
+// The same sums with the loads of each digit issued SS_KSIP_STAGES - 1 digits
+// ahead as asynchronous global-to-shared copies (cp.async, 16 bytes: this
+// thread's two coefficients of one row), so that several digits' key and
+// extended words are in flight per thread without holding registers. Every
+// thread reads back only the words it copied itself, so no block barrier is
+// needed. Ring layout: [slot][row][thread] of 16 bytes, row 0 the key's b
+// part, 1 its a part, 2 + b the extended (or own-digit) words of ciphertext b;
+// consecutive threads read consecutive 16 bytes (no bank conflicts).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
+}
+
+template <int OB, int S>
+__device__ __forceinline__ void ks_sums_async(const u64* __restrict__ d, long d_os, const u64* __restrict__ ext,
+                                              long ext_os, const u64* __restrict__ kb, const u64* __restrict__ ka,
+                                              int m, int g, int n, int nb, int level, int alpha, int T, int N,
+                                              ulonglong2* ring, Acc128 (&s0)[OB][2], Acc128 (&s1)[OB][2]) {
+  constexpr int R = 2 + OB;
+  const int dn = (level + alpha - 1) / alpha;
+  const int nlx = level + alpha;
+  const int jown = m < level ? m / alpha : -1;
+  const u64* kbp = kb + (size_t)g * N + n;
+  const u64* kap = ka + (size_t)g * N + n;
+  const size_t kstride = (size_t)T * N;
+  const u64* ep = ext + (long)m * N + n;
+  const u64* dp = d + (long)m * N + n;
+  const long jstride = (long)nlx * N;
+  const int nt = blockDim.x;
+  ulonglong2* mine = ring + threadIdx.x;
+#pragma unroll
+  for (int b = 0; b < OB; ++b)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      s0[b][v].zero();
+      s1[b][v].zero();
+    }
+  auto issue = [&](int j) {
+    if (j < dn) {
+      ulonglong2* slot = mine + (j % S) * R * nt;
+      cp_async16(slot, kbp + j * kstride);
+      cp_async16(slot + nt, kap + j * kstride);
+#pragma unroll
+      for (int b = 0; b < OB; ++b)
+        if (b < nb) cp_async16(slot + (2 + b) * nt, j == jown ? dp + b * d_os : ep + b * ext_os + j * jstride);
+    }
+    cp_async_commit();  // an empty group past the last digit keeps the count uniform
+  };
+#pragma unroll
+  for (int j = 0; j < S - 1; ++j) issue(j);
+  for (int j = 0; j < dn; ++j) {
+    issue(j + S - 1);
+    cp_async_wait<S - 1>();  // the group of digit j has landed
+    const ulonglong2* slot = mine + (j % S) * R * nt;
+    const ulonglong2 wb = slot[0], wa = slot[nt];
+#pragma unroll
+    for (int b = 0; b < OB; ++b) {
+      if (b < nb) {
+        const ulonglong2 x = slot[(2 + b) * nt];
+        s0[b][0].mac_wide(x.x, wb.x);
+        s0[b][1].mac_wide(x.y, wb.y);
+        s1[b][0].mac_wide(x.x, wa.x);
+        s1[b][1].mac_wide(x.y, wa.y);
+      }
+    }
+  }
+}
+
 // Arguments of one key-switch inner-product launch (see ks_block).
 struct KsJob {
   int type;  // 0: reduced sums to acc; 1: fused ModDown by P; 2: fused relinearise-and-drop
@@ -446,9 +537,9 @@ struct KsJob {
 //    TYPE 1 (ModDown by P):
 //          out_c[m] = (acc_c[m] - delta_c[m]) * P^{-1} (+ x_c[m] when x is
 //          given; component 1 only when add_c1).
-template <int OB, int TYPE>
+template <int OB, int TYPE, int STAGES = 0>
 __device__ __forceinline__ void ks_block(const KsJob& J, int bx, int by) {
-  constexpr int V = SS_KSIP_V;  // consecutive coefficients per thread (1, 2 or 4)
+  constexpr int V = STAGES > 0 ? 2 : SS_KSIP_V;  // consecutive coefficients per thread (1, 2 or 4)
   const int N = J.N;
   const int ngroups = (J.n_outer + OB - 1) / OB;
   const int o0 = (bx % ngroups) * OB;
@@ -459,8 +550,14 @@ __device__ __forceinline__ void ks_block(const KsJob& J, int bx, int by) {
   const int g = m < J.level ? m : J.L + (m - J.level);
   const Modulus md = MOD(J.mods, g);
   Acc128 s0[OB][V], s1[OB][V];
-  ks_sums<OB, V>(J.d + o0 * J.d_os, J.d_os, J.ext + o0 * J.ext_os, J.ext_os, J.kb, J.ka, m, g, n, nb, J.level,
-                 J.alpha, J.T, N, s0, s1);
+  if constexpr (STAGES > 0) {
+    extern __shared__ ulonglong2 ks_ring[];
+    ks_sums_async<OB, STAGES>(J.d + o0 * J.d_os, J.d_os, J.ext + o0 * J.ext_os, J.ext_os, J.kb, J.ka, m, g, n, nb,
+                              J.level, J.alpha, J.T, N, ks_ring, s0, s1);
+  } else {
+    ks_sums<OB, V>(J.d + o0 * J.d_os, J.d_os, J.ext + o0 * J.ext_os, J.ext_os, J.kb, J.ka, m, g, n, nb, J.level,
+                   J.alpha, J.T, N, s0, s1);
+  }
   if (TYPE == 0) {
     u64* out = J.acc + o0 * J.acc_os + (long)(m - J.m0) * N + n;
 #pragma unroll
@@ -515,6 +612,12 @@ __device__ __forceinline__ void ks_block(const KsJob& J, int bx, int by) {
 template <int OB, int TYPE>
 __global__ void __launch_bounds__(256, SS_KSIP_MINB) k_ks_ip_impl(const __grid_constant__ KsJob J) {
   ks_block<OB, TYPE>(J, blockIdx.x, blockIdx.y);
+}
+
+// dynamic shared memory: SS_KSIP_STAGES slots x (2 + OB) rows x 256 threads x 16 bytes
+template <int OB, int TYPE>
+__global__ void __launch_bounds__(256, SS_KSIP_ASYNC_MINB) k_ks_ip_async(const __grid_constant__ KsJob J) {
+  ks_block<OB, TYPE, SS_KSIP_STAGES>(J, blockIdx.x, blockIdx.y);
 }
 
 // Several inner-product launches (any contexts, levels and types) as one
@@ -1093,17 +1196,22 @@ void k_tensor(Context& C, const Buf& a, const Buf& b, Buf& out, cudaStream_t st)
 
 void k_bconv(Context& C, const u64* src, long src_os, int ns, int sp0, const u64* c1, const u64* c2, u64* dst,
              long dst_os, int nd, int nq, int skip_lo, int skip_hi, const u64* post, int n_outer, cudaStream_t st,
-             int nsq) {
+             int nsq, bool pre_w1) {
   if (nsq < 0) nsq = ns;  // every source is the data or special prime sp0 + s
   dim3 g = grid_for(C.N, n_outer);
   if (ns < 1 || ns > 64) throw Error(SS_ERR_PARAM, "base conversion from 1..64 primes");
+  static_assert(SS_BCONV_V == 2, "both base-conversion kernels cover 2 * 256 coefficients per block");
+  if (pre_w1 && (C.m_odd != 1 || (C.N / 2) % (SS_BCONV_V * TPB) != 0))
+    throw Error(SS_ERR_PARAM, "node-1 twiddle folding needs the ring X^N + 1 and N >= 1024");
   if (skip_hi <= skip_lo) skip_lo = skip_hi = nd;
+  const int pre = pre_w1 ? 1 : 0;
   size_t smem = (size_t)nd * (2 + ns) * 8;
   if (smem > 48 * 1024) throw Error(SS_ERR_PARAM, "base conversion tables exceed 48 KiB of shared memory");
   int kr_ = kt_begin(C, st);
 #define SS_BCONV(NSV, VV)                                                                                        \
   k_bconv_impl<NSV, VV><<<dim3((g.x + VV - 1) / VV, g.y), TPB, smem, st>>>(                                       \
-      src, src_os, ns, sp0, nsq, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo, skip_hi, post, C.N, C.d_mod)
+      src, src_os, ns, sp0, nsq, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo, skip_hi, post, C.N, C.d_mod,     \
+      C.d_r64, pre)
   switch (ns) {
     case 1: SS_BCONV(1, SS_BCONV_V); break;
     case 2: SS_BCONV(2, SS_BCONV_V); break;
@@ -1111,7 +1219,8 @@ void k_bconv(Context& C, const u64* src, long src_os, int ns, int sp0, const u64
     case 4: SS_BCONV(4, SS_BCONV_V); break;
     default:
       k_bconv_many_impl<4, 2><<<dim3((g.x + 1) / 2, g.y), TPB, smem, st>>>(
-          src, src_os, ns, sp0, nsq, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo, skip_hi, post, C.N, C.d_mod);
+          src, src_os, ns, sp0, nsq, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo, skip_hi, post, C.N, C.d_mod,
+          C.d_r64, pre);
       break;
   }
 #undef SS_BCONV
@@ -1168,11 +1277,27 @@ static void ks_launch(Context& C, const KsJob& J, int nlimbs, double bytes, cuda
   }
   constexpr int OB = SS_KSIP_OB;
   const dim3 grid((unsigned)J.gx, (unsigned)nlimbs);
+#if SS_KSIP_STAGES > 0
+  static_assert(SS_KSIP_V == 2, "the cp.async inner product copies two coefficients per thread");
+  constexpr size_t ring = (size_t)SS_KSIP_STAGES * (2 + OB) * TPB * 16;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    SS_CUDA(cudaFuncSetAttribute(k_ks_ip_async<OB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring));
+    SS_CUDA(cudaFuncSetAttribute(k_ks_ip_async<OB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring));
+    SS_CUDA(cudaFuncSetAttribute(k_ks_ip_async<OB, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring));
+  });
+  switch (J.type) {
+    case 0: TIMED(KC_KSIP, bytes, (k_ks_ip_async<OB, 0><<<grid, TPB, ring, st>>>(J))); break;
+    case 1: TIMED(KC_KSIP, bytes, (k_ks_ip_async<OB, 1><<<grid, TPB, ring, st>>>(J))); break;
+    default: TIMED(KC_KSIP, bytes, (k_ks_ip_async<OB, 2><<<grid, TPB, ring, st>>>(J))); break;
+  }
+#else
   switch (J.type) {
     case 0: TIMED(KC_KSIP, bytes, (k_ks_ip_impl<OB, 0><<<grid, TPB, 0, st>>>(J))); break;
     case 1: TIMED(KC_KSIP, bytes, (k_ks_ip_impl<OB, 1><<<grid, TPB, 0, st>>>(J))); break;
     default: TIMED(KC_KSIP, bytes, (k_ks_ip_impl<OB, 2><<<grid, TPB, 0, st>>>(J))); break;
   }
+#endif
   LAUNCHED();
 }
 

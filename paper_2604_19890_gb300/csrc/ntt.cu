@@ -48,6 +48,7 @@ struct NttArgs {
   const u64* split;  // m = 5N/2: per prime 12 (value, shoup) pairs of the four-way split (split4_fwd/inv)
   const u64* src;    // out-of-place first phase: polynomial (o, i) is read at src + o src_os + i N
   long src_os;
+  int pre_w1;        // forward, X^N + 1: upper halves already carry psi^(N/2) (PolySet::pre_w1)
 };
 
 // Blocks walk the polynomials limb-major (all outer copies of limb 0, then of
@@ -141,7 +142,7 @@ __device__ __forceinline__ void split4_inv(u64& b0, u64& b1, u64& b2, u64& b3, c
 // (U + V - t, 2t), both scaled by N^-1 with the rest afterwards.
 template <bool FWD, int JLO, int JHI, int RING>
 __device__ __forceinline__ void ntt_round(u64 (&x)[8], int rbase, int logu, int logS, int mg,
-                                          const ulonglong2* __restrict__ tw, u64 q) {
+                                          const ulonglong2* __restrict__ tw, u64 q, bool pre1) {
   const u64 q2 = 2 * q;
 #pragma unroll
   for (int jj = JLO; jj <= JHI; ++jj) {
@@ -175,7 +176,7 @@ __device__ __forceinline__ void ntt_round(u64 (&x)[8], int rbase, int logu, int 
           }
         } else if (FWD) {
           if (U >= q2) U -= q2;
-          V = shoup_lazy(V, w, wp, q);
+          if (!(pre1 && widx == 1)) V = shoup_lazy(V, w, wp, q);  // pre1: node 1's product already applied
           x[k] = U + V;
           x[k + d] = U - V + q2;
         } else {
@@ -191,14 +192,14 @@ __device__ __forceinline__ void ntt_round(u64 (&x)[8], int rbase, int logu, int 
 
 template <bool FWD, int RING>
 __device__ __forceinline__ void ntt_round_dispatch(int jlo, int jhi, u64 (&x)[8], int rbase, int logu, int logS, int mg,
-                                                   const ulonglong2* tw, u64 q) {
+                                                   const ulonglong2* tw, u64 q, bool pre1) {
   switch (jlo * 3 + jhi) {
-    case 0: ntt_round<FWD, 0, 0, RING>(x, rbase, logu, logS, mg, tw, q); break;
-    case 1: ntt_round<FWD, 0, 1, RING>(x, rbase, logu, logS, mg, tw, q); break;
-    case 2: ntt_round<FWD, 0, 2, RING>(x, rbase, logu, logS, mg, tw, q); break;
-    case 4: ntt_round<FWD, 1, 1, RING>(x, rbase, logu, logS, mg, tw, q); break;
-    case 5: ntt_round<FWD, 1, 2, RING>(x, rbase, logu, logS, mg, tw, q); break;
-    default: ntt_round<FWD, 2, 2, RING>(x, rbase, logu, logS, mg, tw, q); break;
+    case 0: ntt_round<FWD, 0, 0, RING>(x, rbase, logu, logS, mg, tw, q, pre1); break;
+    case 1: ntt_round<FWD, 0, 1, RING>(x, rbase, logu, logS, mg, tw, q, pre1); break;
+    case 2: ntt_round<FWD, 0, 2, RING>(x, rbase, logu, logS, mg, tw, q, pre1); break;
+    case 4: ntt_round<FWD, 1, 1, RING>(x, rbase, logu, logS, mg, tw, q, pre1); break;
+    case 5: ntt_round<FWD, 1, 2, RING>(x, rbase, logu, logS, mg, tw, q, pre1); break;
+    default: ntt_round<FWD, 2, 2, RING>(x, rbase, logu, logS, mg, tw, q, pre1); break;
   }
 }
 
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, in
       int r = rbase + (k << logu);
       x[k] = sm[swz(COLS ? (r << logCPB) + c : (c << logS) + r)];
     }
-    ntt_round_dispatch<FWD, RING>(a - logu, b - logu, x, rbase, logu, logS, mg, tw, q);
+    ntt_round_dispatch<FWD, RING>(a - logu, b - logu, x, rbase, logu, logS, mg, tw, q, RING == 1 && A.pre_w1);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       int r = rbase + (k << logu);
@@ -438,6 +439,9 @@ __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0,
         // applies N^-1: sums times N^-1, differences times N^-1 psi^(-N/2)
         const bool fold = LAST && !FWD && rho == NR - 1 && jj == ns - 1;
         const bool split = RING == 3 && COLS && FWD && rho == 0 && jj == 0;
+        // node 1 of X^N + 1 (the column phase's first forward stage) on inputs
+        // whose upper half already carries its twiddle: no product
+        const bool pre1 = RING == 1 && COLS && FWD && rho == 0 && jj == 0 && A.pre_w1;
         // m = 5N/2: the first two forward stages and the last two inverse
         // stages of the column phase are the four-way split on the registers
         // k, k+4, k+8, k+12 (the quarters), k < 4
@@ -465,7 +469,7 @@ __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0,
             if (PRE && rho == 0 && jj == 0) {
               w = pre[PRE ? blk : 0].x;
               wp = pre[PRE ? blk : 0].y;
-            } else if (!fold) {
+            } else if (!fold && !pre1) {
               const int widx = (mg << sg) + ((rbase + (k0 << logu)) >> (logt + 1));
               const ulonglong2 wv = __ldg(tw + widx);
               w = wv.x;
@@ -488,6 +492,9 @@ __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0,
                   const u64 t = shoup_lazy(V, w, wp, q);
                   x[k] = U + t;
                   x[k + d] = U + V + q2 - t;
+                } else if (pre1) {  // U, V < q
+                  x[k] = U + V;
+                  x[k + d] = U - V + q2;
                 } else if (FWD) {
                   V = shoup_lazy(V, w, wp, q);
                   x[k] = U + V;
@@ -632,7 +639,18 @@ NttArgs make_args(Context& C, const PolySet& s) {
   A.split = C.d_split;
   A.src = nullptr;
   A.src_os = 0;
+  if (s.pre_w1 && C.m_odd != 1) throw Error(SS_ERR_PARAM, "node-1 twiddle folding is for the ring X^N + 1");
+  A.pre_w1 = s.pre_w1 ? 1 : 0;
   return A;
+}
+
+double active_polys(const PolySet& s);
+
+// Shoup products of one transform of the set: N/2 per stage and polynomial,
+// less node 1's when folded (pre_w1), plus the inverse's N^-1 on the sums
+double ntt_products(const Context& C, const PolySet& s, bool fwd) {
+  const double half = C.N / 2.0;
+  return active_polys(s) * half * (C.logN + (fwd ? (s.pre_w1 ? -1 : 0) : 1));
 }
 
 // polynomials a transform actually touches (ModUp outputs skip the digit's own limbs)
@@ -689,6 +707,7 @@ static void launch(Context& C, const PolySet& s, bool fwd, cudaStream_t st, cons
       else k_ntt<false, false, true><<<g, thr, smem(N), st>>>(A, logN, 0, 1);
     }
     ++C.launches;
+    if (kr >= 0) C.kt.ntt_products += ntt_products(C, s, fwd);
     kt_end(C, kr, KC_NTT, 16.0 * N * active_polys(s), st);
   } else {
     int kr = kt_begin(C, st);
@@ -716,6 +735,7 @@ static void launch(Context& C, const PolySet& s, bool fwd, cudaStream_t st, cons
       else launch16<false, true, true>(log1, g1, thr, smem(tile), st, A, logc1, 1);
     }
     C.launches += 2;
+    if (kr >= 0) C.kt.ntt_products += ntt_products(C, s, fwd);
     kt_end(C, kr, KC_NTT, 16.0 * N * active_polys(s), st);
   }
   SS_CUDA(cudaGetLastError());
@@ -751,7 +771,7 @@ void ntt_multi(const std::vector<NttReq>& reqs, bool fwd, int tile_log, cudaStre
     NttMulti P1, P2;
     P1.njobs = P2.njobs = 0;
     P1.total = P2.total = 0;
-    double bytes = 0;
+    double bytes = 0, prods = 0;
     for (size_t r = b0; r < b1; ++r) {
       const NttReq& q = reqs[r];
       Context& C = *q.C;
@@ -775,6 +795,7 @@ void ntt_multi(const std::vector<NttReq>& reqs, bool fwd, int tile_log, cudaStre
       P1.total += npoly * j1.tiles;
       P2.total += npoly * j2.tiles;
       bytes += 16.0 * C.N * active_polys(q.s);
+      prods += ntt_products(C, q.s, fwd);
     }
     if (P1.njobs == 0) continue;
     Context& C0 = *reqs[b0].C;
@@ -787,6 +808,7 @@ void ntt_multi(const std::vector<NttReq>& reqs, bool fwd, int tile_log, cudaStre
       launch_multi<false, true, true, false>(P2, thr, smem, st);
     }
     C0.launches += 2;
+    if (kr >= 0) C0.kt.ntt_products += prods;
     kt_end(C0, kr, KC_NTT, bytes, st);
   }
 }

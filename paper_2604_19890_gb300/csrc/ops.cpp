@@ -69,6 +69,15 @@ BufP slice_buf(const BufP& a, int b0, int count, int N) {
 }
 
 // ------------------------------------------------------------------ key switching
+// On X^N + 1 a base conversion whose output is transformed forward next (the
+// ModUp digits, the ModDown and modulus-switch corrections) multiplies the
+// upper half of every output limb by the forward transform's node-1 twiddle
+// psi^(N/2), so the transform's first stage needs no product (one Shoup
+// product per word pair of the first stage saved; the words are unchanged).
+// Other rings split node 1; below N = 1024 a base-conversion block would
+// straddle the two halves.
+static bool bconv_folds_w1(const Context& C) { return C.m_odd == 1 && C.N >= 1024; }
+
 // out.comp0 = addend.comp0 + KS(in.comp)[0]; out.comp1 = (addend ? addend.comp1 : 0) + KS[1]
 // addend_comp1 selects whether the addend's component 1 is added too.
 static void keyswitch_impl(Context& C, const Buf& in, int comp, const KeyDev& K, const Buf* addend, bool add_c1,
@@ -81,20 +90,23 @@ static void keyswitch_impl(Context& C, const Buf& in, int comp, const KeyDev& K,
   u64* dc = static_cast<u64*>(pool_alloc((size_t)B * l * N * 8, st));
   ntt_inverse_from(C, PolySet{dc, (long)l * N, B, l, 0, l}, d, in_os, st);
   // 2. ModUp of every digit to the other data primes and the special primes
+  //    (X^N + 1: the base conversion also applies the transform's first twiddle)
   const long ext_os = (long)dn * nx * N;
   u64* ext = static_cast<u64*>(pool_alloc((size_t)B * ext_os * 8, st));
+  const bool pre = bconv_folds_w1(C);
   for (int j = 0; j < dn; ++j) {
     int lo = j * a, hi = std::min(lo + a, l);
     size_t off = C.off_modup.at({j, hi});
     const u64* c1 = C.d_tables + off;
     const u64* c2 = c1 + 2 * (hi - lo);
     k_bconv(C, dc + (size_t)lo * N, (long)l * N, hi - lo, lo, c1, c2, ext + (size_t)j * nx * N, ext_os, nx, l, lo,
-            hi, nullptr, B, st);
+            hi, nullptr, B, st, -1, pre);
   }
   PolySet ps{ext, (long)nx * N, B * dn, nx, 0, l};
   ps.skip_w = a;
   ps.skip_mod = dn;
   ps.skip_level = l;
+  ps.pre_w1 = pre;
   ntt_forward(C, ps, st);
   pool_free(dc, st);
   // 3. inner product with the key on the special primes (both components)
@@ -107,8 +119,10 @@ static void keyswitch_impl(Context& C, const Buf& in, int comp, const KeyDev& K,
   const u64* c1 = C.d_tables + C.off_md_c1[in.t_exp];
   const u64* c2 = C.d_tables + C.off_md_c2;
   const u64* post = C.d_tmod + (size_t)in.t_exp * C.ntot * 2;
-  k_bconv(C, acc, (long)a * N, a, C.L, c1, c2, delta, (long)l * N, l, l, 0, 0, post, 2 * B, st);
-  ntt_forward(C, PolySet{delta, (long)l * N, 2 * B, l, 0, l}, st);
+  k_bconv(C, acc, (long)a * N, a, C.L, c1, c2, delta, (long)l * N, l, l, 0, 0, post, 2 * B, st, -1, pre);
+  PolySet pd{delta, (long)l * N, 2 * B, l, 0, l};
+  pd.pre_w1 = pre;
+  ntt_forward(C, pd, st);
   pool_free(acc, st);
   // 5. inner product on the data primes fused with out = (acc - delta) P^-1 (+ addend)
   const u64* pinv = C.d_tables + C.off_md_pinv;
@@ -152,17 +166,19 @@ void op_relin_drop(Context& C, const Buf& in, Buf& out, cudaStream_t st) {
   ntt_inverse_from(C, PolySet{dc, (long)l * N, B, l, 0, l}, d, in_os, st);
   const long ext_os = (long)dn * nx * N;
   u64* ext = static_cast<u64*>(pool_alloc((size_t)B * ext_os * 8, st));
+  const bool pre = bconv_folds_w1(C);
   for (int j = 0; j < dn; ++j) {
     int lo = j * a, hi = std::min(lo + a, l);
     const u64* c1 = C.d_tables + C.off_modup.at({j, hi});
     const u64* c2 = c1 + 2 * (hi - lo);
     k_bconv(C, dc + (size_t)lo * N, (long)l * N, hi - lo, lo, c1, c2, ext + (size_t)j * nx * N, ext_os, nx, l, lo,
-            hi, nullptr, B, st);
+            hi, nullptr, B, st, -1, pre);
   }
   PolySet ps{ext, (long)nx * N, B * dn, nx, 0, l};
   ps.skip_w = a;
   ps.skip_mod = dn;
   ps.skip_level = l;
+  ps.pre_w1 = pre;
   ntt_forward(C, ps, st);
   pool_free(dc, st);
   // 3. inner product on q_{l-1} and the special primes (the limbs the ModDown drops)
@@ -179,8 +195,10 @@ void op_relin_drop(Context& C, const Buf& in, Buf& out, cudaStream_t st) {
   const u64* inv = c2 + (size_t)(a + 1) * C.ntot;
   const u64* c1 = C.d_tables + C.off_rd_c1.at({l, in.t_exp});
   const u64* post = C.d_tmod + (size_t)in.t_exp * C.ntot * 2;
-  k_bconv(C, acc, (long)ns * N, ns, l - 1, c1, c2, delta, (long)nl * N, nl, nl, 0, 0, post, 2 * B, st, 1);
-  ntt_forward(C, PolySet{delta, (long)nl * N, 2 * B, nl, 0, nl}, st);
+  k_bconv(C, acc, (long)ns * N, ns, l - 1, c1, c2, delta, (long)nl * N, nl, nl, 0, 0, post, 2 * B, st, 1, pre);
+  PolySet pd{delta, (long)nl * N, 2 * B, nl, 0, nl};
+  pd.pre_w1 = pre;
+  ntt_forward(C, pd, st);
   pool_free(acc, st);
   // 5. inner product on the kept primes fused with the combine
   //    out_c = ((P d_c + acc_c) - delta_c) (q_{l-1} P)^-1
@@ -206,8 +224,11 @@ void op_modswitch(Context& C, const Buf& a, int k, Buf& out, cudaStream_t st) {
   const u64* qinv = c2 + (size_t)k * C.ntot;
   const u64* c1 = C.d_tables + C.off_ms_c1.at(std::make_tuple(l, k, a.t_exp));
   const u64* post = C.d_tmod + (size_t)a.t_exp * C.ntot * 2;
-  k_bconv(C, x, (long)k * N, k, nl, c1, c2, delta, (long)nl * N, nl, nl, 0, 0, post, B * nc, st);
-  ntt_forward(C, PolySet{delta, (long)nl * N, B * nc, nl, 0, nl}, st);
+  const bool pre = bconv_folds_w1(C);
+  k_bconv(C, x, (long)k * N, k, nl, c1, c2, delta, (long)nl * N, nl, nl, 0, 0, post, B * nc, st, -1, pre);
+  PolySet pd{delta, (long)nl * N, B * nc, nl, 0, nl};
+  pd.pre_w1 = pre;
+  ntt_forward(C, pd, st);
   k_sub_scale(C, a.data, (long)a.cap * N, delta, (long)nl * N, qinv, nullptr, 0, out.data, (long)out.cap * N, nl,
               B * nc, st);
   pool_free(x, st);
