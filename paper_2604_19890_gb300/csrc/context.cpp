@@ -645,11 +645,11 @@ void build_context(Context& C, const ss_params& prm) {
   // twiddles: psi^brv(i) and psi^-brv(i) with Shoup companions (m = 2N; m = 3N below)
   {
     std::vector<u64> tw((size_t)T * 4 * N);
-    std::vector<u64> ninv(4 * T), pinv(2 * T), r64(2 * T, 0);
+    std::vector<u64> ninv(4 * T), pinv(2 * T), r64(4 * T, 0);
     std::vector<u64> split(C.m_odd == 5 ? (size_t)T * 24 : 0);
     for (int i = 0; i < T; ++i) {
       u64 q = C.primes[i], ps = C.psi[i], pi = nt::inv(ps, q);
-      r64[2 * i] = (UINT64_MAX % q + 1) % q;  // 2^64 mod q
+      r64[4 * i] = (UINT64_MAX % q + 1) % q;  // 2^64 mod q
       u64* o = &tw[(size_t)i * 4 * N];
       auto put = [&](int k, u64 f, u64 bk) {
         o[2 * k] = f;
@@ -728,7 +728,10 @@ void build_context(Context& C, const ss_params& prm) {
           put(k, fw[rk], bw[rk]);
         }
         // 2^64 times the forward node-1 twiddle psi^bitrev(1) = psi^(N/2)
-        r64[2 * i + 1] = nt::mul(r64[2 * i], fw[N / 2], q);
+        r64[4 * i + 1] = nt::mul(r64[4 * i], fw[N / 2], q);
+        // 2^64 N^-1 and 2^64 N^-1 psi^(-N/2): the inverse's last-stage factors of the lower and upper half
+        r64[4 * i + 2] = nt::mul(r64[4 * i], ni, q);
+        r64[4 * i + 3] = nt::mul(r64[4 * i + 2], bw[N / 2], q);
         // N^-1 times the last inverse stage's twiddle psi^-bitrev(1) = psi^(-N/2)
         const u64 wni = nt::mul(ni, bw[N / 2], q);
         ninv[4 * i + 2] = wni;

@@ -208,23 +208,35 @@ __global__ void k_tensor_impl(const u64* a, const u64* b, u64* out, int N, int l
 // half (the host checks that they divide N/2), so a block of the upper half
 // stages c2'[s] w_1 2^64 instead (the factor 2^64 w_1 mod q comes from the
 // per-prime table r64 beside 2^64 mod q; no product per output).
+// dscale (sources from an inverse transform with PolySet::post_scale): the
+// source words still lack N^-1 (lower half) or N^-1 psi^(-N/2) (upper half),
+// and may be up to 4q; the first step then uses c1_s times that factor in
+// Montgomery form (staged per block after the targets' rows) and a Montgomery
+// reduction in place of the Shoup product, which accepts any 64-bit word.
 template <int NS, int V>
 __global__ void __launch_bounds__(256) k_bconv_impl(const u64* __restrict__ src, long src_os, int ns, int sp0, int nsq,
                                                     const u64* __restrict__ c1, const u64* __restrict__ c2, int T,
                                                     u64* __restrict__ dst, long dst_os, int nd, int nq, int L,
                                                     int skip_lo, int skip_hi, const u64* __restrict__ post, int N,
-                                                    const ModDesc* mods, const u64* __restrict__ r64, int pre) {
+                                                    const ModDesc* mods, const u64* __restrict__ r64, int pre,
+                                                    int dscale) {
   extern __shared__ u64 sh[];
   const int ns_ = NS > 0 ? NS : ns;
   const int W = 2 + ns_;
-  const int upper = pre && 2 * V * blockIdx.x * blockDim.x >= N ? 1 : 0;  // block-uniform
+  const int half = 2 * V * blockIdx.x * blockDim.x >= N ? 1 : 0;  // block-uniform
+  const int upper = pre ? half : 0;
+  if (dscale)
+    for (int s = threadIdx.x; s < ns_; s += blockDim.x) {
+      const int gs = s < nsq ? sp0 + s : L + (s - nsq);
+      sh[nd * W + s] = mul_mod(__ldg(c1 + 2 * s), __ldg(r64 + 4 * gs + 2 + half), MOD(mods, gs));
+    }
   for (int m = threadIdx.x; m < nd; m += blockDim.x) {
     const int g = m < nq ? m : L + (m - nq);
     const Modulus& md = MOD(mods, g);
     u64* e = sh + m * W;
     e[0] = md.q;
     e[1] = md.qinv;
-    const u64 R = __ldg(r64 + 2 * g + upper);  // 2^64 (times w_1) mod q
+    const u64 R = __ldg(r64 + 4 * g + upper);  // 2^64 (times w_1) mod q
     for (int s = 0; s < ns_; ++s) {
       u64 v = c2[(long)s * T + g];
       if (post) v = shoup(v, post[2 * g], post[2 * g + 1], md.q);
@@ -241,11 +253,17 @@ __global__ void __launch_bounds__(256) k_bconv_impl(const u64* __restrict__ src,
   for (int s = 0; s < MAXS; ++s) {
     if (s < ns_) {
       const int gs = s < nsq ? sp0 + s : L + (s - nsq);
-      const u64 qs = MOD(mods, gs).q;
+      const Modulus& ms = MOD(mods, gs);
       u64 v[V];
       ldv<V>(src + o * src_os + (long)s * N + n, v);
+      if (dscale) {
+        const u64 cm = sh[nd * W + s];
 #pragma unroll
-      for (int i = 0; i < V; ++i) y[i][s] = shoup(v[i], c1[2 * s], c1[2 * s + 1], qs);
+        for (int i = 0; i < V; ++i) y[i][s] = redc128(mulhi64(v[i], cm), v[i] * cm, ms.q, ms.qinv);
+      } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) y[i][s] = shoup(v[i], c1[2 * s], c1[2 * s + 1], ms.q);
+      }
     }
   }
   u64* out = dst + o * dst_os + n;
@@ -278,24 +296,31 @@ __global__ void __launch_bounds__(256) k_bconv_impl(const u64* __restrict__ src,
 // k_bconv_impl, but the sources stream through registers once per chunk of TC
 // targets, so a thread holds TC x V 128-bit sums instead of every source word.
 // The sums are exact, so the outputs are the same words in any order. pre: the
-// node-1 twiddle folded into the upper half, as in k_bconv_impl.
+// node-1 twiddle folded into the upper half, dscale: the inverse's deferred last
+// stage folded into the source constants, as in k_bconv_impl.
 template <int TC, int V>
 __global__ void __launch_bounds__(256) k_bconv_many_impl(const u64* __restrict__ src, long src_os, int ns, int sp0,
                                                          int nsq, const u64* __restrict__ c1,
                                                          const u64* __restrict__ c2, int T, u64* __restrict__ dst,
                                                          long dst_os, int nd, int nq, int L, int skip_lo, int skip_hi,
                                                          const u64* __restrict__ post, int N, const ModDesc* mods,
-                                                         const u64* __restrict__ r64, int pre) {
+                                                         const u64* __restrict__ r64, int pre, int dscale) {
   extern __shared__ u64 sh[];
   const int W = 2 + ns;
-  const int upper = pre && 2 * V * blockIdx.x * blockDim.x >= N ? 1 : 0;  // block-uniform
+  const int half = 2 * V * blockIdx.x * blockDim.x >= N ? 1 : 0;  // block-uniform
+  const int upper = pre ? half : 0;
+  if (dscale)
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+      const int gs = s < nsq ? sp0 + s : L + (s - nsq);
+      sh[nd * W + s] = mul_mod(__ldg(c1 + 2 * s), __ldg(r64 + 4 * gs + 2 + half), MOD(mods, gs));
+    }
   for (int m = threadIdx.x; m < nd; m += blockDim.x) {
     const int g = m < nq ? m : L + (m - nq);
     const Modulus& md = MOD(mods, g);
     u64* e = sh + m * W;
     e[0] = md.q;
     e[1] = md.qinv;
-    const u64 R = __ldg(r64 + 2 * g + upper);  // 2^64 (times w_1) mod q
+    const u64 R = __ldg(r64 + 4 * g + upper);  // 2^64 (times w_1) mod q
     for (int s = 0; s < ns; ++s) {
       u64 v = c2[(long)s * T + g];
       if (post) v = shoup(v, post[2 * g], post[2 * g + 1], md.q);
@@ -324,12 +349,18 @@ __global__ void __launch_bounds__(256) k_bconv_many_impl(const u64* __restrict__
       for (int i = 0; i < V; ++i) acc[c][i].zero();
     for (int s = 0; s < ns; ++s) {
       const int gs = s < nsq ? sp0 + s : L + (s - nsq);
-      const u64 qs = MOD(mods, gs).q;
-      const u64 w = __ldg(c1 + 2 * s), wp = __ldg(c1 + 2 * s + 1);
+      const Modulus& ms = MOD(mods, gs);
       u64 v[V];
       ldv<V>(sp + (long)s * N, v);
+      if (dscale) {
+        const u64 cm = sh[nd * W + s];
 #pragma unroll
-      for (int i = 0; i < V; ++i) v[i] = shoup(v[i], w, wp, qs);
+        for (int i = 0; i < V; ++i) v[i] = redc128(mulhi64(v[i], cm), v[i] * cm, ms.q, ms.qinv);
+      } else {
+        const u64 w = __ldg(c1 + 2 * s), wp = __ldg(c1 + 2 * s + 1);
+#pragma unroll
+        for (int i = 0; i < V; ++i) v[i] = shoup(v[i], w, wp, ms.q);
+      }
 #pragma unroll
       for (int c = 0; c < TC; ++c) {
         const u64 cs = sh[tm[c] * W + 2 + s];
@@ -1196,22 +1227,22 @@ void k_tensor(Context& C, const Buf& a, const Buf& b, Buf& out, cudaStream_t st)
 
 void k_bconv(Context& C, const u64* src, long src_os, int ns, int sp0, const u64* c1, const u64* c2, u64* dst,
              long dst_os, int nd, int nq, int skip_lo, int skip_hi, const u64* post, int n_outer, cudaStream_t st,
-             int nsq, bool pre_w1) {
+             int nsq, bool pre_w1, bool post_scale) {
   if (nsq < 0) nsq = ns;  // every source is the data or special prime sp0 + s
   dim3 g = grid_for(C.N, n_outer);
   if (ns < 1 || ns > 64) throw Error(SS_ERR_PARAM, "base conversion from 1..64 primes");
   static_assert(SS_BCONV_V == 2, "both base-conversion kernels cover 2 * 256 coefficients per block");
-  if (pre_w1 && (C.m_odd != 1 || (C.N / 2) % (SS_BCONV_V * TPB) != 0))
-    throw Error(SS_ERR_PARAM, "node-1 twiddle folding needs the ring X^N + 1 and N >= 1024");
+  if ((pre_w1 || post_scale) && (C.m_odd != 1 || (C.N / 2) % (SS_BCONV_V * TPB) != 0))
+    throw Error(SS_ERR_PARAM, "twiddle folding needs the ring X^N + 1 and N >= 1024");
   if (skip_hi <= skip_lo) skip_lo = skip_hi = nd;
-  const int pre = pre_w1 ? 1 : 0;
-  size_t smem = (size_t)nd * (2 + ns) * 8;
+  const int pre = pre_w1 ? 1 : 0, dscale = post_scale ? 1 : 0;
+  size_t smem = (size_t)(nd * (2 + ns) + dscale * ns) * 8;
   if (smem > 48 * 1024) throw Error(SS_ERR_PARAM, "base conversion tables exceed 48 KiB of shared memory");
   int kr_ = kt_begin(C, st);
 #define SS_BCONV(NSV, VV)                                                                                        \
   k_bconv_impl<NSV, VV><<<dim3((g.x + VV - 1) / VV, g.y), TPB, smem, st>>>(                                       \
       src, src_os, ns, sp0, nsq, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo, skip_hi, post, C.N, C.d_mod,     \
-      C.d_r64, pre)
+      C.d_r64, pre, dscale)
   switch (ns) {
     case 1: SS_BCONV(1, SS_BCONV_V); break;
     case 2: SS_BCONV(2, SS_BCONV_V); break;
@@ -1220,7 +1251,7 @@ void k_bconv(Context& C, const u64* src, long src_os, int ns, int sp0, const u64
     default:
       k_bconv_many_impl<4, 2><<<dim3((g.x + 1) / 2, g.y), TPB, smem, st>>>(
           src, src_os, ns, sp0, nsq, c1, c2, C.ntot, dst, dst_os, nd, nq, C.L, skip_lo, skip_hi, post, C.N, C.d_mod,
-          C.d_r64, pre);
+          C.d_r64, pre, dscale);
       break;
   }
 #undef SS_BCONV

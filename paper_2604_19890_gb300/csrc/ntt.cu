@@ -49,6 +49,7 @@ struct NttArgs {
   const u64* src;    // out-of-place first phase: polynomial (o, i) is read at src + o src_os + i N
   long src_os;
   int pre_w1;        // forward, X^N + 1: upper halves already carry psi^(N/2) (PolySet::pre_w1)
+  int post_scale;    // inverse, X^N + 1: last stage without its products (PolySet::post_scale)
 };
 
 // Blocks walk the polynomials limb-major (all outer copies of limb 0, then of
@@ -485,6 +486,9 @@ __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0,
                   const u64 lo = shoup(U + V, ni, nip, q), cr = shoup(dv, cni, cnip, q);
                   x[k] = lo >= cr ? lo - cr : lo + q - cr;
                   x[k + d] = shoup(dv, w, wp, q);
+                } else if (fold && A.post_scale) {  // N^-1 and N^-1 psi^(-N/2) left to the consumer
+                  x[k] = U + V;
+                  x[k + d] = U - V + q2;
                 } else if (fold) {
                   x[k] = shoup(U + V, ni, nip, q);
                   x[k + d] = shoup(U - V + q2, w, wp, q);
@@ -640,7 +644,10 @@ NttArgs make_args(Context& C, const PolySet& s) {
   A.src = nullptr;
   A.src_os = 0;
   if (s.pre_w1 && C.m_odd != 1) throw Error(SS_ERR_PARAM, "node-1 twiddle folding is for the ring X^N + 1");
+  if (s.post_scale && (C.m_odd != 1 || C.N <= TILE))
+    throw Error(SS_ERR_PARAM, "deferred inverse scaling is for two-phase transforms on the ring X^N + 1");
   A.pre_w1 = s.pre_w1 ? 1 : 0;
+  A.post_scale = s.post_scale ? 1 : 0;
   return A;
 }
 
@@ -648,9 +655,10 @@ double active_polys(const PolySet& s);
 
 // Shoup products of one transform of the set: N/2 per stage and polynomial,
 // less node 1's when folded (pre_w1), plus the inverse's N^-1 on the sums
+// unless its last stage is deferred (post_scale: no products there)
 double ntt_products(const Context& C, const PolySet& s, bool fwd) {
   const double half = C.N / 2.0;
-  return active_polys(s) * half * (C.logN + (fwd ? (s.pre_w1 ? -1 : 0) : 1));
+  return active_polys(s) * half * (C.logN + (fwd ? (s.pre_w1 ? -1 : 0) : (s.post_scale ? -1 : 1)));
 }
 
 // polynomials a transform actually touches (ModUp outputs skip the digit's own limbs)

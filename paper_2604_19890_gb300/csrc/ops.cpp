@@ -77,6 +77,16 @@ BufP slice_buf(const BufP& a, int b0, int count, int N) {
 // Other rings split node 1; below N = 1024 a base-conversion block would
 // straddle the two halves.
 static bool bconv_folds_w1(const Context& C) { return C.m_odd == 1 && C.N >= 1024; }
+// Likewise an inverse transform whose output only feeds a base conversion (the
+// ModUp digit source, the ModDown and modulus-switch dropped limbs) leaves its
+// last stage's N^-1 and N^-1 psi^(-N/2) to the base conversion's per-source
+// constants (PolySet::post_scale): that stage runs without products. Two-phase
+// transforms only (N > 4096).
+static bool bconv_folds_inverse(const Context& C) { return bconv_folds_w1(C) && C.N > 4096; }
+static PolySet scaled_later(PolySet s, bool post) {
+  s.post_scale = post;
+  return s;
+}
 
 // out.comp0 = addend.comp0 + KS(in.comp)[0]; out.comp1 = (addend ? addend.comp1 : 0) + KS[1]
 // addend_comp1 selects whether the addend's component 1 is added too.
@@ -88,7 +98,8 @@ static void keyswitch_impl(Context& C, const Buf& in, int comp, const KeyDev& K,
   const u64* d = in.data + (size_t)comp * in.cap * N;
   // 1. coefficient form of the digit source (read in place, written to dc)
   u64* dc = static_cast<u64*>(pool_alloc((size_t)B * l * N * 8, st));
-  ntt_inverse_from(C, PolySet{dc, (long)l * N, B, l, 0, l}, d, in_os, st);
+  const bool post = bconv_folds_inverse(C);
+  ntt_inverse_from(C, scaled_later(PolySet{dc, (long)l * N, B, l, 0, l}, post), d, in_os, st);
   // 2. ModUp of every digit to the other data primes and the special primes
   //    (X^N + 1: the base conversion also applies the transform's first twiddle)
   const long ext_os = (long)dn * nx * N;
@@ -100,7 +111,7 @@ static void keyswitch_impl(Context& C, const Buf& in, int comp, const KeyDev& K,
     const u64* c1 = C.d_tables + off;
     const u64* c2 = c1 + 2 * (hi - lo);
     k_bconv(C, dc + (size_t)lo * N, (long)l * N, hi - lo, lo, c1, c2, ext + (size_t)j * nx * N, ext_os, nx, l, lo,
-            hi, nullptr, B, st, -1, pre);
+            hi, nullptr, B, st, -1, pre, post);
   }
   PolySet ps{ext, (long)nx * N, B * dn, nx, 0, l};
   ps.skip_w = a;
@@ -114,12 +125,12 @@ static void keyswitch_impl(Context& C, const Buf& in, int comp, const KeyDev& K,
   u64* acc = static_cast<u64*>(pool_alloc((size_t)B * sp_os * 8, st));
   k_ks_ip(C, d, in_os, ext, ext_os, K, l, acc, sp_os, B, st, l, a);
   // 4. ModDown: delta = t * conv_P->Q(t^-1 acc mod P) on the data primes
-  ntt_inverse(C, PolySet{acc, (long)a * N, 2 * B, a, C.L, 0}, st);
+  ntt_inverse(C, scaled_later(PolySet{acc, (long)a * N, 2 * B, a, C.L, 0}, post), st);
   u64* delta = static_cast<u64*>(pool_alloc((size_t)2 * B * l * N * 8, st));
   const u64* c1 = C.d_tables + C.off_md_c1[in.t_exp];
   const u64* c2 = C.d_tables + C.off_md_c2;
-  const u64* post = C.d_tmod + (size_t)in.t_exp * C.ntot * 2;
-  k_bconv(C, acc, (long)a * N, a, C.L, c1, c2, delta, (long)l * N, l, l, 0, 0, post, 2 * B, st, -1, pre);
+  const u64* tpost = C.d_tmod + (size_t)in.t_exp * C.ntot * 2;
+  k_bconv(C, acc, (long)a * N, a, C.L, c1, c2, delta, (long)l * N, l, l, 0, 0, tpost, 2 * B, st, -1, pre, post);
   PolySet pd{delta, (long)l * N, 2 * B, l, 0, l};
   pd.pre_w1 = pre;
   ntt_forward(C, pd, st);
@@ -163,7 +174,8 @@ void op_relin_drop(Context& C, const Buf& in, Buf& out, cudaStream_t st) {
   const u64* d = in.data + (size_t)2 * in.cap * N;
   // 1-3: ModUp and inner product, as in keyswitch_impl
   u64* dc = static_cast<u64*>(pool_alloc((size_t)B * l * N * 8, st));
-  ntt_inverse_from(C, PolySet{dc, (long)l * N, B, l, 0, l}, d, in_os, st);
+  const bool post = bconv_folds_inverse(C);
+  ntt_inverse_from(C, scaled_later(PolySet{dc, (long)l * N, B, l, 0, l}, post), d, in_os, st);
   const long ext_os = (long)dn * nx * N;
   u64* ext = static_cast<u64*>(pool_alloc((size_t)B * ext_os * 8, st));
   const bool pre = bconv_folds_w1(C);
@@ -172,7 +184,7 @@ void op_relin_drop(Context& C, const Buf& in, Buf& out, cudaStream_t st) {
     const u64* c1 = C.d_tables + C.off_modup.at({j, hi});
     const u64* c2 = c1 + 2 * (hi - lo);
     k_bconv(C, dc + (size_t)lo * N, (long)l * N, hi - lo, lo, c1, c2, ext + (size_t)j * nx * N, ext_os, nx, l, lo,
-            hi, nullptr, B, st, -1, pre);
+            hi, nullptr, B, st, -1, pre, post);
   }
   PolySet ps{ext, (long)nx * N, B * dn, nx, 0, l};
   ps.skip_w = a;
@@ -189,13 +201,13 @@ void op_relin_drop(Context& C, const Buf& in, Buf& out, cudaStream_t st) {
   // 4. ModDown by q_{l-1} P: delta = t conv([t^-1 (P d + acc)]_D) on the first l-1 primes
   const u64* pmod = C.d_tables + C.off_pmod;
   k_fixup_last(C, acc, sp_os, ns, 0, in, l, pmod, B, st);
-  ntt_inverse(C, PolySet{acc, (long)ns * N, 2 * B, ns, l - 1, 1}, st);
+  ntt_inverse(C, scaled_later(PolySet{acc, (long)ns * N, 2 * B, ns, l - 1, 1}, post), st);
   u64* delta = static_cast<u64*>(pool_alloc((size_t)2 * B * nl * N * 8, st));
   const u64* c2 = C.d_tables + C.off_rd[l];
   const u64* inv = c2 + (size_t)(a + 1) * C.ntot;
   const u64* c1 = C.d_tables + C.off_rd_c1.at({l, in.t_exp});
-  const u64* post = C.d_tmod + (size_t)in.t_exp * C.ntot * 2;
-  k_bconv(C, acc, (long)ns * N, ns, l - 1, c1, c2, delta, (long)nl * N, nl, nl, 0, 0, post, 2 * B, st, 1, pre);
+  const u64* tpost = C.d_tmod + (size_t)in.t_exp * C.ntot * 2;
+  k_bconv(C, acc, (long)ns * N, ns, l - 1, c1, c2, delta, (long)nl * N, nl, nl, 0, 0, tpost, 2 * B, st, 1, pre, post);
   PolySet pd{delta, (long)nl * N, 2 * B, nl, 0, nl};
   pd.pre_w1 = pre;
   ntt_forward(C, pd, st);
@@ -217,15 +229,15 @@ void op_modswitch(Context& C, const Buf& a, int k, Buf& out, cudaStream_t st) {
   u64* x = static_cast<u64*>(pool_alloc((size_t)B * nc * k * N * 8, st));
   SS_CUDA(cudaMemcpy2DAsync(x, (size_t)k * N * 8, a.data + (size_t)nl * N, (size_t)a.cap * N * 8, (size_t)k * N * 8,
                             (size_t)B * nc, cudaMemcpyDeviceToDevice, st));
-  ntt_inverse(C, PolySet{x, (long)k * N, B * nc, k, nl, k}, st);
+  const bool pre = bconv_folds_w1(C), post = bconv_folds_inverse(C);
+  ntt_inverse(C, scaled_later(PolySet{x, (long)k * N, B * nc, k, nl, k}, post), st);
   u64* delta = static_cast<u64*>(pool_alloc((size_t)B * nc * nl * N * 8, st));
   size_t off = C.off_ms.at({l, k});
   const u64* c2 = C.d_tables + off;
   const u64* qinv = c2 + (size_t)k * C.ntot;
   const u64* c1 = C.d_tables + C.off_ms_c1.at(std::make_tuple(l, k, a.t_exp));
-  const u64* post = C.d_tmod + (size_t)a.t_exp * C.ntot * 2;
-  const bool pre = bconv_folds_w1(C);
-  k_bconv(C, x, (long)k * N, k, nl, c1, c2, delta, (long)nl * N, nl, nl, 0, 0, post, B * nc, st, -1, pre);
+  const u64* tpost = C.d_tmod + (size_t)a.t_exp * C.ntot * 2;
+  k_bconv(C, x, (long)k * N, k, nl, c1, c2, delta, (long)nl * N, nl, nl, 0, 0, tpost, B * nc, st, -1, pre, post);
   PolySet pd{delta, (long)nl * N, B * nc, nl, 0, nl};
   pd.pre_w1 = pre;
   ntt_forward(C, pd, st);

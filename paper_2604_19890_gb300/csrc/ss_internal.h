@@ -133,7 +133,8 @@ struct Context {
   // device tables
   ModDesc* d_mod = nullptr;           // [ntot]
   u64* d_tw = nullptr;                // per prime 4N words: (psi_brv, shoup) pairs, then (psiinv_brv, shoup) pairs
-  u64* d_r64 = nullptr;               // [ntot][2] 2^64 mod q; X^N + 1: also times psi^(N/2), the forward node 1
+  u64* d_r64 = nullptr;               // [ntot][4] 2^64 mod q; X^N + 1: 2^64 psi^(N/2) (forward node 1),
+                                      //   2^64 N^-1, 2^64 N^-1 psi^(-N/2) (the inverse's last stage)
   u64* d_ninv = nullptr;              // [ntot][4] N^{-1}, shoup, N^{-1} psi^{-N/2} (m = 3N: 2 N^{-1}), shoup
   u64* d_split = nullptr;             // m = 5N/2: [ntot][12][2] four-way split constants (forward 5, inverse 7)
   u64* d_pinv = nullptr;              // [ntot][2] p^{-1}, shoup
@@ -190,14 +191,19 @@ void pool_free(void* p, cudaStream_t s);
 // i < nq ? q0 + i : L + (i - nq). Limbs inside [skip_lo, skip_hi) of digit
 // (o % skip_mod) * skip_w .. are skipped when skip_w > 0 (ModUp outputs).
 // pre_w1 (forward, ring X^N + 1): the upper half of every polynomial already
-// carries the node-1 twiddle psi^(N/2) (the ModUp base conversion applied it),
-// so the first stage adds and subtracts without its product.
+// carries the node-1 twiddle psi^(N/2) (the base conversion that wrote it
+// applied it), so the first stage adds and subtracts without its product.
+// post_scale (inverse, ring X^N + 1, N > 4096): the last stage adds and
+// subtracts without its products and leaves N^-1 (lower half) and
+// N^-1 psi^(-N/2) (upper half) to the consumer, a base conversion that folds
+// them into its per-source constants; the words are then unreduced (< 4q).
 struct PolySet {
   u64* base;
   long outer_stride;
   int n_outer, nl, q0, nq;
   int skip_w = 0, skip_mod = 1, skip_level = 0;
   bool pre_w1 = false;
+  bool post_scale = false;
 };
 void ntt_forward(Context& C, const PolySet& s, cudaStream_t st);
 void ntt_inverse(Context& C, const PolySet& s, cudaStream_t st);
@@ -246,7 +252,7 @@ void k_tensor(Context& C, const Buf& a, const Buf& b, Buf& out, cudaStream_t st)
 // sources s < nsq are data primes sp0 + s, the rest special primes L + (s - nsq) (nsq < 0: all sp0 + s)
 void k_bconv(Context& C, const u64* src, long src_os, int ns, int sp0, const u64* c1, const u64* c2, u64* dst,
              long dst_os, int nd, int nq, int skip_lo, int skip_hi, const u64* post, int n_outer, cudaStream_t st,
-             int nsq = -1, bool pre_w1 = false);
+             int nsq = -1, bool pre_w1 = false, bool post_scale = false);
 // acc_c[acc_limb] += P * d_c[l-1] (acc: nx limbs per component)
 void k_fixup_last(Context& C, u64* acc, long acc_os, int nx, int acc_limb, const Buf& d, int l, const u64* pmod,
                   int B, cudaStream_t st);
