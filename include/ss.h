@@ -372,8 +372,9 @@ ss_status ss_kernel_stats(ss_ctx* ctx, int32_t cls, uint64_t* launches, double* 
  * that the timed transform launches performed since kernel timing was switched
  * on: per polynomial N/2 log2 N forward, less N/2 when the base conversion
  * that wrote the input already applied the first stage's twiddle (ring
- * X^N + 1), and N/2 (log2 N + 1) inverse (the last stage also scales the sums
- * by N^-1), N/2 (log2 N - 1) when that stage's factors are left to the base
+ * X^N + 1), and N/2 (log2 N + 1) inverse for N > 4096 (the last stage also
+ * scales the sums by N^-1), N/2 (log2 N + 2) for N <= 4096 (N^-1 on every
+ * word), N/2 (log2 N - 1) when the last stage's factors are left to the base
  * conversion that reads the output (ring X^N + 1, N > 4096). The
  * split stages of the m = 3N and 5N/2 rings count as the radix-2 stages they
  * replace. Written to *products; SS_ERR_PARAM on a null argument. The paper has

@@ -654,11 +654,13 @@ NttArgs make_args(Context& C, const PolySet& s) {
 double active_polys(const PolySet& s);
 
 // Shoup products of one transform of the set: N/2 per stage and polynomial,
-// less node 1's when folded (pre_w1), plus the inverse's N^-1 on the sums
-// unless its last stage is deferred (post_scale: no products there)
+// less node 1's when folded (pre_w1), plus the inverse's N^-1: on the sums of
+// the last stage (two-phase transforms, N/2) or on every word (single-phase,
+// N), none when the last stage is deferred (post_scale: no products there)
 double ntt_products(const Context& C, const PolySet& s, bool fwd) {
   const double half = C.N / 2.0;
-  return active_polys(s) * half * (C.logN + (fwd ? (s.pre_w1 ? -1 : 0) : (s.post_scale ? -1 : 1)));
+  const int inv_extra = s.post_scale ? -1 : (C.N <= TILE ? 2 : 1);
+  return active_polys(s) * half * (C.logN + (fwd ? (s.pre_w1 ? -1 : 0) : inv_extra));
 }
 
 // polynomials a transform actually touches (ModUp outputs skip the digit's own limbs)
