@@ -375,9 +375,7 @@ ss_status ss_kernel_stats(ss_ctx* ctx, int32_t cls, uint64_t* launches, double* 
  * X^N + 1), and N/2 (log2 N + 1) inverse for N > 4096 (the last stage also
  * scales the sums by N^-1), N/2 (log2 N + 2) for N <= 4096 (N^-1 on every
  * word), N/2 (log2 N - 1) when the last stage's factors are left to the base
- * conversion that reads the output (ring X^N + 1, N > 4096), and N more per
- * polynomial where a modulus switch's epilogue (c - delta) q^-1 runs inside
- * the transform's last phase. The
+ * conversion that reads the output (ring X^N + 1, N > 4096). The
  * split stages of the m = 3N and 5N/2 rings count as the radix-2 stages they
  * replace. Written to *products; SS_ERR_PARAM on a null argument. The paper has
  * no counterpart of this call; it is measurement (the work term of the

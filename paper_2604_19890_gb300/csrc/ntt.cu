@@ -52,16 +52,6 @@ struct NttArgs {
   int post_scale;    // inverse, X^N + 1: last stage without its products (PolySet::post_scale)
 };
 
-// forward chunk phase with the modulus-switch epilogue (EPI kernels): the
-// transform's words d are not written; out[o][i] = (a[o][i] - d) * scale_i
-struct EpiArgs {
-  const u64* a;
-  long a_os;
-  u64* out;
-  long out_os;
-  const u64* scale;  // (value, Shoup) per limb
-};
-
 // Blocks walk the polynomials limb-major (all outer copies of limb 0, then of
 // limb 1, ...) so consecutive blocks share a prime and its twiddles stay in L2.
 __device__ __forceinline__ bool poly_of(const NttArgs& A, int poly, u64*& ptr, int& pidx) {
@@ -343,11 +333,8 @@ __global__ void __launch_bounds__(512) k_ntt(NttArgs A, int logS, int logCPB, in
 // Forward it adds up to 6q to the bound, so the transform stays below 40q.
 // Inverse it is fused with N^-1: with c = (2 rho - 1)^-1 N^-1 (inverse
 // twiddle word 0), high = (U - V) 2c, low = (U + V) N^-1 - (U - V) c.
-// EPI (forward chunk phase, LAST): the modulus-switch epilogue of NttArgs
-// applied to the reduced words instead of writing them.
-template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC, int RING = 1, bool EPI = false>
-__device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0, int tile, int poly,
-                                           const EpiArgs* E = nullptr) {
+template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC, int RING = 1>
+__device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0, int tile, int poly) {
   extern __shared__ u64 sm[];
   u64* ptr;
   int pidx;
@@ -547,17 +534,7 @@ __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0,
       __syncthreads();
     }
   }
-  if (!DOUT && EPI) {
-    static_assert(!EPI || (FWD && LAST && !COLS), "the epilogue follows the forward chunk phase");
-    const int i = poly / A.n_outer, o = poly % A.n_outer;
-    const u64* ga = E->a + (long)o * E->a_os + (long)i * A.N + (long)tile * W;
-    u64* go = E->out + (long)o * E->out_os + (long)i * A.N + (long)tile * W;
-    const u64 sc = __ldg(E->scale + 2 * i), scp = __ldg(E->scale + 2 * i + 1);
-    for (int lin = tid; lin < W; lin += T) {
-      const u64 v = reduce_lazy(sm[swz(lin)], q, kb, mq);
-      go[lin] = shoup(sub_mod(ga[lin], v, q), sc, scp, q);
-    }
-  } else if (!DOUT) {
+  if (!DOUT) {
     for (int lin = tid; lin < W; lin += T) {
       u64 v = sm[swz(lin)];
       if (LAST && FWD) v = reduce_lazy(v, q, kb, mq);
@@ -570,11 +547,6 @@ template <bool FWD, bool COLS, bool LAST, int LOGS, bool SRC = false, int RING =
 __global__ void __launch_bounds__(256, RING == 5 ? SS_NTT_MINB_R5 : (FWD ? SS_NTT_MINB_F : SS_NTT_MINB_I))
     k_ntt16(NttArgs A, int logCPB, int m0) {
   ntt16_tile<FWD, COLS, LAST, LOGS, SRC, RING>(A, logCPB, m0, blockIdx.x, blockIdx.y);
-}
-
-// the forward chunk phase (X^N + 1, 256-word chunks) with the modulus-switch epilogue
-__global__ void __launch_bounds__(256, SS_NTT_MINB_F) k_ntt16_sub_scale(NttArgs A, int logCPB, int m0, EpiArgs E) {
-  ntt16_tile<true, false, true, 8, false, 1, true>(A, logCPB, m0, blockIdx.x, blockIdx.y, &E);
 }
 
 // ---------------------------------------------------------------- persistent multi-transform phase
@@ -852,33 +824,6 @@ void ntt_multi(const std::vector<NttReq>& reqs, bool fwd, int tile_log, cudaStre
 }
 
 void ntt_forward(Context& C, const PolySet& s, cudaStream_t st) { launch(C, s, true, st); }
-
-bool ntt_forward_sub_scale(Context& C, const PolySet& s, const u64* a, long a_os, const u64* scale, u64* out,
-                           long out_os, cudaStream_t st) {
-  // two-phase transforms of X^N + 1 outside the batched form's merged lanes only
-  if (C.N <= TILE || C.m_odd != 1 || ntt_merger() || chunk_log(C) != 8 || s.q0 != 0 || s.skip_w > 0) return false;
-  const int npoly = s.n_outer * s.nl;
-  if (npoly == 0) return true;
-  if (npoly > 65535) throw Error(SS_ERR_SHAPE, "too many polynomials in one transform");
-  NttArgs A = make_args(C, s);
-  const EpiArgs E{a, a_os, out, out_os, scale};
-  auto smem = [](int words) { return (size_t)(words + words / 8) * 8; };
-  int kr = kt_begin(C, st);
-  const int log2n = 8, log1 = C.logN - log2n;
-  const int tl = C.ntt_tile_log == 11 ? 11 : 12, tile = 1 << tl;
-  const int logc1 = tl - log1, logc2 = tl - log2n;
-  dim3 g1(1 << (log2n - logc1), npoly), g2(1 << (log1 - logc2), npoly);
-  const int thr = tile / 16;
-  launch16<true, true, false>(log1, g1, thr, smem(tile), st, A, logc1, 1);
-  k_ntt16_sub_scale<<<g2, thr, smem(tile), st>>>(A, logc2, 1 << log1, E);
-  C.launches += 2;
-  // the transform's products and the epilogue's one per word
-  if (kr >= 0) C.kt.ntt_products += ntt_products(C, s, true) + (double)C.N * npoly;
-  // the transform's bytes, plus the epilogue's read of a and write of out in place of the words' write
-  kt_end(C, kr, KC_NTT, 16.0 * C.N * active_polys(s) + 8.0 * C.N * npoly, st);
-  SS_CUDA(cudaGetLastError());
-  return true;
-}
 
 void ntt_inverse(Context& C, const PolySet& s, cudaStream_t st) { launch(C, s, false, st); }
 

@@ -240,12 +240,9 @@ void op_modswitch(Context& C, const Buf& a, int k, Buf& out, cudaStream_t st) {
   k_bconv(C, x, (long)k * N, k, nl, c1, c2, delta, (long)nl * N, nl, nl, 0, 0, tpost, B * nc, st, -1, pre, post);
   PolySet pd{delta, (long)nl * N, B * nc, nl, 0, nl};
   pd.pre_w1 = pre;
-  // out = (a - delta) q_drop^-1, fused into the transform's last phase where it applies
-  if (!ntt_forward_sub_scale(C, pd, a.data, (long)a.cap * N, qinv, out.data, (long)out.cap * N, st)) {
-    ntt_forward(C, pd, st);
-    k_sub_scale(C, a.data, (long)a.cap * N, delta, (long)nl * N, qinv, nullptr, 0, out.data, (long)out.cap * N, nl,
-                B * nc, st);
-  }
+  ntt_forward(C, pd, st);
+  k_sub_scale(C, a.data, (long)a.cap * N, delta, (long)nl * N, qinv, nullptr, 0, out.data, (long)out.cap * N, nl,
+              B * nc, st);
   pool_free(x, st);
   pool_free(delta, st);
 }

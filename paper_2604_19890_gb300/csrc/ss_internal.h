@@ -206,13 +206,6 @@ struct PolySet {
   bool post_scale = false;
 };
 void ntt_forward(Context& C, const PolySet& s, cudaStream_t st);
-// Forward transform of s fused with the modulus-switch epilogue: for every
-// polynomial (o, i) of s, out[o][i] = (a[o][i] - NTT(s)[o][i]) * scale_i
-// (scale: (value, Shoup) per limb; s.q0 = 0), without writing NTT(s). Returns
-// false, having done nothing, where the fused form does not apply (N <= 4096,
-// other rings, the batched form's merged lanes).
-bool ntt_forward_sub_scale(Context& C, const PolySet& s, const u64* a, long a_os, const u64* scale, u64* out,
-                           long out_os, cudaStream_t st);
 void ntt_inverse(Context& C, const PolySet& s, cudaStream_t st);
 // Inverse transform of the polynomials at src (same shape as s, outer stride
 // src_os) written to s: the first phase reads src, so src is left unchanged.
