@@ -148,6 +148,20 @@ KS_SETS = [
 
 @pytest.mark.parametrize("prm,count", KS_SETS, ids=["n8192", "n16384"])
 def test_keyswitch_parity_two_phase(prm, count):
+    keyswitch_case(prm, count)
+
+
+@pytest.mark.parametrize("prm,count", [
+    (dict(logN=10, L=6, alpha=2, bits=36, p=17, r=2, h=64, seed=503), 2),
+    (dict(logN=12, L=7, alpha=3, bits=55, p=257, r=2, h=120, seed=504), 3)], ids=["n1024", "n4096"])
+def test_keyswitch_parity_single_phase_folded(prm, count):
+    """N = 1024 and 4096: the single-phase transform with the node-1 twiddle
+    folded into the base conversions that feed it (the smallest ring where a
+    base-conversion block lies in one half, and the largest single-phase ring)."""
+    keyswitch_case(prm, count)
+
+
+def keyswitch_case(prm, count):
     import paper_2604_19890_gb300 as ssg
     g = ssg.Context(nmax=0, **prm)
     o = O.Oracle(**prm)
