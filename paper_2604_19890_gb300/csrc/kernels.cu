@@ -8,7 +8,7 @@
 // 8-byte words of one limb (256 B, fully coalesced).
 #include <cstdio>
 #include <cstring>
-#include <mutex>
+#include <atomic>
 
 #include "modarith.cuh"
 #include "philox.h"
@@ -1311,12 +1311,18 @@ static void ks_launch(Context& C, const KsJob& J, int nlimbs, double bytes, cuda
 #if SS_KSIP_STAGES > 0
   static_assert(SS_KSIP_V == 2, "the cp.async inner product copies two coefficients per thread");
   constexpr size_t ring = (size_t)SS_KSIP_STAGES * (2 + OB) * TPB * 16;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    SS_CUDA(cudaFuncSetAttribute(k_ks_ip_async<OB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring));
-    SS_CUDA(cudaFuncSetAttribute(k_ks_ip_async<OB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring));
-    SS_CUDA(cudaFuncSetAttribute(k_ks_ip_async<OB, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring));
-  });
+  if (ring > 48 * 1024) {  // beyond the default limit: opt in once per device (the attribute is per device)
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    SS_CUDA(cudaGetDevice(&dev));
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(done.load() & bit)) {
+      SS_CUDA(cudaFuncSetAttribute(k_ks_ip_async<OB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring));
+      SS_CUDA(cudaFuncSetAttribute(k_ks_ip_async<OB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring));
+      SS_CUDA(cudaFuncSetAttribute(k_ks_ip_async<OB, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring));
+      done.fetch_or(bit);
+    }
+  }
   switch (J.type) {
     case 0: TIMED(KC_KSIP, bytes, (k_ks_ip_async<OB, 0><<<grid, TPB, ring, st>>>(J))); break;
     case 1: TIMED(KC_KSIP, bytes, (k_ks_ip_async<OB, 1><<<grid, TPB, ring, st>>>(J))); break;
