@@ -70,6 +70,22 @@ __device__ __forceinline__ bool poly_of(const NttArgs& A, int poly, u64*& ptr, i
 // spreads the strided round accesses over all banks.
 __device__ __forceinline__ int swz(int lin) { return lin + (lin >> 3); }
 
+#ifndef SS_NTT_XSWZ
+#define SS_NTT_XSWZ 1  // chunk phases of the radix-16 kernels: XOR swizzle instead of the padded one
+#endif
+// Chunk tiles of the radix-16 kernels: within every aligned group of 16 words
+// the low four index bits are XORed with the next four. A half-warp then hits
+// 16 distinct bank pairs both when it touches 16 consecutive words (rounds of
+// spacing >= 16, the linear staging loops: the XOR is one permutation of the
+// group) and when it touches one word of each of 16 consecutive groups
+// (rounds of spacing 1: thread B holds words 16B .. 16B+15), where the padded
+// swizzle left two threads on each bank pair. It needs no padding.
+template <bool COLS>
+__device__ __forceinline__ int swz16(int lin) {
+  if (COLS || !SS_NTT_XSWZ) return swz(lin);
+  return lin ^ ((lin >> 4) & 15);
+}
+
 // v < 64q  ->  v mod q. The quotient estimate k = floor(t * mq / 2^24) from
 // t = floor(v / 2^(kb-8)) and mq = floor(2^(kb+16) / q) satisfies
 // v/q - 2 < k <= v/q, so v - k q lies in [0, 2q) and one subtraction ends it.
@@ -372,7 +388,7 @@ __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0,
     for (int i = 0; i < (PRE ? 8 : 1); ++i) pre[i] = __ldg(tp + i);
   }
   if (!DIN) {
-    for (int lin = tid; lin < W; lin += T) sm[swz(lin)] = gsrc[lin];
+    for (int lin = tid; lin < W; lin += T) sm[swz16<COLS>(lin)] = gsrc[lin];
     __syncthreads();
   }
   u64 ni = 0, nip = 0;
@@ -423,7 +439,7 @@ __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0,
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         int r = rbase + (k << logu);
-        x[k] = sm[swz(COLS ? (r << logCPB) + c : (c << LOGS) + r)];
+        x[k] = sm[swz16<COLS>(COLS ? (r << logCPB) + c : (c << LOGS) + r)];
       }
     }
     // stages j in [a - logu, b - logu]: d = 2^j registers apart
@@ -529,14 +545,14 @@ __device__ __forceinline__ void ntt16_tile(const NttArgs& A, int logCPB, int m0,
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         int r = rbase + (k << logu);
-        sm[swz(COLS ? (r << logCPB) + c : (c << LOGS) + r)] = x[k];
+        sm[swz16<COLS>(COLS ? (r << logCPB) + c : (c << LOGS) + r)] = x[k];
       }
       __syncthreads();
     }
   }
   if (!DOUT) {
     for (int lin = tid; lin < W; lin += T) {
-      u64 v = sm[swz(lin)];
+      u64 v = sm[swz16<COLS>(lin)];
       if (LAST && FWD) v = reduce_lazy(v, q, kb, mq);
       gbase[lin] = v;
     }
