@@ -41,7 +41,7 @@ WIDE_PER_BUTTERFLY = 5
 # DRAM bytes per limb transform (forward and inverse, both phases each) from one
 # ncu capture of the transform kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum per limb), over the 1 MB (16 N) it must move.
-NTT_TRAFFIC_PER_ALGO_BYTE = 1.869
+NTT_TRAFFIC_PER_ALGO_BYTE = 1.860
 
 
 def hbm_peak():
