@@ -557,7 +557,10 @@ def _sub_json(argv, timeout):
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
     if r.returncode != 0 or not lines:
         return None, "exit %d: %s" % (r.returncode, (r.stderr or r.stdout).strip().splitlines()[-1:] or "")
-    return json.loads(lines[-1]), None
+    try:
+        return json.loads(lines[-1]), None
+    except ValueError as e:
+        return None, "unreadable output: %r" % (e,)
 
 
 def run_extras():
@@ -568,25 +571,30 @@ def run_extras():
     tuned, graph-replayed batch. The full sweeps are `--serve` and `--batched`."""
     out = {}
     t0 = time.perf_counter()
-    sv, err = _sub_json(["--serve", "--serve-queries", "100", "--serve-rates", "2c", "--no-serve-burst"], 600)
-    if sv is None:
-        out["served"] = {"error": err}
-    else:
+
+    def served(sv):
         runs = {r["form"]: {k: round(r[k], 2) for k in ("qps", "p50_ms", "p99_ms")} for r in sv["runs"]}
-        out["served"] = {"workload": sv["config"]["workload"], "unit": "queries/s",
-                         "capacity_qps": round(sv["capacity_qps"], 2), "arrivals": sv["runs"][0]["queries"],
-                         "arrival_qps": sv["runs"][0]["arrival_qps"], "plain": runs.get("plain"),
-                         "served": runs.get("served"), "verified_against_plaintext": sv["verified_against_plaintext"]}
-    bt, err = _sub_json(["--batched", "--steps", "3"], 600)
-    if bt is None:
-        out["batched"] = {"error": err}
-    else:
-        out["batched"] = {"workload": bt["metric"], "unit": "pairs/s",
-                          "plain_pairs_per_s": round(bt["plain_pairs_per_s"], 1),
-                          "batched_pairs_per_s": round(bt["batched_pairs_per_s"], 1),
-                          "speedup": round(bt["speedup"], 3), "tuned": bt["tuned"],
-                          "merged_lanes_graph_ms": bt["merged_lanes_graph_ms"],
-                          "verified_against_plaintext": bt["verified_against_plaintext"]}
+        return {"workload": sv["config"]["workload"], "unit": "queries/s",
+                "capacity_qps": round(sv["capacity_qps"], 2), "arrivals": sv["runs"][0]["queries"],
+                "arrival_qps": sv["runs"][0]["arrival_qps"], "plain": runs.get("plain"),
+                "served": runs.get("served"), "verified_against_plaintext": sv["verified_against_plaintext"]}
+
+    def batched(bt):
+        return {"workload": bt["metric"], "unit": "pairs/s",
+                "plain_pairs_per_s": round(bt["plain_pairs_per_s"], 1),
+                "batched_pairs_per_s": round(bt["batched_pairs_per_s"], 1),
+                "speedup": round(bt["speedup"], 3), "tuned": bt["tuned"],
+                "merged_lanes_graph_ms": bt["merged_lanes_graph_ms"],
+                "verified_against_plaintext": bt["verified_against_plaintext"]}
+
+    for key, argv, summary in (
+            ("served", ["--serve", "--serve-queries", "100", "--serve-rates", "2c", "--no-serve-burst"], served),
+            ("batched", ["--batched", "--steps", "3"], batched)):
+        res, err = _sub_json(argv, 600)
+        try:
+            out[key] = {"error": err} if res is None else summary(res)
+        except (KeyError, IndexError, TypeError, ValueError) as e:  # unexpected child output
+            out[key] = {"error": "unexpected output: %r" % (e,)}
     out["extras_s"] = round(time.perf_counter() - t0, 1)
     return out
 

@@ -36,3 +36,43 @@ def test_reference_arm_line():
 
 def test_reference_arm_other_ranks_are_silent():
     assert run({"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def test_short_served_and_batched_runs_are_summarised(monkeypatch):
+    """The default run adds `served` and `batched` objects from child runs of
+    `--serve` and `--batched`; a child that fails leaves an error string in
+    place of the object instead of breaking the line (children faked here)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    serve_out = {"config": {"workload": "mixed"}, "capacity_qps": 9.0, "verified_against_plaintext": True,
+                 "runs": [{"form": "plain", "queries": 100, "arrival_qps": 18.0, "qps": 9.1, "p50_ms": 3200.0,
+                           "p99_ms": 5400.0},
+                          {"form": "served", "queries": 100, "arrival_qps": 18.0, "qps": 12.9, "p50_ms": 2400.0,
+                           "p99_ms": 3700.0}]}
+    batch_out = {"metric": "batched", "plain_pairs_per_s": 214.1, "batched_pairs_per_s": 423.1, "speedup": 1.976,
+                 "tuned": {"chunk": 32, "streams": 3, "ntt_tile_words": 2048},
+                 "merged_lanes_graph_ms": {"chunk 8": 204.0}, "verified_against_plaintext": True}
+    calls = []
+
+    class R:
+        def __init__(self, rc, out, err=""):
+            self.returncode, self.stdout, self.stderr = rc, out, err
+
+    def fake_run(cmd, **kw):
+        calls.append(cmd)
+        if "--serve" in cmd:
+            assert "--no-serve-burst" in cmd and cmd[cmd.index("--serve-rates") + 1] == "2c"
+            return R(0, "log line\n" + json.dumps(serve_out) + "\n")
+        return R(1, "", "boom: no device")
+
+    monkeypatch.setattr(bench.subprocess, "run", fake_run)
+    out = bench.run_extras()
+    assert len(calls) == 2
+    sv = out["served"]
+    assert sv["plain"] == {"qps": 9.1, "p50_ms": 3200.0, "p99_ms": 5400.0}
+    assert sv["served"]["qps"] == 12.9 and sv["arrivals"] == 100 and sv["verified_against_plaintext"] is True
+    assert "error" in out["batched"] and "boom" in out["batched"]["error"]
+    monkeypatch.setattr(bench.subprocess, "run", lambda cmd, **kw: R(0, json.dumps(batch_out) + "\n"))
+    bt = bench.run_extras()["batched"]
+    assert bt["speedup"] == 1.976 and bt["batched_pairs_per_s"] == 423.1 and bt["tuned"]["streams"] == 3
